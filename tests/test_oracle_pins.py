@@ -1,0 +1,598 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every test here checks the oracle against something other than itself: isotropy
+identities, moment constraints stated in the appendix, exact invariants, closed
+forms of the hydrodynamic limit, hand-worked fixtures under tests/golden/, values
+printed in the paper, and qualitative statements of the paper turned into sign
+checks.  Each is chosen so that a plausible slip (a dropped term, a flipped sign,
+a wrong index or weight) fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1306_0788_gb300 import inputs
+
+CS2 = 1.0 / 3.0
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+NOP = (np.zeros((0, 3)), np.zeros((0, 3)))
+
+
+def _no_particles():
+    return np.zeros((0, 3)), np.zeros((0, 3))
+
+
+# ---------------------------------------------------------------- lattice and equilibrium
+def test_d3q19_isotropy():
+    """Eqs. (weights), (velo), (isotropy), (isotropyb)."""
+    c, w = oracle.lattice()
+    c = c.astype(float)
+    assert np.isclose(w.sum(), 1.0, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia->a", w, c), 0, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), CS2 * np.eye(3), atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib,ig->abg", w, c, c, c), 0, atol=1e-15)
+    d = np.eye(3)
+    four = CS2 ** 2 * (np.einsum("ab,gz->abgz", d, d) + np.einsum("ag,bz->abgz", d, d)
+                       + np.einsum("az,bg->abgz", d, d))
+    assert np.allclose(np.einsum("i,ia,ib,ig,iz->abgz", w, c, c, c, c), four, atol=1e-15)
+    # 1 rest, 6 axis, 12 face-diagonal velocities; opposite directions adjacent (reading R10)
+    n2 = (c * c).sum(1)
+    assert n2[0] == 0 and (n2[1:7] == 1).all() and (n2[7:] == 2).all()
+    for i in range(1, 19, 2):
+        assert (c[i] == -c[i + 1]).all()
+    assert len({tuple(v) for v in c}) == 19
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_equilibrium_moments(seed):
+    """Eq. (feq): zeroth, first and second moments are rho, rho u, rho cs2 1 + rho u u."""
+    g = np.random.default_rng(seed)
+    rho = g.uniform(0.2, 3.0)
+    u = g.uniform(-0.1, 0.1, 3)
+    c, _ = oracle.lattice()
+    c = c.astype(float)
+    f = oracle.feq(rho, u)
+    assert np.isclose(f.sum(), rho, rtol=1e-14)
+    assert np.allclose(f @ c, rho * u, atol=1e-14)
+    assert np.allclose(np.einsum("i,ia,ib->ab", f, c, c), rho * CS2 * np.eye(3) + rho * np.outer(u, u),
+                       atol=1e-14)
+
+
+@pytest.mark.parametrize("lams", [(-1.0, -1.0, -1.0), (-0.7, -1.3, -1.8), (-1.9, -0.4, -1.1)])
+def test_forcing_moments_match_constraints(lams):
+    """Appendix: the forcing term must satisfy sum_i Delta^g = 0 (forces do not change the
+    mass), the first-moment constraint (CON1) sum_i c_i Delta^g = ((2+lM)/2) g and the
+    second-moment constraints (CON2): traceless part (2+ls)/2 (ug+gu)^ and trace (2+lb) u.g."""
+    lM, ls, lb = lams
+    g_ = np.random.default_rng(5)
+    for _ in range(5):
+        gv = g_.normal(size=3)
+        u = g_.uniform(-0.1, 0.1, 3)
+        c, _w = oracle.lattice()
+        c = c.astype(float)
+        d = oracle.forcing(gv, u, lM, ls, lb)
+        assert abs(d.sum()) < 1e-15
+        assert np.allclose(d @ c, 0.5 * (2 + lM) * gv, atol=1e-14)
+        M2 = np.einsum("i,ia,ib->ab", d, c, c)
+        ug = np.outer(u, gv) + np.outer(gv, u)
+        tl = lambda m: m - np.trace(m) / 3.0 * np.eye(3)  # noqa: E731
+        assert np.allclose(tl(M2), 0.5 * (2 + ls) * tl(ug), atol=1e-14)
+        assert np.isclose(np.trace(M2), (2 + lb) * (u @ gv), atol=1e-14)
+
+
+# ---------------------------------------------------------------- Shan-Chen force
+def test_sc_force_pairwise_cancellation():
+    """Sec. 2: with g_AB = g_BA the total Shan-Chen force vanishes identically."""
+    g = np.random.default_rng(3)
+    rA = g.uniform(0.5, 1.5, size=(5, 6, 7))
+    rB = g.uniform(0.5, 1.5, size=(5, 6, 7))
+    gA, gB, _, _ = oracle.sc_force(rA, rB, 1.7, 1.7)
+    tot = (gA + gB).reshape(-1, 3).sum(0)
+    scale = np.abs(gA).sum()
+    assert np.abs(tot).max() < 1e-14 * scale
+    # ... and it does not vanish when g_AB != g_BA (the check can fail)
+    gA2, gB2, _, _ = oracle.sc_force(rA, rB, 1.7, 1.2)
+    assert np.abs((gA2 + gB2).reshape(-1, 3).sum(0)).max() > 1e-6 * scale
+
+
+def test_sc_force_continuum_limit():
+    """Eq. (Taylor) with the c_s^2 of Eq. (fbulk): g_A ~ -c_s^2 g rho_A grad rho_B for smooth
+    fields; the lattice sum differs by O(k^2)."""
+    L = 64
+    k = 2 * np.pi / L
+    x = np.arange(L)
+    rB = (1.0 + 0.1 * np.sin(k * x))[None, None, :] * np.ones((2, 3, L))
+    rA = np.full((2, 3, L), 0.8)
+    gA, gB, SA, SB = oracle.sc_force(rA, rB, 1.5, 1.5)
+    expect = -CS2 * 1.5 * 0.8 * 0.1 * k * np.cos(k * x)
+    assert np.allclose(gA[0, 0, :, 0], expect, rtol=0, atol=2e-3 * np.abs(expect).max())
+    assert np.abs(gA[..., 1:]).max() < 1e-15
+    # the gradient estimate S/cs2 used for particles (reading R6)
+    assert np.allclose(SB[0, 0, :, 0] / CS2, 0.1 * k * np.cos(k * x), atol=2e-3 * 0.1 * k)
+
+
+def _phi_mode(f, axis_len, k, fn):
+    phi = f[0].sum(0) - f[1].sum(0)
+    prof = phi.reshape(-1, axis_len).mean(0) if phi.ndim else phi
+    return (prof * fn(k * np.arange(axis_len))).sum() * 2 / axis_len
+
+
+@pytest.mark.parametrize("g,grows", [(0.9, False), (1.1, True)])
+def test_spinodal_threshold(g, grows):
+    """Eq. (fbulk): the uniform mixture rho_A = rho_B = rho is unstable iff g rho > 1
+    (second derivative of F_bulk in the composition).  A long-wavelength composition
+    mode must decay below and grow above the threshold."""
+    L = 32
+    k = 2 * np.pi / L
+    x = np.arange(L)
+    eps = 1e-5
+    rA = (1 + eps * np.cos(k * x))[None, None, :]
+    rB = (1 - eps * np.cos(k * x))[None, None, :]
+    f = oracle.init_equilibrium(rA, rB)
+    s = oracle.System(dims=(L, 1, 1), tau_r=1.0, g_AB=g, g_BA=g)
+    a0 = _phi_mode(f, L, k, np.cos)
+    oracle.run(s, f, *_no_particles(), 300)
+    a1 = _phi_mode(f, L, k, np.cos)
+    assert (a1 > a0) == grows
+    # growth/decay rate close to the continuum mu cs2 (g rho - 1) k^2, mu = tau_r - 1/2
+    rate = np.log(a1 / a0) / 300
+    assert abs(rate - 0.5 * CS2 * (g - 1) * k * k) < 0.5 * abs(0.5 * CS2 * (g - 1) * k * k)
+
+
+def test_density_rescaling_invariance():
+    """Sec. 3: rho -> alpha rho together with g -> g/alpha keeps the profiles; in the discrete
+    model every population scales by alpha exactly (alpha = 2 is exact in binary floating
+    point)."""
+    dims = (6, 5, 4)
+    rA, rB = inputs.uniform_noise(dims, 1.0, 0.05, seed=7)
+    f1 = oracle.init_equilibrium(rA, rB)
+    f2 = oracle.init_equilibrium(2 * rA, 2 * rB)
+    s1 = oracle.System(dims=dims, tau_r=0.9, g_AB=1.6, g_BA=1.6)
+    s2 = oracle.System(dims=dims, tau_r=0.9, g_AB=0.8, g_BA=0.8)
+    oracle.run(s1, f1, *_no_particles(), 5)
+    oracle.run(s2, f2, *_no_particles(), 5)
+    assert np.array_equal(f2, 2 * f1)
+    f3 = oracle.init_equilibrium(3 * rA, 3 * rB)
+    oracle.run(oracle.System(dims=dims, tau_r=0.9, g_AB=1.6 / 3, g_BA=1.6 / 3), f3, *_no_particles(), 5)
+    assert np.allclose(f3, 3 * f1, rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------- collision and streaming
+def test_rest_equilibrium_is_fixed_point():
+    """Uniform densities at rest: the SC force vanishes (sum_i w_i c_i = 0) and f^eq is
+    reproduced by collision and streaming."""
+    dims = (4, 5, 6)
+    rA = np.full((6, 5, 4), 0.7)
+    rB = np.full((6, 5, 4), 1.3)
+    f = oracle.init_equilibrium(rA, rB)
+    f0 = f.copy()
+    oracle.run(oracle.System(dims=dims, tau_r=0.8, g_AB=1.9, g_BA=1.9), f, *_no_particles(), 3)
+    assert np.abs(f - f0).max() < 1e-15
+
+
+def test_uniform_flow_is_fixed_point():
+    """Galilean check: a uniform mixture in uniform motion stays unchanged."""
+    dims = (4, 4, 4)
+    u = np.zeros((4, 4, 4, 3))
+    u[..., :] = (0.05, -0.02, 0.01)
+    f = oracle.init_equilibrium(np.full((4, 4, 4), 0.9), np.full((4, 4, 4), 1.1), u)
+    f0 = f.copy()
+    oracle.run(oracle.System(dims=dims, tau_r=1.3), f, *_no_particles(), 3)
+    assert np.abs(f - f0).max() < 1e-15
+
+
+def test_advection_direction_and_speed():
+    """Eq. (cont): a composition bump in a uniform flow u moves by u t in the +u direction
+    (fixes the streaming direction f(r + c_i, t+1) = f*(r, t))."""
+    L = 64
+    x = np.arange(L)
+    bump = 0.05 * np.exp(-0.5 * ((x - 20) / 3.0) ** 2)
+    rA = (1 + bump)[None, None, :]
+    rB = (1 - bump)[None, None, :]
+    u = np.zeros((1, 1, L, 3))
+    u[..., 0] = 0.05
+    f = oracle.init_equilibrium(rA, rB, u)
+    oracle.run(oracle.System(dims=(L, 1, 1), tau_r=0.6), f, *_no_particles(), 200)
+    phi = f[0].sum(0)[0, 0] - f[1].sum(0)[0, 0]
+    centre = (phi * x).sum() / phi.sum()
+    assert abs(centre - (20 + 0.05 * 200)) < 0.15
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.0, 1.5])
+def test_shear_wave_decay(tau):
+    """Eqs. (MERGING1b), (TRANSPORTCOEFF): a shear wave decays at nu k^2 with
+    nu = eta_s/rho = c_s^2 tau (-1/lambda_s - 1/2) = c_s^2 (tau_r - 1/2)."""
+    L = 64
+    k = 2 * np.pi / L
+    y = np.arange(L)
+    u = np.zeros((1, L, 1, 3))
+    u[0, :, 0, 0] = 1e-3 * np.sin(k * y)
+    f = oracle.init_equilibrium(np.full((1, L, 1), 0.6), np.full((1, L, 1), 0.4), u)
+    c, _ = oracle.lattice()
+    s = oracle.System(dims=(1, L, 1), tau_r=tau)
+
+    def amp():
+        j = np.einsum("zinyx,i->nyx", f, c[:, 0].astype(float))
+        return (j[0, :, 0] * np.sin(k * y)).sum() * 2 / L
+
+    oracle.run(s, f, *_no_particles(), 50)
+    a0 = amp()
+    oracle.run(s, f, *_no_particles(), 250, first_step=50)
+    a1 = amp()
+    rate = -np.log(a1 / a0) / 250
+    assert abs(rate / (CS2 * (tau - 0.5) * k * k) - 1) < 0.01
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.0, 1.5])
+def test_interdiffusion_decay(tau):
+    """Eqs. (MERGING1), (TRANSPORTCOEFF): at g = 0 a composition wave decays at D k^2 with
+    D = mu c_s^2, mu = -tau (1/lambda_M + 1/2) = tau_r - 1/2."""
+    L = 64
+    k = 2 * np.pi / L
+    x = np.arange(L)
+    rA = (1 + 1e-3 * np.sin(k * x))[None, None, :]
+    rB = (1 - 1e-3 * np.sin(k * x))[None, None, :]
+    f = oracle.init_equilibrium(rA, rB)
+    s = oracle.System(dims=(L, 1, 1), tau_r=tau)
+    oracle.run(s, f, *_no_particles(), 50)
+    a0 = _phi_mode(f, L, k, np.sin)
+    oracle.run(s, f, *_no_particles(), 250, first_step=50)
+    a1 = _phi_mode(f, L, k, np.sin)
+    rate = -np.log(a1 / a0) / 250
+    assert abs(rate / (CS2 * (tau - 0.5) * k * k) - 1) < 0.01
+
+
+def test_flat_interface_coexistence_and_rest():
+    """Sec. 2 (flat interface) with Eqs. (fbulk), (comp_D): at steady state the barycentric
+    velocity vanishes and the bulk phases satisfy the equality of the chemical potentials
+    of F_bulk, log(rho_1/rho_2) = g (rho_1 - rho_2) for the symmetric pair of phases."""
+    L = 32
+    g = 1.2
+    z = np.arange(L)
+    inside = (z >= 8) & (z < 24)
+    rA = np.where(inside, 1.5, 0.5)[:, None, None] * 1.0
+    rB = np.where(inside, 0.5, 1.5)[:, None, None] * 1.0
+    f = oracle.init_equilibrium(rA, rB)
+    s = oracle.System(dims=(1, 1, L), tau_r=1.0, g_AB=g, g_BA=g)
+    oracle.run(s, f, *_no_particles(), 2999)
+    st, tr = oracle.step(s, f, *_no_particles(), 2999, trace=True)
+    A = tr["rho"][0, :, 0, 0]
+    B = tr["rho"][1, :, 0, 0]
+    r1, r2 = A[16], B[16]
+    assert r1 > 3 * r2  # demixed
+    assert np.isclose(A[0], r2, rtol=1e-9) and np.isclose(B[0], r1, rtol=1e-9)
+    lhs, rhs = np.log(r1 / r2), g * (r1 - r2)
+    assert abs(lhs - rhs) < 0.01 * lhs
+    assert np.abs(tr["u_cpl"]).max() < 1e-5
+
+
+@pytest.mark.slow
+def test_laplace_law_2d_droplets():
+    """Laplace's law (Sec. 4.3), quasi-2D: for A-rich disks Delta p = gamma / R, so
+    Delta p * R is the same for every radius and Delta p against 1/R is a line through
+    the origin.  p is the bulk pressure of F_bulk, c_s^2 (rho_A + rho_B) + c_s^2 g rho_A rho_B."""
+    g = 1.68
+    L = 32
+    res = []
+    for R in (5.0, 7.0, 9.0):
+        dims = (L, L, 1)
+        rA, rB = inputs.disk(dims, R, 1.8, 0.2, width=1.0)
+        f = oracle.init_equilibrium(rA, rB)
+        s = oracle.System(dims=dims, tau_r=1.0, g_AB=g, g_BA=g)
+        oracle.run(s, f, *_no_particles(), 2999)
+        _, tr = oracle.step(s, f, *_no_particles(), 2999, trace=True)
+        A, B = tr["rho"][0, 0], tr["rho"][1, 0]
+        p = CS2 * (A + B) + CS2 * g * A * B
+        dp = p[L // 2, L // 2] - p[0, 0]
+        area = ((A - A[0, 0]) / (A[L // 2, L // 2] - A[0, 0])).sum()
+        res.append((np.sqrt(area / np.pi), dp))
+    Rs = np.array([r for r, _ in res])
+    dps = np.array([d for _, d in res])
+    assert (dps > 0).all()
+    prod = dps * Rs
+    assert prod.std() / prod.mean() < 0.05
+    slope, icept = np.linalg.lstsq(np.vstack([1 / Rs, np.ones(3)]).T, dps, rcond=None)[0]
+    assert slope > 0 and abs(icept) < 0.2 * dps.max()
+
+
+# ---------------------------------------------------------------- particles
+def _one_type(**kw):
+    base = dict(kappa=np.zeros((1, 2)), lam=np.zeros((1, 2)), gamma=np.ones(1), mass=np.ones(1),
+                wca_eps=np.zeros((1, 1)), wca_sig=np.ones((1, 1)))
+    base.update(kw)
+    return base
+
+
+def test_fs_geometry_golden():
+    """Hand-worked fixtures of the geometric factor of Eq. (solvation_lambda)."""
+    cases = json.load(open(os.path.join(GOLDEN, "solvation_lambda_geometry.json")))["cases"]
+    for c in cases:
+        assert np.allclose(oracle.fs_geometry(c["d"]), c["sum"], atol=1e-14), c
+
+
+def test_friction_momentum_exchange_and_spreading_centre():
+    """Eq. (NEWTON) and the linear interpolation of Sec. 2: a particle moving through a fluid
+    at rest loses gamma v dt, the fluid gains exactly that, and the spread force is centred
+    on the particle (first moment of the trilinear weights = particle position)."""
+    dims = (6, 6, 6)
+    f = oracle.init_equilibrium(np.full((6, 6, 6), 1.0), np.full((6, 6, 6), 1.0))
+    xp = np.array([[2.3, 3.7, 1.45]])
+    v = np.array([[0.1, -0.2, 0.05]])
+    x = xp.copy()
+    s = oracle.System(dims=dims, tau_r=1.0, type=np.zeros(1, dtype=np.int32), q=np.zeros(1),
+                      **_one_type(gamma=np.array([0.7])))
+    p0 = oracle.fluid_moments(f)
+    st, tr = oracle.step(s, f, x, v, 0, trace=True)
+    p1 = oracle.fluid_moments(f)
+    assert np.allclose(tr["f_fric"][0], -0.7 * np.array([0.1, -0.2, 0.05]), atol=1e-15)
+    assert np.allclose(p1[2:] - p0[2:], 0.7 * np.array([0.1, -0.2, 0.05]), atol=1e-14)
+    assert np.allclose(v[0], 0.3 * np.array([0.1, -0.2, 0.05]), atol=1e-15)
+    gtot = tr["g"].sum(0)  # [z, y, x, 3]
+    idx = np.argwhere(np.abs(gtot[..., 0]) > 0)
+    assert len(idx) == 8
+    wsum = sum(gtot[tuple(i)][0] for i in idx)
+    centre = sum(gtot[tuple(i)][0] * i[::-1] for i in idx) / wsum
+    assert np.allclose(centre, xp[0], atol=1e-12)
+
+
+def test_solvation_kappa_follows_gradient():
+    """Eq. (solvation_kappa): F^ps = -kappa grad rho; particles are driven towards maxima of
+    rho for kappa < 0 (Sec. 2).  Closed form for a sinusoidal profile."""
+    L = 32
+    k = 2 * np.pi / L
+    z = np.arange(L)
+    rA = (1.0 + 0.05 * np.sin(k * z))[:, None, None] * np.ones((L, 4, 4))
+    rB = np.ones((L, 4, 4))
+    f = oracle.init_equilibrium(rA, rB)
+    zp = 5.3
+    x = np.array([[1.5, 2.25, zp]])
+    v = np.zeros((1, 3))
+    kap = -2.0
+    s = oracle.System(dims=(4, 4, L), tau_r=1.0, type=np.zeros(1, dtype=np.int32), q=np.zeros(1),
+                      **_one_type(kappa=np.array([[kap, 0.0]]), gamma=np.array([0.0])))
+    _, tr = oracle.step(s, f, x, v, 0, trace=True)
+    expect = -kap * 0.05 * k * np.cos(k * zp)
+    assert np.sign(tr["f_ps"][0, 2]) == np.sign(0.05 * k * np.cos(k * zp))  # uphill for kappa<0
+    assert abs(tr["f_ps"][0, 2] - expect) < 0.02 * abs(expect)
+    assert np.abs(tr["f_ps"][0, :2]).max() < 1e-15
+
+
+@pytest.mark.parametrize("comp", [0, 1])
+def test_solvation_kappa_acts_per_component(comp):
+    """Eq. (solvation_kappa) sums kappa_z grad rho_z over components: a gradient in one
+    component is felt only through that component's kappa."""
+    L = 32
+    k = 2 * np.pi / L
+    z = np.arange(L)
+    prof = (1.0 + 0.05 * np.sin(k * z))[:, None, None] * np.ones((L, 4, 4))
+    flat = np.ones((L, 4, 4))
+    f = oracle.init_equilibrium(prof if comp == 0 else flat, flat if comp == 0 else prof)
+    zp = 11.7
+    kap = np.zeros((1, 2))
+    kap[0, comp] = 1.5
+    kap_other = np.zeros((1, 2))
+    kap_other[0, 1 - comp] = 1.5
+    out = []
+    for kk in (kap, kap_other):
+        s = oracle.System(dims=(4, 4, L), tau_r=1.0, type=np.zeros(1, dtype=np.int32), q=np.zeros(1),
+                          **_one_type(kappa=kk, gamma=np.array([0.0])))
+        f2 = f.copy()
+        _, tr = oracle.step(s, f2, np.array([[2.5, 1.0, zp]]), np.zeros((1, 3)), 0, trace=True)
+        out.append(tr["f_ps"][0, 2])
+    expect = -1.5 * 0.05 * k * np.cos(k * zp)
+    assert abs(out[0] - expect) < 0.02 * abs(expect)
+    assert abs(out[1]) < 1e-15
+
+
+def test_solvation_free_energy_across_interface():
+    """Eq. (solvation_density): the line integral of the solvation force from one bulk phase
+    to the other is Delta E = -sum_z kappa_z Delta rho_z.  Integrate the force on a particle
+    held at positions across a steady flat interface (paper example kappa_A = -1,
+    kappa_B = -2)."""
+    L = 32
+    g = 1.2
+    z = np.arange(L)
+    inside = (z >= 8) & (z < 24)
+    rA = np.where(inside, 1.5, 0.5)[:, None, None] * np.ones((L, 2, 2))
+    rB = np.where(inside, 0.5, 1.5)[:, None, None] * np.ones((L, 2, 2))
+    f = oracle.init_equilibrium(rA, rB)
+    oracle.run(oracle.System(dims=(2, 2, L), tau_r=1.0, g_AB=g, g_BA=g), f, *_no_particles(), 3000)
+    kap = np.array([[-1.0, -2.0]])
+    s = oracle.System(dims=(2, 2, L), tau_r=1.0, g_AB=g, g_BA=g, type=np.zeros(1, dtype=np.int32),
+                      q=np.zeros(1), **_one_type(kappa=kap, gamma=np.array([0.0])))
+    zs = np.linspace(16.0, 31.99, 321)  # from the A-rich centre to the B-rich bulk
+    F = []
+    for zp in zs:
+        f2 = f.copy()
+        _, tr = oracle.step(s, f2, np.array([[0.5, 0.5, zp]]), np.zeros((1, 3)), 0, trace=True)
+        F.append(tr["f_ps"][0, 2])
+    dE = np.trapezoid(F, zs)
+    rho = tr["rho"]
+    dA = rho[0, 31, 0, 0] - rho[0, 16, 0, 0]
+    dB = rho[1, 31, 0, 0] - rho[1, 16, 0, 0]
+    expect = -(kap[0, 0] * dA + kap[0, 1] * dB)
+    assert abs(dE - expect) < 0.02 * abs(expect)
+
+
+@pytest.mark.parametrize("lam,sign", [(0.05, -1), (-0.05, +1)])
+def test_solvation_lambda_density_response(lam, sign):
+    """Eq. (solvation_lambda) as printed: Theta selects the links pointing towards the
+    particle and the force carries -lambda, so a positive lambda pushes the fluid away
+    from the particle (the analogue of a positive g in Eq. SCforce, which the paper draws
+    explicitly) and a negative lambda pulls it in.  The sentence after the equation states
+    the opposite sign convention; the equation is followed.  The particle is held fixed
+    by resetting it after each step."""
+    n = 8
+    dims = (n, n, n)
+    f = oracle.init_equilibrium(np.full((n, n, n), 1.0), np.full((n, n, n), 1.0))
+    s = oracle.System(dims=dims, tau_r=1.0, type=np.zeros(1, dtype=np.int32), q=np.zeros(1),
+                      **_one_type(lam=np.array([[lam, 0.0]]), gamma=np.array([0.0])))
+    for t in range(40):
+        x = np.array([[4.5, 4.5, 4.5]])
+        v = np.zeros((1, 3))
+        oracle.step(s, f, x, v, t)
+    rhoA = f[0].sum(0)
+    near = rhoA[4:6, 4:6, 4:6].mean()
+    far = rhoA[0, 0, 0]
+    assert sign * (near - far) > 1e-4
+    assert np.isclose(rhoA.sum(), n ** 3, rtol=1e-13)
+
+
+def test_noise_statistics():
+    """Eq. (NEWTON): <R_a R_b> = 2 kT gamma delta_ab per unit time; with dt = 1 each
+    component of R has variance 2 kT gamma and zero mean.  Also Box-Muller normals."""
+    zs = np.array([oracle.normals(123, t, p) for t in range(40) for p in range(100)])
+    assert abs(zs.mean()) < 0.03
+    assert abs(zs.var() - 1) < 0.05
+    assert abs(np.corrcoef(zs[:, 0], zs[:, 1])[0, 1]) < 0.05
+    dims = (8, 8, 8)
+    f = oracle.init_equilibrium(np.ones((8, 8, 8)), np.ones((8, 8, 8)))
+    npart = 300
+    x = inputs.random_particles(npart, dims, 0.0, seed=3)
+    v = np.zeros((npart, 3))
+    kT, gam = 0.5, 1.5
+    s = oracle.System(dims=dims, tau_r=1.0, kT=kT, seed=9, type=np.zeros(npart, dtype=np.int32),
+                      q=np.zeros(npart), **_one_type(gamma=np.array([gam])))
+    _, tr = oracle.step(s, f, x, v, 0, trace=True)
+    R = tr["f_fric"]  # fluid at rest and v = 0: friction force = noise
+    assert abs(R.var() / (2 * kT * gam) - 1) < 0.1
+
+
+def test_philox_known_answers():
+    data = json.load(open(os.path.join(GOLDEN, "philox4x32_10_kat.json")))
+    for c in data["cases"]:
+        out = oracle.philox4x32_10([int(v, 16) for v in c["ctr"]], [int(v, 16) for v in c["key"]])
+        assert [int(v, 16) for v in c["out"]] == out.tolist()
+
+
+def test_pair_potentials():
+    """WCA (Sec. 4.1): zero at sigma, -eps and zero force at the cut-off 2^(1/6) sigma,
+    minimum there; DH (Sec. 4.4): value at the cut-off about 0.04 kT; every force is the
+    negative derivative of its energy."""
+    rc = 2 ** (1 / 6)
+    assert abs(oracle.pair_energy(oracle.PAIR_WCA, 1.0, 1.0, 0, 1.0)) < 1e-15
+    assert np.isclose(oracle.pair_energy(oracle.PAIR_WCA, 0.7, 1.0, 0, rc * (1 - 1e-12)), -0.7, rtol=1e-9)
+    assert abs(oracle.pair_force(oracle.PAIR_WCA, 1.0, 1.0, 0, rc * (1 - 1e-12))) < 1e-9
+    assert oracle.pair_energy(oracle.PAIR_WCA, 1.0, 1.0, 0, rc * 1.0001) == 0.0
+    dh = json.load(open(os.path.join(GOLDEN, "debye_hueckel_cutoff.json")))
+    u_rc = oracle.pair_energy(oracle.PAIR_DH, dh["qq"] * dh["lB"], dh["kappa_D"], 1e9, dh["rc"])
+    assert abs(u_rc - dh["paper_value"]) < dh["paper_precision"]
+    assert oracle.pair_energy(oracle.PAIR_DH, 1.0, 0.25, 6.0, 6.0) == 0.0
+    h = 1e-6
+    for kind, p in [(oracle.PAIR_WCA, (1.0, 1.0, 0)), (oracle.PAIR_WCA, (0.1, 0.7, 0)),
+                    (oracle.PAIR_DH, (-1.0, 0.25, 3.0)), (oracle.BOND_FENE, (30.0, 1.5, 0)),
+                    (oracle.BOND_HARMONIC, (20.0, 0.8, 0))]:
+        for r in (0.75, 0.9, 1.0, 1.05, 1.3):
+            if kind == oracle.PAIR_WCA and r * (1 + h) >= 2 ** (1 / 6) * p[1]:
+                continue
+            num = -(oracle.pair_energy(kind, *p, r + h) - oracle.pair_energy(kind, *p, r - h)) / (2 * h)
+            assert np.isclose(oracle.pair_force(kind, *p, r), num, rtol=1e-6, atol=1e-8), (kind, r)
+    # repulsive WCA and like-charge DH push apart, FENE pulls together
+    assert oracle.pair_force(oracle.PAIR_WCA, 1.0, 1.0, 0, 0.95) > 0
+    assert oracle.pair_force(oracle.PAIR_DH, 1.0, 0.25, 3.0, 1.5) > 0
+    assert oracle.pair_force(oracle.BOND_FENE, 30.0, 1.5, 0, 1.0) < 0
+
+
+def _busy_system(dims, npart, seed, g=1.3, kT=0.05):
+    """A small system with every coupling switched on, gentle enough to stay smooth over
+    ten steps at dt = 1: bonded pairs 1.3 apart, one pair inside the WCA range, weak
+    potentials."""
+    rA, rB = inputs.uniform_noise(dims, 1.0, 0.05, seed=seed)
+    f = oracle.init_equilibrium(rA, rB)
+    x = inputs.random_particles(npart, dims, 2.2, seed=seed + 1)
+    x[1] = (x[0] + (1.3, 0.0, 0.0)) % np.array(dims, dtype=float)
+    x[3] = (x[2] + (1.3, 0.0, 0.0)) % np.array(dims, dtype=float)
+    x[5] = (x[4] + (0.0, 0.6, 0.7)) % np.array(dims, dtype=float)  # inside the WCA range
+    v = np.random.default_rng(seed).normal(scale=0.05, size=(npart, 3))
+    typ = (np.arange(npart) % 2).astype(np.int32)
+    q = np.where(np.arange(npart) % 4 < 2, 1.0, -1.0)
+    s = oracle.System(dims=dims, tau_r=0.9, g_AB=g, g_BA=g, kT=kT, seed=11,
+                      kappa=np.array([[-0.3, 0.2], [0.1, -0.4]]), lam=np.array([[0.02, -0.01], [0.0, 0.03]]),
+                      gamma=np.array([1.0, 0.5]), mass=np.array([1.0, 2.0]),
+                      wca_eps=np.array([[0.01, 0.005], [0.005, 0.01]]),
+                      wca_sig=np.array([[1.0, 0.9], [0.9, 0.8]]),
+                      dh_lB=0.05, dh_kappa=0.25, dh_rc=2.5, type=typ, q=q,
+                      bonds=np.array([[0, 1], [2, 3]], dtype=np.int32), bond_kind=oracle.BOND_FENE,
+                      bond_k=0.05, bond_r=3.0)
+    return s, f, x, v
+
+
+def test_mass_and_total_momentum_conservation():
+    """Appendix (forces do not change the mass density) and Sec. 2 (g_AB = g_BA makes the
+    Shan-Chen forces momentum-free; the solvation and friction momenta are returned with
+    the same interpolation): per-component mass and total fluid + particle momentum are
+    conserved to rounding, with every term switched on."""
+    dims = (7, 6, 5)
+    s, f, x, v = _busy_system(dims, 6, seed=4)
+    m = np.asarray(s.mass)[s.type][:, None]
+    m0 = oracle.fluid_moments(f)
+    P0 = m0[2:] + (m * v).sum(0)
+    for t in range(10):
+        st, tr = oracle.step(s, f, x, v, t, trace=True)
+        assert st == 0
+        assert np.abs(tr["f_pair"].sum(0)).max() < 1e-12
+        assert np.abs(tr["f_bond"].sum(0)).max() < 1e-12
+    m1 = oracle.fluid_moments(f)
+    P1 = m1[2:] + (m * v).sum(0)
+    assert np.allclose(m1[:2], m0[:2], rtol=1e-13, atol=0)
+    assert np.abs(P1 - P0).max() < 1e-12
+    # the fluid alone does not conserve momentum here: the exchange is real
+    assert np.abs(m1[2:] - m0[2:]).max() > 1e-6
+
+
+def test_friction_split_keeps_composition_uniform():
+    """Eq. (comp_D): a force split g_z = (rho_z/rho) g drives no interdiffusion.  Particle
+    forces must therefore leave a uniform composition uniform when kappa_A = kappa_B and
+    lambda_A = lambda_B (g = 0): rho_A/rho stays constant to rounding."""
+    dims = (6, 6, 6)
+    cA = 0.35
+    rho = 1.0 + 0.03 * np.random.default_rng(2).uniform(-1, 1, size=(6, 6, 6))
+    f = oracle.init_equilibrium(cA * rho, (1 - cA) * rho)
+    npart = 6
+    x = inputs.random_particles(npart, dims, 1.2, seed=8)
+    v = np.random.default_rng(1).normal(scale=0.05, size=(npart, 3))
+    s = oracle.System(dims=dims, tau_r=0.8, kT=0.02, seed=5, type=np.zeros(npart, dtype=np.int32),
+                      q=np.zeros(npart), **_one_type(kappa=np.array([[0.4, 0.4]]), lam=np.array([[0.02, 0.02]]),
+                                                     wca_eps=np.full((1, 1), 0.01)))
+    oracle.run(s, f, x, v, 15)
+    ratio = f[0].sum(0) / (f[0].sum(0) + f[1].sum(0))
+    assert np.abs(ratio - cA).max() < 1e-13
+
+
+def test_particle_at_rest_in_fluid_at_rest_feels_no_drag():
+    """Eqs. (NEWTON), (momentum_definition): at a steady flat interface the barycentric
+    velocity u = (j' + g/2)/rho vanishes while j' itself does not; a resting particle there
+    must feel no friction (reading R5)."""
+    L = 32
+    g = 1.2
+    z = np.arange(L)
+    inside = (z >= 8) & (z < 24)
+    rA = np.where(inside, 1.5, 0.5)[:, None, None] * np.ones((L, 2, 2))
+    rB = np.where(inside, 0.5, 1.5)[:, None, None] * np.ones((L, 2, 2))
+    f = oracle.init_equilibrium(rA, rB)
+    s = oracle.System(dims=(2, 2, L), tau_r=1.0, g_AB=g, g_BA=g)
+    oracle.run(s, f, *_no_particles(), 3000)
+    c, _ = oracle.lattice()
+    jz = np.einsum("zinyx,i->nyx", f, c[:, 2].astype(float))
+    assert np.abs(jz).max() > 1e-3
+    x = np.array([[0.5, 0.5, 7.6]])
+    v = np.zeros((1, 3))
+    sp = oracle.System(dims=(2, 2, L), tau_r=1.0, g_AB=g, g_BA=g, type=np.zeros(1, dtype=np.int32),
+                       q=np.zeros(1), **_one_type())
+    _, tr = oracle.step(sp, f, x, v, 3000, trace=True)
+    assert np.abs(tr["f_fric"]).max() < 1e-5 * np.abs(jz).max()
+
+
+def test_free_flight_integrator():
+    """Reading R9: without forces x advances by v dt and wraps periodically."""
+    dims = (4, 4, 4)
+    f = oracle.init_equilibrium(np.ones((4, 4, 4)), np.ones((4, 4, 4)))
+    x = np.array([[3.9, 0.05, 2.0]])
+    v = np.array([[0.3, -0.1, 0.25]])
+    s = oracle.System(dims=dims, type=np.zeros(1, dtype=np.int32), q=np.zeros(1),
+                      **_one_type(gamma=np.zeros(1)))
+    oracle.step(s, f, x, v, 0)
+    assert np.allclose(x[0], [0.2, 3.95, 2.25], atol=1e-14)
