@@ -184,20 +184,19 @@ void orc_normals(uint64_t seed, uint64_t step, uint32_t id, double *n) {
 
 /* Geometric factor of Eq. (solvation_lambda) for one particle seen from one node, readings R8:
  *   sum over the 18 neighbours r' = r + c_i of Theta[d_hat . c_hat_i] c_i / |c_i|^2,
- * with d = r_particle - r and Theta(x) = 1 for 0 < x < 1. */
+ * with d = r_particle - r and Theta(x) = 1 for 0 < x < 1.  By Cauchy-Schwarz d_hat . c_hat <= 1
+ * with equality iff d is parallel to c_i, so 0 < x < 1 is tested exactly as
+ * (d . c_i > 0 and d x c_i != 0), free of rounding in the normalisation. */
 void orc_fs_geometry(const double *d, double *out) {
   out[0] = out[1] = out[2] = 0.0;
-  double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-  if (dn == 0.0) return;
   for (int i = 1; i < ORC_Q; ++i) {
-    double c2 = 0.0, dc = 0.0;
-    for (int a = 0; a < 3; ++a) {
-      c2 += (double)(orc_c[i][a] * orc_c[i][a]);
-      dc += d[a] * orc_c[i][a];
-    }
-    double t = dc / (dn * sqrt(c2));
-    if (t > 0.0 && t < 1.0)
-      for (int a = 0; a < 3; ++a) out[a] += orc_c[i][a] / c2;
+    const int *c = orc_c[i];
+    double c2 = (double)(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    double dc = d[0] * c[0] + d[1] * c[1] + d[2] * c[2];
+    double cross[3] = {d[1] * c[2] - d[2] * c[1], d[2] * c[0] - d[0] * c[2], d[0] * c[1] - d[1] * c[0]};
+    int parallel = cross[0] == 0.0 && cross[1] == 0.0 && cross[2] == 0.0;
+    if (dc > 0.0 && !parallel)
+      for (int a = 0; a < 3; ++a) out[a] += c[a] / c2;
   }
 }
 
