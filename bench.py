@@ -1,0 +1,351 @@
+"""Throughput benchmark of the coupled two-component D3Q19 Shan-Chen LB / MD step.
+
+One bench "step" is one full coupled time step (Shan-Chen force, fluid-side solvation,
+coupling velocity, particle forces, momentum return, stream + collide for both components,
+cell-list pair forces, particle update) over the whole lattice.  Default workload: a 256^3
+lattice with a flat slab interface plus spherical droplets of radii 8-32 and 2e4 point
+particles with solvation coupling preferring component B and WCA pairs (synthetic, seeded).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled 2-comp D3Q19 MLUPS & HBM-roofline %; replica p50/p99 latency"
+UNIT = "MLUPS"
+HBM_FALLBACK_GBS = 6800.0
+
+# Bulk coexistence of F_bulk (Eq. fbulk) for g = 1.68 with rho_A + rho_B = 2:
+# log(rho_hi / rho_lo) = g (rho_hi - rho_lo)  ->  rho_hi = 1.9103, rho_lo = 0.0897.
+G_COUPLING = 1.68
+RHO_HI, RHO_LO = 1.9103, 0.0897
+
+WORKLOADS = {
+    # name: (edge, particles, description)
+    "slab_droplets_256": (256, 20000, "256^3 two-component LB FP32, flat slab + 8 droplets (R 8-32), "
+                                      "2e4 solvation-coupled point particles (kappa_A=-0.05, kappa_B=-0.1), WCA"),
+    "noise_32": (32, 64, "32^3 two-component LB FP32, rho=1+-0.01, 64 friction-coupled particles, WCA"),
+}
+
+
+def algorithmic_bytes_per_site() -> int:
+    """Bytes per site of the lattice update kernel: both components' 19 populations read
+    (pull) and written, FP32 (2*19*4*2 = 304), plus the two stored densities of the
+    stencil read (8)."""
+    return 2 * 19 * 4 * 2 + 8
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def rd():
+            for line in self.proc.stdout:
+                self.lines.append(line.strip())
+
+        self.thread = threading.Thread(target=rd, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_workload(name: str, seed: int):
+    from paper_1306_0788_gb300 import inputs
+    edge, npart, _ = WORKLOADS[name]
+    dims = (edge, edge, edge)
+    if name == "slab_droplets_256":
+        rA, rB, drops = inputs.slab_and_droplets(dims, RHO_HI, RHO_LO, n_drops=8, r_min=8, r_max=32, width=4.0,
+                                                 seed=seed)
+        types = [(-0.05, -0.1, 0.0, 0.0, 1.0, 1.0)]
+        kT = 1e-4
+    else:
+        rA, rB = inputs.uniform_noise(dims, 1.0, 0.01, seed=seed)
+        types = [(0.0, 0.0, 0.0, 0.0, 1.0, 1.0)]
+        kT = 1e-4
+    x = inputs.random_particles(npart, dims, 2 ** (1 / 6), seed=seed + 1)
+    return dims, rA.astype(np.float32), rB.astype(np.float32), x, types, kT
+
+
+def run_cuda(args):
+    import torch
+    from paper_1306_0788_gb300 import lbmd as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+
+    dims, rA, rB, x, types, kT = build_workload(args.workload, seed=1234 + rank)
+    npart = len(x)
+    N = dims[0] * dims[1] * dims[2]
+    prm = L.params(dims, tau_r=1.0, g_AB=G_COUPLING, kT=kT, seed=42 + rank)
+    ctx, _ = L.lbmd_create(prm, stream)
+    L.lbmd_set_types(ctx, [L.lbmd_ptype(*t) for t in types], [L.lbmd_pair(0, 0, 1.0, 1.0)])
+    L.lbmd_init_fluid(ctx, rA, rB)
+    L.lbmd_set_particles(ctx, x, np.zeros_like(x), np.zeros(npart, dtype=np.int32))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    L.lbmd_step(ctx, args.warmup)
+    barrier()
+    L.lbmd_profile_enable(ctx, True)
+    L.lbmd_profile_read(ctx, reset=True)
+    launches0 = L.lbmd_launch_count(ctx)
+    sampler = ClockSampler(dev)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        L.lbmd_step(ctx, args.steps)
+        e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = L.lbmd_launch_count(ctx) - launches0
+    k_ms, k_n = L.lbmd_profile_read(ctx, reset=True)
+    L.lbmd_profile_enable(ctx, False)
+    state_ok = True
+    try:
+        L.lbmd_sync(ctx)
+    except L.LbmdError:
+        state_ok = False
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    # end-to-end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        hA, hB = pin(rA), pin(rB)
+        hx, hv = pin(x.astype(np.float64)), pin(np.zeros_like(x, dtype=np.float64))
+        ht = pin(np.zeros(npart, dtype=np.int32))
+        outA, outB = pin(np.empty_like(rA)), pin(np.empty_like(rB))
+        outU = pin(np.empty(rA.shape + (3,), dtype=np.float32))
+        ox, ov, of = (pin(np.empty((npart, 3))) for _ in range(3))
+        import ctypes
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        lib = L._lib
+        barrier()
+        t0 = time.perf_counter()
+        rc = lib.lbmd_init_fluid(ctx, p(hA), p(hB), None)
+        rc |= lib.lbmd_set_particles(ctx, npart, p(hx), p(hv), p(ht), None)
+        rc |= lib.lbmd_step(ctx, args.steps)
+        rc |= lib.lbmd_get_fields(ctx, p(outA), p(outB), p(outU))
+        rc |= lib.lbmd_get_particles(ctx, p(ox), p(ov), p(of))
+        barrier()
+        t_e2e = time.perf_counter() - t0
+        h2d = (2 * N * 4 + npart * (6 * 8 + 4)) / args.steps
+        d2h = (5 * N * 4 + npart * 9 * 8) / args.steps
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": round(world * N * args.steps / float(tt.item()) / 1e6, 3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "status": int(rc),
+               "what": "lbmd_init_fluid + lbmd_set_particles (pinned host) + lbmd_step(K) + "
+                       "lbmd_get_fields + lbmd_get_particles (pinned host), wall clock"}
+    L.lbmd_destroy(ctx)
+
+    peak, peak_kind = measured_hbm_peak()
+    bps = algorithmic_bytes_per_site()
+    avg_kernel_ms = k_ms / max(k_n, 1)
+    achieved = bps * N / (avg_kernel_ms * 1e-3) / 1e9
+    value = world * N * args.steps / (ms_max * 1e-3) / 1e6
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload][2],
+                       "lattice": list(dims), "particles": npart, "tau_r": 1.0, "g_AB": G_COUPLING, "kT": kT,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (N * 152 / 1e9)
+                       if N * 152 > 129e6 else "L2-resident lattice (latency regime)"},
+            "roofline": {"bound": "hbm", "kernel": "k_collide (stream + collide + forcing + coupling gather)",
+                         "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "bytes_per_site": bps,
+                         "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,
+                         "traffic": None},
+            "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks, "state_ok": state_ok,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def oracle_sample(workload: str, edge: int, seed: int):
+    """A bounded sample of the workload for the CPU oracle: an edge^3 box with the same
+    particle density and the same fluid recipe."""
+    import oracle
+    from paper_1306_0788_gb300 import inputs
+    full_edge, npart_full, _ = WORKLOADS[workload]
+    dims = (edge, edge, edge)
+    n = max(1, int(round(npart_full * (edge / full_edge) ** 3)))
+    if workload == "slab_droplets_256":
+        rA, rB, _ = inputs.slab_and_droplets(dims, RHO_HI, RHO_LO, n_drops=1, r_min=edge / 8, r_max=edge / 8,
+                                             width=4.0, seed=seed)
+        kap = np.array([[-0.05, -0.1]])
+    else:
+        rA, rB = inputs.uniform_noise(dims, 1.0, 0.01, seed=seed)
+        kap = np.zeros((1, 2))
+    x = inputs.random_particles(n, dims, 2 ** (1 / 6), seed=seed + 1)
+    s = oracle.System(dims=dims, tau_r=1.0, g_AB=G_COUPLING, g_BA=G_COUPLING, kT=1e-4, seed=42,
+                      kappa=kap, lam=np.zeros((1, 2)), gamma=np.ones(1), mass=np.ones(1),
+                      wca_eps=np.ones((1, 1)), wca_sig=np.ones((1, 1)), type=np.zeros(n, dtype=np.int32),
+                      q=np.zeros(n))
+    f = oracle.init_equilibrium(rA.astype(np.float32).astype(np.float64), rB.astype(np.float32).astype(np.float64))
+    return s, f, x.copy(), np.zeros((n, 3)), n
+
+
+def cpu_baseline(workload: str, budget_s: float = 15.0, edge: int = 32):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample (edge^3 with the
+    workload's particle density), timed for about budget_s seconds."""
+    import oracle
+    s, f, x, v, n = oracle_sample(workload, edge, seed=7)
+    oracle.step(s, f, x, v, 0)  # load and warm
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        oracle.step(s, f, x, v, 1 + steps)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(edge ** 3 * steps / dt / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d^3 lattice, %d particles (same density and recipe), %d steps, %.1f s" % (edge, n, steps, dt)}
+
+
+def run_reference(args):
+    """The oracle arm: rank 0 times the FP64 CPU oracle, K steps of a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    # size the sample so that warm-up + K steps take about two minutes at ~0.3 MLUPS
+    sites = max(8 ** 3, min(32 ** 3, int(0.3e6 * 120.0 / max(args.steps + args.warmup, 1))))
+    edge = max(8, int(round(sites ** (1 / 3))))
+    s, f, x, v, n = oracle_sample(args.workload, edge, seed=7)
+    for k in range(args.warmup):
+        oracle.step(s, f, x, v, k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.step(s, f, x, v, args.warmup + k)
+    dt = time.perf_counter() - t0
+    value = edge ** 3 * args.steps / dt / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "description": WORKLOADS[args.workload][2],
+                      "sample": "%d^3 lattice, %d particles" % (edge, n)},
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "%d^3 lattice, %d particles, %d steps" % (edge, n, args.steps)},
+           "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="slab_droplets_256")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * lbmd.h -- C ABI of the GB300 (sm_103a) implementation of one time step of the
+ * two-component D3Q19 Shan-Chen lattice Boltzmann fluid coupled to off-lattice point
+ * particles by Ahlrichs-Duenweg friction and solvation forces, after Sega, Sbragaglia,
+ * Kantorovich, Ivanov, "Mesoscale Structures at Complex Fluid-Fluid Interfaces: a Novel
+ * Lattice Boltzmann / Molecular Dynamics Coupling" (arXiv:1306.0788).
+ *
+ * Conventions shared by every call
+ *   Units      lattice units: spacing a = 1, lattice time step tau = 1 (Sec. 3).
+ *   Lattice    nx * ny * nz nodes at integer positions, periodic in x, y and z.  Site
+ *              index s = (z * ny + y) * nx + x (x fastest).
+ *   Components 0 = A, 1 = B.
+ *   D3Q19      velocity order i = 0; +x,-x,+y,-y,+z,-z; (+x+y),(-x-y),(+x-y),(-x+y),
+ *              (+x+z),(-x-z),(+x-z),(-x+z), (+y+z),(-y-z),(+y-z),(-y+z)  (Eq. velo; the
+ *              paper leaves the order within a shell free).  Weights 1/3, 1/18, 1/36
+ *              (Eq. weights).
+ *   Populations are exchanged as the post-streaming values f_zi(r, t) at a step
+ *              boundary, layout [19][nz][ny][nx] per component, FP32.
+ *   Particles  positions in [0, n) per axis (wrapped on input), given and returned in
+ *              the caller's original order (index = particle id).
+ *   Pointers   every pointer argument is caller-owned HOST memory, read or written
+ *              before the call returns, unless the name ends in _dev.  The library owns
+ *              all device memory it allocates; lbmd_destroy frees it.
+ *   Streams    all device work of a context is issued on the stream given to
+ *              lbmd_create (NULL = the legacy default stream).  Calls that return data
+ *              to the host synchronise that stream.
+ *   Errors     every int-returning call returns LBMD_OK (0) or a negative LBMD_E_* code;
+ *              lbmd_last_error gives a message for the last failure of the context.
+ *              Device-side failures (negative or non-finite density, broken bond,
+ *              particle outside the box) are recorded in a device error word during
+ *              lbmd_step and reported by the next call that synchronises (lbmd_sync,
+ *              getters, lbmd_diagnostics); they are sticky until lbmd_clear_error.
+ *   Threads    a context must not be used from two host threads at once.
+ */
+#ifndef LBMD_H
+#define LBMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBMD_OK 0
+#define LBMD_E_INVALID_ARG (-1)
+#define LBMD_E_NOMEM (-2)
+#define LBMD_E_CUDA (-3)
+#define LBMD_E_NEGATIVE_DENSITY (-4) /* Sec. 3: large lambda can drive densities negative */
+#define LBMD_E_NONFINITE (-5)
+#define LBMD_E_TIMEOUT (-6)
+#define LBMD_E_UNIMPLEMENTED (-7)
+#define LBMD_E_BOND_BROKEN (-8) /* FENE bond stretched to or beyond R0 */
+#define LBMD_E_STATE (-9)       /* call out of order (e.g. step before init_fluid) */
+
+/* population storage (the benchmark spec precision pattern); only FP32 is implemented for now */
+#define LBMD_STORAGE_FP32 0
+#define LBMD_STORAGE_FP16_SHIFTED 1
+#define LBMD_STORAGE_BF16_SHIFTED 2
+
+/* bonded interactions */
+#define LBMD_BOND_FENE 2     /* U = -(k R0^2 / 2) ln(1 - (r/R0)^2) (Kremer-Grest form) */
+#define LBMD_BOND_HARMONIC 3 /* U = (k/2) (r - d)^2 (Sec. 4.3, 4.4) */
+
+/* warnings (bit mask) raised by lbmd_create / lbmd_set_types for the stability limits of
+ * Sec. 3; they never fail a call */
+#define LBMD_WARN_GAMMA_DT (1u << 0)   /* gamma dt / m not << 1 (here: > 0.5) */
+#define LBMD_WARN_VISCOSITY (1u << 1)  /* eta/rho = c_s^2 (tau_r - 1/2) below 1e-3 */
+#define LBMD_WARN_BOLTZMANN (1u << 2)  /* Bo = sqrt(kT / (rho c_s^2)) above 0.5 */
+#define LBMD_WARN_ASYMMETRIC_G (1u << 3) /* g_AB != g_BA: no momentum guarantee (Sec. 2) */
+
+#define LBMD_MAX_TYPES 8
+
+typedef struct lbmd_ctx lbmd_ctx;
+
+/* Model and numerics.  tau_r: BGK relaxation time (> 1/2); every relaxation eigenvalue
+ * of the collision operator (Eq. collis, Eq. MODES) is -1/tau_r.  g_AB, g_BA: Shan-Chen
+ * couplings of Eq. (SCforce) with psi = rho and g_AA = g_BB = 0; the lattice sum uses
+ * the isotropy weights w_i.  kT: thermal energy of the particle noise (Eq. NEWTON).
+ * dt: particle time step, must equal the lattice time step 1.  storage: LBMD_STORAGE_*.
+ * rho0_A, rho0_B: shift reference of the 16-bit storages (ignored for FP32).  seed: key
+ * of the counter-based particle noise. */
+typedef struct {
+  int nx, ny, nz;
+  double tau_r;
+  double g_AB, g_BA;
+  double kT;
+  double dt;
+  int storage;
+  double rho0_A, rho0_B;
+  uint64_t seed;
+} lbmd_params;
+
+/* Per particle type: kappa_A, kappa_B of Eq. (solvation_kappa), lambda_A, lambda_B of
+ * Eq. (solvation_lambda), friction gamma of Eq. (NEWTON), mass. */
+typedef struct {
+  double kappa_A, kappa_B, lambda_A, lambda_B, gamma, mass;
+} lbmd_ptype;
+
+/* WCA pair parameters (Sec. 4.1): U = 4 eps [(sigma/r)^12 - (sigma/r)^6] for r < 2^(1/6) sigma. */
+typedef struct {
+  int type_i, type_j;
+  double wca_eps, wca_sigma;
+} lbmd_pair;
+
+/* Create a context for an nx*ny*nz lattice on the current CUDA device.  stream: a
+ * cudaStream_t (may be NULL).  Allocates both population buffers; fails with
+ * LBMD_E_NOMEM if they do not fit.  *warnings (may be NULL) receives LBMD_WARN_* bits.
+ * Errors: LBMD_E_INVALID_ARG for sizes < 1, tau_r <= 1/2, dt != 1, unknown storage. */
+int lbmd_create(const lbmd_params *params, void *stream, lbmd_ctx **out, unsigned *warnings);
+
+/* Destroy a context and free its device memory (NULL is ignored). */
+void lbmd_destroy(lbmd_ctx *ctx);
+
+/* Particle types and WCA pairs.  ntypes in [1, LBMD_MAX_TYPES]; pairs not listed have no
+ * WCA interaction; each listed pair applies to (i,j) and (j,i).  Copied before return. */
+int lbmd_set_types(lbmd_ctx *ctx, int ntypes, const lbmd_ptype *types, int npairs,
+                   const lbmd_pair *pairs, unsigned *warnings);
+
+/* Screened Coulomb (Sec. 4.4): U = q_i q_j lB exp(-kappa_D r)/r for r < rc; lB = 0
+ * switches it off.  rc must be below half the smallest box edge. */
+int lbmd_set_debye_hueckel(lbmd_ctx *ctx, double lB, double kappa_D, double rc);
+
+/* Initialise the fluid at equilibrium, f_zi = f^eq_i(rho_z, u) (Eq. feq), from host
+ * arrays rhoA, rhoB [nz][ny][nx] (> 0) and u [nz][ny][nx][3] (NULL = at rest).  Resets
+ * the step counter to 0. */
+int lbmd_init_fluid(lbmd_ctx *ctx, const float *rhoA, const float *rhoB, const float *u);
+
+/* Set / get the post-streaming populations of component comp (0 = A, 1 = B), host array
+ * f [19][nz][ny][nx]. */
+int lbmd_set_populations(lbmd_ctx *ctx, int comp, const float *f);
+int lbmd_get_populations(lbmd_ctx *ctx, int comp, float *f);
+
+/* Set the particles: n >= 0; x, v [n][3] doubles (positions wrapped into the box), type
+ * [n] in [0, ntypes), q [n] charges (NULL = all zero).  Replaces all particles and bonds
+ * stay as set (they refer to particle indices). */
+int lbmd_set_particles(lbmd_ctx *ctx, int n, const double *x, const double *v, const int *type,
+                       const double *q);
+
+/* Bonds between particle indices pairs [nb][2]; kind LBMD_BOND_FENE (k, r = R0) or
+ * LBMD_BOND_HARMONIC (k, r = d).  nb = 0 removes all bonds. */
+int lbmd_set_bonds(lbmd_ctx *ctx, int nb, const int *pairs, int kind, double k, double r);
+
+/* Advance nsteps >= 0 coupled steps (Sec. 2 and the appendix): Shan-Chen force, fluid-side
+ * solvation force, coupling velocity, particle forces (friction + noise, solvation, WCA,
+ * screened Coulomb, bonds), momentum return onto the 8 nodes of each particle's cell, BGK
+ * collision with forcing and pull streaming for both components, particle update.
+ * Asynchronous on the context stream; device errors surface at the next synchronising
+ * call. */
+int lbmd_step(lbmd_ctx *ctx, int nsteps);
+
+/* Wait for the context stream; returns the first recorded device error, if any. */
+int lbmd_sync(lbmd_ctx *ctx);
+int lbmd_clear_error(lbmd_ctx *ctx);
+
+/* Densities rhoA, rhoB [nz][ny][nx] and barycentric velocity u [nz][ny][nx][3]
+ * (Eq. momentum_definition, u = (j' + g/2)/rho with the force of the last step's
+ * collision) at the current step; any pointer may be NULL. */
+int lbmd_get_fields(lbmd_ctx *ctx, float *rhoA, float *rhoB, float *u);
+
+/* Particle positions x, velocities v and the total force f of the last step, each
+ * [n][3] doubles in the caller's order; any pointer may be NULL. */
+int lbmd_get_particles(lbmd_ctx *ctx, double *x, double *v, double *f);
+
+/* FP64 reductions on the device: out[0..1] = total mass of A and B, out[2..4] = fluid
+ * momentum sum_r j'(r), out[5..7] = particle momentum sum m v. */
+int lbmd_diagnostics(lbmd_ctx *ctx, double out[8]);
+
+/* Number of completed steps. */
+int64_t lbmd_step_count(const lbmd_ctx *ctx);
+
+/* Kernel timing of the lattice kernel: when enabled, lbmd_step brackets every launch of
+ * the fused stream-collide kernel with CUDA events on the context stream;
+ * lbmd_profile_read returns the summed milliseconds and the launch count since the last
+ * reset (synchronises). */
+int lbmd_profile_enable(lbmd_ctx *ctx, int on);
+int lbmd_profile_read(lbmd_ctx *ctx, double *ms, int64_t *launches, int reset);
+
+/* Number of kernel launches issued by lbmd_step so far (host-side count). */
+int64_t lbmd_launch_count(const lbmd_ctx *ctx);
+
+/* Message of the last failure of ctx, or of the last failed lbmd_create if ctx is NULL. */
+const char *lbmd_last_error(const lbmd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMD_H */

@@ -1,0 +1,611 @@
+// lbmd_api.cu -- the C ABI (include/lbmd.h): context, device memory, argument checks and the
+// launch sequence of one coupled step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbmd_internal.cuh"
+
+using namespace lbmd;
+
+struct lbmd_ctx {
+  lbmd_params prm{};
+  cudaStream_t st = nullptr;
+  int dev = 0;
+  StepParams P{};
+  float *pop[2] = {nullptr, nullptr};
+  int cur = 0;
+  float *rho = nullptr;  // [2][N]
+  float *jp = nullptr;   // [3][N]
+  // particles
+  int np = 0, cap = 0;
+  ParticleArrays pa[2]{};
+  int pcur = 0;
+  ParticleForces pf{};
+  int *slot_of_id = nullptr;
+  int *row_of = nullptr, *row_count = nullptr, *row_start = nullptr, *row_cursor = nullptr, *perm = nullptr;
+  int *bond_start = nullptr, *bond_other = nullptr;
+  int nbonds = 0;
+  unsigned *err = nullptr;
+  double *diag_partial = nullptr, *diag_out = nullptr;
+  int diag_blocks = 0;
+  int64_t steps = 0, launches = 0;
+  bool fluid_ready = false, types_set = false;
+  unsigned sticky = 0;
+  std::string msg;
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;  // pairs (start, stop)
+  size_t ev_used = 0;
+  double prof_ms = 0.0;
+  int64_t prof_launches = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(lbmd_ctx *c, int code, const std::string &m) {
+  if (c)
+    c->msg = m;
+  else
+    g_create_error = m;
+  return code;
+}
+
+int cuda_fail(lbmd_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, LBMD_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                          \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return cudaSuccess;
+  return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+template <class T>
+void dfree(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+int launched(lbmd_ctx *c, const char *where, int n = 1) {
+  c->launches += n;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  return LBMD_OK;
+}
+
+int map_device_error(lbmd_ctx *c, unsigned bits) {
+  if (bits & kErrNonFinite) return fail(c, LBMD_E_NONFINITE, "non-finite density or particle state");
+  if (bits & kErrNegDensity) return fail(c, LBMD_E_NEGATIVE_DENSITY, "negative fluid density");
+  if (bits & kErrBond) return fail(c, LBMD_E_BOND_BROKEN, "FENE bond stretched to or beyond R0");
+  if (bits & kErrParticle) return fail(c, LBMD_E_NONFINITE, "particle position out of range");
+  return LBMD_OK;
+}
+
+int sync_and_check(lbmd_ctx *c) {
+  CK(cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
+  unsigned bits = 0;
+  CK(cudaMemcpy(&bits, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read error word");
+  c->sticky |= bits;
+  return map_device_error(c, c->sticky);
+}
+
+void free_particles(lbmd_ctx *c) {
+  for (int b = 0; b < 2; ++b) {
+    dfree(c->pa[b].cell);
+    dfree(c->pa[b].frac);
+    dfree(c->pa[b].vel);
+    dfree(c->pa[b].pid);
+  }
+  dfree(c->pf.fric); dfree(c->pf.psA); dfree(c->pf.psB); dfree(c->pf.fsr); dfree(c->pf.pair); dfree(c->pf.total);
+  dfree(c->slot_of_id); dfree(c->row_of); dfree(c->perm);
+  c->cap = 0;
+}
+
+int sort_particles(lbmd_ctx *c) {
+  const StepParams &P = c->P;
+  CK(cudaMemsetAsync(c->row_count, 0, sizeof(int) * (P.nrows + 1), c->st), "memset rows");
+  launch_bin(P, c->pa[c->pcur], c->row_of, c->row_count, c->err, c->st);
+  launch_scan_rows(P.nrows, c->row_count, c->row_start, c->row_cursor, c->st);
+  launch_scatter(P.np, c->row_of, c->row_cursor, c->perm, c->st);
+  launch_row_sort(P, c->row_start, c->pa[c->pcur], c->perm, c->st);
+  launch_permute(P.np, c->perm, c->pa[c->pcur], c->pa[1 - c->pcur], c->slot_of_id, c->st);
+  c->pcur = 1 - c->pcur;
+  return launched(c, "particle sort", 6);
+}
+
+double max_range(const lbmd_ctx *c) {
+  double r = 0.0;
+  for (int i = 0; i < c->P.ntypes; ++i)
+    for (int j = 0; j < c->P.ntypes; ++j) {
+      const PairParams &pp = c->P.pairs[i * LBMD_MAX_TYPES + j];
+      if (pp.eps > 0.f) r = std::fmax(r, std::sqrt((double)pp.rc2));
+    }
+  if (c->P.dh_lB != 0.f) r = std::fmax(r, std::sqrt((double)c->P.dh_rc2));
+  return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbmd_last_error(const lbmd_ctx *c) { return c ? c->msg.c_str() : g_create_error.c_str(); }
+
+int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *warnings) {
+  lbmd_ctx *c = nullptr;
+  if (!prm || !out) return fail(c, LBMD_E_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (warnings) *warnings = 0;
+  if (prm->nx < 1 || prm->ny < 1 || prm->nz < 1) return fail(c, LBMD_E_INVALID_ARG, "lattice sizes must be >= 1");
+  if ((double)prm->nx * prm->ny * prm->nz > 4.0e9 / 38.0 * 16.0)
+    return fail(c, LBMD_E_INVALID_ARG, "lattice too large");
+  if (!(prm->tau_r > 0.5)) return fail(c, LBMD_E_INVALID_ARG, "tau_r must exceed 1/2");
+  if (prm->dt != 1.0) return fail(c, LBMD_E_INVALID_ARG, "dt must equal the lattice time step 1");
+  if (!(prm->kT >= 0.0)) return fail(c, LBMD_E_INVALID_ARG, "kT must be >= 0");
+  if (prm->storage != LBMD_STORAGE_FP32) {
+    if (prm->storage == LBMD_STORAGE_FP16_SHIFTED || prm->storage == LBMD_STORAGE_BF16_SHIFTED)
+      return fail(c, LBMD_E_UNIMPLEMENTED, "16-bit population storage is not implemented");
+    return fail(c, LBMD_E_INVALID_ARG, "unknown storage");
+  }
+  c = new lbmd_ctx();
+  c->prm = *prm;
+  c->st = (cudaStream_t)stream;
+  cudaGetDevice(&c->dev);
+  StepParams &P = c->P;
+  P.nx = prm->nx; P.ny = prm->ny; P.nz = prm->nz;
+  P.nrows = prm->ny * prm->nz;
+  P.N = (long long)prm->nx * prm->ny * prm->nz;
+  P.inv_tau = (float)(1.0 / prm->tau_r);
+  P.force_pref = (float)(1.0 - 0.5 / prm->tau_r);
+  P.gAB = (float)prm->g_AB; P.gBA = (float)prm->g_BA;
+  P.dt = (float)prm->dt;
+  P.seed = prm->seed;
+  P.ntypes = 0;
+  P.bond_kind = LBMD_BOND_FENE;
+  cudaError_t e = cudaSuccess;
+  const size_t npop = (size_t)2 * kQ * P.N;
+  if ((e = dalloc(&c->pop[0], npop)) != cudaSuccess || (e = dalloc(&c->pop[1], npop)) != cudaSuccess ||
+      (e = dalloc(&c->rho, (size_t)2 * P.N)) != cudaSuccess || (e = dalloc(&c->jp, (size_t)3 * P.N)) != cudaSuccess ||
+      (e = dalloc(&c->err, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    lbmd_destroy(c);
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? LBMD_E_NOMEM : LBMD_E_CUDA,
+                std::string("device allocation: ") + cudaGetErrorString(e));
+  }
+  c->diag_blocks = fluid_sum_blocks(P);
+  if ((e = dalloc(&c->diag_partial, (size_t)5 * c->diag_blocks)) != cudaSuccess ||
+      (e = dalloc(&c->diag_out, 8)) != cudaSuccess ||
+      (e = cudaMemset(c->err, 0, sizeof(unsigned))) != cudaSuccess) {
+    cudaGetLastError();
+    lbmd_destroy(c);
+    return fail(nullptr, LBMD_E_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
+  }
+  unsigned w = 0;
+  if (1.0 / 3.0 * (prm->tau_r - 0.5) < 1e-3) w |= LBMD_WARN_VISCOSITY;
+  if (prm->g_AB != prm->g_BA) w |= LBMD_WARN_ASYMMETRIC_G;
+  const double r0 = prm->rho0_A + prm->rho0_B;
+  if (prm->kT > 0.0 && r0 > 0.0 && std::sqrt(prm->kT / (r0 / 3.0)) > 0.5) w |= LBMD_WARN_BOLTZMANN;
+  if (warnings) *warnings = w;
+  *out = c;
+  return LBMD_OK;
+}
+
+void lbmd_destroy(lbmd_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->dev);
+  if (c->st) cudaStreamSynchronize(c->st);
+  dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho); dfree(c->jp); dfree(c->err);
+  dfree(c->diag_partial); dfree(c->diag_out);
+  free_particles(c);
+  dfree(c->row_count); dfree(c->row_start); dfree(c->row_cursor);
+  dfree(c->bond_start); dfree(c->bond_other);
+  for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
+  delete c;
+}
+
+int lbmd_set_types(lbmd_ctx *c, int ntypes, const lbmd_ptype *types, int npairs, const lbmd_pair *pairs,
+                   unsigned *warnings) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  if (warnings) *warnings = 0;
+  if (ntypes < 1 || ntypes > LBMD_MAX_TYPES || !types || npairs < 0 || (npairs > 0 && !pairs))
+    return fail(c, LBMD_E_INVALID_ARG, "bad type table");
+  StepParams &P = c->P;
+  unsigned w = 0;
+  for (int t = 0; t < ntypes; ++t) {
+    const lbmd_ptype &T = types[t];
+    if (!(T.mass > 0.0) || !(T.gamma >= 0.0)) return fail(c, LBMD_E_INVALID_ARG, "mass must be > 0, gamma >= 0");
+    TypeParams &D = P.types[t];
+    D.kappa[0] = (float)T.kappa_A; D.kappa[1] = (float)T.kappa_B;
+    D.lam[0] = (float)T.lambda_A; D.lam[1] = (float)T.lambda_B;
+    D.gamma = (float)T.gamma;
+    D.inv_mass = (float)(1.0 / T.mass);
+    D.mass = (float)T.mass;
+    D.noise_amp = (float)std::sqrt(2.0 * c->prm.kT * T.gamma / c->prm.dt);
+    if (T.gamma * c->prm.dt / T.mass > 0.5) w |= LBMD_WARN_GAMMA_DT;
+  }
+  for (int i = 0; i < LBMD_MAX_TYPES * LBMD_MAX_TYPES; ++i) P.pairs[i] = PairParams{0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < npairs; ++k) {
+    const lbmd_pair &pp = pairs[k];
+    if (pp.type_i < 0 || pp.type_i >= ntypes || pp.type_j < 0 || pp.type_j >= ntypes || pp.wca_eps < 0 ||
+        !(pp.wca_sigma > 0))
+      return fail(c, LBMD_E_INVALID_ARG, "bad pair entry");
+    const double rc = std::pow(2.0, 1.0 / 6.0) * pp.wca_sigma;
+    if (2.0 * rc >= std::min(P.nx, std::min(P.ny, P.nz)))
+      return fail(c, LBMD_E_INVALID_ARG, "WCA range must be below half the smallest box edge");
+    PairParams d{(float)pp.wca_eps, (float)(pp.wca_sigma * pp.wca_sigma), (float)(rc * rc), 0.f};
+    P.pairs[pp.type_i * LBMD_MAX_TYPES + pp.type_j] = d;
+    P.pairs[pp.type_j * LBMD_MAX_TYPES + pp.type_i] = d;
+  }
+  P.ntypes = ntypes;
+  P.reach = (int)std::ceil(max_range(c));
+  c->types_set = true;
+  if (warnings) *warnings = w;
+  return LBMD_OK;
+}
+
+int lbmd_set_debye_hueckel(lbmd_ctx *c, double lB, double kappa_D, double rc) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  if (lB != 0.0) {
+    if (!(rc > 0.0) || !(kappa_D >= 0.0)) return fail(c, LBMD_E_INVALID_ARG, "bad Debye-Hueckel parameters");
+    if (2.0 * rc >= std::min(c->P.nx, std::min(c->P.ny, c->P.nz)))
+      return fail(c, LBMD_E_INVALID_ARG, "cut-off must be below half the smallest box edge");
+  }
+  c->P.dh_lB = (float)lB;
+  c->P.dh_kappa = (float)kappa_D;
+  c->P.dh_rc2 = (float)(rc * rc);
+  c->P.reach = (int)std::ceil(max_range(c));
+  return LBMD_OK;
+}
+
+int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const float *u) {
+  if (!c || !rhoA || !rhoB) return c ? fail(c, LBMD_E_INVALID_ARG, "null density") : LBMD_E_INVALID_ARG;
+  cudaSetDevice(c->dev);
+  const long long N = c->P.N;
+  for (long long s = 0; s < N; ++s)
+    if (!(rhoA[s] > 0.f) || !(rhoB[s] > 0.f) || !std::isfinite(rhoA[s]) || !std::isfinite(rhoB[s]))
+      return fail(c, LBMD_E_INVALID_ARG, "densities must be finite and > 0");
+  // stage through the (not yet used) second population buffer
+  float *stage = c->pop[1 - c->cur];
+  const size_t bytes = sizeof(float) * (size_t)N;
+  CK(cudaMemcpyAsync(stage, rhoA, bytes, cudaMemcpyHostToDevice, c->st), "upload rhoA");
+  CK(cudaMemcpyAsync(stage + N, rhoB, bytes, cudaMemcpyHostToDevice, c->st), "upload rhoB");
+  const float *du = nullptr;
+  if (u) {
+    CK(cudaMemcpyAsync(stage + 2 * N, u, 3 * bytes, cudaMemcpyHostToDevice, c->st), "upload u");
+    du = stage + 2 * N;
+  }
+  launch_init_equilibrium(c->P, stage, stage + N, du, c->pop[c->cur], c->st);
+  int r = launched(c, "init_equilibrium");
+  if (r) return r;
+  CK(cudaStreamSynchronize(c->st), "sync");
+  c->fluid_ready = true;
+  c->steps = 0;
+  return LBMD_OK;
+}
+
+int lbmd_set_populations(lbmd_ctx *c, int comp, const float *f) {
+  if (!c || !f || comp < 0 || comp > 1) return c ? fail(c, LBMD_E_INVALID_ARG, "bad arguments") : LBMD_E_INVALID_ARG;
+  cudaSetDevice(c->dev);
+  float *stage = c->pop[1 - c->cur];
+  CK(cudaMemcpyAsync(stage, f, sizeof(float) * kQ * (size_t)c->P.N, cudaMemcpyHostToDevice, c->st), "upload f");
+  launch_restream(c->P, stage, comp, c->pop[c->cur], c->st);
+  int r = launched(c, "restream");
+  if (r) return r;
+  CK(cudaStreamSynchronize(c->st), "sync");
+  c->fluid_ready = true;
+  return LBMD_OK;
+}
+
+int lbmd_get_populations(lbmd_ctx *c, int comp, float *f) {
+  if (!c || !f || comp < 0 || comp > 1) return c ? fail(c, LBMD_E_INVALID_ARG, "bad arguments") : LBMD_E_INVALID_ARG;
+  if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
+  cudaSetDevice(c->dev);
+  float *stage = c->pop[1 - c->cur];
+  launch_unstream(c->P, c->pop[c->cur], comp, stage, c->st);
+  int r = launched(c, "unstream");
+  if (r) return r;
+  CK(cudaMemcpyAsync(f, stage, sizeof(float) * kQ * (size_t)c->P.N, cudaMemcpyDeviceToHost, c->st), "download f");
+  return sync_and_check(c);
+}
+
+int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, const int *type, const double *q) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!x || !v || !type))) return fail(c, LBMD_E_INVALID_ARG, "bad particle arrays");
+  if (n > 0 && !c->types_set) return fail(c, LBMD_E_STATE, "set the particle types first");
+  cudaSetDevice(c->dev);
+  StepParams &P = c->P;
+  const int L[3] = {P.nx, P.ny, P.nz};
+  std::vector<int4> hc(n);
+  std::vector<float4> hf(n), hv(n);
+  std::vector<int> hid(n);
+  for (int p = 0; p < n; ++p) {
+    if (type[p] < 0 || type[p] >= P.ntypes) return fail(c, LBMD_E_INVALID_ARG, "particle type out of range");
+    int ci[3];
+    float fr[3];
+    for (int a = 0; a < 3; ++a) {
+      const double xa = x[3 * p + a];
+      if (!std::isfinite(xa) || !std::isfinite(v[3 * p + a])) return fail(c, LBMD_E_INVALID_ARG, "non-finite particle");
+      double w = xa - L[a] * std::floor(xa / L[a]);
+      if (w >= L[a]) w = 0.0;
+      int cell = (int)std::floor(w);
+      float f = (float)(w - cell);
+      if (f >= 1.f) {
+        f = 0.f;
+        cell = (cell + 1) % L[a];
+      }
+      ci[a] = cell;
+      fr[a] = f;
+    }
+    hc[p] = make_int4(ci[0], ci[1], ci[2], type[p]);
+    hf[p] = make_float4(fr[0], fr[1], fr[2], q ? (float)q[p] : 0.f);
+    hv[p] = make_float4((float)v[3 * p], (float)v[3 * p + 1], (float)v[3 * p + 2], 0.f);
+    hid[p] = p;
+  }
+  if (n > c->cap) {
+    free_particles(c);
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      if ((e = dalloc(&c->pa[b].cell, n)) != cudaSuccess) break;
+      if ((e = dalloc(&c->pa[b].frac, n)) != cudaSuccess) break;
+      if ((e = dalloc(&c->pa[b].vel, n)) != cudaSuccess) break;
+      e = dalloc(&c->pa[b].pid, n);
+    }
+    if (e == cudaSuccess) e = dalloc(&c->pf.fric, n);
+    if (e == cudaSuccess) e = dalloc(&c->pf.psA, n);
+    if (e == cudaSuccess) e = dalloc(&c->pf.psB, n);
+    if (e == cudaSuccess) e = dalloc(&c->pf.fsr, n);
+    if (e == cudaSuccess) e = dalloc(&c->pf.pair, n);
+    if (e == cudaSuccess) e = dalloc(&c->pf.total, n);
+    if (e == cudaSuccess) e = dalloc(&c->slot_of_id, n);
+    if (e == cudaSuccess) e = dalloc(&c->row_of, n);
+    if (e == cudaSuccess) e = dalloc(&c->perm, n);
+    if (e == cudaSuccess && !c->row_count) e = dalloc(&c->row_count, (size_t)P.nrows + 1);
+    if (e == cudaSuccess && !c->row_start) e = dalloc(&c->row_start, (size_t)P.nrows + 1);
+    if (e == cudaSuccess && !c->row_cursor) e = dalloc(&c->row_cursor, (size_t)P.nrows + 1);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_particles(c);
+      c->np = 0;
+      P.np = 0;
+      return fail(c, LBMD_E_NOMEM, std::string("particle allocation: ") + cudaGetErrorString(e));
+    }
+    c->cap = n;
+  }
+  if (!c->row_count) {  // rows are needed by the lattice kernels' gather even without particles
+    CK(dalloc(&c->row_count, (size_t)P.nrows + 1), "alloc rows");
+    CK(dalloc(&c->row_start, (size_t)P.nrows + 1), "alloc rows");
+    CK(dalloc(&c->row_cursor, (size_t)P.nrows + 1), "alloc rows");
+  }
+  c->np = n;
+  P.np = n;
+  c->pcur = 0;
+  if (n > 0) {
+    CK(cudaMemcpyAsync(c->pa[0].cell, hc.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, c->st), "upload");
+    CK(cudaMemcpyAsync(c->pa[0].frac, hf.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, c->st), "upload");
+    CK(cudaMemcpyAsync(c->pa[0].vel, hv.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, c->st), "upload");
+    CK(cudaMemcpyAsync(c->pa[0].pid, hid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st), "upload");
+    CK(cudaMemsetAsync(c->pf.total, 0, sizeof(float4) * n, c->st), "memset");
+    int r = sort_particles(c);
+    if (r) return r;
+  }
+  CK(cudaStreamSynchronize(c->st), "sync");
+  return LBMD_OK;
+}
+
+int lbmd_set_bonds(lbmd_ctx *c, int nb, const int *pairs, int kind, double k, double r) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  if (nb < 0 || (nb > 0 && !pairs)) return fail(c, LBMD_E_INVALID_ARG, "bad bond list");
+  if (kind != LBMD_BOND_FENE && kind != LBMD_BOND_HARMONIC) return fail(c, LBMD_E_INVALID_ARG, "unknown bond kind");
+  if (nb > 0 && (!(k >= 0.0) || !(r > 0.0 || kind == LBMD_BOND_HARMONIC)))
+    return fail(c, LBMD_E_INVALID_ARG, "bad bond parameters");
+  cudaSetDevice(c->dev);
+  dfree(c->bond_start);
+  dfree(c->bond_other);
+  c->nbonds = 0;
+  if (nb == 0) return LBMD_OK;
+  const int n = c->np;
+  std::vector<int> deg(n + 1, 0), other(2 * (size_t)nb);
+  for (int b = 0; b < nb; ++b) {
+    const int i = pairs[2 * b], j = pairs[2 * b + 1];
+    if (i < 0 || i >= n || j < 0 || j >= n || i == j) return fail(c, LBMD_E_INVALID_ARG, "bond index out of range");
+    deg[i + 1]++;
+    deg[j + 1]++;
+  }
+  for (int i = 0; i < n; ++i) deg[i + 1] += deg[i];
+  std::vector<int> fill(deg.begin(), deg.end() - 1);
+  for (int b = 0; b < nb; ++b) {
+    const int i = pairs[2 * b], j = pairs[2 * b + 1];
+    other[fill[i]++] = j;
+    other[fill[j]++] = i;
+  }
+  CK(dalloc(&c->bond_start, (size_t)n + 1), "alloc bonds");
+  CK(dalloc(&c->bond_other, 2 * (size_t)nb), "alloc bonds");
+  CK(cudaMemcpy(c->bond_start, deg.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice), "upload bonds");
+  CK(cudaMemcpy(c->bond_other, other.data(), sizeof(int) * 2 * nb, cudaMemcpyHostToDevice), "upload bonds");
+  c->nbonds = nb;
+  c->P.bond_kind = kind;
+  c->P.bond_k = (float)k;
+  c->P.bond_r = (float)r;
+  return LBMD_OK;
+}
+
+int lbmd_step(lbmd_ctx *c, int nsteps) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  if (nsteps < 0) return fail(c, LBMD_E_INVALID_ARG, "nsteps < 0");
+  if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
+  cudaSetDevice(c->dev);
+  StepParams &P = c->P;
+  P.np = c->np;
+  const CellIndex ci{c->row_start};
+  for (int s = 0; s < nsteps; ++s) {
+    P.step = (unsigned long long)c->steps;
+    const float *fin = c->pop[c->cur];
+    float *fout = c->pop[1 - c->cur];
+    int r;
+    if (P.np > 0 && (r = sort_particles(c))) return r;
+    launch_moments(P, fin, c->rho, P.np > 0 ? c->jp : nullptr, c->st);
+    if ((r = launched(c, "moments"))) return r;
+    if (P.np > 0) {
+      launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
+      launch_pairs(P, c->pa[c->pcur], ci, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf,
+                   c->err, c->st);
+      if ((r = launched(c, "particle forces", 2))) return r;
+    }
+    if (c->prof) {
+      if (c->ev_used + 2 > c->ev.size()) {
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a), "event");
+        CK(cudaEventCreate(&b), "event");
+        c->ev.push_back(a);
+        c->ev.push_back(b);
+      }
+      CK(cudaEventRecord(c->ev[c->ev_used], c->st), "event");
+    }
+    launch_collide(P, fin, fout, c->rho, c->pa[c->pcur], c->pf, ci, c->err, c->st);
+    if ((r = launched(c, "collide"))) return r;
+    if (c->prof) {
+      CK(cudaEventRecord(c->ev[c->ev_used + 1], c->st), "event");
+      c->ev_used += 2;
+    }
+    if (P.np > 0) {
+      launch_integrate(P, c->pa[c->pcur], c->pf, c->err, c->st);
+      if ((r = launched(c, "integrate"))) return r;
+    }
+    c->cur = 1 - c->cur;
+    c->steps++;
+  }
+  return LBMD_OK;
+}
+
+int lbmd_sync(lbmd_ctx *c) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  cudaSetDevice(c->dev);
+  return sync_and_check(c);
+}
+
+int lbmd_clear_error(lbmd_ctx *c) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  cudaSetDevice(c->dev);
+  CK(cudaStreamSynchronize(c->st), "sync");
+  CK(cudaMemset(c->err, 0, sizeof(unsigned)), "clear error word");
+  c->sticky = 0;
+  c->msg.clear();
+  return LBMD_OK;
+}
+
+int lbmd_get_fields(lbmd_ctx *c, float *rhoA, float *rhoB, float *u) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
+  cudaSetDevice(c->dev);
+  const long long N = c->P.N;
+  float *stage = c->pop[1 - c->cur];
+  launch_moments(c->P, c->pop[c->cur], c->rho, nullptr, c->st);
+  launch_fields(c->P, c->pop[c->cur], c->rho, stage, stage + N, stage + 2 * N, c->st);
+  int r = launched(c, "fields", 2);
+  if (r) return r;
+  const size_t bytes = sizeof(float) * (size_t)N;
+  if (rhoA) CK(cudaMemcpyAsync(rhoA, stage, bytes, cudaMemcpyDeviceToHost, c->st), "download");
+  if (rhoB) CK(cudaMemcpyAsync(rhoB, stage + N, bytes, cudaMemcpyDeviceToHost, c->st), "download");
+  if (u) CK(cudaMemcpyAsync(u, stage + 2 * N, 3 * bytes, cudaMemcpyDeviceToHost, c->st), "download");
+  return sync_and_check(c);
+}
+
+int lbmd_get_particles(lbmd_ctx *c, double *x, double *v, double *f) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  cudaSetDevice(c->dev);
+  const int n = c->np;
+  if (n == 0) return sync_and_check(c);
+  std::vector<int4> hc(n);
+  std::vector<float4> hf(n), hv(n), ht(n);
+  std::vector<int> hid(n);
+  const ParticleArrays &pa = c->pa[c->pcur];
+  CK(cudaMemcpyAsync(hc.data(), pa.cell, sizeof(int4) * n, cudaMemcpyDeviceToHost, c->st), "download");
+  CK(cudaMemcpyAsync(hf.data(), pa.frac, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->st), "download");
+  CK(cudaMemcpyAsync(hv.data(), pa.vel, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->st), "download");
+  CK(cudaMemcpyAsync(ht.data(), c->pf.total, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->st), "download");
+  CK(cudaMemcpyAsync(hid.data(), pa.pid, sizeof(int) * n, cudaMemcpyDeviceToHost, c->st), "download");
+  int r = sync_and_check(c);
+  for (int j = 0; j < n; ++j) {
+    const int id = hid[j];
+    if (id < 0 || id >= n) return fail(c, LBMD_E_CUDA, "corrupt particle ids");
+    if (x) {
+      x[3 * id] = hc[j].x + (double)hf[j].x;
+      x[3 * id + 1] = hc[j].y + (double)hf[j].y;
+      x[3 * id + 2] = hc[j].z + (double)hf[j].z;
+    }
+    if (v) {
+      v[3 * id] = hv[j].x; v[3 * id + 1] = hv[j].y; v[3 * id + 2] = hv[j].z;
+    }
+    if (f) {
+      f[3 * id] = ht[j].x; f[3 * id + 1] = ht[j].y; f[3 * id + 2] = ht[j].z;
+    }
+  }
+  return r;
+}
+
+int lbmd_diagnostics(lbmd_ctx *c, double out[8]) {
+  if (!c || !out) return c ? fail(c, LBMD_E_INVALID_ARG, "null output") : LBMD_E_INVALID_ARG;
+  if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
+  cudaSetDevice(c->dev);
+  launch_fluid_sums(c->P, c->pop[c->cur], c->diag_partial, c->diag_blocks, c->st);
+  launch_finish_sums(c->diag_partial, c->diag_blocks, 5, c->diag_out, c->st);
+  int r = launched(c, "fluid sums", 2);
+  if (r) return r;
+  double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (c->np > 0) {
+    StepParams P = c->P;
+    P.np = c->np;
+    const int nb = std::min(c->diag_blocks, (c->np + 255) / 256);
+    launch_particle_momentum(P, c->pa[c->pcur], c->diag_partial + (size_t)5 * c->diag_blocks - 3 * (size_t)nb, nb,
+                             c->st);
+    launch_finish_sums(c->diag_partial + (size_t)5 * c->diag_blocks - 3 * (size_t)nb, nb, 3, c->diag_out + 5, c->st);
+    if ((r = launched(c, "particle momentum", 2))) return r;
+    CK(cudaMemcpyAsync(h, c->diag_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->st), "download");
+  } else {
+    CK(cudaMemcpyAsync(h, c->diag_out, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->st), "download");
+  }
+  r = sync_and_check(c);
+  std::memcpy(out, h, sizeof(h));
+  return r;
+}
+
+int64_t lbmd_step_count(const lbmd_ctx *c) { return c ? c->steps : -1; }
+int64_t lbmd_launch_count(const lbmd_ctx *c) { return c ? c->launches : -1; }
+
+int lbmd_profile_enable(lbmd_ctx *c, int on) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  c->prof = on != 0;
+  return LBMD_OK;
+}
+
+int lbmd_profile_read(lbmd_ctx *c, double *ms, int64_t *nl, int reset) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  cudaSetDevice(c->dev);
+  CK(cudaStreamSynchronize(c->st), "sync");
+  for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]), "event time");
+    c->prof_ms += t;
+    c->prof_launches++;
+  }
+  c->ev_used = 0;
+  if (ms) *ms = c->prof_ms;
+  if (nl) *nl = c->prof_launches;
+  if (reset) {
+    c->prof_ms = 0.0;
+    c->prof_launches = 0;
+  }
+  return LBMD_OK;
+}
+
+}  // extern "C"

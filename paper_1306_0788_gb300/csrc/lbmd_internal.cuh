@@ -1,0 +1,227 @@
+// lbmd_internal.cuh -- device-side types, lattice constants and helpers shared by the
+// sm_103a kernels of the coupled Shan-Chen LB / MD step.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbmd.h"
+
+namespace lbmd {
+
+constexpr int kQ = 19;
+
+// D3Q19 velocities (Eq. velo) in the ABI order: rest; +x,-x,+y,-y,+z,-z; then the xy, xz, yz
+// face diagonals with opposite directions adjacent.
+__device__ constexpr int kCx[kQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+__device__ constexpr int kCy[kQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+__device__ constexpr int kCz[kQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+// Weights (Eq. weights): 1/3, 1/18 (axis), 1/36 (diagonal).
+__device__ constexpr float kW[kQ] = {1.f / 3.f,  1.f / 18.f, 1.f / 18.f, 1.f / 18.f, 1.f / 18.f,
+                                     1.f / 18.f, 1.f / 18.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f,
+                                     1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f,
+                                     1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
+constexpr float kCs2 = 1.f / 3.f;
+
+// device error word bits
+constexpr unsigned kErrNegDensity = 1u << 0;
+constexpr unsigned kErrNonFinite = 1u << 1;
+constexpr unsigned kErrBond = 1u << 2;
+constexpr unsigned kErrParticle = 1u << 3;
+
+struct TypeParams {
+  float kappa[2];   // Eq. (solvation_kappa)
+  float lam[2];     // Eq. (solvation_lambda)
+  float gamma;      // Eq. (NEWTON)
+  float inv_mass;
+  float noise_amp;  // sqrt(2 kT gamma / dt)
+  float mass;
+};
+
+struct PairParams {
+  float eps, sigma2, rc2, pad;  // WCA: epsilon, sigma^2, (2^(1/6) sigma)^2; eps = 0 -> none
+};
+
+// Everything a step needs, passed by value to every kernel.
+struct StepParams {
+  int nx, ny, nz;
+  int nrows;             // ny * nz
+  long long N;           // nx * ny * nz
+  float inv_tau;         // 1 / tau_r
+  float force_pref;      // 1 - 1/(2 tau_r)  (the (2 + lambda)/2 factor of the forcing term)
+  float gAB, gBA;
+  float dt;
+  int np, ntypes;
+  float dh_lB, dh_kappa, dh_rc2;
+  int bond_kind;
+  float bond_k, bond_r;
+  int reach;             // cells to scan for pair forces: ceil(max interaction range)
+  unsigned long long seed, step;
+  TypeParams types[LBMD_MAX_TYPES];
+  PairParams pairs[LBMD_MAX_TYPES * LBMD_MAX_TYPES];
+};
+
+// Particle state in sorted order (by lattice row (z, y), then x cell, then id).
+struct ParticleArrays {
+  int4 *cell;    // cx, cy, cz, type
+  float4 *frac;  // fractional position in the cell (x, y, z) and charge q (w)
+  float4 *vel;   // vx, vy, vz, 0
+  int *pid;      // caller's particle index
+};
+
+// Per-particle forces of the current step (sorted order).
+struct ParticleForces {
+  float4 *fric;   // friction + noise (Eq. NEWTON)
+  float4 *psA;    // -kappa_A grad rho_A
+  float4 *psB;    // -kappa_B grad rho_B
+  float4 *fsr;    // reaction of the fluid-side solvation force (minus what the particle exerts)
+  float4 *pair;   // WCA + screened Coulomb + bonds
+  float4 *total;  // sum, written by the integrator
+};
+
+struct CellIndex {
+  const int *row_start;  // [nrows + 1] offsets into the sorted particle arrays
+};
+
+__host__ __device__ __forceinline__ int wrapi(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ long long site_index(const StepParams &P, int x, int y, int z) {
+  return ((long long)z * P.ny + y) * P.nx + x;
+}
+
+// Geometric factor of Eq. (solvation_lambda): sum over the 18 neighbours of
+// Theta[d_hat . c_hat] c / |c|^2 with Theta(x) = 1 for 0 < x < 1, tested exactly as
+// d.c > 0 and d not parallel to c (d.c_hat = |d| iff parallel).
+__device__ __forceinline__ float3 fs_geometry(float dx, float dy, float dz) {
+  float3 s = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const float c2 = (float)(kCx[i] * kCx[i] + kCy[i] * kCy[i] + kCz[i] * kCz[i]);
+    const float dc = dx * kCx[i] + dy * kCy[i] + dz * kCz[i];
+    const float crx = dy * kCz[i] - dz * kCy[i];
+    const float cry = dz * kCx[i] - dx * kCz[i];
+    const float crz = dx * kCy[i] - dy * kCx[i];
+    const bool parallel = (crx == 0.f) && (cry == 0.f) && (crz == 0.f);
+    if (dc > 0.f && !parallel) {
+      const float inv = 1.f / c2;
+      s.x += kCx[i] * inv;
+      s.y += kCy[i] * inv;
+      s.z += kCz[i] * inv;
+    }
+  }
+  return s;
+}
+
+// Fluid-side solvation force (Eq. solvation_lambda) and momentum return (Sec. 2) gathered at
+// node (x, y, z) from the particles of the 8 unit cells having that node as a corner.
+__device__ __forceinline__ void gather_coupling(const StepParams &P, int x, int y, int z, float rA, float rB,
+                                                const ParticleArrays &pa, const ParticleForces &pf,
+                                                CellIndex ci, bool with_momentum, float3 &gA, float3 &gB) {
+  const float rinv = 1.f / (rA + rB);
+  const float sA = rA * rinv, sB = rB * rinv;
+#pragma unroll
+  for (int oz = 0; oz < 2; ++oz) {
+    const int cz = oz ? (z == 0 ? P.nz - 1 : z - 1) : z;
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) {
+      const int cy = oy ? (y == 0 ? P.ny - 1 : y - 1) : y;
+      const int row = cz * P.ny + cy;
+      const int q0 = __ldg(ci.row_start + row), q1 = __ldg(ci.row_start + row + 1);
+      for (int q = q0; q < q1; ++q) {
+        const int4 c = __ldg(pa.cell + q);
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox) {
+          const int cx = ox ? (x == 0 ? P.nx - 1 : x - 1) : x;
+          if (c.x != cx) continue;
+          const float4 fr = __ldg(pa.frac + q);
+          const TypeParams &T = P.types[c.w];
+          const float dx = fr.x - ox, dy = fr.y - oy, dz = fr.z - oz;
+          if (T.lam[0] != 0.f || T.lam[1] != 0.f) {
+            const float3 geo = fs_geometry(dx, dy, dz);
+            const float a = -T.lam[0] * rA, b = -T.lam[1] * rB;
+            gA.x += a * geo.x; gA.y += a * geo.y; gA.z += a * geo.z;
+            gB.x += b * geo.x; gB.y += b * geo.y; gB.z += b * geo.z;
+          }
+          if (with_momentum) {
+            const float w = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
+            const float4 ff = __ldg(pf.fric + q), pA = __ldg(pf.psA + q), pB = __ldg(pf.psB + q);
+            gA.x += w * (-sA * ff.x - pA.x); gA.y += w * (-sA * ff.y - pA.y); gA.z += w * (-sA * ff.z - pA.z);
+            gB.x += w * (-sB * ff.x - pB.x); gB.y += w * (-sB * ff.y - pB.y); gB.z += w * (-sB * ff.z - pB.z);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): multipliers 0xD2511F53, 0xCD9E8D57,
+// Weyl key increments 0x9E3779B9, 0xBB67AE85, ten rounds.
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = 0xD2511F53ull * c.x;
+    const unsigned long long p1 = 0xCD9E8D57ull * c.z;
+    const unsigned hi0 = (unsigned)(p0 >> 32), lo0 = (unsigned)p0;
+    const unsigned hi1 = (unsigned)(p1 >> 32), lo1 = (unsigned)p1;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Three standard normals for (seed, step, particle id): counter (id, step lo, step hi,
+// 0x4c42), key (seed lo, seed hi); uniforms from the top 24 bits; Box-Muller.
+__device__ __forceinline__ float3 particle_normals(unsigned long long seed, unsigned long long step,
+                                                   unsigned id) {
+  const uint4 r = philox4x32_10(make_uint4(id, (unsigned)step, (unsigned)(step >> 32), 0x4c42u),
+                                make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+  const float s = 1.f / 16777216.f;
+  const float u0 = ((float)(r.x >> 8) + 0.5f) * s, u1 = ((float)(r.y >> 8) + 0.5f) * s;
+  const float u2 = ((float)(r.z >> 8) + 0.5f) * s, u3 = ((float)(r.w >> 8) + 0.5f) * s;
+  const float a = sqrtf(-2.f * logf(u0)), b = sqrtf(-2.f * logf(u2));
+  float s1, c1, s3, c3;
+  sincospif(2.f * u1, &s1, &c1);
+  sincospif(2.f * u3, &s3, &c3);
+  return make_float3(a * c1, a * s1, b * c3);
+}
+
+// ------------------------------------------------------------------ launch wrappers
+// lattice (lb_fluid.cu)
+void launch_init_equilibrium(const StepParams &P, const float *rhoA, const float *rhoB, const float *u,
+                             float *store, cudaStream_t st);
+void launch_restream(const StepParams &P, const float *post, int comp, float *store, cudaStream_t st);
+void launch_unstream(const StepParams &P, const float *store, int comp, float *post, cudaStream_t st);
+void launch_moments(const StepParams &P, const float *store, float *rho, float *jp, cudaStream_t st);
+void launch_collide(const StepParams &P, const float *fin, float *fout, const float *rho,
+                    const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci, unsigned *err,
+                    cudaStream_t st);
+void launch_fields(const StepParams &P, const float *store, const float *rho, float *rhoA, float *rhoB,
+                   float *u, cudaStream_t st);
+void launch_fluid_sums(const StepParams &P, const float *store, double *partial, int nblocks,
+                       cudaStream_t st);
+void launch_finish_sums(const double *partial, int nblocks, int nvals, double *out, cudaStream_t st);
+int fluid_sum_blocks(const StepParams &P);
+
+// particles (lb_particles.cu)
+void launch_bin(const StepParams &P, const ParticleArrays &pa, int *row_of, int *row_count,
+                unsigned *err, cudaStream_t st);
+void launch_scan_rows(int nrows, const int *row_count, int *row_start, int *row_cursor, cudaStream_t st);
+void launch_scatter(int np, const int *row_of, int *row_cursor, int *perm, cudaStream_t st);
+void launch_row_sort(const StepParams &P, const int *row_start, const ParticleArrays &pa, int *perm,
+                     cudaStream_t st);
+void launch_permute(int np, const int *perm, const ParticleArrays &src, const ParticleArrays &dst,
+                    int *slot_of_id, cudaStream_t st);
+void launch_couple(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho,
+                   const float *jp, const ParticleForces &pf, cudaStream_t st);
+void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const int *bond_start,
+                  const int *bond_other, const int *slot_of_id, const ParticleForces &pf, unsigned *err,
+                  cudaStream_t st);
+void launch_integrate(const StepParams &P, const ParticleArrays &pa, const ParticleForces &pf,
+                      unsigned *err, cudaStream_t st);
+void launch_particle_momentum(const StepParams &P, const ParticleArrays &pa, double *partial, int nblocks,
+                              cudaStream_t st);
+
+}  // namespace lbmd

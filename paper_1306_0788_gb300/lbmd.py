@@ -1,0 +1,254 @@
+"""Python binding of the C ABI in include/lbmd.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing
+but convert arguments (numpy arrays, Python scalars, CUDA stream handles) and
+turn negative return codes into :class:`LbmdError`.  All computation runs in
+``liblbmd.so`` (hand-written sm_103a CUDA).  There is no fallback: if the
+library is missing, importing the binding fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbmd.so")
+
+LBMD_OK = 0
+LBMD_E_INVALID_ARG = -1
+LBMD_E_NOMEM = -2
+LBMD_E_CUDA = -3
+LBMD_E_NEGATIVE_DENSITY = -4
+LBMD_E_NONFINITE = -5
+LBMD_E_TIMEOUT = -6
+LBMD_E_UNIMPLEMENTED = -7
+LBMD_E_BOND_BROKEN = -8
+LBMD_E_STATE = -9
+
+LBMD_STORAGE_FP32 = 0
+LBMD_STORAGE_FP16_SHIFTED = 1
+LBMD_STORAGE_BF16_SHIFTED = 2
+LBMD_BOND_FENE = 2
+LBMD_BOND_HARMONIC = 3
+LBMD_WARN_GAMMA_DT = 1 << 0
+LBMD_WARN_VISCOSITY = 1 << 1
+LBMD_WARN_BOLTZMANN = 1 << 2
+LBMD_WARN_ASYMMETRIC_G = 1 << 3
+LBMD_MAX_TYPES = 8
+
+# every symbol include/lbmd.h declares
+EXPORTS = ("lbmd_create", "lbmd_destroy", "lbmd_set_types", "lbmd_set_debye_hueckel", "lbmd_init_fluid",
+           "lbmd_set_populations", "lbmd_get_populations", "lbmd_set_particles", "lbmd_set_bonds",
+           "lbmd_step", "lbmd_sync", "lbmd_clear_error", "lbmd_get_fields", "lbmd_get_particles",
+           "lbmd_diagnostics", "lbmd_step_count", "lbmd_profile_enable", "lbmd_profile_read",
+           "lbmd_launch_count", "lbmd_last_error")
+
+
+class LbmdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("lbmd error %d: %s" % (code, msg))
+        self.code = code
+
+
+class lbmd_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("tau_r", ctypes.c_double), ("g_AB", ctypes.c_double), ("g_BA", ctypes.c_double),
+                ("kT", ctypes.c_double), ("dt", ctypes.c_double), ("storage", ctypes.c_int),
+                ("rho0_A", ctypes.c_double), ("rho0_B", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class lbmd_ptype(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("kappa_A", "kappa_B", "lambda_A", "lambda_B", "gamma", "mass")]
+
+
+class lbmd_pair(ctypes.Structure):
+    _fields_ = [("type_i", ctypes.c_int), ("type_j", ctypes.c_int), ("wca_eps", ctypes.c_double),
+                ("wca_sigma", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblbmd.so is not built (run paper_1306_0788_gb300/build.py or "
+                          "__graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    sig = {
+        "lbmd_create": (I, [ctypes.POINTER(lbmd_params), P, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_uint)]),
+        "lbmd_destroy": (None, [P]),
+        "lbmd_set_types": (I, [P, I, P, I, P, ctypes.POINTER(ctypes.c_uint)]),
+        "lbmd_set_debye_hueckel": (I, [P, D, D, D]),
+        "lbmd_init_fluid": (I, [P, P, P, P]),
+        "lbmd_set_populations": (I, [P, I, P]),
+        "lbmd_get_populations": (I, [P, I, P]),
+        "lbmd_set_particles": (I, [P, I, P, P, P, P]),
+        "lbmd_set_bonds": (I, [P, I, P, I, D, D]),
+        "lbmd_step": (I, [P, I]),
+        "lbmd_sync": (I, [P]),
+        "lbmd_clear_error": (I, [P]),
+        "lbmd_get_fields": (I, [P, P, P, P]),
+        "lbmd_get_particles": (I, [P, P, P, P]),
+        "lbmd_diagnostics": (I, [P, P]),
+        "lbmd_step_count": (ctypes.c_int64, [P]),
+        "lbmd_profile_enable": (I, [P, I]),
+        "lbmd_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64), I]),
+        "lbmd_launch_count": (ctypes.c_int64, [P]),
+        "lbmd_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _check(ctx, code: int):
+    if code != LBMD_OK:
+        raise LbmdError(code, _lib.lbmd_last_error(ctx).decode(errors="replace"))
+    return code
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def stream_handle(stream) -> int | None:
+    """Accept a raw cudaStream_t (int), a torch.cuda.Stream, or None."""
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------ entry points
+def lbmd_create(params: lbmd_params, stream=None):
+    """Returns (ctx, warnings)."""
+    ctx = ctypes.c_void_p()
+    w = ctypes.c_uint(0)
+    _check(None, _lib.lbmd_create(ctypes.byref(params), stream_handle(stream), ctypes.byref(ctx), ctypes.byref(w)))
+    return ctx, w.value
+
+
+def lbmd_destroy(ctx) -> None:
+    _lib.lbmd_destroy(ctx)
+
+
+def lbmd_set_types(ctx, types, pairs=()) -> int:
+    t = (lbmd_ptype * len(types))(*types)
+    pr = (lbmd_pair * max(1, len(pairs)))(*pairs)
+    w = ctypes.c_uint(0)
+    _check(ctx, _lib.lbmd_set_types(ctx, len(types), t, len(pairs), pr, ctypes.byref(w)))
+    return w.value
+
+
+def lbmd_set_debye_hueckel(ctx, lB: float, kappa_D: float, rc: float) -> None:
+    _check(ctx, _lib.lbmd_set_debye_hueckel(ctx, lB, kappa_D, rc))
+
+
+def lbmd_init_fluid(ctx, rhoA, rhoB, u=None) -> None:
+    a, b, c = _f32(rhoA), _f32(rhoB), _f32(u)
+    _check(ctx, _lib.lbmd_init_fluid(ctx, _p(a), _p(b), _p(c)))
+
+
+def lbmd_set_populations(ctx, comp: int, f) -> None:
+    a = _f32(f)
+    _check(ctx, _lib.lbmd_set_populations(ctx, comp, _p(a)))
+
+
+def lbmd_get_populations(ctx, comp: int, shape) -> np.ndarray:
+    """shape = (nz, ny, nx); returns [19, nz, ny, nx] float32."""
+    out = np.empty((19,) + tuple(shape), dtype=np.float32)
+    _check(ctx, _lib.lbmd_get_populations(ctx, comp, _p(out)))
+    return out
+
+
+def lbmd_set_particles(ctx, x, v, type_, q=None) -> None:
+    x, v = _f64(x).reshape(-1, 3), _f64(v).reshape(-1, 3)
+    t = np.ascontiguousarray(type_, dtype=np.int32)
+    qq = _f64(q)
+    _check(ctx, _lib.lbmd_set_particles(ctx, len(t), _p(x), _p(v), _p(t), _p(qq)))
+
+
+def lbmd_set_bonds(ctx, pairs, kind: int, k: float, r: float) -> None:
+    b = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    _check(ctx, _lib.lbmd_set_bonds(ctx, len(b), _p(b), kind, k, r))
+
+
+def lbmd_step(ctx, nsteps: int) -> None:
+    _check(ctx, _lib.lbmd_step(ctx, nsteps))
+
+
+def lbmd_sync(ctx) -> None:
+    _check(ctx, _lib.lbmd_sync(ctx))
+
+
+def lbmd_clear_error(ctx) -> None:
+    _check(ctx, _lib.lbmd_clear_error(ctx))
+
+
+def lbmd_get_fields(ctx, shape, want_u: bool = True):
+    """Returns rhoA, rhoB [nz, ny, nx] and u [nz, ny, nx, 3] (or None)."""
+    a = np.empty(tuple(shape), dtype=np.float32)
+    b = np.empty(tuple(shape), dtype=np.float32)
+    u = np.empty(tuple(shape) + (3,), dtype=np.float32) if want_u else None
+    _check(ctx, _lib.lbmd_get_fields(ctx, _p(a), _p(b), _p(u)))
+    return a, b, u
+
+
+def lbmd_get_particles(ctx, n: int):
+    """Returns x, v, f, each [n, 3] float64 in the caller's particle order."""
+    x, v, f = np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3))
+    _check(ctx, _lib.lbmd_get_particles(ctx, _p(x), _p(v), _p(f)))
+    return x, v, f
+
+
+def lbmd_diagnostics(ctx) -> np.ndarray:
+    out = np.zeros(8)
+    _check(ctx, _lib.lbmd_diagnostics(ctx, _p(out)))
+    return out
+
+
+def lbmd_step_count(ctx) -> int:
+    return int(_lib.lbmd_step_count(ctx))
+
+
+def lbmd_launch_count(ctx) -> int:
+    return int(_lib.lbmd_launch_count(ctx))
+
+
+def lbmd_profile_enable(ctx, on: bool) -> None:
+    _check(ctx, _lib.lbmd_profile_enable(ctx, int(bool(on))))
+
+
+def lbmd_profile_read(ctx, reset: bool = True):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(ctx, _lib.lbmd_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n), int(bool(reset))))
+    return ms.value, n.value
+
+
+def lbmd_last_error(ctx) -> str:
+    return _lib.lbmd_last_error(ctx).decode(errors="replace")
+
+
+def params(dims, tau_r=1.0, g_AB=0.0, g_BA=None, kT=0.0, seed=0, storage=LBMD_STORAGE_FP32,
+           rho0=(0.0, 0.0)) -> lbmd_params:
+    """Convenience constructor of lbmd_params (dims = (nx, ny, nz))."""
+    nx, ny, nz = dims
+    return lbmd_params(nx, ny, nz, tau_r, g_AB, g_AB if g_BA is None else g_BA, kT, 1.0, storage,
+                       rho0[0], rho0[1], seed)

@@ -1,0 +1,58 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every entry point
+include/lbmd.h declares, and rejects invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "lbmd.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbmd_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1306_0788_gb300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_1306_0788_gb300 import lbmd
+    assert sorted(lbmd.EXPORTS) == names
+
+
+def test_binding_has_the_same_names():
+    from paper_1306_0788_gb300 import lbmd
+    for n in _declared():
+        assert callable(getattr(lbmd, n)), n
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("tau_r", 0.5), ("dt", 0.5), ("kT", -1.0), ("storage", 7)])
+def test_create_rejects_invalid_params_without_device(field, value):
+    from paper_1306_0788_gb300 import lbmd
+    p = lbmd.params((4, 4, 4))
+    setattr(p, field, value)
+    with pytest.raises(lbmd.LbmdError) as e:
+        lbmd.lbmd_create(p)
+    assert e.value.code == lbmd.LBMD_E_INVALID_ARG
+    assert lbmd.lbmd_last_error(None)
+
+
+def test_product_path_has_no_oracle_or_cpu_fallback():
+    """The library binding must not import the oracle and must fail loudly without the .so."""
+    src = open(os.path.join(ROOT, "paper_1306_0788_gb300", "lbmd.py")).read()
+    assert "oracle" not in src.replace("oracle-free", "")
+    csrc = os.path.join(ROOT, "paper_1306_0788_gb300", "csrc")
+    for f in os.listdir(csrc):
+        assert "lbmd_oracle" not in open(os.path.join(csrc, f)).read()
+    assert "raise ImportError" in src
