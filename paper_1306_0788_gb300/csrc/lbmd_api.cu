@@ -27,7 +27,7 @@ struct lbmd_ctx {
   int *slot_of_id = nullptr;
   int *row_of = nullptr, *row_count = nullptr, *row_start = nullptr, *row_cursor = nullptr, *perm = nullptr;
   int *bond_start = nullptr, *bond_other = nullptr;
-  int nbonds = 0;
+  int nbonds = 0, bond_np = 0;  // bonds index particles 0..bond_np-1
   unsigned *err = nullptr;
   double *diag_partial = nullptr, *diag_out = nullptr;
   int diag_blocks = 0;
@@ -433,6 +433,7 @@ int lbmd_set_bonds(lbmd_ctx *c, int nb, const int *pairs, int kind, double k, do
   CK(cudaMemcpy(c->bond_start, deg.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice), "upload bonds");
   CK(cudaMemcpy(c->bond_other, other.data(), sizeof(int) * 2 * nb, cudaMemcpyHostToDevice), "upload bonds");
   c->nbonds = nb;
+  c->bond_np = n;
   c->P.bond_kind = kind;
   c->P.bond_k = (float)k;
   c->P.bond_r = (float)r;
@@ -444,6 +445,8 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
   if (nsteps < 0) return fail(c, LBMD_E_INVALID_ARG, "nsteps < 0");
   if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
   cudaSetDevice(c->dev);
+  if (c->nbonds > 0 && c->bond_np != c->np)
+    return fail(c, LBMD_E_STATE, "bonds refer to a different particle set; call lbmd_set_bonds again");
   StepParams &P = c->P;
   P.np = c->np;
   const CellIndex ci{c->row_start};
