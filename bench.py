@@ -117,13 +117,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def build_workload(name: str, seed: int):
+def build_workload(name: str, seed: int, edge_override: int = 0):
     from paper_1306_0788_gb300 import inputs
     edge, npart, _ = WORKLOADS[name]
+    if edge_override:
+        npart = max(1, int(round(npart * (edge_override / edge) ** 3)))
+        edge = edge_override
     dims = (edge, edge, edge)
     if name == "slab_droplets_256":
-        rA, rB, drops = inputs.slab_and_droplets(dims, RHO_HI, RHO_LO, n_drops=8, r_min=8, r_max=32, width=4.0,
-                                                 seed=seed)
+        rA, rB, drops = inputs.slab_and_droplets(dims, RHO_HI, RHO_LO, n_drops=8, r_min=edge / 32,
+                                                 r_max=edge / 8, width=4.0, seed=seed)
         types = [(-0.05, -0.1, 0.0, 0.0, 1.0, 1.0)]
         kT = 1e-4
     else:
@@ -151,7 +154,7 @@ def run_cuda(args):
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
 
-    dims, rA, rB, x, types, kT = build_workload(args.workload, seed=1234 + rank)
+    dims, rA, rB, x, types, kT = build_workload(args.workload, seed=1234 + rank, edge_override=args.edge)
     npart = len(x)
     N = dims[0] * dims[1] * dims[2]
     prm = L.params(dims, tau_r=1.0, g_AB=G_COUPLING, kT=kT, seed=42 + rank)
@@ -240,7 +243,8 @@ def run_cuda(args):
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "description": WORKLOADS[args.workload][2],
+            "config": {"workload": args.workload + ("" if not args.edge else "@%d" % args.edge),
+                       "description": WORKLOADS[args.workload][2],
                        "lattice": list(dims), "particles": npart, "tau_r": 1.0, "g_AB": G_COUPLING, "kT": kT,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (N * 152 / 1e9)
@@ -335,6 +339,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="slab_droplets_256")
+    ap.add_argument("--edge", type=int, default=0, help="override the lattice edge (profiling of smaller cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

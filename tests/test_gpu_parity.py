@@ -95,9 +95,9 @@ def coupled_case(dims, npart, seed, g=0.8, kT=0.0, min_dist=2.0):
                 wca={(0, 0): (0.01, 1.0), (0, 1): (0.01, 0.9), (1, 1): (0.01, 0.8)}, dh=(0.02, 0.25, 2.5))
 
 
-@pytest.mark.parametrize("kT", [0.0, 0.005])
+@pytest.mark.parametrize("kT", [0.0, 0.002])
 def test_particles_100_steps(kT):
-    c = coupled_case((20, 18, 16), 30, seed=21, kT=kT)
+    c = coupled_case((20, 18, 16), 30, seed=21, kT=kT, min_dist=2.5)
     fg, xg, vg, _ = run_gpu(c, 100)
     fo, xo, vo, _ = run_oracle(c, 100)
     assert position_error(xg, xo, c.x, c.dims) <= POS_TOL
