@@ -133,60 +133,181 @@ __global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const float *_
   }
 }
 
-// The lattice update of one step at one node: pull, densities and momentum, Shan-Chen force
+// ---------------------------------------------------------------------------------------
+// The lattice update of one step: pull streaming, densities and momentum, Shan-Chen force
 // (Eq. SCforce with psi = rho, g_AA = g_BB = 0), fluid-side solvation force and momentum
-// return from the particles (Sec. 2), barycentric velocity (Eq. momentum_definition), BGK
-// collision with forcing for both components, write.
+// return gathered from the particles (Sec. 2), barycentric velocity (Eq.
+// momentum_definition), BGK collision with forcing (appendix) for both components.
+//
+// One persistent kernel.  Each block owns an (x, y) tile of kTX x kTY nodes and marches
+// along z over a balanced range of tile-planes.  For the plane z+1 it pulls the
+// populations of the tile plus a one-node halo and keeps only their sums (rho_A, rho_B,
+// and j' for the tile) in a shared-memory ring that holds the planes z-1, z, z+1; then it
+// collides plane z one component at a time, pulling that component's 19 populations again
+// (they were read one plane earlier and hit in L2).  DRAM traffic per node is the 2 x 19
+// populations read once and written once; the Shan-Chen stencil never touches DRAM.
+constexpr int kTX = 32, kTY = 8, kFusedThreads = kTX * kTY;
+constexpr int kRX = kTX + 2, kRY = kTY + 2;
+
+struct FusedShared {
+  float rho[4][2][kRY][kRX];  // ring of densities: planes z-1, z, z+1 (+1 slot being filled)
+  float j[3][3][kTY][kTX];    // j' of the tile for planes z, z+1 (+1 slot being filled)
+};
+
+__device__ __forceinline__ void fused_fill(const StepParams &P, const float *__restrict__ fin, FusedShared &sh,
+                                           int p, int zs, int x0, int y0, int w, int h) {
+  const int gz = wrapi(p, P.nz);
+  const int slot = (p - zs + 1) & 3;
+  const int jslot = (p - zs + 1) % 3;
+  int zn[3];
+  zn[0] = gz == 0 ? P.nz - 1 : gz - 1;
+  zn[1] = gz;
+  zn[2] = gz == P.nz - 1 ? 0 : gz + 1;
+  const int n = kRX * (h + 2);
+  for (int idx = threadIdx.x; idx < n; idx += kFusedThreads) {
+    const int ry = idx / kRX, rx = idx - ry * kRX;
+    if (rx > w + 1) continue;
+    const int gx = wrapi(x0 + rx - 1, P.nx), gy = wrapi(y0 + ry - 1, P.ny);
+    int xn[3], yn[3];
+    xn[0] = gx == 0 ? P.nx - 1 : gx - 1;
+    xn[1] = gx;
+    xn[2] = gx == P.nx - 1 ? 0 : gx + 1;
+    yn[0] = gy == 0 ? P.ny - 1 : gy - 1;
+    yn[1] = gy;
+    yn[2] = gy == P.ny - 1 ? 0 : gy + 1;
+    float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll 1
+    for (int comp = 0; comp < 2; ++comp) {  // one component's 19 loads in flight at a time
+      asm volatile("" ::: "memory");
+      const float *fc = fin + (long long)comp * kQ * P.N;
+      const unsigned N32 = (unsigned)P.N;
+      float r = 0.f;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        // 32-bit offsets: 19 * N < 2^32 is enforced when the context is created
+        const unsigned src = ((unsigned)zn[1 - kCz[i]] * P.ny + yn[1 - kCy[i]]) * P.nx + xn[1 - kCx[i]];
+        const float a = __ldg(fc + (i * N32 + src));
+        r += a;
+        jx += kCx[i] * a;
+        jy += kCy[i] * a;
+        jz += kCz[i] * a;
+      }
+      sh.rho[slot][comp][ry][rx] = r;
+    }
+    if (rx >= 1 && rx <= w && ry >= 1 && ry <= h) {
+      sh.j[jslot][0][ry - 1][rx - 1] = jx;
+      sh.j[jslot][1][ry - 1][rx - 1] = jy;
+      sh.j[jslot][2][ry - 1][rx - 1] = jz;
+    }
+  }
+}
+
+// Collide both components at one node: pull their 2 x 19 populations, BGK + forcing
+// (f* = f - (f - f^eq)/tau + Delta^g), write.  Directions [I0, I1) form one batch: its loads
+// are issued together, then its updates and stores.
+template <int I0, int I1>
+__device__ __forceinline__ void fused_collide_batch(const StepParams &P, const float *__restrict__ fin,
+                                                    float *__restrict__ fout, unsigned s, const int xn[3],
+                                                    const int yn[3], const int zn[3], float rA, float rB,
+                                                    float ux, float uy, float uz, float usq15, float3 gA,
+                                                    float3 gB, float ugA3, float ugB3) {
+  asm volatile("" ::: "memory");  // one batch of loads in registers at a time
+  // per-component base pointers; offsets within a component stay below 19 N < 2^32
+  const unsigned N32 = (unsigned)P.N;
+  const float *finA = fin, *finB = fin + (size_t)kQ * N32;
+  float *foutA = fout, *foutB = fout + (size_t)kQ * N32;
+  float fA[I1 - I0], fB[I1 - I0];
+#pragma unroll
+  for (int i = I0; i < I1; ++i) {
+    const unsigned src = ((unsigned)zn[1 - kCz[i]] * P.ny + yn[1 - kCy[i]]) * P.nx + xn[1 - kCx[i]];
+    fA[i - I0] = __ldg(finA + (i * N32 + src));
+    fB[i - I0] = __ldg(finB + (i * N32 + src));
+  }
+  const float om = P.inv_tau, fp = P.force_pref;
+#pragma unroll
+  for (int i = I0; i < I1; ++i) {
+    const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
+    const float poly = kW[i] * (1.f + 3.f * cu + 4.5f * cu * cu - usq15);
+    const float cgA = kCx[i] * gA.x + kCy[i] * gA.y + kCz[i] * gA.z;
+    const float cgB = kCx[i] * gB.x + kCy[i] * gB.y + kCz[i] * gB.z;
+    const float dgA = kW[i] * fp * (3.f * cgA + 9.f * cu * cgA - ugA3);
+    const float dgB = kW[i] * fp * (3.f * cgB + 9.f * cu * cgB - ugB3);
+    foutA[i * N32 + s] = fA[i - I0] - om * (fA[i - I0] - rA * poly) + dgA;
+    foutB[i * N32 + s] = fB[i - I0] - om * (fB[i - I0] - rB * poly) + dgB;
+  }
+}
+
+__device__ __forceinline__ void fused_collide(const StepParams &P, const float *__restrict__ fin,
+                                              float *__restrict__ fout, unsigned s, const int xn[3],
+                                              const int yn[3], const int zn[3], float rA, float rB, float ux,
+                                              float uy, float uz, float3 gA, float3 gB) {
+  const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+  const float ugA3 = 3.f * (ux * gA.x + uy * gA.y + uz * gA.z);
+  const float ugB3 = 3.f * (ux * gB.x + uy * gB.y + uz * gB.z);
+  fused_collide_batch<0, 10>(P, fin, fout, s, xn, yn, zn, rA, rB, ux, uy, uz, usq15, gA, gB, ugA3, ugB3);
+  fused_collide_batch<10, kQ>(P, fin, fout, s, xn, yn, zn, rA, rB, ux, uy, uz, usq15, gA, gB, ugA3, ugB3);
+}
+
 template <bool kParticles>
-__global__ void __launch_bounds__(kBlock) k_collide(StepParams P, const float *__restrict__ fin,
-                                                    float *__restrict__ fout, const float *__restrict__ rho,
-                                                    ParticleArrays pa, ParticleForces pf, CellIndex ci,
-                                                    unsigned *err) {
-  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= P.N) return;
-  const Coord c = site_coord(P, s);
-  int xs[3], ys[3], zs[3];
-  neighbours(P, c, xs, ys, zs);
-  float fA[kQ], fB[kQ];
+__global__ void __launch_bounds__(kFusedThreads, 4)
+    k_lattice(StepParams P, const float *__restrict__ fin, float *__restrict__ fout, ParticleArrays pa,
+              ParticleForces pf, CellIndex ci, unsigned *err, int tiles_x, long long work) {
+  __shared__ FusedShared sh;
+  const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+  const long long G = gridDim.x;
+  long long w0 = work * blockIdx.x / G;
+  const long long w1 = work * (blockIdx.x + 1) / G;
+  while (w0 < w1) {
+    const long long tile = w0 / P.nz;
+    const int zs = (int)(w0 - tile * P.nz);
+    const int ze = (int)(zs + (w1 - w0) < P.nz ? zs + (w1 - w0) : P.nz);
+    const int x0 = (int)(tile % tiles_x) * kTX, y0 = (int)(tile / tiles_x) * kTY;
+    const int w = min(kTX, P.nx - x0), h = min(kTY, P.ny - y0);
+    __syncthreads();  // the previous segment's readers of the rings are done
+    fused_fill(P, fin, sh, zs - 1, zs, x0, y0, w, h);
+    fused_fill(P, fin, sh, zs, zs, x0, y0, w, h);
+    for (int z = zs; z < ze; ++z) {
+      fused_fill(P, fin, sh, z + 1, zs, x0, y0, w, h);
+      __syncthreads();
+      if (lx < w && ly < h) {
+        const int gx = x0 + lx, gy = y0 + ly;
+        int xn[3], yn[3], zn[3];
+        xn[0] = gx == 0 ? P.nx - 1 : gx - 1;
+        xn[1] = gx;
+        xn[2] = gx == P.nx - 1 ? 0 : gx + 1;
+        yn[0] = gy == 0 ? P.ny - 1 : gy - 1;
+        yn[1] = gy;
+        yn[2] = gy == P.ny - 1 ? 0 : gy + 1;
+        zn[0] = z == 0 ? P.nz - 1 : z - 1;
+        zn[1] = z;
+        zn[2] = z == P.nz - 1 ? 0 : z + 1;
+        const int sl[3] = {(z - zs) & 3, (z - zs + 1) & 3, (z - zs + 2) & 3};  // planes z-1, z, z+1
+        const int js = (z - zs + 1) % 3;
+        const float rA = sh.rho[sl[1]][0][ly + 1][lx + 1], rB = sh.rho[sl[1]][1][ly + 1][lx + 1];
+        const float jx = sh.j[js][0][ly][lx], jy = sh.j[js][1][ly][lx], jz = sh.j[js][2][ly][lx];
+        float SAx = 0.f, SAy = 0.f, SAz = 0.f, SBx = 0.f, SBy = 0.f, SBz = 0.f;
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const long long src = pull_source(P, i, xs, ys, zs);
-    fA[i] = __ldg(fin + (long long)i * P.N + src);
-    fB[i] = __ldg(fin + (long long)(kQ + i) * P.N + src);
-  }
-  float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    rA += fA[i];
-    rB += fB[i];
-    jx += kCx[i] * (fA[i] + fB[i]);
-    jy += kCy[i] * (fA[i] + fB[i]);
-    jz += kCz[i] * (fA[i] + fB[i]);
-  }
-  // S_z = sum_i w_i rho_z(r + c_i) c_i from the density field of this step
-  float SAx = 0.f, SAy = 0.f, SAz = 0.f, SBx = 0.f, SBy = 0.f, SBz = 0.f;
-#pragma unroll
-  for (int i = 1; i < kQ; ++i) {
-    const long long nb = ((long long)zs[1 + kCz[i]] * P.ny + ys[1 + kCy[i]]) * P.nx + xs[1 + kCx[i]];
-    const float a = kW[i] * __ldg(rho + nb), b = kW[i] * __ldg(rho + P.N + nb);
-    SAx += kCx[i] * a; SAy += kCy[i] * a; SAz += kCz[i] * a;
-    SBx += kCx[i] * b; SBy += kCy[i] * b; SBz += kCz[i] * b;
-  }
-  float3 gA = make_float3(-P.gAB * rA * SBx, -P.gAB * rA * SBy, -P.gAB * rA * SBz);
-  float3 gB = make_float3(-P.gBA * rB * SAx, -P.gBA * rB * SAy, -P.gBA * rB * SAz);
-  if (kParticles) gather_coupling(P, c.x, c.y, c.z, rA, rB, pa, pf, ci, true, gA, gB);
-  const float r = rA + rB;
-  if (!(rA > 0.f) || !(rB > 0.f) || !isfinite(r)) atomicOr(err, isfinite(r) ? kErrNegDensity : kErrNonFinite);
-  const float rinv = 1.f / r;
-  const float ux = (jx + 0.5f * (gA.x + gB.x)) * rinv;
-  const float uy = (jy + 0.5f * (gA.y + gB.y)) * rinv;
-  const float uz = (jz + 0.5f * (gA.z + gB.z)) * rinv;
-  collide_component(P, fA, rA, ux, uy, uz, gA.x, gA.y, gA.z);
-  collide_component(P, fB, rB, ux, uy, uz, gB.x, gB.y, gB.z);
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    fout[(long long)i * P.N + s] = fA[i];
-    fout[(long long)(kQ + i) * P.N + s] = fB[i];
+        for (int i = 1; i < kQ; ++i) {
+          const int s3 = sl[1 + kCz[i]];
+          const float a = kW[i] * sh.rho[s3][0][ly + 1 + kCy[i]][lx + 1 + kCx[i]];
+          const float b = kW[i] * sh.rho[s3][1][ly + 1 + kCy[i]][lx + 1 + kCx[i]];
+          SAx += kCx[i] * a; SAy += kCy[i] * a; SAz += kCz[i] * a;
+          SBx += kCx[i] * b; SBy += kCy[i] * b; SBz += kCz[i] * b;
+        }
+        float3 gA = make_float3(-P.gAB * rA * SBx, -P.gAB * rA * SBy, -P.gAB * rA * SBz);
+        float3 gB = make_float3(-P.gBA * rB * SAx, -P.gBA * rB * SAy, -P.gBA * rB * SAz);
+        if (kParticles) gather_coupling(P, gx, gy, z, rA, rB, pa, pf, ci, true, gA, gB);
+        const float r = rA + rB;
+        if (!(rA > 0.f) || !(rB > 0.f) || !isfinite(r)) atomicOr(err, isfinite(r) ? kErrNegDensity : kErrNonFinite);
+        const float rinv = 1.f / r;
+        const float ux = (jx + 0.5f * (gA.x + gB.x)) * rinv;
+        const float uy = (jy + 0.5f * (gA.y + gB.y)) * rinv;
+        const float uz = (jz + 0.5f * (gA.z + gB.z)) * rinv;
+        const unsigned s = ((unsigned)z * P.ny + gy) * P.nx + gx;
+        fused_collide(P, fin, fout, s, xn, yn, zn, rA, rB, ux, uy, uz, gA, gB);
+      }
+    }
+    w0 += ze - zs;
   }
 }
 
@@ -291,10 +412,25 @@ void launch_moments(const StepParams &P, const float *store, float *rho, float *
 void launch_collide(const StepParams &P, const float *fin, float *fout, const float *rho,
                     const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci, unsigned *err,
                     cudaStream_t st) {
+  (void)rho;
+  const int tiles_x = (P.nx + kTX - 1) / kTX, tiles_y = (P.ny + kTY - 1) / kTY;
+  const long long work = (long long)tiles_x * tiles_y * P.nz;
+  static int grid_cap = 0;  // resident blocks of the persistent kernel (all SMs, full occupancy)
+  if (grid_cap == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lattice<true>, kFusedThreads, 0);
+    grid_cap = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  // at least ~4 planes per block so the two prologue planes stay a small overhead
+  long long grid = (work + 3) / 4;
+  if (grid > grid_cap) grid = grid_cap;
+  if (grid < 1) grid = 1;
   if (P.np > 0)
-    k_collide<true><<<grid_for(P.N), kBlock, 0, st>>>(P, fin, fout, rho, pa, pf, ci, err);
+    k_lattice<true><<<(unsigned)grid, kFusedThreads, 0, st>>>(P, fin, fout, pa, pf, ci, err, tiles_x, work);
   else
-    k_collide<false><<<grid_for(P.N), kBlock, 0, st>>>(P, fin, fout, rho, pa, pf, ci, err);
+    k_lattice<false><<<(unsigned)grid, kFusedThreads, 0, st>>>(P, fin, fout, pa, pf, ci, err, tiles_x, work);
 }
 void launch_fields(const StepParams &P, const float *store, const float *rho, float *rhoA, float *rhoB,
                    float *u, cudaStream_t st) {

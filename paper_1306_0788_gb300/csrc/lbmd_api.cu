@@ -26,6 +26,7 @@ struct lbmd_ctx {
   ParticleForces pf{};
   int *slot_of_id = nullptr;
   int *row_of = nullptr, *row_count = nullptr, *row_start = nullptr, *row_cursor = nullptr, *perm = nullptr;
+  int *row_bsum = nullptr;  // block sums of the row scan
   int *bond_start = nullptr, *bond_other = nullptr;
   int nbonds = 0, bond_np = 0;  // bonds index particles 0..bond_np-1
   unsigned *err = nullptr;
@@ -116,12 +117,12 @@ int sort_particles(lbmd_ctx *c) {
   const StepParams &P = c->P;
   CK(cudaMemsetAsync(c->row_count, 0, sizeof(int) * (P.nrows + 1), c->st), "memset rows");
   launch_bin(P, c->pa[c->pcur], c->row_of, c->row_count, c->err, c->st);
-  launch_scan_rows(P.nrows, c->row_count, c->row_start, c->row_cursor, c->st);
+  launch_scan_rows(P.nrows, c->row_count, c->row_start, c->row_cursor, c->row_bsum, c->st);
   launch_scatter(P.np, c->row_of, c->row_cursor, c->perm, c->st);
   launch_row_sort(P, c->row_start, c->pa[c->pcur], c->perm, c->st);
   launch_permute(P.np, c->perm, c->pa[c->pcur], c->pa[1 - c->pcur], c->slot_of_id, c->st);
   c->pcur = 1 - c->pcur;
-  return launched(c, "particle sort", 6);
+  return launched(c, "particle sort", 8);
 }
 
 double max_range(const lbmd_ctx *c) {
@@ -147,8 +148,8 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
   *out = nullptr;
   if (warnings) *warnings = 0;
   if (prm->nx < 1 || prm->ny < 1 || prm->nz < 1) return fail(c, LBMD_E_INVALID_ARG, "lattice sizes must be >= 1");
-  if ((double)prm->nx * prm->ny * prm->nz > 4.0e9 / 38.0 * 16.0)
-    return fail(c, LBMD_E_INVALID_ARG, "lattice too large");
+  if ((double)prm->nx * prm->ny * prm->nz * kQ >= 4294967296.0)  // 32-bit population offsets
+    return fail(c, LBMD_E_INVALID_ARG, "lattice too large: nx*ny*nz must be below 2^32/19");
   if (!(prm->tau_r > 0.5)) return fail(c, LBMD_E_INVALID_ARG, "tau_r must exceed 1/2");
   if (prm->dt != 1.0) return fail(c, LBMD_E_INVALID_ARG, "dt must equal the lattice time step 1");
   if (!(prm->kT >= 0.0)) return fail(c, LBMD_E_INVALID_ARG, "kT must be >= 0");
@@ -207,7 +208,7 @@ void lbmd_destroy(lbmd_ctx *c) {
   dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho); dfree(c->jp); dfree(c->err);
   dfree(c->diag_partial); dfree(c->diag_out);
   free_particles(c);
-  dfree(c->row_count); dfree(c->row_start); dfree(c->row_cursor);
+  dfree(c->row_count); dfree(c->row_start); dfree(c->row_cursor); dfree(c->row_bsum);
   dfree(c->bond_start); dfree(c->bond_other);
   for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
   delete c;
@@ -372,6 +373,7 @@ int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, con
     if (e == cudaSuccess && !c->row_count) e = dalloc(&c->row_count, (size_t)P.nrows + 1);
     if (e == cudaSuccess && !c->row_start) e = dalloc(&c->row_start, (size_t)P.nrows + 1);
     if (e == cudaSuccess && !c->row_cursor) e = dalloc(&c->row_cursor, (size_t)P.nrows + 1);
+    if (e == cudaSuccess && !c->row_bsum) e = dalloc(&c->row_bsum, (size_t)scan_blocks(P.nrows) + 1);
     if (e != cudaSuccess) {
       cudaGetLastError();
       free_particles(c);
@@ -385,6 +387,7 @@ int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, con
     CK(dalloc(&c->row_count, (size_t)P.nrows + 1), "alloc rows");
     CK(dalloc(&c->row_start, (size_t)P.nrows + 1), "alloc rows");
     CK(dalloc(&c->row_cursor, (size_t)P.nrows + 1), "alloc rows");
+    CK(dalloc(&c->row_bsum, (size_t)scan_blocks(P.nrows) + 1), "alloc rows");
   }
   c->np = n;
   P.np = n;
@@ -456,13 +459,19 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
     float *fout = c->pop[1 - c->cur];
     int r;
     if (P.np > 0 && (r = sort_particles(c))) return r;
-    launch_moments(P, fin, c->rho, P.np > 0 ? c->jp : nullptr, c->st);
-    if ((r = launched(c, "moments"))) return r;
     if (P.np > 0) {
-      launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
+      // dense particles: one density pass over the lattice is cheaper than a node cube per particle
+      if ((long long)P.np * 64 > P.N / 2) {
+        launch_moments(P, fin, c->rho, c->jp, c->st);
+        launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
+        if ((r = launched(c, "moments + couple", 2))) return r;
+      } else {
+        launch_couple_cube(P, fin, c->pa[c->pcur], ci, c->pf, c->st);
+        if ((r = launched(c, "couple"))) return r;
+      }
       launch_pairs(P, c->pa[c->pcur], ci, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf,
                    c->err, c->st);
-      if ((r = launched(c, "particle forces", 2))) return r;
+      if ((r = launched(c, "pair forces"))) return r;
     }
     if (c->prof) {
       if (c->ev_used + 2 > c->ev.size()) {

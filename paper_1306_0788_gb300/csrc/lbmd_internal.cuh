@@ -208,7 +208,8 @@ int fluid_sum_blocks(const StepParams &P);
 // particles (lb_particles.cu)
 void launch_bin(const StepParams &P, const ParticleArrays &pa, int *row_of, int *row_count,
                 unsigned *err, cudaStream_t st);
-void launch_scan_rows(int nrows, const int *row_count, int *row_start, int *row_cursor, cudaStream_t st);
+int scan_blocks(int nrows);  // size of the block-sum scratch is scan_blocks(nrows) + 1
+void launch_scan_rows(int nrows, const int *row_count, int *row_start, int *row_cursor, int *bsum, cudaStream_t st);
 void launch_scatter(int np, const int *row_of, int *row_cursor, int *perm, cudaStream_t st);
 void launch_row_sort(const StepParams &P, const int *row_start, const ParticleArrays &pa, int *perm,
                      cudaStream_t st);
@@ -216,6 +217,8 @@ void launch_permute(int np, const int *perm, const ParticleArrays &src, const Pa
                     int *slot_of_id, cudaStream_t st);
 void launch_couple(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho,
                    const float *jp, const ParticleForces &pf, cudaStream_t st);
+void launch_couple_cube(const StepParams &P, const float *fin, const ParticleArrays &pa, CellIndex ci,
+                        const ParticleForces &pf, cudaStream_t st);
 void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const int *bond_start,
                   const int *bond_other, const int *slot_of_id, const ParticleForces &pf, unsigned *err,
                   cudaStream_t st);
