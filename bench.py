@@ -43,10 +43,9 @@ WORKLOADS = {
 
 
 def algorithmic_bytes_per_site() -> int:
-    """Bytes per site of the lattice update kernel: both components' 19 populations read
-    (pull) and written, FP32 (2*19*4*2 = 304), plus the two stored densities of the
-    stencil read (8)."""
-    return 2 * 19 * 4 * 2 + 8
+    """Algorithmic bytes per node of the lattice update kernel: both components' 19
+    populations read (pull) and written once, FP32: 2*19*4*2 = 304."""
+    return 2 * 19 * 4 * 2
 
 
 def measured_hbm_peak():
@@ -59,7 +58,8 @@ def measured_hbm_peak():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 500 ms during the timed region (a
+    query stalls host-side launches briefly, so the timed region is kept long)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -74,7 +74,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "500"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -249,7 +249,7 @@ def run_cuda(args):
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (N * 152 / 1e9)
                        if N * 152 > 129e6 else "L2-resident lattice (latency regime)"},
-            "roofline": {"bound": "hbm", "kernel": "k_collide (stream + collide + forcing + coupling gather)",
+            "roofline": {"bound": "hbm", "kernel": "k_lattice (fused pull-stream + Shan-Chen + coupling gather + BGK/forcing, both components)",
                          "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_site": bps,
                          "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,

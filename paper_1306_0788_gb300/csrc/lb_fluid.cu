@@ -44,22 +44,6 @@ __device__ __forceinline__ void neighbours(const StepParams &P, const Coord &c, 
   zs[2] = c.z == P.nz - 1 ? 0 : c.z + 1;
 }
 
-// f^eq (Eq. feq) and the forcing term (appendix, BGK: G = (1 - 1/2tau)(ug + gu)) folded into
-// the BGK update f* = f - (f - f^eq)/tau + Delta^g for one component.
-__device__ __forceinline__ void collide_component(const StepParams &P, float (&f)[kQ], float rho_c,
-                                                  float ux, float uy, float uz, float gx, float gy, float gz) {
-  const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-  const float ug3 = 3.f * (ux * gx + uy * gy + uz * gz);
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
-    const float cg = kCx[i] * gx + kCy[i] * gy + kCz[i] * gz;
-    const float feq = kW[i] * rho_c * (1.f + 3.f * cu + 4.5f * cu * cu - usq15);
-    const float dg = kW[i] * P.force_pref * (3.f * cg + 9.f * cu * cg - ug3);
-    f[i] = f[i] - P.inv_tau * (f[i] - feq) + dg;
-  }
-}
-
 __global__ void __launch_bounds__(kBlock) k_init_equilibrium(StepParams P, const float *__restrict__ rhoA,
                                                              const float *__restrict__ rhoB,
                                                              const float *__restrict__ u, float *__restrict__ store) {
@@ -139,175 +123,180 @@ __global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const float *_
 // return gathered from the particles (Sec. 2), barycentric velocity (Eq.
 // momentum_definition), BGK collision with forcing (appendix) for both components.
 //
-// One persistent kernel.  Each block owns an (x, y) tile of kTX x kTY nodes and marches
-// along z over a balanced range of tile-planes.  For the plane z+1 it pulls the
-// populations of the tile plus a one-node halo and keeps only their sums (rho_A, rho_B,
-// and j' for the tile) in a shared-memory ring that holds the planes z-1, z, z+1; then it
-// collides plane z one component at a time, pulling that component's 19 populations again
-// (they were read one plane earlier and hit in L2).  DRAM traffic per node is the 2 x 19
-// populations read once and written once; the Shan-Chen stencil never touches DRAM.
+// Each block owns an (x, y) tile of kTX x kTY nodes and marches along a z-range; blocks are
+// numbered z-chunk-major so that all tiles of a chunk march in step.  For plane z+1 the
+// block pulls the 2 x 19 populations of its tile into shared memory (they are collided one
+// plane later without touching DRAM again) and sums them to rho_A, rho_B, j'; it also
+// pulls the one-node halo around the tile, keeping only the densities.  A ring of four
+// density planes gives the Shan-Chen stencil of plane z.  DRAM traffic per node: the
+// populations read once and written once (304 B) plus the halo reads, which hit in L2
+// because the neighbouring tile pulls the same lines in the same plane at the same time.
 constexpr int kTX = 32, kTY = 8, kFusedThreads = kTX * kTY;
 constexpr int kRX = kTX + 2, kRY = kTY + 2;
 
 struct FusedShared {
-  float rho[4][2][kRY][kRX];  // ring of densities: planes z-1, z, z+1 (+1 slot being filled)
-  float j[3][3][kTY][kTX];    // j' of the tile for planes z, z+1 (+1 slot being filled)
+  float pops[2][2][kQ][kTY][kTX];  // pulled populations of planes z, z+1: [slot][comp][i][y][x]
+  float rho[4][2][kRY][kRX];       // densities of planes z-1, z, z+1 (+1 being filled), with halo
+  float j[2][3][kTY][kTX];         // j' of the tile, planes z, z+1
 };
 
-__device__ __forceinline__ void fused_fill(const StepParams &P, const float *__restrict__ fin, FusedShared &sh,
-                                           int p, int zs, int x0, int y0, int w, int h) {
+struct Neigh {
+  int xn[3], yn[3], zn[3];  // wrapped coordinates r - 1, r, r + 1 per axis
+};
+
+__device__ __forceinline__ Neigh neighbours_of(const StepParams &P, int gx, int gy, int gz) {
+  Neigh n;
+  n.xn[0] = gx == 0 ? P.nx - 1 : gx - 1; n.xn[1] = gx; n.xn[2] = gx == P.nx - 1 ? 0 : gx + 1;
+  n.yn[0] = gy == 0 ? P.ny - 1 : gy - 1; n.yn[1] = gy; n.yn[2] = gy == P.ny - 1 ? 0 : gy + 1;
+  n.zn[0] = gz == 0 ? P.nz - 1 : gz - 1; n.zn[1] = gz; n.zn[2] = gz == P.nz - 1 ? 0 : gz + 1;
+  return n;
+}
+
+__device__ __forceinline__ unsigned pull_src(const StepParams &P, const Neigh &n, int i) {
+  // 32-bit: 19 N < 2^32 is enforced when the context is created
+  return ((unsigned)n.zn[1 - kCz[i]] * P.ny + n.yn[1 - kCy[i]]) * P.nx + n.xn[1 - kCx[i]];
+}
+
+// Pull the 2 x 19 populations of this thread's node of plane p into registers (prefetch).
+__device__ __forceinline__ void fused_prefetch(const StepParams &P, const float *__restrict__ fin, int p, int x0,
+                                               int y0, float (&fa)[kQ], float (&fb)[kQ]) {
+  const unsigned N32 = (unsigned)P.N;
+  const float *finB = fin + (size_t)kQ * N32;
+  const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+  const Neigh n = neighbours_of(P, wrapi(x0 + lx, P.nx), wrapi(y0 + ly, P.ny), wrapi(p, P.nz));
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const unsigned src = pull_src(P, n, i);
+    fa[i] = __ldg(fin + (i * N32 + src));
+    fb[i] = __ldg(finB + (i * N32 + src));
+  }
+}
+
+// Commit plane p: the prefetched populations go to shared memory with their sums rho_A,
+// rho_B, j' (tile nodes); the one-node halo around the tile is pulled and summed (rho only).
+__device__ __forceinline__ void fused_commit(const StepParams &P, const float *__restrict__ fin, FusedShared &sh,
+                                             int p, int zs, int x0, int y0, int w, int h, bool keep_pops,
+                                             const float (&fa)[kQ], const float (&fb)[kQ]) {
   const int gz = wrapi(p, P.nz);
   const int slot = (p - zs + 1) & 3;
-  const int jslot = (p - zs + 1) % 3;
-  int zn[3];
-  zn[0] = gz == 0 ? P.nz - 1 : gz - 1;
-  zn[1] = gz;
-  zn[2] = gz == P.nz - 1 ? 0 : gz + 1;
-  const int n = kRX * (h + 2);
-  for (int idx = threadIdx.x; idx < n; idx += kFusedThreads) {
-    const int ry = idx / kRX, rx = idx - ry * kRX;
-    if (rx > w + 1) continue;
-    const int gx = wrapi(x0 + rx - 1, P.nx), gy = wrapi(y0 + ry - 1, P.ny);
-    int xn[3], yn[3];
-    xn[0] = gx == 0 ? P.nx - 1 : gx - 1;
-    xn[1] = gx;
-    xn[2] = gx == P.nx - 1 ? 0 : gx + 1;
-    yn[0] = gy == 0 ? P.ny - 1 : gy - 1;
-    yn[1] = gy;
-    yn[2] = gy == P.ny - 1 ? 0 : gy + 1;
-    float jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll 1
-    for (int comp = 0; comp < 2; ++comp) {  // one component's 19 loads in flight at a time
-      asm volatile("" ::: "memory");
-      const float *fc = fin + (long long)comp * kQ * P.N;
-      const unsigned N32 = (unsigned)P.N;
-      float r = 0.f;
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) {
-        // 32-bit offsets: 19 * N < 2^32 is enforced when the context is created
-        const unsigned src = ((unsigned)zn[1 - kCz[i]] * P.ny + yn[1 - kCy[i]]) * P.nx + xn[1 - kCx[i]];
-        const float a = __ldg(fc + (i * N32 + src));
-        r += a;
-        jx += kCx[i] * a;
-        jy += kCy[i] * a;
-        jz += kCz[i] * a;
-      }
-      sh.rho[slot][comp][ry][rx] = r;
-    }
-    if (rx >= 1 && rx <= w && ry >= 1 && ry <= h) {
-      sh.j[jslot][0][ry - 1][rx - 1] = jx;
-      sh.j[jslot][1][ry - 1][rx - 1] = jy;
-      sh.j[jslot][2][ry - 1][rx - 1] = jz;
-    }
-  }
-}
-
-// Collide both components at one node: pull their 2 x 19 populations, BGK + forcing
-// (f* = f - (f - f^eq)/tau + Delta^g), write.  Directions [I0, I1) form one batch: its loads
-// are issued together, then its updates and stores.
-template <int I0, int I1>
-__device__ __forceinline__ void fused_collide_batch(const StepParams &P, const float *__restrict__ fin,
-                                                    float *__restrict__ fout, unsigned s, const int xn[3],
-                                                    const int yn[3], const int zn[3], float rA, float rB,
-                                                    float ux, float uy, float uz, float usq15, float3 gA,
-                                                    float3 gB, float ugA3, float ugB3) {
-  asm volatile("" ::: "memory");  // one batch of loads in registers at a time
-  // per-component base pointers; offsets within a component stay below 19 N < 2^32
+  const int ps = p & 1;
   const unsigned N32 = (unsigned)P.N;
-  const float *finA = fin, *finB = fin + (size_t)kQ * N32;
-  float *foutA = fout, *foutB = fout + (size_t)kQ * N32;
-  float fA[I1 - I0], fB[I1 - I0];
+  const float *finB = fin + (size_t)kQ * N32;
+  const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+  if (lx < w && ly < h) {
+    float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
-  for (int i = I0; i < I1; ++i) {
-    const unsigned src = ((unsigned)zn[1 - kCz[i]] * P.ny + yn[1 - kCy[i]]) * P.nx + xn[1 - kCx[i]];
-    fA[i - I0] = __ldg(finA + (i * N32 + src));
-    fB[i - I0] = __ldg(finB + (i * N32 + src));
+    for (int i = 0; i < kQ; ++i) {
+      if (keep_pops) {
+        sh.pops[ps][0][i][ly][lx] = fa[i];
+        sh.pops[ps][1][i][ly][lx] = fb[i];
+      }
+      rA += fa[i];
+      rB += fb[i];
+      jx += kCx[i] * (fa[i] + fb[i]);
+      jy += kCy[i] * (fa[i] + fb[i]);
+      jz += kCz[i] * (fa[i] + fb[i]);
+    }
+    sh.rho[slot][0][ly + 1][lx + 1] = rA;
+    sh.rho[slot][1][ly + 1][lx + 1] = rB;
+    sh.j[ps][0][ly][lx] = jx;
+    sh.j[ps][1][ly][lx] = jy;
+    sh.j[ps][2][ly][lx] = jz;
   }
-  const float om = P.inv_tau, fp = P.force_pref;
+  // halo ring of the (w+2) x (h+2) region: rows 0 and h+1, then columns 0 and w+1
+  const int nrow = w + 2, nhalo = 2 * nrow + 2 * h;
+  for (int k = threadIdx.x; k < nhalo; k += kFusedThreads) {
+    int rx, ry;
+    if (k < 2 * nrow) {
+      ry = k < nrow ? 0 : h + 1;
+      rx = k < nrow ? k : k - nrow;
+    } else {
+      const int c = k - 2 * nrow;
+      rx = c < h ? 0 : w + 1;
+      ry = 1 + (c < h ? c : c - h);
+    }
+    const Neigh n = neighbours_of(P, wrapi(x0 + rx - 1, P.nx), wrapi(y0 + ry - 1, P.ny), gz);
+    float rA = 0.f, rB = 0.f;
 #pragma unroll
-  for (int i = I0; i < I1; ++i) {
-    const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
-    const float poly = kW[i] * (1.f + 3.f * cu + 4.5f * cu * cu - usq15);
-    const float cgA = kCx[i] * gA.x + kCy[i] * gA.y + kCz[i] * gA.z;
-    const float cgB = kCx[i] * gB.x + kCy[i] * gB.y + kCz[i] * gB.z;
-    const float dgA = kW[i] * fp * (3.f * cgA + 9.f * cu * cgA - ugA3);
-    const float dgB = kW[i] * fp * (3.f * cgB + 9.f * cu * cgB - ugB3);
-    foutA[i * N32 + s] = fA[i - I0] - om * (fA[i - I0] - rA * poly) + dgA;
-    foutB[i * N32 + s] = fB[i - I0] - om * (fB[i - I0] - rB * poly) + dgB;
+    for (int i = 0; i < kQ; ++i) {
+      const unsigned src = pull_src(P, n, i);
+      rA += __ldg(fin + (i * N32 + src));
+      rB += __ldg(finB + (i * N32 + src));
+    }
+    sh.rho[slot][0][ry][rx] = rA;
+    sh.rho[slot][1][ry][rx] = rB;
   }
-}
-
-__device__ __forceinline__ void fused_collide(const StepParams &P, const float *__restrict__ fin,
-                                              float *__restrict__ fout, unsigned s, const int xn[3],
-                                              const int yn[3], const int zn[3], float rA, float rB, float ux,
-                                              float uy, float uz, float3 gA, float3 gB) {
-  const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-  const float ugA3 = 3.f * (ux * gA.x + uy * gA.y + uz * gA.z);
-  const float ugB3 = 3.f * (ux * gB.x + uy * gB.y + uz * gB.z);
-  fused_collide_batch<0, 10>(P, fin, fout, s, xn, yn, zn, rA, rB, ux, uy, uz, usq15, gA, gB, ugA3, ugB3);
-  fused_collide_batch<10, kQ>(P, fin, fout, s, xn, yn, zn, rA, rB, ux, uy, uz, usq15, gA, gB, ugA3, ugB3);
 }
 
 template <bool kParticles>
-__global__ void __launch_bounds__(kFusedThreads, 4)
+__global__ void __launch_bounds__(kFusedThreads, 2)
     k_lattice(StepParams P, const float *__restrict__ fin, float *__restrict__ fout, ParticleArrays pa,
-              ParticleForces pf, CellIndex ci, unsigned *err, int tiles_x, long long work) {
-  __shared__ FusedShared sh;
+              ParticleForces pf, CellIndex ci, unsigned *err, int tiles_x, int ntiles, int zlen) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FusedShared &sh = *reinterpret_cast<FusedShared *>(smem_raw);
   const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
-  const long long G = gridDim.x;
-  long long w0 = work * blockIdx.x / G;
-  const long long w1 = work * (blockIdx.x + 1) / G;
-  while (w0 < w1) {
-    const long long tile = w0 / P.nz;
-    const int zs = (int)(w0 - tile * P.nz);
-    const int ze = (int)(zs + (w1 - w0) < P.nz ? zs + (w1 - w0) : P.nz);
-    const int x0 = (int)(tile % tiles_x) * kTX, y0 = (int)(tile / tiles_x) * kTY;
-    const int w = min(kTX, P.nx - x0), h = min(kTY, P.ny - y0);
-    __syncthreads();  // the previous segment's readers of the rings are done
-    fused_fill(P, fin, sh, zs - 1, zs, x0, y0, w, h);
-    fused_fill(P, fin, sh, zs, zs, x0, y0, w, h);
-    for (int z = zs; z < ze; ++z) {
-      fused_fill(P, fin, sh, z + 1, zs, x0, y0, w, h);
-      __syncthreads();
-      if (lx < w && ly < h) {
-        const int gx = x0 + lx, gy = y0 + ly;
-        int xn[3], yn[3], zn[3];
-        xn[0] = gx == 0 ? P.nx - 1 : gx - 1;
-        xn[1] = gx;
-        xn[2] = gx == P.nx - 1 ? 0 : gx + 1;
-        yn[0] = gy == 0 ? P.ny - 1 : gy - 1;
-        yn[1] = gy;
-        yn[2] = gy == P.ny - 1 ? 0 : gy + 1;
-        zn[0] = z == 0 ? P.nz - 1 : z - 1;
-        zn[1] = z;
-        zn[2] = z == P.nz - 1 ? 0 : z + 1;
-        const int sl[3] = {(z - zs) & 3, (z - zs + 1) & 3, (z - zs + 2) & 3};  // planes z-1, z, z+1
-        const int js = (z - zs + 1) % 3;
-        const float rA = sh.rho[sl[1]][0][ly + 1][lx + 1], rB = sh.rho[sl[1]][1][ly + 1][lx + 1];
-        const float jx = sh.j[js][0][ly][lx], jy = sh.j[js][1][ly][lx], jz = sh.j[js][2][ly][lx];
-        float SAx = 0.f, SAy = 0.f, SAz = 0.f, SBx = 0.f, SBy = 0.f, SBz = 0.f;
+  const int tile = blockIdx.x % ntiles;
+  const int zs = (blockIdx.x / ntiles) * zlen;
+  const int ze = min(P.nz, zs + zlen);
+  const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
+  const int w = min(kTX, P.nx - x0), h = min(kTY, P.ny - y0);
+  const unsigned N32 = (unsigned)P.N;
+  float *foutB = fout + (size_t)kQ * N32;
+  float fa[kQ], fb[kQ];  // prefetched populations of the next plane to commit
+  // prologue: densities of plane zs-1, populations of zs, prefetch of zs+1
+  fused_prefetch(P, fin, zs - 1, x0, y0, fa, fb);
+  fused_commit(P, fin, sh, zs - 1, zs, x0, y0, w, h, false, fa, fb);
+  fused_prefetch(P, fin, zs, x0, y0, fa, fb);
+  fused_commit(P, fin, sh, zs, zs, x0, y0, w, h, true, fa, fb);
+  fused_prefetch(P, fin, zs + 1, x0, y0, fa, fb);
+  for (int z = zs; z < ze; ++z) {
+    fused_commit(P, fin, sh, z + 1, zs, x0, y0, w, h, z + 1 < ze, fa, fb);
+    // loads of plane z+2 stay in flight while plane z is collided
+    if (z + 2 <= ze) fused_prefetch(P, fin, z + 2, x0, y0, fa, fb);
+    __syncthreads();
+    if (lx < w && ly < h) {
+      const int gx = x0 + lx, gy = y0 + ly;
+      const int sl[3] = {(z - zs) & 3, (z - zs + 1) & 3, (z - zs + 2) & 3};  // planes z-1, z, z+1
+      const int ps = z & 1;
+      const float rA = sh.rho[sl[1]][0][ly + 1][lx + 1], rB = sh.rho[sl[1]][1][ly + 1][lx + 1];
+      const float jx = sh.j[ps][0][ly][lx], jy = sh.j[ps][1][ly][lx], jz = sh.j[ps][2][ly][lx];
+      float SAx = 0.f, SAy = 0.f, SAz = 0.f, SBx = 0.f, SBy = 0.f, SBz = 0.f;
 #pragma unroll
-        for (int i = 1; i < kQ; ++i) {
-          const int s3 = sl[1 + kCz[i]];
-          const float a = kW[i] * sh.rho[s3][0][ly + 1 + kCy[i]][lx + 1 + kCx[i]];
-          const float b = kW[i] * sh.rho[s3][1][ly + 1 + kCy[i]][lx + 1 + kCx[i]];
-          SAx += kCx[i] * a; SAy += kCy[i] * a; SAz += kCz[i] * a;
-          SBx += kCx[i] * b; SBy += kCy[i] * b; SBz += kCz[i] * b;
-        }
-        float3 gA = make_float3(-P.gAB * rA * SBx, -P.gAB * rA * SBy, -P.gAB * rA * SBz);
-        float3 gB = make_float3(-P.gBA * rB * SAx, -P.gBA * rB * SAy, -P.gBA * rB * SAz);
-        if (kParticles) gather_coupling(P, gx, gy, z, rA, rB, pa, pf, ci, true, gA, gB);
-        const float r = rA + rB;
-        if (!(rA > 0.f) || !(rB > 0.f) || !isfinite(r)) atomicOr(err, isfinite(r) ? kErrNegDensity : kErrNonFinite);
-        const float rinv = 1.f / r;
-        const float ux = (jx + 0.5f * (gA.x + gB.x)) * rinv;
-        const float uy = (jy + 0.5f * (gA.y + gB.y)) * rinv;
-        const float uz = (jz + 0.5f * (gA.z + gB.z)) * rinv;
-        const unsigned s = ((unsigned)z * P.ny + gy) * P.nx + gx;
-        fused_collide(P, fin, fout, s, xn, yn, zn, rA, rB, ux, uy, uz, gA, gB);
+      for (int i = 1; i < kQ; ++i) {
+        const int s3 = sl[1 + kCz[i]];
+        const float a = kW[i] * sh.rho[s3][0][ly + 1 + kCy[i]][lx + 1 + kCx[i]];
+        const float b = kW[i] * sh.rho[s3][1][ly + 1 + kCy[i]][lx + 1 + kCx[i]];
+        SAx += kCx[i] * a; SAy += kCy[i] * a; SAz += kCz[i] * a;
+        SBx += kCx[i] * b; SBy += kCy[i] * b; SBz += kCz[i] * b;
+      }
+      float3 gA = make_float3(-P.gAB * rA * SBx, -P.gAB * rA * SBy, -P.gAB * rA * SBz);
+      float3 gB = make_float3(-P.gBA * rB * SAx, -P.gBA * rB * SAy, -P.gBA * rB * SAz);
+      if (kParticles) gather_coupling(P, gx, gy, z, rA, rB, pa, pf, ci, true, gA, gB);
+      const float r = rA + rB;
+      if (!(rA > 0.f) || !(rB > 0.f) || !isfinite(r)) atomicOr(err, isfinite(r) ? kErrNegDensity : kErrNonFinite);
+      const float rinv = 1.f / r;
+      const float ux = (jx + 0.5f * (gA.x + gB.x)) * rinv;
+      const float uy = (jy + 0.5f * (gA.y + gB.y)) * rinv;
+      const float uz = (jz + 0.5f * (gA.z + gB.z)) * rinv;
+      const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+      const float ugA3 = 3.f * (ux * gA.x + uy * gA.y + uz * gA.z);
+      const float ugB3 = 3.f * (ux * gB.x + uy * gB.y + uz * gB.z);
+      const float om = P.inv_tau, fp = P.force_pref;
+      const unsigned s = ((unsigned)z * P.ny + gy) * P.nx + gx;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
+        const float poly = kW[i] * (1.f + 3.f * cu + 4.5f * cu * cu - usq15);
+        const float cgA = kCx[i] * gA.x + kCy[i] * gA.y + kCz[i] * gA.z;
+        const float cgB = kCx[i] * gB.x + kCy[i] * gB.y + kCz[i] * gB.z;
+        const float dgA = kW[i] * fp * (3.f * cgA + 9.f * cu * cgA - ugA3);
+        const float dgB = kW[i] * fp * (3.f * cgB + 9.f * cu * cgB - ugB3);
+        const float fA = sh.pops[ps][0][i][ly][lx], fB = sh.pops[ps][1][i][ly][lx];
+        fout[i * N32 + s] = fA - om * (fA - rA * poly) + dgA;
+        foutB[i * N32 + s] = fB - om * (fB - rB * poly) + dgB;
       }
     }
-    w0 += ze - zs;
+    __syncthreads();  // plane z's populations and densities are consumed before they are replaced
   }
 }
 
@@ -414,23 +403,29 @@ void launch_collide(const StepParams &P, const float *fin, float *fout, const fl
                     cudaStream_t st) {
   (void)rho;
   const int tiles_x = (P.nx + kTX - 1) / kTX, tiles_y = (P.ny + kTY - 1) / kTY;
-  const long long work = (long long)tiles_x * tiles_y * P.nz;
-  static int grid_cap = 0;  // resident blocks of the persistent kernel (all SMs, full occupancy)
-  if (grid_cap == 0) {
+  const int ntiles = tiles_x * tiles_y;
+  const int smem = (int)sizeof(FusedShared);
+  static int slots = 0;  // resident blocks of the lattice kernel on this device
+  if (slots == 0) {
+    cudaFuncSetAttribute(k_lattice<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_lattice<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lattice<true>, kFusedThreads, 0);
-    grid_cap = sms * (per_sm > 0 ? per_sm : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lattice<true>, kFusedThreads, smem);
+    slots = sms * (per_sm > 0 ? per_sm : 1);
   }
-  // at least ~4 planes per block so the two prologue planes stay a small overhead
-  long long grid = (work + 3) / 4;
-  if (grid > grid_cap) grid = grid_cap;
-  if (grid < 1) grid = 1;
+  // split z into as many chunks as fit next to one another in one wave
+  int chunks = slots / ntiles;
+  if (chunks < 1) chunks = 1;
+  if (chunks > P.nz) chunks = P.nz;
+  const int zlen = (P.nz + chunks - 1) / chunks;
+  chunks = (P.nz + zlen - 1) / zlen;
+  const unsigned grid = (unsigned)ntiles * (unsigned)chunks;
   if (P.np > 0)
-    k_lattice<true><<<(unsigned)grid, kFusedThreads, 0, st>>>(P, fin, fout, pa, pf, ci, err, tiles_x, work);
+    k_lattice<true><<<grid, kFusedThreads, smem, st>>>(P, fin, fout, pa, pf, ci, err, tiles_x, ntiles, zlen);
   else
-    k_lattice<false><<<(unsigned)grid, kFusedThreads, 0, st>>>(P, fin, fout, pa, pf, ci, err, tiles_x, work);
+    k_lattice<false><<<grid, kFusedThreads, smem, st>>>(P, fin, fout, pa, pf, ci, err, tiles_x, ntiles, zlen);
 }
 void launch_fields(const StepParams &P, const float *store, const float *rho, float *rhoA, float *rhoB,
                    float *u, cudaStream_t st) {
