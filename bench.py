@@ -43,9 +43,10 @@ WORKLOADS = {
 
 
 def algorithmic_bytes_per_site() -> int:
-    """Algorithmic bytes per node of the lattice update kernel: both components' 19
-    populations read (pull) and written once, FP32: 2*19*4*2 = 304."""
-    return 2 * 19 * 4 * 2
+    """Algorithmic bytes per node of the collide kernel: both components' 19 populations
+    read (pull) and written once, FP32 (2*19*4*2 = 304), plus the node's two densities of
+    the Shan-Chen stencil (8; the neighbours' come from cache)."""
+    return 2 * 19 * 4 * 2 + 8
 
 
 def measured_hbm_peak():
@@ -249,7 +250,7 @@ def run_cuda(args):
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (N * 152 / 1e9)
                        if N * 152 > 129e6 else "L2-resident lattice (latency regime)"},
-            "roofline": {"bound": "hbm", "kernel": "k_lattice (fused pull-stream + Shan-Chen + coupling gather + BGK/forcing, both components)",
+            "roofline": {"bound": "hbm", "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + BGK/forcing, both components)",
                          "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_site": bps,
                          "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,

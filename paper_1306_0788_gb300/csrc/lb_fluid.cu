@@ -44,6 +44,22 @@ __device__ __forceinline__ void neighbours(const StepParams &P, const Coord &c, 
   zs[2] = c.z == P.nz - 1 ? 0 : c.z + 1;
 }
 
+// f^eq (Eq. feq) and the forcing term (appendix, BGK: G = (1 - 1/2tau)(ug + gu)) folded into
+// the BGK update f* = f - (f - f^eq)/tau + Delta^g for one component.
+__device__ __forceinline__ void collide_component(const StepParams &P, float (&f)[kQ], float rho_c,
+                                                  float ux, float uy, float uz, float gx, float gy, float gz) {
+  const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+  const float ug3 = 3.f * (ux * gx + uy * gy + uz * gz);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
+    const float cg = kCx[i] * gx + kCy[i] * gy + kCz[i] * gz;
+    const float feq = kW[i] * rho_c * (1.f + 3.f * cu + 4.5f * cu * cu - usq15);
+    const float dg = kW[i] * P.force_pref * (3.f * cg + 9.f * cu * cg - ug3);
+    f[i] = f[i] - P.inv_tau * (f[i] - feq) + dg;
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) k_init_equilibrium(StepParams P, const float *__restrict__ rhoA,
                                                              const float *__restrict__ rhoB,
                                                              const float *__restrict__ u, float *__restrict__ store) {
@@ -117,186 +133,60 @@ __global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const float *_
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// The lattice update of one step: pull streaming, densities and momentum, Shan-Chen force
+// The lattice update of one step at one node: pull, densities and momentum, Shan-Chen force
 // (Eq. SCforce with psi = rho, g_AA = g_BB = 0), fluid-side solvation force and momentum
-// return gathered from the particles (Sec. 2), barycentric velocity (Eq.
-// momentum_definition), BGK collision with forcing (appendix) for both components.
-//
-// Each block owns an (x, y) tile of kTX x kTY nodes and marches along a z-range; blocks are
-// numbered z-chunk-major so that all tiles of a chunk march in step.  For plane z+1 the
-// block pulls the 2 x 19 populations of its tile into shared memory (they are collided one
-// plane later without touching DRAM again) and sums them to rho_A, rho_B, j'; it also
-// pulls the one-node halo around the tile, keeping only the densities.  A ring of four
-// density planes gives the Shan-Chen stencil of plane z.  DRAM traffic per node: the
-// populations read once and written once (304 B) plus the halo reads, which hit in L2
-// because the neighbouring tile pulls the same lines in the same plane at the same time.
-constexpr int kTX = 32, kTY = 8, kFusedThreads = kTX * kTY;
-constexpr int kRX = kTX + 2, kRY = kTY + 2;
-
-struct FusedShared {
-  float pops[2][2][kQ][kTY][kTX];  // pulled populations of planes z, z+1: [slot][comp][i][y][x]
-  float rho[4][2][kRY][kRX];       // densities of planes z-1, z, z+1 (+1 being filled), with halo
-  float j[2][3][kTY][kTX];         // j' of the tile, planes z, z+1
-};
-
-struct Neigh {
-  int xn[3], yn[3], zn[3];  // wrapped coordinates r - 1, r, r + 1 per axis
-};
-
-__device__ __forceinline__ Neigh neighbours_of(const StepParams &P, int gx, int gy, int gz) {
-  Neigh n;
-  n.xn[0] = gx == 0 ? P.nx - 1 : gx - 1; n.xn[1] = gx; n.xn[2] = gx == P.nx - 1 ? 0 : gx + 1;
-  n.yn[0] = gy == 0 ? P.ny - 1 : gy - 1; n.yn[1] = gy; n.yn[2] = gy == P.ny - 1 ? 0 : gy + 1;
-  n.zn[0] = gz == 0 ? P.nz - 1 : gz - 1; n.zn[1] = gz; n.zn[2] = gz == P.nz - 1 ? 0 : gz + 1;
-  return n;
-}
-
-__device__ __forceinline__ unsigned pull_src(const StepParams &P, const Neigh &n, int i) {
-  // 32-bit: 19 N < 2^32 is enforced when the context is created
-  return ((unsigned)n.zn[1 - kCz[i]] * P.ny + n.yn[1 - kCy[i]]) * P.nx + n.xn[1 - kCx[i]];
-}
-
-// Pull the 2 x 19 populations of this thread's node of plane p into registers (prefetch).
-__device__ __forceinline__ void fused_prefetch(const StepParams &P, const float *__restrict__ fin, int p, int x0,
-                                               int y0, float (&fa)[kQ], float (&fb)[kQ]) {
-  const unsigned N32 = (unsigned)P.N;
-  const float *finB = fin + (size_t)kQ * N32;
-  const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
-  const Neigh n = neighbours_of(P, wrapi(x0 + lx, P.nx), wrapi(y0 + ly, P.ny), wrapi(p, P.nz));
+// return from the particles (Sec. 2), barycentric velocity (Eq. momentum_definition), BGK
+// collision with forcing for both components, write.
+template <bool kParticles>
+__global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const float *__restrict__ fin,
+                                                    float *__restrict__ fout, const float *__restrict__ rho,
+                                                    ParticleArrays pa, ParticleForces pf, CellIndex ci,
+                                                    unsigned *err) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= P.N) return;
+  const Coord c = site_coord(P, s);
+  int xs[3], ys[3], zs[3];
+  neighbours(P, c, xs, ys, zs);
+  float fA[kQ], fB[kQ];
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const unsigned src = pull_src(P, n, i);
-    fa[i] = __ldg(fin + (i * N32 + src));
-    fb[i] = __ldg(finB + (i * N32 + src));
+    const long long src = pull_source(P, i, xs, ys, zs);
+    fA[i] = __ldg(fin + (long long)i * P.N + src);
+    fB[i] = __ldg(fin + (long long)(kQ + i) * P.N + src);
   }
-}
-
-// Commit plane p: the prefetched populations go to shared memory with their sums rho_A,
-// rho_B, j' (tile nodes); the one-node halo around the tile is pulled and summed (rho only).
-__device__ __forceinline__ void fused_commit(const StepParams &P, const float *__restrict__ fin, FusedShared &sh,
-                                             int p, int zs, int x0, int y0, int w, int h, bool keep_pops,
-                                             const float (&fa)[kQ], const float (&fb)[kQ]) {
-  const int gz = wrapi(p, P.nz);
-  const int slot = (p - zs + 1) & 3;
-  const int ps = p & 1;
-  const unsigned N32 = (unsigned)P.N;
-  const float *finB = fin + (size_t)kQ * N32;
-  const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
-  if (lx < w && ly < h) {
-    float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+  float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      if (keep_pops) {
-        sh.pops[ps][0][i][ly][lx] = fa[i];
-        sh.pops[ps][1][i][ly][lx] = fb[i];
-      }
-      rA += fa[i];
-      rB += fb[i];
-      jx += kCx[i] * (fa[i] + fb[i]);
-      jy += kCy[i] * (fa[i] + fb[i]);
-      jz += kCz[i] * (fa[i] + fb[i]);
-    }
-    sh.rho[slot][0][ly + 1][lx + 1] = rA;
-    sh.rho[slot][1][ly + 1][lx + 1] = rB;
-    sh.j[ps][0][ly][lx] = jx;
-    sh.j[ps][1][ly][lx] = jy;
-    sh.j[ps][2][ly][lx] = jz;
+  for (int i = 0; i < kQ; ++i) {
+    rA += fA[i];
+    rB += fB[i];
+    jx += kCx[i] * (fA[i] + fB[i]);
+    jy += kCy[i] * (fA[i] + fB[i]);
+    jz += kCz[i] * (fA[i] + fB[i]);
   }
-  // halo ring of the (w+2) x (h+2) region: rows 0 and h+1, then columns 0 and w+1
-  const int nrow = w + 2, nhalo = 2 * nrow + 2 * h;
-  for (int k = threadIdx.x; k < nhalo; k += kFusedThreads) {
-    int rx, ry;
-    if (k < 2 * nrow) {
-      ry = k < nrow ? 0 : h + 1;
-      rx = k < nrow ? k : k - nrow;
-    } else {
-      const int c = k - 2 * nrow;
-      rx = c < h ? 0 : w + 1;
-      ry = 1 + (c < h ? c : c - h);
-    }
-    const Neigh n = neighbours_of(P, wrapi(x0 + rx - 1, P.nx), wrapi(y0 + ry - 1, P.ny), gz);
-    float rA = 0.f, rB = 0.f;
+  // S_z = sum_i w_i rho_z(r + c_i) c_i from the density field of this step
+  float SAx = 0.f, SAy = 0.f, SAz = 0.f, SBx = 0.f, SBy = 0.f, SBz = 0.f;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      const unsigned src = pull_src(P, n, i);
-      rA += __ldg(fin + (i * N32 + src));
-      rB += __ldg(finB + (i * N32 + src));
-    }
-    sh.rho[slot][0][ry][rx] = rA;
-    sh.rho[slot][1][ry][rx] = rB;
+  for (int i = 1; i < kQ; ++i) {
+    const long long nb = ((long long)zs[1 + kCz[i]] * P.ny + ys[1 + kCy[i]]) * P.nx + xs[1 + kCx[i]];
+    const float a = kW[i] * __ldg(rho + nb), b = kW[i] * __ldg(rho + P.N + nb);
+    SAx += kCx[i] * a; SAy += kCy[i] * a; SAz += kCz[i] * a;
+    SBx += kCx[i] * b; SBy += kCy[i] * b; SBz += kCz[i] * b;
   }
-}
-
-template <bool kParticles>
-__global__ void __launch_bounds__(kFusedThreads, 2)
-    k_lattice(StepParams P, const float *__restrict__ fin, float *__restrict__ fout, ParticleArrays pa,
-              ParticleForces pf, CellIndex ci, unsigned *err, int tiles_x, int ntiles, int zlen) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  FusedShared &sh = *reinterpret_cast<FusedShared *>(smem_raw);
-  const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
-  const int tile = blockIdx.x % ntiles;
-  const int zs = (blockIdx.x / ntiles) * zlen;
-  const int ze = min(P.nz, zs + zlen);
-  const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
-  const int w = min(kTX, P.nx - x0), h = min(kTY, P.ny - y0);
-  const unsigned N32 = (unsigned)P.N;
-  float *foutB = fout + (size_t)kQ * N32;
-  float fa[kQ], fb[kQ];  // prefetched populations of the next plane to commit
-  // prologue: densities of plane zs-1, populations of zs, prefetch of zs+1
-  fused_prefetch(P, fin, zs - 1, x0, y0, fa, fb);
-  fused_commit(P, fin, sh, zs - 1, zs, x0, y0, w, h, false, fa, fb);
-  fused_prefetch(P, fin, zs, x0, y0, fa, fb);
-  fused_commit(P, fin, sh, zs, zs, x0, y0, w, h, true, fa, fb);
-  fused_prefetch(P, fin, zs + 1, x0, y0, fa, fb);
-  for (int z = zs; z < ze; ++z) {
-    fused_commit(P, fin, sh, z + 1, zs, x0, y0, w, h, z + 1 < ze, fa, fb);
-    // loads of plane z+2 stay in flight while plane z is collided
-    if (z + 2 <= ze) fused_prefetch(P, fin, z + 2, x0, y0, fa, fb);
-    __syncthreads();
-    if (lx < w && ly < h) {
-      const int gx = x0 + lx, gy = y0 + ly;
-      const int sl[3] = {(z - zs) & 3, (z - zs + 1) & 3, (z - zs + 2) & 3};  // planes z-1, z, z+1
-      const int ps = z & 1;
-      const float rA = sh.rho[sl[1]][0][ly + 1][lx + 1], rB = sh.rho[sl[1]][1][ly + 1][lx + 1];
-      const float jx = sh.j[ps][0][ly][lx], jy = sh.j[ps][1][ly][lx], jz = sh.j[ps][2][ly][lx];
-      float SAx = 0.f, SAy = 0.f, SAz = 0.f, SBx = 0.f, SBy = 0.f, SBz = 0.f;
+  float3 gA = make_float3(-P.gAB * rA * SBx, -P.gAB * rA * SBy, -P.gAB * rA * SBz);
+  float3 gB = make_float3(-P.gBA * rB * SAx, -P.gBA * rB * SAy, -P.gBA * rB * SAz);
+  if (kParticles) gather_coupling(P, c.x, c.y, c.z, rA, rB, pa, pf, ci, true, gA, gB);
+  const float r = rA + rB;
+  if (!(rA > 0.f) || !(rB > 0.f) || !isfinite(r)) atomicOr(err, isfinite(r) ? kErrNegDensity : kErrNonFinite);
+  const float rinv = 1.f / r;
+  const float ux = (jx + 0.5f * (gA.x + gB.x)) * rinv;
+  const float uy = (jy + 0.5f * (gA.y + gB.y)) * rinv;
+  const float uz = (jz + 0.5f * (gA.z + gB.z)) * rinv;
+  collide_component(P, fA, rA, ux, uy, uz, gA.x, gA.y, gA.z);
+  collide_component(P, fB, rB, ux, uy, uz, gB.x, gB.y, gB.z);
 #pragma unroll
-      for (int i = 1; i < kQ; ++i) {
-        const int s3 = sl[1 + kCz[i]];
-        const float a = kW[i] * sh.rho[s3][0][ly + 1 + kCy[i]][lx + 1 + kCx[i]];
-        const float b = kW[i] * sh.rho[s3][1][ly + 1 + kCy[i]][lx + 1 + kCx[i]];
-        SAx += kCx[i] * a; SAy += kCy[i] * a; SAz += kCz[i] * a;
-        SBx += kCx[i] * b; SBy += kCy[i] * b; SBz += kCz[i] * b;
-      }
-      float3 gA = make_float3(-P.gAB * rA * SBx, -P.gAB * rA * SBy, -P.gAB * rA * SBz);
-      float3 gB = make_float3(-P.gBA * rB * SAx, -P.gBA * rB * SAy, -P.gBA * rB * SAz);
-      if (kParticles) gather_coupling(P, gx, gy, z, rA, rB, pa, pf, ci, true, gA, gB);
-      const float r = rA + rB;
-      if (!(rA > 0.f) || !(rB > 0.f) || !isfinite(r)) atomicOr(err, isfinite(r) ? kErrNegDensity : kErrNonFinite);
-      const float rinv = 1.f / r;
-      const float ux = (jx + 0.5f * (gA.x + gB.x)) * rinv;
-      const float uy = (jy + 0.5f * (gA.y + gB.y)) * rinv;
-      const float uz = (jz + 0.5f * (gA.z + gB.z)) * rinv;
-      const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-      const float ugA3 = 3.f * (ux * gA.x + uy * gA.y + uz * gA.z);
-      const float ugB3 = 3.f * (ux * gB.x + uy * gB.y + uz * gB.z);
-      const float om = P.inv_tau, fp = P.force_pref;
-      const unsigned s = ((unsigned)z * P.ny + gy) * P.nx + gx;
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) {
-        const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
-        const float poly = kW[i] * (1.f + 3.f * cu + 4.5f * cu * cu - usq15);
-        const float cgA = kCx[i] * gA.x + kCy[i] * gA.y + kCz[i] * gA.z;
-        const float cgB = kCx[i] * gB.x + kCy[i] * gB.y + kCz[i] * gB.z;
-        const float dgA = kW[i] * fp * (3.f * cgA + 9.f * cu * cgA - ugA3);
-        const float dgB = kW[i] * fp * (3.f * cgB + 9.f * cu * cgB - ugB3);
-        const float fA = sh.pops[ps][0][i][ly][lx], fB = sh.pops[ps][1][i][ly][lx];
-        fout[i * N32 + s] = fA - om * (fA - rA * poly) + dgA;
-        foutB[i * N32 + s] = fB - om * (fB - rB * poly) + dgB;
-      }
-    }
-    __syncthreads();  // plane z's populations and densities are consumed before they are replaced
+  for (int i = 0; i < kQ; ++i) {
+    fout[(long long)i * P.N + s] = fA[i];
+    fout[(long long)(kQ + i) * P.N + s] = fB[i];
   }
 }
 
@@ -401,31 +291,10 @@ void launch_moments(const StepParams &P, const float *store, float *rho, float *
 void launch_collide(const StepParams &P, const float *fin, float *fout, const float *rho,
                     const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci, unsigned *err,
                     cudaStream_t st) {
-  (void)rho;
-  const int tiles_x = (P.nx + kTX - 1) / kTX, tiles_y = (P.ny + kTY - 1) / kTY;
-  const int ntiles = tiles_x * tiles_y;
-  const int smem = (int)sizeof(FusedShared);
-  static int slots = 0;  // resident blocks of the lattice kernel on this device
-  if (slots == 0) {
-    cudaFuncSetAttribute(k_lattice<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_lattice<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lattice<true>, kFusedThreads, smem);
-    slots = sms * (per_sm > 0 ? per_sm : 1);
-  }
-  // split z into as many chunks as fit next to one another in one wave
-  int chunks = slots / ntiles;
-  if (chunks < 1) chunks = 1;
-  if (chunks > P.nz) chunks = P.nz;
-  const int zlen = (P.nz + chunks - 1) / chunks;
-  chunks = (P.nz + zlen - 1) / zlen;
-  const unsigned grid = (unsigned)ntiles * (unsigned)chunks;
   if (P.np > 0)
-    k_lattice<true><<<grid, kFusedThreads, smem, st>>>(P, fin, fout, pa, pf, ci, err, tiles_x, ntiles, zlen);
+    k_collide<true><<<grid_for(P.N), kBlock, 0, st>>>(P, fin, fout, rho, pa, pf, ci, err);
   else
-    k_lattice<false><<<grid, kFusedThreads, smem, st>>>(P, fin, fout, pa, pf, ci, err, tiles_x, ntiles, zlen);
+    k_collide<false><<<grid_for(P.N), kBlock, 0, st>>>(P, fin, fout, rho, pa, pf, ci, err);
 }
 void launch_fields(const StepParams &P, const float *store, const float *rho, float *rhoA, float *rhoB,
                    float *u, cudaStream_t st) {

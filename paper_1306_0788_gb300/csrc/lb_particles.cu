@@ -228,107 +228,6 @@ __global__ void __launch_bounds__(kPBlock) k_couple(StepParams P, ParticleArrays
   pf.fsr[p] = make_float4(fsr.x, fsr.y, fsr.z, 0.f);
 }
 
-// The same coupling forces as k_couple, without a dense density pass: one warp per
-// particle pulls the populations of the 4 x 4 x 4 nodes around its cell (the 8 corners and
-// their stencil neighbours), sums them to rho_A, rho_B, j' in shared memory, then 8 lanes
-// evaluate the corners and the warp reduces their trilinear contributions.
-constexpr int kCubeWarps = 4;
-__global__ void __launch_bounds__(32 * kCubeWarps) k_couple_cube(StepParams P, const float *__restrict__ fin,
-                                                                  ParticleArrays pa, CellIndex ci, ParticleForces pf) {
-  __shared__ float cube[kCubeWarps][5][64];  // rho_A, rho_B, jx, jy, jz at node (1+ox) + 4(1+oy) + 16(1+oz)
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int p = blockIdx.x * kCubeWarps + warp;
-  if (p >= P.np) return;  // whole warps exit together
-  const int4 c = pa.cell[p];
-  const unsigned N32 = (unsigned)P.N;
-#pragma unroll 1
-  for (int k = lane; k < 64; k += 32) {
-    const int gx = wrapi(c.x + (k & 3) - 1, P.nx), gy = wrapi(c.y + ((k >> 2) & 3) - 1, P.ny);
-    const int gz = wrapi(c.z + (k >> 4) - 1, P.nz);
-    const int xn[3] = {gx == 0 ? P.nx - 1 : gx - 1, gx, gx == P.nx - 1 ? 0 : gx + 1};
-    const int yn[3] = {gy == 0 ? P.ny - 1 : gy - 1, gy, gy == P.ny - 1 ? 0 : gy + 1};
-    const int zn[3] = {gz == 0 ? P.nz - 1 : gz - 1, gz, gz == P.nz - 1 ? 0 : gz + 1};
-    float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      const unsigned src = ((unsigned)zn[1 - kCz[i]] * P.ny + yn[1 - kCy[i]]) * P.nx + xn[1 - kCx[i]];
-      const float a = __ldg(fin + (i * N32 + src));
-      const float b = __ldg(fin + (size_t)kQ * N32 + (i * N32 + src));
-      rA += a;
-      rB += b;
-      jx += kCx[i] * (a + b);
-      jy += kCy[i] * (a + b);
-      jz += kCz[i] * (a + b);
-    }
-    cube[warp][0][k] = rA;
-    cube[warp][1][k] = rB;
-    cube[warp][2][k] = jx;
-    cube[warp][3][k] = jy;
-    cube[warp][4][k] = jz;
-  }
-  __syncwarp();
-  const float4 fr = pa.frac[p];
-  const TypeParams &T = P.types[c.w];
-  float3 up = make_float3(0.f, 0.f, 0.f), gA = up, gB = up, fsr = up;
-  if (lane < 8) {
-    const int ox = lane & 1, oy = (lane >> 1) & 1, oz = (lane >> 2) & 1;
-    const int X = c.x + ox == P.nx ? 0 : c.x + ox;
-    const int Y = c.y + oy == P.ny ? 0 : c.y + oy;
-    const int Z = c.z + oz == P.nz ? 0 : c.z + oz;
-    const int k0 = (1 + ox) + 4 * (1 + oy) + 16 * (1 + oz);
-    const float rA = cube[warp][0][k0], rB = cube[warp][1][k0];
-    float3 SA = make_float3(0.f, 0.f, 0.f), SB = SA;
-#pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-      const int kn = k0 + kCx[i] + 4 * kCy[i] + 16 * kCz[i];
-      const float a = kW[i] * cube[warp][0][kn], b = kW[i] * cube[warp][1][kn];
-      SA.x += kCx[i] * a; SA.y += kCy[i] * a; SA.z += kCz[i] * a;
-      SB.x += kCx[i] * b; SB.y += kCy[i] * b; SB.z += kCz[i] * b;
-    }
-    float3 fA = make_float3(-P.gAB * rA * SB.x, -P.gAB * rA * SB.y, -P.gAB * rA * SB.z);
-    float3 fB = make_float3(-P.gBA * rB * SA.x, -P.gBA * rB * SA.y, -P.gBA * rB * SA.z);
-    gather_coupling(P, X, Y, Z, rA, rB, pa, pf, ci, false, fA, fB);
-    const float rinv = 1.f / (rA + rB);
-    const float w = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
-    up.x = w * (cube[warp][2][k0] + 0.5f * (fA.x + fB.x)) * rinv;
-    up.y = w * (cube[warp][3][k0] + 0.5f * (fA.y + fB.y)) * rinv;
-    up.z = w * (cube[warp][4][k0] + 0.5f * (fA.z + fB.z)) * rinv;
-    gA = make_float3(w * SA.x, w * SA.y, w * SA.z);
-    gB = make_float3(w * SB.x, w * SB.y, w * SB.z);
-    if (T.lam[0] != 0.f || T.lam[1] != 0.f) {
-      const float3 geo = fs_geometry(fr.x - ox, fr.y - oy, fr.z - oz);
-      const float a = T.lam[0] * rA + T.lam[1] * rB;
-      fsr = make_float3(a * geo.x, a * geo.y, a * geo.z);
-    }
-  }
-  // reduce the 8 corner contributions in corner order 0..7 (lanes 8..31 hold zeros)
-#pragma unroll
-  for (int o = 1; o < 8; o <<= 1) {
-    up.x += __shfl_xor_sync(0xffffffffu, up.x, o); up.y += __shfl_xor_sync(0xffffffffu, up.y, o);
-    up.z += __shfl_xor_sync(0xffffffffu, up.z, o);
-    gA.x += __shfl_xor_sync(0xffffffffu, gA.x, o); gA.y += __shfl_xor_sync(0xffffffffu, gA.y, o);
-    gA.z += __shfl_xor_sync(0xffffffffu, gA.z, o);
-    gB.x += __shfl_xor_sync(0xffffffffu, gB.x, o); gB.y += __shfl_xor_sync(0xffffffffu, gB.y, o);
-    gB.z += __shfl_xor_sync(0xffffffffu, gB.z, o);
-    fsr.x += __shfl_xor_sync(0xffffffffu, fsr.x, o); fsr.y += __shfl_xor_sync(0xffffffffu, fsr.y, o);
-    fsr.z += __shfl_xor_sync(0xffffffffu, fsr.z, o);
-  }
-  if (lane == 0) {
-    const float4 v = pa.vel[p];
-    float3 R = make_float3(0.f, 0.f, 0.f);
-    if (T.noise_amp > 0.f) {
-      const float3 nn = particle_normals(P.seed, P.step, (unsigned)pa.pid[p]);
-      R = make_float3(T.noise_amp * nn.x, T.noise_amp * nn.y, T.noise_amp * nn.z);
-    }
-    pf.fric[p] = make_float4(-T.gamma * (v.x - up.x) + R.x, -T.gamma * (v.y - up.y) + R.y,
-                             -T.gamma * (v.z - up.z) + R.z, 0.f);
-    const float kA = -T.kappa[0] / kCs2, kB = -T.kappa[1] / kCs2;
-    pf.psA[p] = make_float4(kA * gA.x, kA * gA.y, kA * gA.z, 0.f);
-    pf.psB[p] = make_float4(kB * gB.x, kB * gB.y, kB * gB.z, 0.f);
-    pf.fsr[p] = make_float4(fsr.x, fsr.y, fsr.z, 0.f);
-  }
-}
-
 __device__ __forceinline__ int min_image_cells(int d, int n) {
   d = wrapi(d, n);
   return 2 * d > n ? d - n : d;
@@ -511,10 +410,6 @@ void launch_permute(int np, const int *perm, const ParticleArrays &src, const Pa
 void launch_couple(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho, const float *jp,
                    const ParticleForces &pf, cudaStream_t st) {
   k_couple<<<pgrid(P.np), kPBlock, 0, st>>>(P, pa, ci, rho, jp, pf);
-}
-void launch_couple_cube(const StepParams &P, const float *fin, const ParticleArrays &pa, CellIndex ci,
-                        const ParticleForces &pf, cudaStream_t st) {
-  k_couple_cube<<<(unsigned)((P.np + kCubeWarps - 1) / kCubeWarps), 32 * kCubeWarps, 0, st>>>(P, fin, pa, ci, pf);
 }
 void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const int *bond_start,
                   const int *bond_other, const int *slot_of_id, const ParticleForces &pf, unsigned *err,

@@ -459,19 +459,14 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
     float *fout = c->pop[1 - c->cur];
     int r;
     if (P.np > 0 && (r = sort_particles(c))) return r;
+    // densities (and j' for the particle coupling) of this step's populations
+    launch_moments(P, fin, c->rho, P.np > 0 ? c->jp : nullptr, c->st);
+    if ((r = launched(c, "moments"))) return r;
     if (P.np > 0) {
-      // dense particles: one density pass over the lattice is cheaper than a node cube per particle
-      if ((long long)P.np * 64 > P.N / 2) {
-        launch_moments(P, fin, c->rho, c->jp, c->st);
-        launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
-        if ((r = launched(c, "moments + couple", 2))) return r;
-      } else {
-        launch_couple_cube(P, fin, c->pa[c->pcur], ci, c->pf, c->st);
-        if ((r = launched(c, "couple"))) return r;
-      }
+      launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
       launch_pairs(P, c->pa[c->pcur], ci, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf,
                    c->err, c->st);
-      if ((r = launched(c, "pair forces"))) return r;
+      if ((r = launched(c, "particle forces", 2))) return r;
     }
     if (c->prof) {
       if (c->ev_used + 2 > c->ev.size()) {

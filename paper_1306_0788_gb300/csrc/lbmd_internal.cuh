@@ -217,8 +217,6 @@ void launch_permute(int np, const int *perm, const ParticleArrays &src, const Pa
                     int *slot_of_id, cudaStream_t st);
 void launch_couple(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho,
                    const float *jp, const ParticleForces &pf, cudaStream_t st);
-void launch_couple_cube(const StepParams &P, const float *fin, const ParticleArrays &pa, CellIndex ci,
-                        const ParticleForces &pf, cudaStream_t st);
 void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const int *bond_start,
                   const int *bond_other, const int *slot_of_id, const ParticleForces &pf, unsigned *err,
                   cudaStream_t st);
