@@ -29,15 +29,22 @@ METRIC = "coupled 2-comp D3Q19 MLUPS & HBM-roofline %; replica p50/p99 latency"
 UNIT = "MLUPS"
 HBM_FALLBACK_GBS = 6800.0
 
-# Bulk coexistence of F_bulk (Eq. fbulk) for g = 1.68 with rho_A + rho_B = 2:
-# log(rho_hi / rho_lo) = g (rho_hi - rho_lo)  ->  rho_hi = 1.9103, rho_lo = 0.0897.
-G_COUPLING = 1.68
-RHO_HI, RHO_LO = 1.9103, 0.0897
+# The slab/droplet workload uses the density scale of the paper's ferrofluid example (Sec. 4.5):
+# mean density 78.4 per component with g = 0.0214 (g rho = 1.68).  Bulk coexistence of F_bulk
+# (Eq. fbulk) at g rho = 1.68 with rho_A + rho_B = 2 rho: log(rho_hi / rho_lo) = g (rho_hi - rho_lo)
+# -> rho_hi / rho = 1.9103, rho_lo / rho = 0.0897.
+RHO_SCALE = 78.4
+G_COUPLING = 0.0214
+RHO_HI, RHO_LO = 1.9103 * RHO_SCALE, 0.0897 * RHO_SCALE
+# The 32^3 noise workload keeps the configuration's own densities 1 +- 0.01 with g = 1.68.
+G_NOISE = 1.68
+PARTICLE_MASS = 200.0
 
 WORKLOADS = {
     # name: (edge, particles, description)
     "slab_droplets_256": (256, 20000, "256^3 two-component LB FP32, flat slab + 8 droplets (R 8-32), "
-                                      "2e4 solvation-coupled point particles (kappa_A=-0.05, kappa_B=-0.1), WCA"),
+                                      "2e4 solvation-coupled point particles (kappa_A=-0.001, kappa_B=-0.002, gamma=1, "
+                                      "m=200, kT=0.01), WCA, mean density 78.4 per component, g=0.0214"),
     "noise_32": (32, 64, "32^3 two-component LB FP32, rho=1+-0.01, 64 friction-coupled particles, WCA"),
 }
 
@@ -128,14 +135,16 @@ def build_workload(name: str, seed: int, edge_override: int = 0):
     if name == "slab_droplets_256":
         rA, rB, drops = inputs.slab_and_droplets(dims, RHO_HI, RHO_LO, n_drops=8, r_min=edge / 32,
                                                  r_max=edge / 8, width=4.0, seed=seed)
-        types = [(-0.05, -0.1, 0.0, 0.0, 1.0, 1.0)]
-        kT = 1e-4
+        # mass 200: gamma dt / m = 0.005 << 1 (Sec. 3) and WCA contacts stay inside the
+        # stability range of the explicit integrator at dt = 1
+        types = [(-0.001, -0.002, 0.0, 0.0, 1.0, PARTICLE_MASS)]
+        kT, g = 0.01, G_COUPLING
     else:
         rA, rB = inputs.uniform_noise(dims, 1.0, 0.01, seed=seed)
         types = [(0.0, 0.0, 0.0, 0.0, 1.0, 1.0)]
-        kT = 1e-4
+        kT, g = 1e-4, G_NOISE
     x = inputs.random_particles(npart, dims, 2 ** (1 / 6), seed=seed + 1)
-    return dims, rA.astype(np.float32), rB.astype(np.float32), x, types, kT
+    return dims, rA.astype(np.float32), rB.astype(np.float32), x, types, kT, g
 
 
 def run_cuda(args):
@@ -155,10 +164,10 @@ def run_cuda(args):
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
 
-    dims, rA, rB, x, types, kT = build_workload(args.workload, seed=1234 + rank, edge_override=args.edge)
+    dims, rA, rB, x, types, kT, g_ab = build_workload(args.workload, seed=1234 + rank, edge_override=args.edge)
     npart = len(x)
     N = dims[0] * dims[1] * dims[2]
-    prm = L.params(dims, tau_r=1.0, g_AB=G_COUPLING, kT=kT, seed=42 + rank)
+    prm = L.params(dims, tau_r=1.0, g_AB=g_ab, kT=kT, seed=42 + rank)
     ctx, _ = L.lbmd_create(prm, stream)
     L.lbmd_set_types(ctx, [L.lbmd_ptype(*t) for t in types], [L.lbmd_pair(0, 0, 1.0, 1.0)])
     L.lbmd_init_fluid(ctx, rA, rB)
@@ -246,7 +255,7 @@ def run_cuda(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload + ("" if not args.edge else "@%d" % args.edge),
                        "description": WORKLOADS[args.workload][2],
-                       "lattice": list(dims), "particles": npart, "tau_r": 1.0, "g_AB": G_COUPLING, "kT": kT,
+                       "lattice": list(dims), "particles": npart, "tau_r": 1.0, "g_AB": g_ab, "kT": kT,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (N * 152 / 1e9)
                        if N * 152 > 129e6 else "L2-resident lattice (latency regime)"},
@@ -276,13 +285,13 @@ def oracle_sample(workload: str, edge: int, seed: int):
     if workload == "slab_droplets_256":
         rA, rB, _ = inputs.slab_and_droplets(dims, RHO_HI, RHO_LO, n_drops=1, r_min=edge / 8, r_max=edge / 8,
                                              width=4.0, seed=seed)
-        kap = np.array([[-0.05, -0.1]])
+        kap, kT, g, m = np.array([[-0.001, -0.002]]), 0.01, G_COUPLING, PARTICLE_MASS
     else:
         rA, rB = inputs.uniform_noise(dims, 1.0, 0.01, seed=seed)
-        kap = np.zeros((1, 2))
+        kap, kT, g, m = np.zeros((1, 2)), 1e-4, G_NOISE, 1.0
     x = inputs.random_particles(n, dims, 2 ** (1 / 6), seed=seed + 1)
-    s = oracle.System(dims=dims, tau_r=1.0, g_AB=G_COUPLING, g_BA=G_COUPLING, kT=1e-4, seed=42,
-                      kappa=kap, lam=np.zeros((1, 2)), gamma=np.ones(1), mass=np.ones(1),
+    s = oracle.System(dims=dims, tau_r=1.0, g_AB=g, g_BA=g, kT=kT, seed=42,
+                      kappa=kap, lam=np.zeros((1, 2)), gamma=np.ones(1), mass=np.array([m]),
                       wca_eps=np.ones((1, 1)), wca_sig=np.ones((1, 1)), type=np.zeros(n, dtype=np.int32),
                       q=np.zeros(n))
     f = oracle.init_equilibrium(rA.astype(np.float32).astype(np.float64), rB.astype(np.float32).astype(np.float64))
