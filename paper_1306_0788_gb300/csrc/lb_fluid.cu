@@ -44,6 +44,31 @@ __device__ __forceinline__ void neighbours(const StepParams &P, const Coord &c, 
   zs[2] = c.z == P.nz - 1 ? 0 : c.z + 1;
 }
 
+// Periodic neighbour offsets of site s: d[a][0] is the offset to coordinate a - 1, d[a][1] to a + 1
+// (wrap-aware), so the site r + c is s + d[0][c_x] + d[1][c_y] + d[2][c_z] in 32-bit arithmetic
+// (19 N < 2^32 is enforced when a context is created).
+struct NOff {
+  int m[3], p[3];  // offsets to the -1 and +1 neighbour along x, y, z
+};
+
+__device__ __forceinline__ NOff neighbour_offsets(const StepParams &P, const Coord &c) {
+  NOff o;
+  const int nxny = P.nx * P.ny;
+  o.m[0] = c.x == 0 ? P.nx - 1 : -1;
+  o.p[0] = c.x == P.nx - 1 ? -(P.nx - 1) : 1;
+  o.m[1] = c.y == 0 ? (P.ny - 1) * P.nx : -P.nx;
+  o.p[1] = c.y == P.ny - 1 ? -(P.ny - 1) * P.nx : P.nx;
+  o.m[2] = c.z == 0 ? (P.nz - 1) * nxny : -nxny;
+  o.p[2] = c.z == P.nz - 1 ? -(P.nz - 1) * nxny : nxny;
+  return o;
+}
+
+// offset of r + (cx, cy, cz) relative to r, each component in {-1, 0, 1}
+__device__ __forceinline__ int shift(const NOff &o, int cx, int cy, int cz) {
+  return (cx < 0 ? o.m[0] : cx > 0 ? o.p[0] : 0) + (cy < 0 ? o.m[1] : cy > 0 ? o.p[1] : 0) +
+         (cz < 0 ? o.m[2] : cz > 0 ? o.p[2] : 0);
+}
+
 // f^eq (Eq. feq) and the forcing term (appendix, BGK: G = (1 - 1/2tau)(ug + gu)) folded into
 // the BGK update f* = f - (f - f^eq)/tau + Delta^g for one component.
 __device__ __forceinline__ void collide_component(const StepParams &P, float (&f)[kQ], float rho_c,
@@ -110,14 +135,15 @@ __global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const float *_
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.N) return;
   const Coord c = site_coord(P, s);
-  int xs[3], ys[3], zs[3];
-  neighbours(P, c, xs, ys, zs);
+  const NOff o = neighbour_offsets(P, c);
+  const unsigned N32 = (unsigned)P.N, s32 = (unsigned)s;
+  const float *finB = fin + (size_t)kQ * N32;
   float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const long long src = pull_source(P, i, xs, ys, zs);
-    const float a = __ldg(fin + (long long)i * P.N + src);
-    const float b = __ldg(fin + (long long)(kQ + i) * P.N + src);
+    const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
+    const float a = __ldg(fin + src);
+    const float b = __ldg(finB + src);
     rA += a;
     rB += b;
     jx += kCx[i] * (a + b);
@@ -145,14 +171,15 @@ __global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const float
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.N) return;
   const Coord c = site_coord(P, s);
-  int xs[3], ys[3], zs[3];
-  neighbours(P, c, xs, ys, zs);
+  const NOff o = neighbour_offsets(P, c);
+  const unsigned N32 = (unsigned)P.N, s32 = (unsigned)s;
+  const float *finB = fin + (size_t)kQ * N32;
   float fA[kQ], fB[kQ];
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const long long src = pull_source(P, i, xs, ys, zs);
-    fA[i] = __ldg(fin + (long long)i * P.N + src);
-    fB[i] = __ldg(fin + (long long)(kQ + i) * P.N + src);
+    const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
+    fA[i] = __ldg(fin + src);
+    fB[i] = __ldg(finB + src);
   }
   float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -164,11 +191,12 @@ __global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const float
     jz += kCz[i] * (fA[i] + fB[i]);
   }
   // S_z = sum_i w_i rho_z(r + c_i) c_i from the density field of this step
+  const float *rhoB = rho + N32;
   float SAx = 0.f, SAy = 0.f, SAz = 0.f, SBx = 0.f, SBy = 0.f, SBz = 0.f;
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
-    const long long nb = ((long long)zs[1 + kCz[i]] * P.ny + ys[1 + kCy[i]]) * P.nx + xs[1 + kCx[i]];
-    const float a = kW[i] * __ldg(rho + nb), b = kW[i] * __ldg(rho + P.N + nb);
+    const unsigned nb = (unsigned)((int)s32 + shift(o, kCx[i], kCy[i], kCz[i]));
+    const float a = kW[i] * __ldg(rho + nb), b = kW[i] * __ldg(rhoB + nb);
     SAx += kCx[i] * a; SAy += kCy[i] * a; SAz += kCz[i] * a;
     SBx += kCx[i] * b; SBy += kCy[i] * b; SBz += kCz[i] * b;
   }
@@ -183,10 +211,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const float
   const float uz = (jz + 0.5f * (gA.z + gB.z)) * rinv;
   collide_component(P, fA, rA, ux, uy, uz, gA.x, gA.y, gA.z);
   collide_component(P, fB, rB, ux, uy, uz, gB.x, gB.y, gB.z);
+  float *foutB = fout + (size_t)kQ * N32;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    fout[(long long)i * P.N + s] = fA[i];
-    fout[(long long)(kQ + i) * P.N + s] = fB[i];
+    fout[i * N32 + s32] = fA[i];
+    foutB[i * N32 + s32] = fB[i];
   }
 }
 
