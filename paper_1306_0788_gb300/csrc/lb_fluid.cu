@@ -69,22 +69,6 @@ __device__ __forceinline__ int shift(const NOff &o, int cx, int cy, int cz) {
          (cz < 0 ? o.m[2] : cz > 0 ? o.p[2] : 0);
 }
 
-// f^eq (Eq. feq) and the forcing term (appendix, BGK: G = (1 - 1/2tau)(ug + gu)) folded into
-// the BGK update f* = f - (f - f^eq)/tau + Delta^g for one component.
-__device__ __forceinline__ void collide_component(const StepParams &P, float (&f)[kQ], float rho_c,
-                                                  float ux, float uy, float uz, float gx, float gy, float gz) {
-  const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-  const float ug3 = 3.f * (ux * gx + uy * gy + uz * gz);
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
-    const float cg = kCx[i] * gx + kCy[i] * gy + kCz[i] * gz;
-    const float feq = kW[i] * rho_c * (1.f + 3.f * cu + 4.5f * cu * cu - usq15);
-    const float dg = kW[i] * P.force_pref * (3.f * cg + 9.f * cu * cg - ug3);
-    f[i] = f[i] - P.inv_tau * (f[i] - feq) + dg;
-  }
-}
-
 __global__ void __launch_bounds__(kBlock) k_init_equilibrium(StepParams P, const float *__restrict__ rhoA,
                                                              const float *__restrict__ rhoB,
                                                              const float *__restrict__ u, float *__restrict__ store) {
@@ -129,7 +113,8 @@ __global__ void __launch_bounds__(kBlock) k_unstream(StepParams P, const float *
     post[(long long)i * P.N + s] = store[((long long)comp * kQ + i) * P.N + pull_source(P, i, xs, ys, zs)];
 }
 
-// Densities rho_z = sum_i f_zi (appendix, zeroth mode) and j' = sum_z sum_i f_zi c_i.
+// Densities rho_z = sum_i f_zi (appendix, zeroth mode), stored interleaved (rho_A, rho_B) per
+// site, and j' = sum_z sum_i f_zi c_i.
 __global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const float *__restrict__ fin,
                                                     float *__restrict__ rho, float *__restrict__ jp) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,8 +135,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const float *_
     jy += kCy[i] * (a + b);
     jz += kCz[i] * (a + b);
   }
-  rho[s] = rA;
-  rho[P.N + s] = rB;
+  reinterpret_cast<float2 *>(rho)[s] = make_float2(rA, rB);
   if (jp) {
     jp[s] = jx;
     jp[P.N + s] = jy;
@@ -191,12 +175,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const float
     jz += kCz[i] * (fA[i] + fB[i]);
   }
   // S_z = sum_i w_i rho_z(r + c_i) c_i from the density field of this step
-  const float *rhoB = rho + N32;
+  const float2 *rho2 = reinterpret_cast<const float2 *>(rho);
   float SAx = 0.f, SAy = 0.f, SAz = 0.f, SBx = 0.f, SBy = 0.f, SBz = 0.f;
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const unsigned nb = (unsigned)((int)s32 + shift(o, kCx[i], kCy[i], kCz[i]));
-    const float a = kW[i] * __ldg(rho + nb), b = kW[i] * __ldg(rhoB + nb);
+    const float2 r2 = __ldg(rho2 + nb);
+    const float a = kW[i] * r2.x, b = kW[i] * r2.y;
     SAx += kCx[i] * a; SAy += kCy[i] * a; SAz += kCz[i] * a;
     SBx += kCx[i] * b; SBy += kCy[i] * b; SBz += kCz[i] * b;
   }
@@ -209,8 +194,33 @@ __global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const float
   const float ux = (jx + 0.5f * (gA.x + gB.x)) * rinv;
   const float uy = (jy + 0.5f * (gA.y + gB.y)) * rinv;
   const float uz = (jz + 0.5f * (gA.z + gB.z)) * rinv;
-  collide_component(P, fA, rA, ux, uy, uz, gA.x, gA.y, gA.z);
-  collide_component(P, fB, rB, ux, uy, uz, gB.x, gB.y, gB.z);
+  // BGK + forcing, f* = (1 - 1/tau) f + (1/tau) f^eq + Delta^g, per pair of opposite directions
+  // (c_j = -c_i): f^eq and Delta^g split into parts even and odd in c.
+  {
+    const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float ugA3 = 3.f * (ux * gA.x + uy * gA.y + uz * gA.z);
+    const float ugB3 = 3.f * (ux * gB.x + uy * gB.y + uz * gB.z);
+    const float om = P.inv_tau, om1 = 1.f - om, fp = P.force_pref;
+    const float aA = om * rA, aB = om * rB;
+    fA[0] = om1 * fA[0] + aA * kW[0] * (1.f - usq15) - kW[0] * fp * ugA3;
+    fB[0] = om1 * fB[0] + aB * kW[0] * (1.f - usq15) - kW[0] * fp * ugB3;
+#pragma unroll
+    for (int i = 1; i < kQ; i += 2) {
+      const int j = i + 1;
+      const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
+      const float cgA = kCx[i] * gA.x + kCy[i] * gA.y + kCz[i] * gA.z;
+      const float cgB = kCx[i] * gB.x + kCy[i] * gB.y + kCz[i] * gB.z;
+      const float sym = kW[i] * (1.f + 4.5f * cu * cu - usq15), anti = 3.f * kW[i] * cu;
+      const float wf = kW[i] * fp;
+      const float symA = wf * (9.f * cu * cgA - ugA3), antiA = 3.f * wf * cgA;
+      const float symB = wf * (9.f * cu * cgB - ugB3), antiB = 3.f * wf * cgB;
+      const float fAi = fA[i], fAj = fA[j], fBi = fB[i], fBj = fB[j];
+      fA[i] = om1 * fAi + aA * (sym + anti) + symA + antiA;
+      fA[j] = om1 * fAj + aA * (sym - anti) + symA - antiA;
+      fB[i] = om1 * fBi + aB * (sym + anti) + symB + antiB;
+      fB[j] = om1 * fBj + aB * (sym - anti) + symB - antiB;
+    }
+  }
   float *foutB = fout + (size_t)kQ * N32;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
@@ -235,12 +245,13 @@ __global__ void __launch_bounds__(kBlock) k_fields(StepParams P, const float *__
     const float a = store[(long long)i * P.N + src] + store[(long long)(kQ + i) * P.N + src];
     jx += kCx[i] * a; jy += kCy[i] * a; jz += kCz[i] * a;
   }
-  const float rA = rho[s], rB = rho[P.N + s];
+  const float2 *rho2 = reinterpret_cast<const float2 *>(rho);
+  const float rA = rho2[s].x, rB = rho2[s].y;
   float SAx = 0.f, SAy = 0.f, SAz = 0.f, SBx = 0.f, SBy = 0.f, SBz = 0.f;
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const long long nb = ((long long)zs[1 + kCz[i]] * P.ny + ys[1 + kCy[i]]) * P.nx + xs[1 + kCx[i]];
-    const float a = kW[i] * rho[nb], b = kW[i] * rho[P.N + nb];
+    const float a = kW[i] * rho2[nb].x, b = kW[i] * rho2[nb].y;
     SAx += kCx[i] * a; SAy += kCy[i] * a; SAz += kCz[i] * a;
     SBx += kCx[i] * b; SBy += kCy[i] * b; SBz += kCz[i] * b;
   }

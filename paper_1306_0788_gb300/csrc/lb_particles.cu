@@ -163,15 +163,17 @@ struct NodeState {
 __device__ __forceinline__ NodeState node_state(const StepParams &P, const float *__restrict__ rho, int x, int y,
                                                 int z) {
   NodeState n;
+  const float2 *rho2 = reinterpret_cast<const float2 *>(rho);  // interleaved (rho_A, rho_B)
   const long long s = site_index(P, x, y, z);
-  n.rA = __ldg(rho + s);
-  n.rB = __ldg(rho + P.N + s);
+  n.rA = __ldg(rho2 + s).x;
+  n.rB = __ldg(rho2 + s).y;
   n.SA = make_float3(0.f, 0.f, 0.f);
   n.SB = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const long long nb = site_index(P, wrapi(x + kCx[i], P.nx), wrapi(y + kCy[i], P.ny), wrapi(z + kCz[i], P.nz));
-    const float a = kW[i] * __ldg(rho + nb), b = kW[i] * __ldg(rho + P.N + nb);
+    const float2 r2 = __ldg(rho2 + nb);
+    const float a = kW[i] * r2.x, b = kW[i] * r2.y;
     n.SA.x += kCx[i] * a; n.SA.y += kCy[i] * a; n.SA.z += kCz[i] * a;
     n.SB.x += kCx[i] * b; n.SB.y += kCy[i] * b; n.SB.z += kCz[i] * b;
   }

@@ -17,7 +17,7 @@ struct lbmd_ctx {
   StepParams P{};
   float *pop[2] = {nullptr, nullptr};
   int cur = 0;
-  float *rho = nullptr;  // [2][N]
+  float *rho = nullptr;  // [N][2] interleaved rho_A, rho_B
   float *jp = nullptr;   // [3][N]
   // particles
   int np = 0, cap = 0;
