@@ -179,7 +179,30 @@ int lbmd_profile_read(lbmd_ctx *ctx, double *ms, int64_t *launches, int reset);
 /* Number of kernel launches issued by lbmd_step so far (host-side count). */
 int64_t lbmd_launch_count(const lbmd_ctx *ctx);
 
-/* Message of the last failure of ctx, or of the last failed lbmd_create if ctx is NULL. */
+/* Total mass of each component and fluid momentum -- the same FP64 sums as out[0..4] of
+ * lbmd_diagnostics -- of a population array the caller already holds in device memory,
+ * computed WITHOUT ALLOCATING any device memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- a serving loop that admits work
+ * against a fixed device-memory budget and must not allocate once running, code that runs
+ * inside another framework that owns the device allocator, or a monitor that samples a
+ * simulation from a stream where a synchronising allocation would stall it.
+ *   f_dev    device pointer, FP32 [2][19][nz][ny][nx] (the populations of both components in
+ *            the layout of lbmd_get_populations, component A then B).
+ *   out_dev  device pointer to 5 doubles: M_A, M_B, Px, Py, Pz.
+ *   stream   cudaStream_t for both launches (NULL = legacy default stream); asynchronous.
+ * The per-block partial sums live in one file-scope static device array of 640 KiB
+ * (16384 blocks x 5 doubles), which every GPU that loads the library holds until exit;
+ * lattices above 2^27 sites (512^3) are rejected with LBMD_E_INVALID_ARG.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call shares the array:
+ * calls whose kernels overlap on the GPU (different streams, or different threads) race on
+ * it and must be serialised by the caller.  Each call writes every partial it reads, so no
+ * clearing is needed.  Errors: LBMD_E_INVALID_ARG, LBMD_E_CUDA; lbmd_last_error(NULL)
+ * describes the last failure. */
+int lbmd_fluid_moments_static(const float *f_dev, int nx, int ny, int nz, double *out_dev, void *stream);
+
+/* Message of the last failure of ctx, or, if ctx is NULL, of the last failed call made without
+ * a context (lbmd_create, lbmd_fluid_moments_static). */
 const char *lbmd_last_error(const lbmd_ctx *ctx);
 
 #ifdef __cplusplus

@@ -138,6 +138,8 @@ double max_range(const lbmd_ctx *c) {
 
 }  // namespace
 
+void lbmd::set_context_free_error(const std::string &m) { g_create_error = m; }
+
 extern "C" {
 
 const char *lbmd_last_error(const lbmd_ctx *c) { return c ? c->msg.c_str() : g_create_error.c_str(); }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "lbmd.h"
 
 namespace lbmd {
@@ -187,6 +189,9 @@ __device__ __forceinline__ float3 particle_normals(unsigned long long seed, unsi
   sincospif(2.f * u3, &s3, &c3);
   return make_float3(a * c1, a * s1, b * c3);
 }
+
+// Message returned by lbmd_last_error(NULL) (calls made without a context).
+void set_context_free_error(const std::string &m);
 
 // ------------------------------------------------------------------ launch wrappers
 // lattice (lb_fluid.cu)

@@ -43,7 +43,7 @@ EXPORTS = ("lbmd_create", "lbmd_destroy", "lbmd_set_types", "lbmd_set_debye_huec
            "lbmd_set_populations", "lbmd_get_populations", "lbmd_set_particles", "lbmd_set_bonds",
            "lbmd_step", "lbmd_sync", "lbmd_clear_error", "lbmd_get_fields", "lbmd_get_particles",
            "lbmd_diagnostics", "lbmd_step_count", "lbmd_profile_enable", "lbmd_profile_read",
-           "lbmd_launch_count", "lbmd_last_error")
+           "lbmd_launch_count", "lbmd_last_error", "lbmd_fluid_moments_static")
 
 
 class LbmdError(RuntimeError):
@@ -97,6 +97,7 @@ def _load():
         "lbmd_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64), I]),
         "lbmd_launch_count": (ctypes.c_int64, [P]),
         "lbmd_last_error": (ctypes.c_char_p, [P]),
+        "lbmd_fluid_moments_static": (I, [P, I, I, I, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -240,6 +241,12 @@ def lbmd_profile_read(ctx, reset: bool = True):
     n = ctypes.c_int64(0)
     _check(ctx, _lib.lbmd_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n), int(bool(reset))))
     return ms.value, n.value
+
+
+def lbmd_fluid_moments_static(f_dev_ptr: int, dims, out_dev_ptr: int, stream=None) -> None:
+    """Device pointers in, device pointer out (no allocation); dims = (nx, ny, nz)."""
+    nx, ny, nz = dims
+    _check(None, _lib.lbmd_fluid_moments_static(f_dev_ptr, nx, ny, nz, out_dev_ptr, stream_handle(stream)))
 
 
 def lbmd_last_error(ctx) -> str:
