@@ -28,6 +28,10 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled 2-comp D3Q19 MLUPS & HBM-roofline %; replica p50/p99 latency"
 UNIT = "MLUPS"
 HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes per node moved by k_collide (dram__bytes_read + dram__bytes_write of one ncu capture
+# of the 128^3 case of this workload, scaled per node; profiles/k_collide_slab_droplets_256.md).
+# Must be set to None whenever k_collide changes until it is measured again.
+COLLIDE_TRAFFIC_BYTES_PER_NODE = 290.3
 
 # The slab/droplet workload uses the density scale of the paper's ferrofluid example (Sec. 4.5):
 # mean density 78.4 per component with g = 0.0214 (g rho = 1.68).  Bulk coexistence of F_bulk
@@ -263,7 +267,8 @@ def run_cuda(args):
                          "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_site": bps,
                          "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,
-                         "traffic": None},
+                         "traffic": (None if COLLIDE_TRAFFIC_BYTES_PER_NODE is None
+                                     else int(COLLIDE_TRAFFIC_BYTES_PER_NODE * N))},
             "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks, "state_ok": state_ok,
         }
         if world == 1 and not args.no_cpu_baseline:
