@@ -53,11 +53,15 @@ WORKLOADS = {
 }
 
 
-def algorithmic_bytes_per_site() -> int:
+STORAGES = {"fp32": (0, 4), "fp16": (1, 2), "bf16": (2, 2)}  # name: (LBMD_STORAGE_*, bytes per value)
+
+
+def algorithmic_bytes_per_site(storage: str = "fp32") -> int:
     """Algorithmic bytes per node of the collide kernel: both components' 19 populations
-    read (pull) and written once, FP32 (2*19*4*2 = 304), plus the node's two densities of
-    the Shan-Chen stencil (8; the neighbours' come from cache)."""
-    return 2 * 19 * 4 * 2 + 8
+    read (pull) and written once (2*19*2*b for b bytes per stored value: 304 in FP32, 152 in
+    16-bit storage), plus the node's two FP32 densities of the Shan-Chen stencil (8; the
+    neighbours' come from cache)."""
+    return 2 * 19 * 2 * STORAGES[storage][1] + 8
 
 
 def measured_hbm_peak():
@@ -171,7 +175,8 @@ def run_cuda(args):
     dims, rA, rB, x, types, kT, g_ab = build_workload(args.workload, seed=1234 + rank, edge_override=args.edge)
     npart = len(x)
     N = dims[0] * dims[1] * dims[2]
-    prm = L.params(dims, tau_r=1.0, g_AB=g_ab, kT=kT, seed=42 + rank)
+    rho0 = (float(rA.mean()), float(rB.mean()))  # shift reference of the 16-bit storages
+    prm = L.params(dims, tau_r=1.0, g_AB=g_ab, kT=kT, seed=42 + rank, storage=STORAGES[args.storage][0], rho0=rho0)
     ctx, _ = L.lbmd_create(prm, stream)
     L.lbmd_set_types(ctx, [L.lbmd_ptype(*t) for t in types], [L.lbmd_pair(0, 0, 1.0, 1.0)])
     L.lbmd_init_fluid(ctx, rA, rB)
@@ -248,7 +253,7 @@ def run_cuda(args):
     L.lbmd_destroy(ctx)
 
     peak, peak_kind = measured_hbm_peak()
-    bps = algorithmic_bytes_per_site()
+    bps = algorithmic_bytes_per_site(args.storage)
     avg_kernel_ms = k_ms / max(k_n, 1)
     achieved = bps * N / (avg_kernel_ms * 1e-3) / 1e9
     value = world * N * args.steps / (ms_max * 1e-3) / 1e6
@@ -256,10 +261,13 @@ def run_cuda(args):
         out = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "fp32" else "f32 arithmetic, %s shifted population storage" % args.storage,
+            "data": "synthetic",
             "config": {"workload": args.workload + ("" if not args.edge else "@%d" % args.edge),
                        "description": WORKLOADS[args.workload][2],
                        "lattice": list(dims), "particles": npart, "tau_r": 1.0, "g_AB": g_ab, "kT": kT,
+                       "storage": args.storage,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (N * 152 / 1e9)
                        if N * 152 > 129e6 else "L2-resident lattice (latency regime)"},
@@ -267,7 +275,7 @@ def run_cuda(args):
                          "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_site": bps,
                          "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,
-                         "traffic": (None if COLLIDE_TRAFFIC_BYTES_PER_NODE is None
+                         "traffic": (None if COLLIDE_TRAFFIC_BYTES_PER_NODE is None or args.storage != "fp32"
                                      else int(COLLIDE_TRAFFIC_BYTES_PER_NODE * N))},
             "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks, "state_ok": state_ok,
         }
@@ -355,6 +363,8 @@ def main():
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="slab_droplets_256")
     ap.add_argument("--edge", type=int, default=0, help="override the lattice edge (profiling of smaller cases)")
+    ap.add_argument("--storage", choices=sorted(STORAGES), default="fp32",
+                    help="population storage: FP32, or FP16 / BF16 shifted by w_i rho0 (FP32 arithmetic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

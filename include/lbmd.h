@@ -53,7 +53,9 @@ extern "C" {
 #define LBMD_E_BOND_BROKEN (-8) /* FENE bond stretched to or beyond R0 */
 #define LBMD_E_STATE (-9)       /* call out of order (e.g. step before init_fluid) */
 
-/* population storage (the benchmark spec precision pattern); only FP32 is implemented for now */
+/* population storage: FP32, or 16-bit (IEEE half or bfloat16) holding the shifted value
+ * f_zi - w_i rho0_z (lbmd_params.rho0_A / rho0_B); collisions always compute in FP32 and the
+ * diagnostics in FP64 */
 #define LBMD_STORAGE_FP32 0
 #define LBMD_STORAGE_FP16_SHIFTED 1
 #define LBMD_STORAGE_BF16_SHIFTED 2
@@ -106,7 +108,8 @@ typedef struct {
 /* Create a context for an nx*ny*nz lattice on the current CUDA device.  stream: a
  * cudaStream_t (may be NULL).  Allocates both population buffers; fails with
  * LBMD_E_NOMEM if they do not fit.  *warnings (may be NULL) receives LBMD_WARN_* bits.
- * Errors: LBMD_E_INVALID_ARG for sizes < 1, tau_r <= 1/2, dt != 1, unknown storage. */
+ * Errors: LBMD_E_INVALID_ARG for sizes < 1, tau_r <= 1/2, dt != 1, unknown storage,
+ * negative rho0. */
 int lbmd_create(const lbmd_params *params, void *stream, lbmd_ctx **out, unsigned *warnings);
 
 /* Destroy a context and free its device memory (NULL is ignored). */

@@ -1,9 +1,15 @@
 // lb_fluid.cu -- lattice kernels of the coupled Shan-Chen LB / MD step (sm_103a).
 //
-// Storage: populations of both components in one FP32 buffer [2][19][nz][ny][nx]
-// (structure of arrays, x fastest).  The buffer holds the post-collision values f*(r, t-1)
-// at their source node; a kernel "pulls" f_i(r, t) = f*_i(r - c_i, t-1), so reads are
-// coalesced along x (shifted by at most one element) and writes are fully coalesced.
+// Storage: populations of both components in one buffer [2][19][nz][ny][nx] (structure of
+// arrays, x fastest).  The buffer holds the post-collision values f*(r, t-1) at their source
+// node; a kernel "pulls" f_i(r, t) = f*_i(r - c_i, t-1), so reads are coalesced along x
+// (shifted by at most one element) and writes are fully coalesced.  Element type: FP32, or a
+// 16-bit type (FP16, BF16) holding the shifted value f_i - w_i rho0_z; all arithmetic is FP32.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "lbmd_internal.cuh"
 
 namespace lbmd {
@@ -11,6 +17,54 @@ namespace lbmd {
 namespace {
 
 constexpr int kBlock = 256;
+
+// Load / store of one population value; `shift` = w_i rho0_z (ignored for FP32 storage).
+// enc / dec convert between the FP32 value and the stored element.
+template <class T>
+struct Pop;
+template <>
+struct Pop<float> {
+  static __device__ __forceinline__ float enc(float v, float) { return v; }
+  static __device__ __forceinline__ float dec(float e, float) { return e; }
+  static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
+  static __device__ __forceinline__ float rd(const float *p, float) { return *p; }
+  static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
+};
+template <>
+struct Pop<__half> {
+  static __device__ __forceinline__ __half enc(float v, float sh) { return __float2half_rn(v - sh); }
+  static __device__ __forceinline__ float dec(__half e, float sh) { return __half2float(e) + sh; }
+  static __device__ __forceinline__ float ld(const __half *p, float sh) { return dec(__ldg(p), sh); }
+  static __device__ __forceinline__ float rd(const __half *p, float sh) { return dec(*p, sh); }
+  static __device__ __forceinline__ void st(__half *p, float v, float sh) { *p = enc(v, sh); }
+};
+template <>
+struct Pop<__nv_bfloat16> {
+  static __device__ __forceinline__ __nv_bfloat16 enc(float v, float sh) { return __float2bfloat16_rn(v - sh); }
+  static __device__ __forceinline__ float dec(__nv_bfloat16 e, float sh) { return __bfloat162float(e) + sh; }
+  static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float sh) { return dec(__ldg(p), sh); }
+  static __device__ __forceinline__ float rd(const __nv_bfloat16 *p, float sh) { return dec(*p, sh); }
+  static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float sh) { *p = enc(v, sh); }
+};
+
+// With 16-bit storage the rest population f_0 (which does not stream) is kept in an FP32 array
+// rest[2][N]; these read / write direction i of component c at site s from the right place.
+template <class T>
+__device__ __forceinline__ float pop_read(const StepParams &P, const T *buf, const float *rest, int c, int i,
+                                          long long s) {
+  if (i == 0 && rest) return rest[(long long)c * P.N + s];
+  return Pop<T>::rd(buf + ((long long)c * kQ + i) * P.N + s, kW[i] * P.rho0[c]);
+}
+template <class T>
+__device__ __forceinline__ void pop_write(const StepParams &P, T *buf, float *rest, int c, int i, long long s,
+                                          float v) {
+  if (i == 0 && rest)
+    rest[(long long)c * P.N + s] = v;
+  else
+    Pop<T>::st(buf + ((long long)c * kQ + i) * P.N + s, v, kW[i] * P.rho0[c]);
+}
+
+__device__ __forceinline__ float pop_shift(const StepParams &P, int comp, int i) { return kW[i] * P.rho0[comp]; }
 
 struct Coord {
   int x, y, z;
@@ -69,9 +123,11 @@ __device__ __forceinline__ int shift(const NOff &o, int cx, int cy, int cz) {
          (cz < 0 ? o.m[2] : cz > 0 ? o.p[2] : 0);
 }
 
+template <class T>
 __global__ void __launch_bounds__(kBlock) k_init_equilibrium(StepParams P, const float *__restrict__ rhoA,
                                                              const float *__restrict__ rhoB,
-                                                             const float *__restrict__ u, float *__restrict__ store) {
+                                                             const float *__restrict__ u, T *__restrict__ store,
+                                                             float *__restrict__ rest) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.N) return;
   const Coord c = site_coord(P, s);
@@ -85,23 +141,26 @@ __global__ void __launch_bounds__(kBlock) k_init_equilibrium(StepParams P, const
     const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
     const float poly = 1.f + 3.f * cu + 4.5f * cu * cu - usq15;
 #pragma unroll
-    for (int z = 0; z < 2; ++z) store[((long long)z * kQ + i) * P.N + dst] = kW[i] * rc[z] * poly;
+    for (int z = 0; z < 2; ++z) pop_write(P, store, rest, z, i, dst, kW[i] * rc[z] * poly);
   }
 }
 
+template <class T>
 __global__ void __launch_bounds__(kBlock) k_restream(StepParams P, const float *__restrict__ post, int comp,
-                                                     float *__restrict__ store) {
+                                                     T *__restrict__ store, float *__restrict__ rest) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.N) return;
   const Coord c = site_coord(P, s);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const long long dst = site_index(P, wrapi(c.x - kCx[i], P.nx), wrapi(c.y - kCy[i], P.ny), wrapi(c.z - kCz[i], P.nz));
-    store[((long long)comp * kQ + i) * P.N + dst] = post[(long long)i * P.N + s];
+    pop_write(P, store, rest, comp, i, dst, post[(long long)i * P.N + s]);
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_unstream(StepParams P, const float *__restrict__ store, int comp,
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_unstream(StepParams P, const T *__restrict__ store,
+                                                     const float *__restrict__ rest, int comp,
                                                      float *__restrict__ post) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.N) return;
@@ -110,25 +169,27 @@ __global__ void __launch_bounds__(kBlock) k_unstream(StepParams P, const float *
   neighbours(P, c, xs, ys, zs);
 #pragma unroll
   for (int i = 0; i < kQ; ++i)
-    post[(long long)i * P.N + s] = store[((long long)comp * kQ + i) * P.N + pull_source(P, i, xs, ys, zs)];
+    post[(long long)i * P.N + s] = pop_read(P, store, rest, comp, i, pull_source(P, i, xs, ys, zs));
 }
 
 // Densities rho_z = sum_i f_zi (appendix, zeroth mode), stored interleaved (rho_A, rho_B) per
 // site, and j' = sum_z sum_i f_zi c_i.
-__global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const float *__restrict__ fin,
-                                                    float *__restrict__ rho, float *__restrict__ jp) {
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const T *__restrict__ fin,
+                                                    const float *__restrict__ rest, float *__restrict__ rho,
+                                                    float *__restrict__ jp) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.N) return;
   const Coord c = site_coord(P, s);
   const NOff o = neighbour_offsets(P, c);
   const unsigned N32 = (unsigned)P.N, s32 = (unsigned)s;
-  const float *finB = fin + (size_t)kQ * N32;
+  const T *finB = fin + (size_t)kQ * N32;
   float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
-    const float a = __ldg(fin + src);
-    const float b = __ldg(finB + src);
+    const float a = (i == 0 && rest) ? __ldg(rest + s32) : Pop<T>::ld(fin + src, pop_shift(P, 0, i));
+    const float b = (i == 0 && rest) ? __ldg(rest + N32 + s32) : Pop<T>::ld(finB + src, pop_shift(P, 1, i));
     rA += a;
     rB += b;
     jx += kCx[i] * (a + b);
@@ -147,23 +208,28 @@ __global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const float *_
 // (Eq. SCforce with psi = rho, g_AA = g_BB = 0), fluid-side solvation force and momentum
 // return from the particles (Sec. 2), barycentric velocity (Eq. momentum_definition), BGK
 // collision with forcing for both components, write.
-template <bool kParticles>
-__global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const float *__restrict__ fin,
-                                                    float *__restrict__ fout, const float *__restrict__ rho,
+template <class T, bool kParticles>
+__global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const T *__restrict__ fin,
+                                                    T *__restrict__ fout, const float *__restrict__ rho,
                                                     ParticleArrays pa, ParticleForces pf, CellIndex ci,
-                                                    unsigned *err) {
+                                                    unsigned *err, const float *__restrict__ rest_in,
+                                                    float *__restrict__ rest_out) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.N) return;
   const Coord c = site_coord(P, s);
   const NOff o = neighbour_offsets(P, c);
   const unsigned N32 = (unsigned)P.N, s32 = (unsigned)s;
-  const float *finB = fin + (size_t)kQ * N32;
+  const T *finB = fin + (size_t)kQ * N32;
   float fA[kQ], fB[kQ];
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
-    fA[i] = __ldg(fin + src);
-    fB[i] = __ldg(finB + src);
+    fA[i] = Pop<T>::ld(fin + src, pop_shift(P, 0, i));
+    fB[i] = Pop<T>::ld(finB + src, pop_shift(P, 1, i));
+  }
+  if (rest_in) {  // 16-bit storage: the rest populations are kept in FP32
+    fA[0] = __ldg(rest_in + s32);
+    fB[0] = __ldg(rest_in + N32 + s32);
   }
   float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -221,16 +287,36 @@ __global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const float
       fB[j] = om1 * fBj + aB * (sym - anti) + symB - antiB;
     }
   }
-  float *foutB = fout + (size_t)kQ * N32;
+  T *foutB = fout + (size_t)kQ * N32;
+  if (rest_out) {
+    // 16-bit storage: each moving population is rounded on store; the FP32 rest population takes
+    // the rounding error of the node's 18 others, so the node's total (and the total mass of each
+    // component) is the one of the collision up to FP32 rounding instead of drifting each step.
+    float eA = 0.f, eB = 0.f;
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    fout[i * N32 + s32] = fA[i];
-    foutB[i * N32 + s32] = fB[i];
+    for (int i = 1; i < kQ; ++i) {
+      const auto a = Pop<T>::enc(fA[i], pop_shift(P, 0, i));
+      const auto b = Pop<T>::enc(fB[i], pop_shift(P, 1, i));
+      fout[i * N32 + s32] = a;
+      foutB[i * N32 + s32] = b;
+      eA += fA[i] - Pop<T>::dec(a, pop_shift(P, 0, i));
+      eB += fB[i] - Pop<T>::dec(b, pop_shift(P, 1, i));
+    }
+    rest_out[s32] = fA[0] + eA;
+    rest_out[N32 + s32] = fB[0] + eB;
+  } else {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      Pop<T>::st(fout + (i * N32 + s32), fA[i], pop_shift(P, 0, i));
+      Pop<T>::st(foutB + (i * N32 + s32), fB[i], pop_shift(P, 1, i));
+    }
   }
 }
 
 // rho_A, rho_B and u = (j' + g^SC/2)/rho at the current step (for readback).
-__global__ void __launch_bounds__(kBlock) k_fields(StepParams P, const float *__restrict__ store,
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_fields(StepParams P, const T *__restrict__ store,
+                                                   const float *__restrict__ rest,
                                                    const float *__restrict__ rho, float *__restrict__ oA,
                                                    float *__restrict__ oB, float *__restrict__ ou) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -242,7 +328,7 @@ __global__ void __launch_bounds__(kBlock) k_fields(StepParams P, const float *__
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const long long src = pull_source(P, i, xs, ys, zs);
-    const float a = store[(long long)i * P.N + src] + store[(long long)(kQ + i) * P.N + src];
+    const float a = pop_read(P, store, rest, 0, i, src) + pop_read(P, store, rest, 1, i, src);
     jx += kCx[i] * a; jy += kCy[i] * a; jz += kCz[i] * a;
   }
   const float2 *rho2 = reinterpret_cast<const float2 *>(rho);
@@ -271,15 +357,17 @@ __global__ void __launch_bounds__(kBlock) k_fields(StepParams P, const float *__
 // FP64 block partial sums of [M_A, M_B, Px, Py, Pz] over the stored buffer (streaming
 // permutes populations, so sums over stored and post-streaming values agree).
 constexpr int kSumBlock = 256;
-__global__ void __launch_bounds__(kSumBlock) k_fluid_sums(StepParams P, const float *__restrict__ store,
+template <class T>
+__global__ void __launch_bounds__(kSumBlock) k_fluid_sums(StepParams P, const T *__restrict__ store,
+                                                          const float *__restrict__ rest,
                                                           double *__restrict__ partial) {
   double acc[5] = {0, 0, 0, 0, 0};
   for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < P.N;
        s += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      const double a = (double)store[(long long)i * P.N + s];
-      const double b = (double)store[(long long)(kQ + i) * P.N + s];
+      const double a = (double)pop_read(P, store, rest, 0, i, s);
+      const double b = (double)pop_read(P, store, rest, 1, i, s);
       acc[0] += a;
       acc[1] += b;
       if (kCx[i]) acc[2] += kCx[i] * (a + b);
@@ -315,37 +403,73 @@ inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBl
 
 }  // namespace
 
+// Run `f` with a typed null pointer of the storage element type of P.
+template <class F>
+void with_storage(const StepParams &P, F f) {
+  switch (P.storage) {
+    case LBMD_STORAGE_FP16_SHIFTED: f((__half *)nullptr); break;
+    case LBMD_STORAGE_BF16_SHIFTED: f((__nv_bfloat16 *)nullptr); break;
+    default: f((float *)nullptr); break;
+  }
+}
+
 void launch_init_equilibrium(const StepParams &P, const float *rhoA, const float *rhoB, const float *u,
-                             float *store, cudaStream_t st) {
-  k_init_equilibrium<<<grid_for(P.N), kBlock, 0, st>>>(P, rhoA, rhoB, u, store);
+                             void *store, float *rest, cudaStream_t st) {
+  with_storage(P, [&](auto t) {
+    using T = std::remove_pointer_t<decltype(t)>;
+    k_init_equilibrium<T><<<grid_for(P.N), kBlock, 0, st>>>(P, rhoA, rhoB, u, static_cast<T *>(store), rest);
+  });
 }
-void launch_restream(const StepParams &P, const float *post, int comp, float *store, cudaStream_t st) {
-  k_restream<<<grid_for(P.N), kBlock, 0, st>>>(P, post, comp, store);
+void launch_restream(const StepParams &P, const float *post, int comp, void *store, float *rest, cudaStream_t st) {
+  with_storage(P, [&](auto t) {
+    using T = std::remove_pointer_t<decltype(t)>;
+    k_restream<T><<<grid_for(P.N), kBlock, 0, st>>>(P, post, comp, static_cast<T *>(store), rest);
+  });
 }
-void launch_unstream(const StepParams &P, const float *store, int comp, float *post, cudaStream_t st) {
-  k_unstream<<<grid_for(P.N), kBlock, 0, st>>>(P, store, comp, post);
+void launch_unstream(const StepParams &P, const void *store, const float *rest, int comp, float *post,
+                     cudaStream_t st) {
+  with_storage(P, [&](auto t) {
+    using T = std::remove_pointer_t<decltype(t)>;
+    k_unstream<T><<<grid_for(P.N), kBlock, 0, st>>>(P, static_cast<const T *>(store), rest, comp, post);
+  });
 }
-void launch_moments(const StepParams &P, const float *store, float *rho, float *jp, cudaStream_t st) {
-  k_moments<<<grid_for(P.N), kBlock, 0, st>>>(P, store, rho, jp);
+void launch_moments(const StepParams &P, const void *store, const float *rest, float *rho, float *jp,
+                    cudaStream_t st) {
+  with_storage(P, [&](auto t) {
+    using T = std::remove_pointer_t<decltype(t)>;
+    k_moments<T><<<grid_for(P.N), kBlock, 0, st>>>(P, static_cast<const T *>(store), rest, rho, jp);
+  });
 }
-void launch_collide(const StepParams &P, const float *fin, float *fout, const float *rho,
+void launch_collide(const StepParams &P, const void *fin, void *fout, float *rest, const float *rho,
                     const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci, unsigned *err,
                     cudaStream_t st) {
-  if (P.np > 0)
-    k_collide<true><<<grid_for(P.N), kBlock, 0, st>>>(P, fin, fout, rho, pa, pf, ci, err);
-  else
-    k_collide<false><<<grid_for(P.N), kBlock, 0, st>>>(P, fin, fout, rho, pa, pf, ci, err);
+  with_storage(P, [&](auto t) {
+    using T = std::remove_pointer_t<decltype(t)>;
+    const T *a = static_cast<const T *>(fin);
+    T *b = static_cast<T *>(fout);
+    if (P.np > 0)
+      k_collide<T, true><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
+    else
+      k_collide<T, false><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
+  });
 }
-void launch_fields(const StepParams &P, const float *store, const float *rho, float *rhoA, float *rhoB,
-                   float *u, cudaStream_t st) {
-  k_fields<<<grid_for(P.N), kBlock, 0, st>>>(P, store, rho, rhoA, rhoB, u);
+void launch_fields(const StepParams &P, const void *store, const float *rest, const float *rho, float *rhoA,
+                   float *rhoB, float *u, cudaStream_t st) {
+  with_storage(P, [&](auto t) {
+    using T = std::remove_pointer_t<decltype(t)>;
+    k_fields<T><<<grid_for(P.N), kBlock, 0, st>>>(P, static_cast<const T *>(store), rest, rho, rhoA, rhoB, u);
+  });
 }
 int fluid_sum_blocks(const StepParams &P) {
   long long b = (P.N + kSumBlock - 1) / kSumBlock;
   return (int)(b < 1024 ? b : 1024);
 }
-void launch_fluid_sums(const StepParams &P, const float *store, double *partial, int nblocks, cudaStream_t st) {
-  k_fluid_sums<<<nblocks, kSumBlock, 0, st>>>(P, store, partial);
+void launch_fluid_sums(const StepParams &P, const void *store, const float *rest, double *partial, int nblocks,
+                       cudaStream_t st) {
+  with_storage(P, [&](auto t) {
+    using T = std::remove_pointer_t<decltype(t)>;
+    k_fluid_sums<T><<<nblocks, kSumBlock, 0, st>>>(P, static_cast<const T *>(store), rest, partial);
+  });
 }
 void launch_finish_sums(const double *partial, int nblocks, int nvals, double *out, cudaStream_t st) {
   k_finish_sums<<<1, 32, 0, st>>>(partial, nblocks, nvals, out);

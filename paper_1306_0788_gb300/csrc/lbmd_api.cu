@@ -15,7 +15,9 @@ struct lbmd_ctx {
   cudaStream_t st = nullptr;
   int dev = 0;
   StepParams P{};
-  float *pop[2] = {nullptr, nullptr};
+  unsigned char *pop[2] = {nullptr, nullptr};  // population buffers, element type P.storage
+  size_t pop_elem = 4;
+  float *rest = nullptr;  // 16-bit storage: FP32 rest populations [2][N] (not double-buffered: local)
   int cur = 0;
   float *rho = nullptr;  // [N][2] interleaved rho_A, rho_B
   float *jp = nullptr;   // [3][N]
@@ -155,11 +157,11 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
   if (!(prm->tau_r > 0.5)) return fail(c, LBMD_E_INVALID_ARG, "tau_r must exceed 1/2");
   if (prm->dt != 1.0) return fail(c, LBMD_E_INVALID_ARG, "dt must equal the lattice time step 1");
   if (!(prm->kT >= 0.0)) return fail(c, LBMD_E_INVALID_ARG, "kT must be >= 0");
-  if (prm->storage != LBMD_STORAGE_FP32) {
-    if (prm->storage == LBMD_STORAGE_FP16_SHIFTED || prm->storage == LBMD_STORAGE_BF16_SHIFTED)
-      return fail(c, LBMD_E_UNIMPLEMENTED, "16-bit population storage is not implemented");
+  if (prm->storage != LBMD_STORAGE_FP32 && prm->storage != LBMD_STORAGE_FP16_SHIFTED &&
+      prm->storage != LBMD_STORAGE_BF16_SHIFTED)
     return fail(c, LBMD_E_INVALID_ARG, "unknown storage");
-  }
+  if (!(prm->rho0_A >= 0.0) || !(prm->rho0_B >= 0.0) || !std::isfinite(prm->rho0_A) || !std::isfinite(prm->rho0_B))
+    return fail(c, LBMD_E_INVALID_ARG, "rho0_A, rho0_B must be finite and >= 0");
   c = new lbmd_ctx();
   c->prm = *prm;
   c->st = (cudaStream_t)stream;
@@ -172,14 +174,19 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
   P.force_pref = (float)(1.0 - 0.5 / prm->tau_r);
   P.gAB = (float)prm->g_AB; P.gBA = (float)prm->g_BA;
   P.dt = (float)prm->dt;
+  P.storage = prm->storage;
+  P.rho0[0] = prm->storage == LBMD_STORAGE_FP32 ? 0.f : (float)prm->rho0_A;
+  P.rho0[1] = prm->storage == LBMD_STORAGE_FP32 ? 0.f : (float)prm->rho0_B;
+  c->pop_elem = prm->storage == LBMD_STORAGE_FP32 ? 4 : 2;
   P.seed = prm->seed;
   P.ntypes = 0;
   P.bond_kind = LBMD_BOND_FENE;
   cudaError_t e = cudaSuccess;
-  const size_t npop = (size_t)2 * kQ * P.N;
+  const size_t npop = (size_t)2 * kQ * P.N * c->pop_elem;  // bytes; >= 19 N floats of staging
   if ((e = dalloc(&c->pop[0], npop)) != cudaSuccess || (e = dalloc(&c->pop[1], npop)) != cudaSuccess ||
       (e = dalloc(&c->rho, (size_t)2 * P.N)) != cudaSuccess || (e = dalloc(&c->jp, (size_t)3 * P.N)) != cudaSuccess ||
-      (e = dalloc(&c->err, 1)) != cudaSuccess) {
+      (e = dalloc(&c->err, 1)) != cudaSuccess ||
+      (c->pop_elem == 2 && (e = dalloc(&c->rest, (size_t)2 * P.N)) != cudaSuccess)) {
     cudaGetLastError();
     lbmd_destroy(c);
     return fail(nullptr, e == cudaErrorMemoryAllocation ? LBMD_E_NOMEM : LBMD_E_CUDA,
@@ -207,7 +214,7 @@ void lbmd_destroy(lbmd_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->dev);
   if (c->st) cudaStreamSynchronize(c->st);
-  dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho); dfree(c->jp); dfree(c->err);
+  dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho); dfree(c->jp); dfree(c->err); dfree(c->rest);
   dfree(c->diag_partial); dfree(c->diag_out);
   free_particles(c);
   dfree(c->row_count); dfree(c->row_start); dfree(c->row_cursor); dfree(c->row_bsum);
@@ -278,7 +285,7 @@ int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const flo
     if (!(rhoA[s] > 0.f) || !(rhoB[s] > 0.f) || !std::isfinite(rhoA[s]) || !std::isfinite(rhoB[s]))
       return fail(c, LBMD_E_INVALID_ARG, "densities must be finite and > 0");
   // stage through the (not yet used) second population buffer
-  float *stage = c->pop[1 - c->cur];
+  float *stage = reinterpret_cast<float *>(c->pop[1 - c->cur]);
   const size_t bytes = sizeof(float) * (size_t)N;
   CK(cudaMemcpyAsync(stage, rhoA, bytes, cudaMemcpyHostToDevice, c->st), "upload rhoA");
   CK(cudaMemcpyAsync(stage + N, rhoB, bytes, cudaMemcpyHostToDevice, c->st), "upload rhoB");
@@ -287,7 +294,7 @@ int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const flo
     CK(cudaMemcpyAsync(stage + 2 * N, u, 3 * bytes, cudaMemcpyHostToDevice, c->st), "upload u");
     du = stage + 2 * N;
   }
-  launch_init_equilibrium(c->P, stage, stage + N, du, c->pop[c->cur], c->st);
+  launch_init_equilibrium(c->P, stage, stage + N, du, c->pop[c->cur], c->rest, c->st);
   int r = launched(c, "init_equilibrium");
   if (r) return r;
   CK(cudaStreamSynchronize(c->st), "sync");
@@ -299,9 +306,9 @@ int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const flo
 int lbmd_set_populations(lbmd_ctx *c, int comp, const float *f) {
   if (!c || !f || comp < 0 || comp > 1) return c ? fail(c, LBMD_E_INVALID_ARG, "bad arguments") : LBMD_E_INVALID_ARG;
   cudaSetDevice(c->dev);
-  float *stage = c->pop[1 - c->cur];
+  float *stage = reinterpret_cast<float *>(c->pop[1 - c->cur]);
   CK(cudaMemcpyAsync(stage, f, sizeof(float) * kQ * (size_t)c->P.N, cudaMemcpyHostToDevice, c->st), "upload f");
-  launch_restream(c->P, stage, comp, c->pop[c->cur], c->st);
+  launch_restream(c->P, stage, comp, c->pop[c->cur], c->rest, c->st);
   int r = launched(c, "restream");
   if (r) return r;
   CK(cudaStreamSynchronize(c->st), "sync");
@@ -313,8 +320,8 @@ int lbmd_get_populations(lbmd_ctx *c, int comp, float *f) {
   if (!c || !f || comp < 0 || comp > 1) return c ? fail(c, LBMD_E_INVALID_ARG, "bad arguments") : LBMD_E_INVALID_ARG;
   if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
   cudaSetDevice(c->dev);
-  float *stage = c->pop[1 - c->cur];
-  launch_unstream(c->P, c->pop[c->cur], comp, stage, c->st);
+  float *stage = reinterpret_cast<float *>(c->pop[1 - c->cur]);
+  launch_unstream(c->P, c->pop[c->cur], c->rest, comp, stage, c->st);
   int r = launched(c, "unstream");
   if (r) return r;
   CK(cudaMemcpyAsync(f, stage, sizeof(float) * kQ * (size_t)c->P.N, cudaMemcpyDeviceToHost, c->st), "download f");
@@ -457,12 +464,12 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
   const CellIndex ci{c->row_start};
   for (int s = 0; s < nsteps; ++s) {
     P.step = (unsigned long long)c->steps;
-    const float *fin = c->pop[c->cur];
-    float *fout = c->pop[1 - c->cur];
+    const void *fin = c->pop[c->cur];
+    void *fout = c->pop[1 - c->cur];
     int r;
     if (P.np > 0 && (r = sort_particles(c))) return r;
     // densities (and j' for the particle coupling) of this step's populations
-    launch_moments(P, fin, c->rho, P.np > 0 ? c->jp : nullptr, c->st);
+    launch_moments(P, fin, c->rest, c->rho, P.np > 0 ? c->jp : nullptr, c->st);
     if ((r = launched(c, "moments"))) return r;
     if (P.np > 0) {
       launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
@@ -480,7 +487,7 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
       }
       CK(cudaEventRecord(c->ev[c->ev_used], c->st), "event");
     }
-    launch_collide(P, fin, fout, c->rho, c->pa[c->pcur], c->pf, ci, c->err, c->st);
+    launch_collide(P, fin, fout, c->rest, c->rho, c->pa[c->pcur], c->pf, ci, c->err, c->st);
     if ((r = launched(c, "collide"))) return r;
     if (c->prof) {
       CK(cudaEventRecord(c->ev[c->ev_used + 1], c->st), "event");
@@ -517,9 +524,9 @@ int lbmd_get_fields(lbmd_ctx *c, float *rhoA, float *rhoB, float *u) {
   if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
   cudaSetDevice(c->dev);
   const long long N = c->P.N;
-  float *stage = c->pop[1 - c->cur];
-  launch_moments(c->P, c->pop[c->cur], c->rho, nullptr, c->st);
-  launch_fields(c->P, c->pop[c->cur], c->rho, stage, stage + N, stage + 2 * N, c->st);
+  float *stage = reinterpret_cast<float *>(c->pop[1 - c->cur]);
+  launch_moments(c->P, c->pop[c->cur], c->rest, c->rho, nullptr, c->st);
+  launch_fields(c->P, c->pop[c->cur], c->rest, c->rho, stage, stage + N, stage + 2 * N, c->st);
   int r = launched(c, "fields", 2);
   if (r) return r;
   const size_t bytes = sizeof(float) * (size_t)N;
@@ -566,7 +573,7 @@ int lbmd_diagnostics(lbmd_ctx *c, double out[8]) {
   if (!c || !out) return c ? fail(c, LBMD_E_INVALID_ARG, "null output") : LBMD_E_INVALID_ARG;
   if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
   cudaSetDevice(c->dev);
-  launch_fluid_sums(c->P, c->pop[c->cur], c->diag_partial, c->diag_blocks, c->st);
+  launch_fluid_sums(c->P, c->pop[c->cur], c->rest, c->diag_partial, c->diag_blocks, c->st);
   launch_finish_sums(c->diag_partial, c->diag_blocks, 5, c->diag_out, c->st);
   int r = launched(c, "fluid sums", 2);
   if (r) return r;

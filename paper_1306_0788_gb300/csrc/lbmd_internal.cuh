@@ -52,6 +52,8 @@ struct StepParams {
   float force_pref;      // 1 - 1/(2 tau_r)  (the (2 + lambda)/2 factor of the forcing term)
   float gAB, gBA;
   float dt;
+  int storage;           // LBMD_STORAGE_*
+  float rho0[2];         // shift reference of the 16-bit storages (f_i - w_i rho0_z is stored)
   int np, ntypes;
   float dh_lB, dh_kappa, dh_rc2;
   int bond_kind;
@@ -194,18 +196,21 @@ __device__ __forceinline__ float3 particle_normals(unsigned long long seed, unsi
 void set_context_free_error(const std::string &m);
 
 // ------------------------------------------------------------------ launch wrappers
-// lattice (lb_fluid.cu)
+// lattice (lb_fluid.cu); population buffers are void*: their element type is P.storage.  With
+// 16-bit storage `rest` is the FP32 array [2][N] of the rest populations (NULL for FP32).
 void launch_init_equilibrium(const StepParams &P, const float *rhoA, const float *rhoB, const float *u,
-                             float *store, cudaStream_t st);
-void launch_restream(const StepParams &P, const float *post, int comp, float *store, cudaStream_t st);
-void launch_unstream(const StepParams &P, const float *store, int comp, float *post, cudaStream_t st);
-void launch_moments(const StepParams &P, const float *store, float *rho, float *jp, cudaStream_t st);
-void launch_collide(const StepParams &P, const float *fin, float *fout, const float *rho,
+                             void *store, float *rest, cudaStream_t st);
+void launch_restream(const StepParams &P, const float *post, int comp, void *store, float *rest, cudaStream_t st);
+void launch_unstream(const StepParams &P, const void *store, const float *rest, int comp, float *post,
+                     cudaStream_t st);
+void launch_moments(const StepParams &P, const void *store, const float *rest, float *rho, float *jp,
+                    cudaStream_t st);
+void launch_collide(const StepParams &P, const void *fin, void *fout, float *rest, const float *rho,
                     const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci, unsigned *err,
                     cudaStream_t st);
-void launch_fields(const StepParams &P, const float *store, const float *rho, float *rhoA, float *rhoB,
-                   float *u, cudaStream_t st);
-void launch_fluid_sums(const StepParams &P, const float *store, double *partial, int nblocks,
+void launch_fields(const StepParams &P, const void *store, const float *rest, const float *rho, float *rhoA,
+                   float *rhoB, float *u, cudaStream_t st);
+void launch_fluid_sums(const StepParams &P, const void *store, const float *rest, double *partial, int nblocks,
                        cudaStream_t st);
 void launch_finish_sums(const double *partial, int nblocks, int nvals, double *out, cudaStream_t st);
 int fluid_sum_blocks(const StepParams &P);
