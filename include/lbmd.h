@@ -208,6 +208,110 @@ int lbmd_fluid_moments_static(const float *f_dev, int nx, int ny, int nz, double
  * a context (lbmd_create, lbmd_fluid_moments_static). */
 const char *lbmd_last_error(const lbmd_ctx *ctx);
 
+/* ==========================================================================================
+ * Batches: many independent replicas (lattices with their particles, each with its own
+ * parameters, sizes and step count) advanced together on one GPU.  Every kernel of the coupled
+ * step runs once per step for all replicas of the batch (shared launches), the launches of a
+ * step sequence are captured once in a CUDA graph, and replicas join and leave between calls
+ * without recapture -- continuous batching.  A replica advances exactly as a context created
+ * with lbmd_create would, and its results do not depend on the other replicas in the batch.
+ *
+ * Life cycle of a replica: lbmd_batch_add (admission: reserves its device memory against the
+ * batch budget) -> lbmd_batch_set_types / lbmd_batch_set_debye_hueckel -> lbmd_batch_init_fluid
+ * -> lbmd_batch_set_particles -> lbmd_batch_step (any number of calls, shared with the other
+ * replicas) -> lbmd_batch_poll until its status is LBMD_SLOT_DONE -> getters ->
+ * lbmd_batch_remove (frees its memory for the next replica).
+ *
+ * The paper defines the model of one system; batching, admission and the autotuner are not in
+ * it.  Bonds (lbmd_set_bonds) are available in single contexts only.
+ * ========================================================================================== */
+typedef struct lbmd_batch lbmd_batch;
+
+/* slot status reported by lbmd_batch_poll */
+#define LBMD_SLOT_EMPTY 0  /* no replica */
+#define LBMD_SLOT_ACTIVE 1 /* admitted, steps still to take (or fluid not initialised yet) */
+#define LBMD_SLOT_DONE 2   /* took all the steps it asked for */
+#define LBMD_SLOT_FAILED 3 /* stopped by a device error (lbmd_batch_slot_error gives the code) */
+
+/* Create a batch on the current device.  mem_budget: bytes of device memory the replicas may
+ * take (0 = 90 % of the free memory); storage: LBMD_STORAGE_* shared by every replica;
+ * max_slots in [1, 65536]; stream: a cudaStream_t for all work of the batch, which must not be
+ * the legacy default stream; NULL = the batch creates (and owns) a non-blocking stream.
+ * Errors: LBMD_E_INVALID_ARG, LBMD_E_NOMEM, LBMD_E_CUDA (message: lbmd_batch_last_error(NULL)). */
+int lbmd_batch_create(size_t mem_budget, int storage, int max_slots, void *stream, lbmd_batch **out);
+
+/* Wait for the batch's work and free everything it holds (NULL is ignored). */
+void lbmd_batch_destroy(lbmd_batch *batch);
+
+/* Admit a replica: params as for lbmd_create (storage must be the batch's), np_max the most
+ * particles it will hold, total_steps the steps it asks for.  Its device memory -- both
+ * population buffers, densities, j', and its share of the particle and row arrays -- is
+ * reserved against the budget; LBMD_E_NOMEM (nothing changed) when it does not fit or every
+ * slot is taken: retry after lbmd_batch_remove.  *slot receives its slot index, *warnings
+ * (may be NULL) LBMD_WARN_* bits.  The replica takes part in lbmd_batch_step once its fluid
+ * is initialised. */
+int lbmd_batch_add(lbmd_batch *batch, const lbmd_params *params, int np_max, int64_t total_steps, int *slot,
+                   unsigned *warnings);
+
+/* Free a replica's memory and slot (its results are gone; read them first). */
+int lbmd_batch_remove(lbmd_batch *batch, int slot);
+
+/* Per replica: as lbmd_set_types, lbmd_set_debye_hueckel, lbmd_init_fluid (resets the
+ * replica's step count) and lbmd_set_particles (n <= np_max). */
+int lbmd_batch_set_types(lbmd_batch *batch, int slot, int ntypes, const lbmd_ptype *types, int npairs,
+                         const lbmd_pair *pairs, unsigned *warnings);
+int lbmd_batch_set_debye_hueckel(lbmd_batch *batch, int slot, double lB, double kappa_D, double rc);
+int lbmd_batch_init_fluid(lbmd_batch *batch, int slot, const float *rhoA, const float *rhoB, const float *u);
+int lbmd_batch_set_particles(lbmd_batch *batch, int slot, int n, const double *x, const double *v,
+                             const int *type, const double *q);
+
+/* Advance every initialised replica by min(nsteps, steps it still asks for) coupled steps
+ * (the step of lbmd_step), all replicas in the same launches.  Asynchronous on the batch
+ * stream; a replica whose state fails on the device (negative or non-finite density, particle
+ * out of range) stops at the end of that step while the others go on. */
+int lbmd_batch_step(lbmd_batch *batch, int nsteps);
+
+/* Wait for the batch's work; status (may be NULL) [max_slots] receives LBMD_SLOT_* per slot. */
+int lbmd_batch_poll(lbmd_batch *batch, int *status);
+
+/* LBMD_E_* code of a failed replica (LBMD_OK if none), and its step count, as of the last
+ * call that waited for the batch (lbmd_batch_poll, getters); -1 / LBMD_E_INVALID_ARG for a
+ * free slot. */
+int lbmd_batch_slot_error(const lbmd_batch *batch, int slot);
+int64_t lbmd_batch_step_count(const lbmd_batch *batch, int slot);
+
+/* Per replica, as lbmd_get_populations, lbmd_get_fields, lbmd_get_particles and
+ * lbmd_diagnostics (all wait for the batch stream). */
+int lbmd_batch_get_populations(lbmd_batch *batch, int slot, int comp, float *f);
+int lbmd_batch_get_fields(lbmd_batch *batch, int slot, float *rhoA, float *rhoB, float *u);
+int lbmd_batch_get_particles(lbmd_batch *batch, int slot, double *x, double *v, double *f);
+int lbmd_batch_diagnostics(lbmd_batch *batch, int slot, double out[8]);
+
+/* Launch shape of the two lattice kernels: the sites per tile (a multiple of 256 in
+ * [256, 65536]), the persistent grid of the density pass and of the update (in [1, 64 x SM
+ * count]), and the register budget of the update, collide_blocks = 3 (80 registers, three
+ * blocks of 256 threads per SM) or 2 (up to 128 registers).  cfg[5] = {tile_sites,
+ * grid_moments, grid_collide, collide_blocks, grid_particles}.  Results do not depend on it. */
+int lbmd_batch_set_config(lbmd_batch *batch, int tile_sites, int grid_moments, int grid_collide,
+                          int collide_blocks);
+int lbmd_batch_get_config(const lbmd_batch *batch, int cfg[5]);
+
+/* Autotuner: times the lattice kernels over the current replicas for tiles of 256, 1024 and
+ * 4096 sites, density-pass grids of 2/4/8 blocks per SM and update variants (register budget
+ * of 3 blocks per SM with grids of 1/2/3 blocks per SM, of 2 blocks per SM with 1/2), keeps
+ * the fastest, and returns it in cfg[5] and the two kernel times in ms[2] (either may be
+ * NULL).  The state of the replicas is unchanged.  Needs at least one initialised replica. */
+int lbmd_batch_tune(lbmd_batch *batch, int cfg[5], double ms[2]);
+
+/* Budget and use in bytes, number of occupied slots, slot count (any pointer may be NULL). */
+int lbmd_batch_info(const lbmd_batch *batch, size_t *budget, size_t *used, int *occupied, int *max_slots);
+
+/* Kernel launches issued by lbmd_batch_step so far (host-side count, 13 per step). */
+int64_t lbmd_batch_launch_count(const lbmd_batch *batch);
+
+/* Message of the last failure of a batch call (NULL: of lbmd_batch_create). */
+const char *lbmd_batch_last_error(const lbmd_batch *batch);
+
 #ifdef __cplusplus
 }
 #endif

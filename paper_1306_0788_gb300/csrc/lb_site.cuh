@@ -1,0 +1,546 @@
+// lb_site.cuh -- the arithmetic of one lattice site and of one particle in a coupled step,
+// shared by the kernels of a single lattice (lb_fluid.cu, lb_particles.cu) and the batched
+// kernels that advance many independent lattices in one launch (lb_batch.cu).  A kernel
+// decides which site or particle a thread owns and which lattice's parameters apply; the
+// bodies below do the rest, so a lattice gives the same bits whichever kernel ran it.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbmd_internal.cuh"
+
+namespace lbmd {
+namespace site {
+
+// Load / store of one population value; `shift` = w_i rho0_z (ignored for FP32 storage).
+// enc / dec convert between the FP32 value and the stored element.
+template <class T>
+struct Pop;
+template <>
+struct Pop<float> {
+  static __device__ __forceinline__ float enc(float v, float) { return v; }
+  static __device__ __forceinline__ float dec(float e, float) { return e; }
+  static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
+  static __device__ __forceinline__ float rd(const float *p, float) { return *p; }
+  static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
+};
+template <>
+struct Pop<__half> {
+  static __device__ __forceinline__ __half enc(float v, float sh) { return __float2half_rn(v - sh); }
+  static __device__ __forceinline__ float dec(__half e, float sh) { return __half2float(e) + sh; }
+  static __device__ __forceinline__ float ld(const __half *p, float sh) { return dec(__ldg(p), sh); }
+  static __device__ __forceinline__ float rd(const __half *p, float sh) { return dec(*p, sh); }
+  static __device__ __forceinline__ void st(__half *p, float v, float sh) { *p = enc(v, sh); }
+};
+template <>
+struct Pop<__nv_bfloat16> {
+  static __device__ __forceinline__ __nv_bfloat16 enc(float v, float sh) { return __float2bfloat16_rn(v - sh); }
+  static __device__ __forceinline__ float dec(__nv_bfloat16 e, float sh) { return __bfloat162float(e) + sh; }
+  static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float sh) { return dec(__ldg(p), sh); }
+  static __device__ __forceinline__ float rd(const __nv_bfloat16 *p, float sh) { return dec(*p, sh); }
+  static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float sh) { *p = enc(v, sh); }
+};
+
+__device__ __forceinline__ float pop_shift(const StepParams &P, int comp, int i) { return kW[i] * P.rho0[comp]; }
+
+// With 16-bit storage the rest population f_0 (which does not stream) is kept in an FP32 array
+// rest[2][N]; these read / write direction i of component c at site s from the right place.
+template <class T>
+__device__ __forceinline__ float pop_read(const StepParams &P, const T *buf, const float *rest, int c, int i,
+                                          long long s) {
+  if (i == 0 && rest) return rest[(long long)c * P.N + s];
+  return Pop<T>::rd(buf + ((long long)c * kQ + i) * P.N + s, kW[i] * P.rho0[c]);
+}
+template <class T>
+__device__ __forceinline__ void pop_write(const StepParams &P, T *buf, float *rest, int c, int i, long long s,
+                                          float v) {
+  if (i == 0 && rest)
+    rest[(long long)c * P.N + s] = v;
+  else
+    Pop<T>::st(buf + ((long long)c * kQ + i) * P.N + s, v, kW[i] * P.rho0[c]);
+}
+
+struct Coord {
+  int x, y, z;
+};
+
+__device__ __forceinline__ Coord site_coord(const StepParams &P, long long s) {
+  Coord c;
+  c.x = (int)(s % P.nx);
+  const long long t = s / P.nx;
+  c.y = (int)(t % P.ny);
+  c.z = (int)(t / P.ny);
+  return c;
+}
+
+__device__ __forceinline__ void neighbours(const StepParams &P, const Coord &c, int xs[3], int ys[3], int zs[3]) {
+  xs[0] = c.x == 0 ? P.nx - 1 : c.x - 1;
+  xs[1] = c.x;
+  xs[2] = c.x == P.nx - 1 ? 0 : c.x + 1;
+  ys[0] = c.y == 0 ? P.ny - 1 : c.y - 1;
+  ys[1] = c.y;
+  ys[2] = c.y == P.ny - 1 ? 0 : c.y + 1;
+  zs[0] = c.z == 0 ? P.nz - 1 : c.z - 1;
+  zs[1] = c.z;
+  zs[2] = c.z == P.nz - 1 ? 0 : c.z + 1;
+}
+
+// source coordinate of direction i for a pull at (x, y, z): r - c_i, periodic
+__device__ __forceinline__ long long pull_source(const StepParams &P, int i, const int xs[3], const int ys[3],
+                                                 const int zs[3]) {
+  // xs = {x-1, x, x+1} wrapped; r - c_i selects index 1 - c
+  return ((long long)zs[1 - kCz[i]] * P.ny + ys[1 - kCy[i]]) * P.nx + xs[1 - kCx[i]];
+}
+
+// Periodic neighbour offsets of site s: m[a] is the offset to coordinate a - 1, p[a] to a + 1
+// (wrap-aware), so the site r + c is s + shift(o, c) in 32-bit arithmetic (19 N < 2^32 is
+// enforced when a lattice is created).
+struct NOff {
+  int m[3], p[3];
+};
+
+__device__ __forceinline__ NOff neighbour_offsets(const StepParams &P, const Coord &c) {
+  NOff o;
+  const int nxny = P.nx * P.ny;
+  o.m[0] = c.x == 0 ? P.nx - 1 : -1;
+  o.p[0] = c.x == P.nx - 1 ? -(P.nx - 1) : 1;
+  o.m[1] = c.y == 0 ? (P.ny - 1) * P.nx : -P.nx;
+  o.p[1] = c.y == P.ny - 1 ? -(P.ny - 1) * P.nx : P.nx;
+  o.m[2] = c.z == 0 ? (P.nz - 1) * nxny : -nxny;
+  o.p[2] = c.z == P.nz - 1 ? -(P.nz - 1) * nxny : nxny;
+  return o;
+}
+
+// offset of r + (cx, cy, cz) relative to r, each component in {-1, 0, 1}
+__device__ __forceinline__ int shift(const NOff &o, int cx, int cy, int cz) {
+  return (cx < 0 ? o.m[0] : cx > 0 ? o.p[0] : 0) + (cy < 0 ? o.m[1] : cy > 0 ? o.p[1] : 0) +
+         (cz < 0 ? o.m[2] : cz > 0 ? o.p[2] : 0);
+}
+
+// Densities rho_z = sum_i f_zi (appendix, zeroth mode) of site s, stored interleaved
+// (rho_A, rho_B), and j' = sum_z sum_i f_zi c_i (written when jp is not NULL).
+template <class T>
+__device__ __forceinline__ void moments(const StepParams &P, long long s, const T *__restrict__ fin,
+                                        const float *__restrict__ rest, float *__restrict__ rho,
+                                        float *__restrict__ jp) {
+  const Coord c = site_coord(P, s);
+  const NOff o = neighbour_offsets(P, c);
+  const unsigned N32 = (unsigned)P.N, s32 = (unsigned)s;
+  const T *finB = fin + (size_t)kQ * N32;
+  float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
+    const float a = (i == 0 && rest) ? __ldg(rest + s32) : Pop<T>::ld(fin + src, pop_shift(P, 0, i));
+    const float b = (i == 0 && rest) ? __ldg(rest + N32 + s32) : Pop<T>::ld(finB + src, pop_shift(P, 1, i));
+    rA += a;
+    rB += b;
+    jx += kCx[i] * (a + b);
+    jy += kCy[i] * (a + b);
+    jz += kCz[i] * (a + b);
+  }
+  reinterpret_cast<float2 *>(rho)[s] = make_float2(rA, rB);
+  if (jp) {
+    jp[s] = jx;
+    jp[P.N + s] = jy;
+    jp[2 * P.N + s] = jz;
+  }
+}
+
+// Fluid-side solvation force (Eq. solvation_lambda) and momentum return (Sec. 2) gathered at
+// node (x, y, z) from the particles of the 8 unit cells having that node as a corner.
+// ci.row_start is indexed by this lattice's row (z * ny + y); pa, pf by the sorted slot.
+__device__ __forceinline__ void gather_coupling(const StepParams &P, int x, int y, int z, float rA, float rB,
+                                                const ParticleArrays &pa, const ParticleForces &pf,
+                                                CellIndex ci, bool with_momentum, float3 &gA, float3 &gB) {
+  const float rinv = 1.f / (rA + rB);
+  const float sA = rA * rinv, sB = rB * rinv;
+#pragma unroll
+  for (int oz = 0; oz < 2; ++oz) {
+    const int cz = oz ? (z == 0 ? P.nz - 1 : z - 1) : z;
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) {
+      const int cy = oy ? (y == 0 ? P.ny - 1 : y - 1) : y;
+      const int row = cz * P.ny + cy;
+      const int q0 = __ldg(ci.row_start + row), q1 = __ldg(ci.row_start + row + 1);
+      for (int q = q0; q < q1; ++q) {
+        const int4 c = __ldg(pa.cell + q);
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox) {
+          const int cx = ox ? (x == 0 ? P.nx - 1 : x - 1) : x;
+          if (c.x != cx) continue;
+          const float4 fr = __ldg(pa.frac + q);
+          const TypeParams &T = P.types[c.w];
+          const float dx = fr.x - ox, dy = fr.y - oy, dz = fr.z - oz;
+          if (T.lam[0] != 0.f || T.lam[1] != 0.f) {
+            const float3 geo = fs_geometry(dx, dy, dz);
+            const float a = -T.lam[0] * rA, b = -T.lam[1] * rB;
+            gA.x += a * geo.x; gA.y += a * geo.y; gA.z += a * geo.z;
+            gB.x += b * geo.x; gB.y += b * geo.y; gB.z += b * geo.z;
+          }
+          if (with_momentum) {
+            const float w = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
+            const float4 ff = __ldg(pf.fric + q), pA = __ldg(pf.psA + q), pB = __ldg(pf.psB + q);
+            gA.x += w * (-sA * ff.x - pA.x); gA.y += w * (-sA * ff.y - pA.y); gA.z += w * (-sA * ff.z - pA.z);
+            gB.x += w * (-sB * ff.x - pB.x); gB.y += w * (-sB * ff.y - pB.y); gB.z += w * (-sB * ff.z - pB.z);
+          }
+        }
+      }
+    }
+  }
+}
+
+// The lattice update of one step at site s: pull, densities and momentum, Shan-Chen force
+// (Eq. SCforce with psi = rho, g_AA = g_BB = 0), fluid-side solvation force and momentum
+// return from the particles (Sec. 2), barycentric velocity (Eq. momentum_definition), BGK
+// collision with forcing for both components, write.  With 16-bit storage rest_in / rest_out
+// are the FP32 rest populations (rest_out may be NULL: then f_0 is stored with the others).
+template <class T, bool kParticles>
+__device__ __forceinline__ void collide(const StepParams &P, long long s, const T *__restrict__ fin,
+                                        T *__restrict__ fout, const float *__restrict__ rho,
+                                        const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci,
+                                        unsigned *err, const float *__restrict__ rest_in,
+                                        float *__restrict__ rest_out) {
+  const Coord c = site_coord(P, s);
+  const NOff o = neighbour_offsets(P, c);
+  const unsigned N32 = (unsigned)P.N, s32 = (unsigned)s;
+  const T *finB = fin + (size_t)kQ * N32;
+  float fA[kQ], fB[kQ];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
+    fA[i] = Pop<T>::ld(fin + src, pop_shift(P, 0, i));
+    fB[i] = Pop<T>::ld(finB + src, pop_shift(P, 1, i));
+  }
+  if (rest_in) {  // 16-bit storage: the rest populations are kept in FP32
+    fA[0] = __ldg(rest_in + s32);
+    fB[0] = __ldg(rest_in + N32 + s32);
+  }
+  float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    rA += fA[i];
+    rB += fB[i];
+    jx += kCx[i] * (fA[i] + fB[i]);
+    jy += kCy[i] * (fA[i] + fB[i]);
+    jz += kCz[i] * (fA[i] + fB[i]);
+  }
+  // S_z = sum_i w_i rho_z(r + c_i) c_i from the density field of this step
+  const float2 *rho2 = reinterpret_cast<const float2 *>(rho);
+  float SAx = 0.f, SAy = 0.f, SAz = 0.f, SBx = 0.f, SBy = 0.f, SBz = 0.f;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const unsigned nb = (unsigned)((int)s32 + shift(o, kCx[i], kCy[i], kCz[i]));
+    const float2 r2 = __ldg(rho2 + nb);
+    const float a = kW[i] * r2.x, b = kW[i] * r2.y;
+    SAx += kCx[i] * a; SAy += kCy[i] * a; SAz += kCz[i] * a;
+    SBx += kCx[i] * b; SBy += kCy[i] * b; SBz += kCz[i] * b;
+  }
+  float3 gA = make_float3(-P.gAB * rA * SBx, -P.gAB * rA * SBy, -P.gAB * rA * SBz);
+  float3 gB = make_float3(-P.gBA * rB * SAx, -P.gBA * rB * SAy, -P.gBA * rB * SAz);
+  if (kParticles) gather_coupling(P, c.x, c.y, c.z, rA, rB, pa, pf, ci, true, gA, gB);
+  const float r = rA + rB;
+  if (!(rA > 0.f) || !(rB > 0.f) || !isfinite(r)) atomicOr(err, isfinite(r) ? kErrNegDensity : kErrNonFinite);
+  const float rinv = 1.f / r;
+  const float ux = (jx + 0.5f * (gA.x + gB.x)) * rinv;
+  const float uy = (jy + 0.5f * (gA.y + gB.y)) * rinv;
+  const float uz = (jz + 0.5f * (gA.z + gB.z)) * rinv;
+  // BGK + forcing, f* = (1 - 1/tau) f + (1/tau) f^eq + Delta^g, per pair of opposite directions
+  // (c_j = -c_i): f^eq and Delta^g split into parts even and odd in c.
+  {
+    const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float ugA3 = 3.f * (ux * gA.x + uy * gA.y + uz * gA.z);
+    const float ugB3 = 3.f * (ux * gB.x + uy * gB.y + uz * gB.z);
+    const float om = P.inv_tau, om1 = 1.f - om, fp = P.force_pref;
+    const float aA = om * rA, aB = om * rB;
+    fA[0] = om1 * fA[0] + aA * kW[0] * (1.f - usq15) - kW[0] * fp * ugA3;
+    fB[0] = om1 * fB[0] + aB * kW[0] * (1.f - usq15) - kW[0] * fp * ugB3;
+#pragma unroll
+    for (int i = 1; i < kQ; i += 2) {
+      const int j = i + 1;
+      const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
+      const float cgA = kCx[i] * gA.x + kCy[i] * gA.y + kCz[i] * gA.z;
+      const float cgB = kCx[i] * gB.x + kCy[i] * gB.y + kCz[i] * gB.z;
+      const float sym = kW[i] * (1.f + 4.5f * cu * cu - usq15), anti = 3.f * kW[i] * cu;
+      const float wf = kW[i] * fp;
+      const float symA = wf * (9.f * cu * cgA - ugA3), antiA = 3.f * wf * cgA;
+      const float symB = wf * (9.f * cu * cgB - ugB3), antiB = 3.f * wf * cgB;
+      const float fAi = fA[i], fAj = fA[j], fBi = fB[i], fBj = fB[j];
+      fA[i] = om1 * fAi + aA * (sym + anti) + symA + antiA;
+      fA[j] = om1 * fAj + aA * (sym - anti) + symA - antiA;
+      fB[i] = om1 * fBi + aB * (sym + anti) + symB + antiB;
+      fB[j] = om1 * fBj + aB * (sym - anti) + symB - antiB;
+    }
+  }
+  T *foutB = fout + (size_t)kQ * N32;
+  if (rest_out) {
+    // 16-bit storage: each moving population is rounded on store; the FP32 rest population takes
+    // the rounding error of the node's 18 others, so the node's total (and the total mass of each
+    // component) is the one of the collision up to FP32 rounding instead of drifting each step.
+    float eA = 0.f, eB = 0.f;
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+      const auto a = Pop<T>::enc(fA[i], pop_shift(P, 0, i));
+      const auto b = Pop<T>::enc(fB[i], pop_shift(P, 1, i));
+      fout[i * N32 + s32] = a;
+      foutB[i * N32 + s32] = b;
+      eA += fA[i] - Pop<T>::dec(a, pop_shift(P, 0, i));
+      eB += fB[i] - Pop<T>::dec(b, pop_shift(P, 1, i));
+    }
+    rest_out[s32] = fA[0] + eA;
+    rest_out[N32 + s32] = fB[0] + eB;
+  } else {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      Pop<T>::st(fout + (i * N32 + s32), fA[i], pop_shift(P, 0, i));
+      Pop<T>::st(foutB + (i * N32 + s32), fB[i], pop_shift(P, 1, i));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ particles
+
+struct NodeState {
+  float rA, rB;
+  float3 SA, SB;  // sum_i w_i rho_z(r + c_i) c_i
+};
+
+__device__ __forceinline__ NodeState node_state(const StepParams &P, const float *__restrict__ rho, int x, int y,
+                                                int z) {
+  NodeState n;
+  const float2 *rho2 = reinterpret_cast<const float2 *>(rho);  // interleaved (rho_A, rho_B)
+  const long long s = site_index(P, x, y, z);
+  n.rA = __ldg(rho2 + s).x;
+  n.rB = __ldg(rho2 + s).y;
+  n.SA = make_float3(0.f, 0.f, 0.f);
+  n.SB = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const long long nb = site_index(P, wrapi(x + kCx[i], P.nx), wrapi(y + kCy[i], P.ny), wrapi(z + kCz[i], P.nz));
+    const float2 r2 = __ldg(rho2 + nb);
+    const float a = kW[i] * r2.x, b = kW[i] * r2.y;
+    n.SA.x += kCx[i] * a; n.SA.y += kCy[i] * a; n.SA.z += kCz[i] * a;
+    n.SB.x += kCx[i] * b; n.SB.y += kCy[i] * b; n.SB.z += kCz[i] * b;
+  }
+  return n;
+}
+
+// Coupling forces on particle p (Sec. 2): the coupling velocity u_cpl = (j' + (g^SC + F^fs)/2)/rho
+// and the node gradients S/c_s^2 are interpolated trilinearly from the 8 corners of the
+// particle's cell; friction + noise (Eq. NEWTON), solvation (Eq. solvation_kappa) and the
+// reaction of the particle's own fluid-side solvation force (Eq. solvation_lambda).  `step`
+// is this lattice's step counter (the noise counter).
+__device__ __forceinline__ void couple(const StepParams &P, unsigned long long step, int p,
+                                       const ParticleArrays &pa, CellIndex ci, const float *__restrict__ rho,
+                                       const float *__restrict__ jp, const ParticleForces &pf) {
+  const int4 c = pa.cell[p];
+  const float4 fr = pa.frac[p];
+  const float4 v = pa.vel[p];
+  const TypeParams &T = P.types[c.w];
+  float3 up = make_float3(0.f, 0.f, 0.f), gA = up, gB = up, fsr = up;
+  for (int k = 0; k < 8; ++k) {
+    const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
+    const int X = c.x + ox == P.nx ? 0 : c.x + ox;
+    const int Y = c.y + oy == P.ny ? 0 : c.y + oy;
+    const int Z = c.z + oz == P.nz ? 0 : c.z + oz;
+    const NodeState n = node_state(P, rho, X, Y, Z);
+    float3 fA = make_float3(-P.gAB * n.rA * n.SB.x, -P.gAB * n.rA * n.SB.y, -P.gAB * n.rA * n.SB.z);
+    float3 fB = make_float3(-P.gBA * n.rB * n.SA.x, -P.gBA * n.rB * n.SA.y, -P.gBA * n.rB * n.SA.z);
+    gather_coupling(P, X, Y, Z, n.rA, n.rB, pa, pf, ci, false, fA, fB);
+    const long long s = site_index(P, X, Y, Z);
+    const float rinv = 1.f / (n.rA + n.rB);
+    const float w = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
+    up.x += w * (__ldg(jp + s) + 0.5f * (fA.x + fB.x)) * rinv;
+    up.y += w * (__ldg(jp + P.N + s) + 0.5f * (fA.y + fB.y)) * rinv;
+    up.z += w * (__ldg(jp + 2 * P.N + s) + 0.5f * (fA.z + fB.z)) * rinv;
+    gA.x += w * n.SA.x; gA.y += w * n.SA.y; gA.z += w * n.SA.z;
+    gB.x += w * n.SB.x; gB.y += w * n.SB.y; gB.z += w * n.SB.z;
+    if (T.lam[0] != 0.f || T.lam[1] != 0.f) {
+      const float3 geo = fs_geometry(fr.x - ox, fr.y - oy, fr.z - oz);
+      const float a = T.lam[0] * n.rA + T.lam[1] * n.rB;
+      fsr.x += a * geo.x; fsr.y += a * geo.y; fsr.z += a * geo.z;
+    }
+  }
+  float3 R = make_float3(0.f, 0.f, 0.f);
+  if (T.noise_amp > 0.f) {
+    const float3 nn = particle_normals(P.seed, step, (unsigned)pa.pid[p]);
+    R = make_float3(T.noise_amp * nn.x, T.noise_amp * nn.y, T.noise_amp * nn.z);
+  }
+  pf.fric[p] = make_float4(-T.gamma * (v.x - up.x) + R.x, -T.gamma * (v.y - up.y) + R.y,
+                           -T.gamma * (v.z - up.z) + R.z, 0.f);
+  const float kA = -T.kappa[0] / kCs2, kB = -T.kappa[1] / kCs2;
+  pf.psA[p] = make_float4(kA * gA.x, kA * gA.y, kA * gA.z, 0.f);
+  pf.psB[p] = make_float4(kB * gB.x, kB * gB.y, kB * gB.z, 0.f);
+  pf.fsr[p] = make_float4(fsr.x, fsr.y, fsr.z, 0.f);
+}
+
+__device__ __forceinline__ int min_image_cells(int d, int n) {
+  d = wrapi(d, n);
+  return 2 * d > n ? d - n : d;
+}
+
+// Short-range pair forces on particle p (WCA, Sec. 4.1; screened Coulomb, Sec. 4.4) over the
+// rows within `reach` cells, and bonded forces from its own bond list (bond_start indexed by
+// the particle id, bond_other holding ids, slot_of_id mapping ids to sorted slots; NULL
+// bond_start = no bonds).  Each particle computes its own force (pairs are visited from both
+// ends): no atomics, fixed order.
+__device__ __forceinline__ void pairs(const StepParams &P, int p, const ParticleArrays &pa, CellIndex ci,
+                                      const int *__restrict__ bond_start, const int *__restrict__ bond_other,
+                                      const int *__restrict__ slot_of_id, const ParticleForces &pf,
+                                      unsigned *err) {
+  const int4 c = pa.cell[p];
+  const float4 fr = pa.frac[p];
+  float3 F = make_float3(0.f, 0.f, 0.f);
+  const int m = P.reach;
+  const bool allz = 2 * m + 1 >= P.nz, ally = 2 * m + 1 >= P.ny, allx = 2 * m + 1 >= P.nx;
+  const int z0 = allz ? 0 : -m, z1 = allz ? P.nz - 1 : m;
+  const int y0 = ally ? 0 : -m, y1 = ally ? P.ny - 1 : m;
+  const float Lx = (float)P.nx, Ly = (float)P.ny, Lz = (float)P.nz;
+  if (m > 0) {
+    for (int dz = z0; dz <= z1; ++dz) {
+      const int cz = allz ? dz : wrapi(c.z + dz, P.nz);
+      for (int dy = y0; dy <= y1; ++dy) {
+        const int cy = ally ? dy : wrapi(c.y + dy, P.ny);
+        const int row = cz * P.ny + cy;
+        const int q0 = ci.row_start[row], q1 = ci.row_start[row + 1];
+        for (int q = q0; q < q1; ++q) {
+          if (q == p) continue;
+          const int4 cq = pa.cell[q];
+          const int dcx = min_image_cells(c.x - cq.x, P.nx);
+          if (!allx && (dcx > m || dcx < -m)) continue;
+          const float4 fq = pa.frac[q];
+          float dx = (float)dcx + (fr.x - fq.x);
+          float dy_ = (float)min_image_cells(c.y - cq.y, P.ny) + (fr.y - fq.y);
+          float dz_ = (float)min_image_cells(c.z - cq.z, P.nz) + (fr.z - fq.z);
+          dx -= Lx * rintf(dx / Lx);
+          dy_ -= Ly * rintf(dy_ / Ly);
+          dz_ -= Lz * rintf(dz_ / Lz);
+          const float r2 = dx * dx + dy_ * dy_ + dz_ * dz_;
+          float fscal = 0.f;  // -dU/dr / r
+          const PairParams &pp = P.pairs[c.w * LBMD_MAX_TYPES + cq.w];
+          if (pp.eps > 0.f && r2 < pp.rc2) {
+            const float sr2 = pp.sigma2 / r2;
+            const float sr6 = sr2 * sr2 * sr2;
+            fscal += 24.f * pp.eps * (2.f * sr6 * sr6 - sr6) / r2;
+          }
+          const float qq = fr.w * fq.w;
+          if (P.dh_lB != 0.f && qq != 0.f && r2 < P.dh_rc2) {
+            const float r = sqrtf(r2);
+            fscal += qq * P.dh_lB * expf(-P.dh_kappa * r) * (1.f / r2 + P.dh_kappa / r) / r;
+          }
+          F.x += fscal * dx;
+          F.y += fscal * dy_;
+          F.z += fscal * dz_;
+        }
+      }
+    }
+  }
+  if (bond_start) {
+    const int id = pa.pid[p];
+    for (int b = bond_start[id]; b < bond_start[id + 1]; ++b) {
+      const int q = slot_of_id[bond_other[b]];
+      const int4 cq = pa.cell[q];
+      const float4 fq = pa.frac[q];
+      float dx = (float)min_image_cells(c.x - cq.x, P.nx) + (fr.x - fq.x);
+      float dy_ = (float)min_image_cells(c.y - cq.y, P.ny) + (fr.y - fq.y);
+      float dz_ = (float)min_image_cells(c.z - cq.z, P.nz) + (fr.z - fq.z);
+      dx -= Lx * rintf(dx / Lx);
+      dy_ -= Ly * rintf(dy_ / Ly);
+      dz_ -= Lz * rintf(dz_ / Lz);
+      const float r2 = dx * dx + dy_ * dy_ + dz_ * dz_;
+      float fscal;
+      if (P.bond_kind == LBMD_BOND_FENE) {
+        const float x2 = r2 / (P.bond_r * P.bond_r);
+        if (!(x2 < 1.f)) {
+          atomicOr(err, kErrBond);
+          continue;
+        }
+        fscal = -P.bond_k / (1.f - x2);
+      } else {
+        const float r = sqrtf(r2);
+        fscal = r > 0.f ? -P.bond_k * (r - P.bond_r) / r : 0.f;
+      }
+      F.x += fscal * dx;
+      F.y += fscal * dy_;
+      F.z += fscal * dz_;
+    }
+  }
+  pf.pair[p] = make_float4(F.x, F.y, F.z, 0.f);
+}
+
+// Particle update of slot p: v += F dt / m, x += v dt, periodic wrap kept as (cell,
+// fraction).  Reads src, writes dst (the same arrays for an update in place).
+__device__ __forceinline__ void integrate(const StepParams &P, int p, const ParticleArrays &src,
+                                          const ParticleArrays &dst, const ParticleForces &pf, unsigned *err) {
+  int4 c = src.cell[p];
+  float4 fr = src.frac[p];
+  float4 v = src.vel[p];
+  if (dst.pid != src.pid) dst.pid[p] = src.pid[p];
+  const TypeParams &T = P.types[c.w];
+  const float4 a = pf.fric[p], b = pf.psA[p], d = pf.psB[p], e = pf.fsr[p], g = pf.pair[p];
+  const float Fx = a.x + b.x + d.x + e.x + g.x;
+  const float Fy = a.y + b.y + d.y + e.y + g.y;
+  const float Fz = a.z + b.z + d.z + e.z + g.z;
+  pf.total[p] = make_float4(Fx, Fy, Fz, 0.f);
+  v.x += Fx * P.dt * T.inv_mass;
+  v.y += Fy * P.dt * T.inv_mass;
+  v.z += Fz * P.dt * T.inv_mass;
+  float nx_ = fr.x + v.x * P.dt, ny_ = fr.y + v.y * P.dt, nz_ = fr.z + v.z * P.dt;
+  const float lim = 1.0e6f;
+  if (!(fabsf(nx_) < lim && fabsf(ny_) < lim && fabsf(nz_) < lim)) {
+    atomicOr(err, kErrParticle | kErrNonFinite);
+    dst.cell[p] = c;  // position kept: every index stays inside the lattice
+    dst.frac[p] = fr;
+    dst.vel[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const float sx = floorf(nx_), sy = floorf(ny_), sz = floorf(nz_);
+  nx_ -= sx; ny_ -= sy; nz_ -= sz;
+  int ix = (int)sx, iy = (int)sy, iz = (int)sz;
+  if (nx_ >= 1.f) { nx_ = 0.f; ++ix; }
+  if (ny_ >= 1.f) { ny_ = 0.f; ++iy; }
+  if (nz_ >= 1.f) { nz_ = 0.f; ++iz; }
+  c.x = wrapi(c.x + ix, P.nx);
+  c.y = wrapi(c.y + iy, P.ny);
+  c.z = wrapi(c.z + iz, P.nz);
+  dst.cell[p] = c;
+  dst.frac[p] = make_float4(nx_, ny_, nz_, fr.w);
+  dst.vel[p] = v;
+}
+
+// ------------------------------------------------------------------ row scan
+
+// Exclusive scan of one value per thread over a block of kScanThreads threads (warp shuffles,
+// then a scan of the warp totals); `total` receives the block's sum.  Every thread of the block
+// must call it.
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = 8;
+constexpr int kScanRows = kScanThreads * kScanPerThread;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot, int &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int t = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = t;  // inclusive warp-total prefix
+  }
+  __syncthreads();
+  total = warp_tot[kScanThreads / 32 - 1];
+  const int before = warp == 0 ? 0 : warp_tot[warp - 1];
+  return before + x - v;
+}
+
+}  // namespace site
+}  // namespace lbmd

@@ -127,17 +127,6 @@ int sort_particles(lbmd_ctx *c) {
   return launched(c, "particle sort", 8);
 }
 
-double max_range(const lbmd_ctx *c) {
-  double r = 0.0;
-  for (int i = 0; i < c->P.ntypes; ++i)
-    for (int j = 0; j < c->P.ntypes; ++j) {
-      const PairParams &pp = c->P.pairs[i * LBMD_MAX_TYPES + j];
-      if (pp.eps > 0.f) r = std::fmax(r, std::sqrt((double)pp.rc2));
-    }
-  if (c->P.dh_lB != 0.f) r = std::fmax(r, std::sqrt((double)c->P.dh_rc2));
-  return r;
-}
-
 }  // namespace
 
 void lbmd::set_context_free_error(const std::string &m) { g_create_error = m; }
@@ -151,36 +140,18 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
   if (!prm || !out) return fail(c, LBMD_E_INVALID_ARG, "null argument");
   *out = nullptr;
   if (warnings) *warnings = 0;
-  if (prm->nx < 1 || prm->ny < 1 || prm->nz < 1) return fail(c, LBMD_E_INVALID_ARG, "lattice sizes must be >= 1");
-  if ((double)prm->nx * prm->ny * prm->nz * kQ >= 4294967296.0)  // 32-bit population offsets
-    return fail(c, LBMD_E_INVALID_ARG, "lattice too large: nx*ny*nz must be below 2^32/19");
-  if (!(prm->tau_r > 0.5)) return fail(c, LBMD_E_INVALID_ARG, "tau_r must exceed 1/2");
-  if (prm->dt != 1.0) return fail(c, LBMD_E_INVALID_ARG, "dt must equal the lattice time step 1");
-  if (!(prm->kT >= 0.0)) return fail(c, LBMD_E_INVALID_ARG, "kT must be >= 0");
-  if (prm->storage != LBMD_STORAGE_FP32 && prm->storage != LBMD_STORAGE_FP16_SHIFTED &&
-      prm->storage != LBMD_STORAGE_BF16_SHIFTED)
-    return fail(c, LBMD_E_INVALID_ARG, "unknown storage");
-  if (!(prm->rho0_A >= 0.0) || !(prm->rho0_B >= 0.0) || !std::isfinite(prm->rho0_A) || !std::isfinite(prm->rho0_B))
-    return fail(c, LBMD_E_INVALID_ARG, "rho0_A, rho0_B must be finite and >= 0");
+  {
+    std::string why;
+    const int r = check_params(prm, why);
+    if (r) return fail(c, r, why);
+  }
   c = new lbmd_ctx();
   c->prm = *prm;
   c->st = (cudaStream_t)stream;
   cudaGetDevice(&c->dev);
   StepParams &P = c->P;
-  P.nx = prm->nx; P.ny = prm->ny; P.nz = prm->nz;
-  P.nrows = prm->ny * prm->nz;
-  P.N = (long long)prm->nx * prm->ny * prm->nz;
-  P.inv_tau = (float)(1.0 / prm->tau_r);
-  P.force_pref = (float)(1.0 - 0.5 / prm->tau_r);
-  P.gAB = (float)prm->g_AB; P.gBA = (float)prm->g_BA;
-  P.dt = (float)prm->dt;
-  P.storage = prm->storage;
-  P.rho0[0] = prm->storage == LBMD_STORAGE_FP32 ? 0.f : (float)prm->rho0_A;
-  P.rho0[1] = prm->storage == LBMD_STORAGE_FP32 ? 0.f : (float)prm->rho0_B;
+  fill_step_params(prm, P);
   c->pop_elem = prm->storage == LBMD_STORAGE_FP32 ? 4 : 2;
-  P.seed = prm->seed;
-  P.ntypes = 0;
-  P.bond_kind = LBMD_BOND_FENE;
   cudaError_t e = cudaSuccess;
   const size_t npop = (size_t)2 * kQ * P.N * c->pop_elem;  // bytes; >= 19 N floats of staging
   if ((e = dalloc(&c->pop[0], npop)) != cudaSuccess || (e = dalloc(&c->pop[1], npop)) != cudaSuccess ||
@@ -200,11 +171,7 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
     lbmd_destroy(c);
     return fail(nullptr, LBMD_E_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
   }
-  unsigned w = 0;
-  if (1.0 / 3.0 * (prm->tau_r - 0.5) < 1e-3) w |= LBMD_WARN_VISCOSITY;
-  if (prm->g_AB != prm->g_BA) w |= LBMD_WARN_ASYMMETRIC_G;
-  const double r0 = prm->rho0_A + prm->rho0_B;
-  if (prm->kT > 0.0 && r0 > 0.0 && std::sqrt(prm->kT / (r0 / 3.0)) > 0.5) w |= LBMD_WARN_BOLTZMANN;
+  const unsigned w = param_warnings(prm);
   if (warnings) *warnings = w;
   *out = c;
   return LBMD_OK;
@@ -227,37 +194,10 @@ int lbmd_set_types(lbmd_ctx *c, int ntypes, const lbmd_ptype *types, int npairs,
                    unsigned *warnings) {
   if (!c) return LBMD_E_INVALID_ARG;
   if (warnings) *warnings = 0;
-  if (ntypes < 1 || ntypes > LBMD_MAX_TYPES || !types || npairs < 0 || (npairs > 0 && !pairs))
-    return fail(c, LBMD_E_INVALID_ARG, "bad type table");
-  StepParams &P = c->P;
   unsigned w = 0;
-  for (int t = 0; t < ntypes; ++t) {
-    const lbmd_ptype &T = types[t];
-    if (!(T.mass > 0.0) || !(T.gamma >= 0.0)) return fail(c, LBMD_E_INVALID_ARG, "mass must be > 0, gamma >= 0");
-    TypeParams &D = P.types[t];
-    D.kappa[0] = (float)T.kappa_A; D.kappa[1] = (float)T.kappa_B;
-    D.lam[0] = (float)T.lambda_A; D.lam[1] = (float)T.lambda_B;
-    D.gamma = (float)T.gamma;
-    D.inv_mass = (float)(1.0 / T.mass);
-    D.mass = (float)T.mass;
-    D.noise_amp = (float)std::sqrt(2.0 * c->prm.kT * T.gamma / c->prm.dt);
-    if (T.gamma * c->prm.dt / T.mass > 0.5) w |= LBMD_WARN_GAMMA_DT;
-  }
-  for (int i = 0; i < LBMD_MAX_TYPES * LBMD_MAX_TYPES; ++i) P.pairs[i] = PairParams{0.f, 0.f, 0.f, 0.f};
-  for (int k = 0; k < npairs; ++k) {
-    const lbmd_pair &pp = pairs[k];
-    if (pp.type_i < 0 || pp.type_i >= ntypes || pp.type_j < 0 || pp.type_j >= ntypes || pp.wca_eps < 0 ||
-        !(pp.wca_sigma > 0))
-      return fail(c, LBMD_E_INVALID_ARG, "bad pair entry");
-    const double rc = std::pow(2.0, 1.0 / 6.0) * pp.wca_sigma;
-    if (2.0 * rc >= std::min(P.nx, std::min(P.ny, P.nz)))
-      return fail(c, LBMD_E_INVALID_ARG, "WCA range must be below half the smallest box edge");
-    PairParams d{(float)pp.wca_eps, (float)(pp.wca_sigma * pp.wca_sigma), (float)(rc * rc), 0.f};
-    P.pairs[pp.type_i * LBMD_MAX_TYPES + pp.type_j] = d;
-    P.pairs[pp.type_j * LBMD_MAX_TYPES + pp.type_i] = d;
-  }
-  P.ntypes = ntypes;
-  P.reach = (int)std::ceil(max_range(c));
+  std::string why;
+  const int r = apply_types(c->P, c->prm.kT, c->prm.dt, ntypes, types, npairs, pairs, w, why);
+  if (r) return fail(c, r, why);
   c->types_set = true;
   if (warnings) *warnings = w;
   return LBMD_OK;
@@ -265,16 +205,9 @@ int lbmd_set_types(lbmd_ctx *c, int ntypes, const lbmd_ptype *types, int npairs,
 
 int lbmd_set_debye_hueckel(lbmd_ctx *c, double lB, double kappa_D, double rc) {
   if (!c) return LBMD_E_INVALID_ARG;
-  if (lB != 0.0) {
-    if (!(rc > 0.0) || !(kappa_D >= 0.0)) return fail(c, LBMD_E_INVALID_ARG, "bad Debye-Hueckel parameters");
-    if (2.0 * rc >= std::min(c->P.nx, std::min(c->P.ny, c->P.nz)))
-      return fail(c, LBMD_E_INVALID_ARG, "cut-off must be below half the smallest box edge");
-  }
-  c->P.dh_lB = (float)lB;
-  c->P.dh_kappa = (float)kappa_D;
-  c->P.dh_rc2 = (float)(rc * rc);
-  c->P.reach = (int)std::ceil(max_range(c));
-  return LBMD_OK;
+  std::string why;
+  const int r = apply_debye_hueckel(c->P, lB, kappa_D, rc, why);
+  return r ? fail(c, r, why) : LBMD_OK;
 }
 
 int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const float *u) {
@@ -334,32 +267,13 @@ int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, con
   if (n > 0 && !c->types_set) return fail(c, LBMD_E_STATE, "set the particle types first");
   cudaSetDevice(c->dev);
   StepParams &P = c->P;
-  const int L[3] = {P.nx, P.ny, P.nz};
-  std::vector<int4> hc(n);
-  std::vector<float4> hf(n), hv(n);
-  std::vector<int> hid(n);
-  for (int p = 0; p < n; ++p) {
-    if (type[p] < 0 || type[p] >= P.ntypes) return fail(c, LBMD_E_INVALID_ARG, "particle type out of range");
-    int ci[3];
-    float fr[3];
-    for (int a = 0; a < 3; ++a) {
-      const double xa = x[3 * p + a];
-      if (!std::isfinite(xa) || !std::isfinite(v[3 * p + a])) return fail(c, LBMD_E_INVALID_ARG, "non-finite particle");
-      double w = xa - L[a] * std::floor(xa / L[a]);
-      if (w >= L[a]) w = 0.0;
-      int cell = (int)std::floor(w);
-      float f = (float)(w - cell);
-      if (f >= 1.f) {
-        f = 0.f;
-        cell = (cell + 1) % L[a];
-      }
-      ci[a] = cell;
-      fr[a] = f;
-    }
-    hc[p] = make_int4(ci[0], ci[1], ci[2], type[p]);
-    hf[p] = make_float4(fr[0], fr[1], fr[2], q ? (float)q[p] : 0.f);
-    hv[p] = make_float4((float)v[3 * p], (float)v[3 * p + 1], (float)v[3 * p + 2], 0.f);
-    hid[p] = p;
+  std::vector<int4> hc;
+  std::vector<float4> hf, hv;
+  std::vector<int> hid;
+  {
+    std::string why;
+    const int r = convert_particles(P, n, x, v, type, q, hc, hf, hv, hid, why);
+    if (r) return fail(c, r, why);
   }
   if (n > c->cap) {
     free_particles(c);

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "lbmd.h"
 
@@ -118,48 +119,6 @@ __device__ __forceinline__ float3 fs_geometry(float dx, float dy, float dz) {
   return s;
 }
 
-// Fluid-side solvation force (Eq. solvation_lambda) and momentum return (Sec. 2) gathered at
-// node (x, y, z) from the particles of the 8 unit cells having that node as a corner.
-__device__ __forceinline__ void gather_coupling(const StepParams &P, int x, int y, int z, float rA, float rB,
-                                                const ParticleArrays &pa, const ParticleForces &pf,
-                                                CellIndex ci, bool with_momentum, float3 &gA, float3 &gB) {
-  const float rinv = 1.f / (rA + rB);
-  const float sA = rA * rinv, sB = rB * rinv;
-#pragma unroll
-  for (int oz = 0; oz < 2; ++oz) {
-    const int cz = oz ? (z == 0 ? P.nz - 1 : z - 1) : z;
-#pragma unroll
-    for (int oy = 0; oy < 2; ++oy) {
-      const int cy = oy ? (y == 0 ? P.ny - 1 : y - 1) : y;
-      const int row = cz * P.ny + cy;
-      const int q0 = __ldg(ci.row_start + row), q1 = __ldg(ci.row_start + row + 1);
-      for (int q = q0; q < q1; ++q) {
-        const int4 c = __ldg(pa.cell + q);
-#pragma unroll
-        for (int ox = 0; ox < 2; ++ox) {
-          const int cx = ox ? (x == 0 ? P.nx - 1 : x - 1) : x;
-          if (c.x != cx) continue;
-          const float4 fr = __ldg(pa.frac + q);
-          const TypeParams &T = P.types[c.w];
-          const float dx = fr.x - ox, dy = fr.y - oy, dz = fr.z - oz;
-          if (T.lam[0] != 0.f || T.lam[1] != 0.f) {
-            const float3 geo = fs_geometry(dx, dy, dz);
-            const float a = -T.lam[0] * rA, b = -T.lam[1] * rB;
-            gA.x += a * geo.x; gA.y += a * geo.y; gA.z += a * geo.z;
-            gB.x += b * geo.x; gB.y += b * geo.y; gB.z += b * geo.z;
-          }
-          if (with_momentum) {
-            const float w = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
-            const float4 ff = __ldg(pf.fric + q), pA = __ldg(pf.psA + q), pB = __ldg(pf.psB + q);
-            gA.x += w * (-sA * ff.x - pA.x); gA.y += w * (-sA * ff.y - pA.y); gA.z += w * (-sA * ff.z - pA.z);
-            gB.x += w * (-sB * ff.x - pB.x); gB.y += w * (-sB * ff.y - pB.y); gB.z += w * (-sB * ff.z - pB.z);
-          }
-        }
-      }
-    }
-  }
-}
-
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): multipliers 0xD2511F53, 0xCD9E8D57,
 // Weyl key increments 0x9E3779B9, 0xBB67AE85, ten rounds.
 __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
@@ -194,6 +153,18 @@ __device__ __forceinline__ float3 particle_normals(unsigned long long seed, unsi
 
 // Message returned by lbmd_last_error(NULL) (calls made without a context).
 void set_context_free_error(const std::string &m);
+
+// Argument handling shared by single contexts and batches (lbmd_api.cu).  Each returns LBMD_OK or
+// an LBMD_E_* code with the reason in `why`; nothing is changed on failure.
+int check_params(const lbmd_params *prm, std::string &why);
+void fill_step_params(const lbmd_params *prm, StepParams &P);
+unsigned param_warnings(const lbmd_params *prm);
+int apply_types(StepParams &P, double kT, double dt, int ntypes, const lbmd_ptype *types, int npairs,
+                const lbmd_pair *pairs, unsigned &warnings, std::string &why);
+int apply_debye_hueckel(StepParams &P, double lB, double kappa_D, double rc, std::string &why);
+int convert_particles(const StepParams &P, int n, const double *x, const double *v, const int *type,
+                      const double *q, std::vector<int4> &cell, std::vector<float4> &frac,
+                      std::vector<float4> &vel, std::vector<int> &id, std::string &why);
 
 // ------------------------------------------------------------------ launch wrappers
 // lattice (lb_fluid.cu); population buffers are void*: their element type is P.storage.  With

@@ -37,13 +37,24 @@ LBMD_WARN_VISCOSITY = 1 << 1
 LBMD_WARN_BOLTZMANN = 1 << 2
 LBMD_WARN_ASYMMETRIC_G = 1 << 3
 LBMD_MAX_TYPES = 8
+LBMD_SLOT_EMPTY = 0
+LBMD_SLOT_ACTIVE = 1
+LBMD_SLOT_DONE = 2
+LBMD_SLOT_FAILED = 3
 
 # every symbol include/lbmd.h declares
 EXPORTS = ("lbmd_create", "lbmd_destroy", "lbmd_set_types", "lbmd_set_debye_hueckel", "lbmd_init_fluid",
            "lbmd_set_populations", "lbmd_get_populations", "lbmd_set_particles", "lbmd_set_bonds",
            "lbmd_step", "lbmd_sync", "lbmd_clear_error", "lbmd_get_fields", "lbmd_get_particles",
            "lbmd_diagnostics", "lbmd_step_count", "lbmd_profile_enable", "lbmd_profile_read",
-           "lbmd_launch_count", "lbmd_last_error", "lbmd_fluid_moments_static")
+           "lbmd_launch_count", "lbmd_last_error", "lbmd_fluid_moments_static",
+           "lbmd_batch_create", "lbmd_batch_destroy", "lbmd_batch_add", "lbmd_batch_remove",
+           "lbmd_batch_set_types", "lbmd_batch_set_debye_hueckel", "lbmd_batch_init_fluid",
+           "lbmd_batch_set_particles", "lbmd_batch_step", "lbmd_batch_poll", "lbmd_batch_slot_error",
+           "lbmd_batch_step_count", "lbmd_batch_get_populations", "lbmd_batch_get_fields",
+           "lbmd_batch_get_particles", "lbmd_batch_diagnostics", "lbmd_batch_set_config",
+           "lbmd_batch_get_config", "lbmd_batch_tune", "lbmd_batch_info", "lbmd_batch_launch_count",
+           "lbmd_batch_last_error")
 
 
 class LbmdError(RuntimeError):
@@ -98,6 +109,30 @@ def _load():
         "lbmd_launch_count": (ctypes.c_int64, [P]),
         "lbmd_last_error": (ctypes.c_char_p, [P]),
         "lbmd_fluid_moments_static": (I, [P, I, I, I, P, P]),
+        "lbmd_batch_create": (I, [ctypes.c_size_t, I, I, P, ctypes.POINTER(P)]),
+        "lbmd_batch_destroy": (None, [P]),
+        "lbmd_batch_add": (I, [P, ctypes.POINTER(lbmd_params), I, ctypes.c_int64, ctypes.POINTER(I),
+                               ctypes.POINTER(ctypes.c_uint)]),
+        "lbmd_batch_remove": (I, [P, I]),
+        "lbmd_batch_set_types": (I, [P, I, I, P, I, P, ctypes.POINTER(ctypes.c_uint)]),
+        "lbmd_batch_set_debye_hueckel": (I, [P, I, D, D, D]),
+        "lbmd_batch_init_fluid": (I, [P, I, P, P, P]),
+        "lbmd_batch_set_particles": (I, [P, I, I, P, P, P, P]),
+        "lbmd_batch_step": (I, [P, I]),
+        "lbmd_batch_poll": (I, [P, P]),
+        "lbmd_batch_slot_error": (I, [P, I]),
+        "lbmd_batch_step_count": (ctypes.c_int64, [P, I]),
+        "lbmd_batch_get_populations": (I, [P, I, I, P]),
+        "lbmd_batch_get_fields": (I, [P, I, P, P, P]),
+        "lbmd_batch_get_particles": (I, [P, I, P, P, P]),
+        "lbmd_batch_diagnostics": (I, [P, I, P]),
+        "lbmd_batch_set_config": (I, [P, I, I, I, I]),
+        "lbmd_batch_get_config": (I, [P, P]),
+        "lbmd_batch_tune": (I, [P, P, P]),
+        "lbmd_batch_info": (I, [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "lbmd_batch_launch_count": (ctypes.c_int64, [P]),
+        "lbmd_batch_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -251,6 +286,138 @@ def lbmd_fluid_moments_static(f_dev_ptr: int, dims, out_dev_ptr: int, stream=Non
 
 def lbmd_last_error(ctx) -> str:
     return _lib.lbmd_last_error(ctx).decode(errors="replace")
+
+
+# ------------------------------------------------------------------ batches
+def _bcheck(b, code: int):
+    if code != LBMD_OK:
+        raise LbmdError(code, _lib.lbmd_batch_last_error(b).decode(errors="replace"))
+    return code
+
+
+def lbmd_batch_create(mem_budget: int = 0, storage: int = LBMD_STORAGE_FP32, max_slots: int = 1024, stream=None):
+    b = ctypes.c_void_p()
+    _bcheck(None, _lib.lbmd_batch_create(mem_budget, storage, max_slots, stream_handle(stream), ctypes.byref(b)))
+    return b
+
+
+def lbmd_batch_destroy(b) -> None:
+    _lib.lbmd_batch_destroy(b)
+
+
+def lbmd_batch_add(b, params: lbmd_params, np_max: int, total_steps: int):
+    """Returns (slot, warnings); raises LbmdError(LBMD_E_NOMEM) when the replica does not fit."""
+    slot = ctypes.c_int(-1)
+    w = ctypes.c_uint(0)
+    _bcheck(b, _lib.lbmd_batch_add(b, ctypes.byref(params), np_max, total_steps, ctypes.byref(slot), ctypes.byref(w)))
+    return slot.value, w.value
+
+
+def lbmd_batch_remove(b, slot: int) -> None:
+    _bcheck(b, _lib.lbmd_batch_remove(b, slot))
+
+
+def lbmd_batch_set_types(b, slot: int, types, pairs=()) -> int:
+    t = (lbmd_ptype * len(types))(*types)
+    pr = (lbmd_pair * max(1, len(pairs)))(*pairs)
+    w = ctypes.c_uint(0)
+    _bcheck(b, _lib.lbmd_batch_set_types(b, slot, len(types), t, len(pairs), pr, ctypes.byref(w)))
+    return w.value
+
+
+def lbmd_batch_set_debye_hueckel(b, slot: int, lB: float, kappa_D: float, rc: float) -> None:
+    _bcheck(b, _lib.lbmd_batch_set_debye_hueckel(b, slot, lB, kappa_D, rc))
+
+
+def lbmd_batch_init_fluid(b, slot: int, rhoA, rhoB, u=None) -> None:
+    x, y, z = _f32(rhoA), _f32(rhoB), _f32(u)
+    _bcheck(b, _lib.lbmd_batch_init_fluid(b, slot, _p(x), _p(y), _p(z)))
+
+
+def lbmd_batch_set_particles(b, slot: int, x, v, type_, q=None) -> None:
+    x, v = _f64(x).reshape(-1, 3), _f64(v).reshape(-1, 3)
+    t = np.ascontiguousarray(type_, dtype=np.int32)
+    qq = _f64(q)
+    _bcheck(b, _lib.lbmd_batch_set_particles(b, slot, len(t), _p(x), _p(v), _p(t), _p(qq)))
+
+
+def lbmd_batch_step(b, nsteps: int) -> None:
+    _bcheck(b, _lib.lbmd_batch_step(b, nsteps))
+
+
+def lbmd_batch_poll(b, max_slots: int) -> np.ndarray:
+    st = np.zeros(max_slots, dtype=np.int32)
+    _bcheck(b, _lib.lbmd_batch_poll(b, _p(st)))
+    return st
+
+
+def lbmd_batch_slot_error(b, slot: int) -> int:
+    return int(_lib.lbmd_batch_slot_error(b, slot))
+
+
+def lbmd_batch_step_count(b, slot: int) -> int:
+    return int(_lib.lbmd_batch_step_count(b, slot))
+
+
+def lbmd_batch_get_populations(b, slot: int, comp: int, shape) -> np.ndarray:
+    out = np.empty((19,) + tuple(shape), dtype=np.float32)
+    _bcheck(b, _lib.lbmd_batch_get_populations(b, slot, comp, _p(out)))
+    return out
+
+
+def lbmd_batch_get_fields(b, slot: int, shape, want_u: bool = True):
+    a = np.empty(tuple(shape), dtype=np.float32)
+    c = np.empty(tuple(shape), dtype=np.float32)
+    u = np.empty(tuple(shape) + (3,), dtype=np.float32) if want_u else None
+    _bcheck(b, _lib.lbmd_batch_get_fields(b, slot, _p(a), _p(c), _p(u)))
+    return a, c, u
+
+
+def lbmd_batch_get_particles(b, slot: int, n: int):
+    x, v, f = np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3))
+    _bcheck(b, _lib.lbmd_batch_get_particles(b, slot, _p(x), _p(v), _p(f)))
+    return x, v, f
+
+
+def lbmd_batch_diagnostics(b, slot: int) -> np.ndarray:
+    out = np.zeros(8)
+    _bcheck(b, _lib.lbmd_batch_diagnostics(b, slot, _p(out)))
+    return out
+
+
+def lbmd_batch_set_config(b, tile_sites: int, grid_moments: int, grid_collide: int, collide_blocks: int) -> None:
+    _bcheck(b, _lib.lbmd_batch_set_config(b, tile_sites, grid_moments, grid_collide, collide_blocks))
+
+
+def lbmd_batch_get_config(b) -> dict:
+    cfg = np.zeros(5, dtype=np.int32)
+    _bcheck(b, _lib.lbmd_batch_get_config(b, _p(cfg)))
+    return dict(zip(("tile_sites", "grid_moments", "grid_collide", "collide_blocks", "grid_particles"),
+                    (int(v) for v in cfg)))
+
+
+def lbmd_batch_tune(b):
+    """Returns (config dict, (moments_ms, collide_ms))."""
+    cfg = np.zeros(5, dtype=np.int32)
+    ms = np.zeros(2)
+    _bcheck(b, _lib.lbmd_batch_tune(b, _p(cfg), _p(ms)))
+    keys = ("tile_sites", "grid_moments", "grid_collide", "collide_blocks", "grid_particles")
+    return dict(zip(keys, (int(v) for v in cfg))), (float(ms[0]), float(ms[1]))
+
+
+def lbmd_batch_info(b) -> dict:
+    bud, used = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    occ, mx = ctypes.c_int(0), ctypes.c_int(0)
+    _bcheck(b, _lib.lbmd_batch_info(b, ctypes.byref(bud), ctypes.byref(used), ctypes.byref(occ), ctypes.byref(mx)))
+    return dict(budget=bud.value, used=used.value, occupied=occ.value, max_slots=mx.value)
+
+
+def lbmd_batch_launch_count(b) -> int:
+    return int(_lib.lbmd_batch_launch_count(b))
+
+
+def lbmd_batch_last_error(b) -> str:
+    return _lib.lbmd_batch_last_error(b).decode(errors="replace")
 
 
 def params(dims, tau_r=1.0, g_AB=0.0, g_BA=None, kT=0.0, seed=0, storage=LBMD_STORAGE_FP32,

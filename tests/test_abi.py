@@ -56,3 +56,12 @@ def test_product_path_has_no_oracle_or_cpu_fallback():
     for f in os.listdir(csrc):
         assert "lbmd_oracle" not in open(os.path.join(csrc, f)).read()
     assert "raise ImportError" in src
+
+
+@pytest.mark.parametrize("storage,max_slots", [(7, 4), (0, 0), (0, 70000)])
+def test_batch_create_rejects_invalid_arguments_without_device(storage, max_slots):
+    from paper_1306_0788_gb300 import lbmd
+    with pytest.raises(lbmd.LbmdError) as e:
+        lbmd.lbmd_batch_create(0, storage, max_slots)
+    assert e.value.code == lbmd.LBMD_E_INVALID_ARG
+    assert lbmd.lbmd_batch_last_error(None)
