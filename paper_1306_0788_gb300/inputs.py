@@ -193,3 +193,38 @@ def bead_spring_chains(n_chains: int, length: int, dims, bond: float = 0.97, see
                       for b in range(length - 1)], dtype=np.int32).reshape(-1, 2)
     q = np.where(np.arange(n) // length < n_chains // 2, 1.0, -1.0)
     return pos, bonds, q
+
+
+def spaced_particles(n: int, dims, spacing: float = 2.0, seed: int = 0):
+    """n points, at most one per cubic cell of edge `spacing` (cells chosen at random without
+    replacement), each uniform in the central half of its cell: any two points are at least
+    spacing / 2 apart, across the periodic boundary too.  Vectorised, for many replicas."""
+    L = np.array(dims, dtype=np.float64)
+    nc = np.maximum((L // spacing).astype(int), 1)
+    ncell = int(nc.prod())
+    if n > ncell:
+        raise ValueError("at most %d particles fit with spacing %g" % (ncell, spacing))
+    g = rng(seed)
+    cells = g.choice(ncell, size=n, replace=False)
+    ci = np.stack([cells % nc[0], (cells // nc[0]) % nc[1], cells // (nc[0] * nc[1])], axis=1)
+    return (ci + 0.25 + 0.5 * g.uniform(0.0, 1.0, size=(n, 3))) * spacing
+
+
+def serving_requests(n: int, rate: float, seed: int = 0, edge=(16, 128), np_max: int = 5000,
+                     g_rho=(1.2, 2.1), gamma=(0.1, 2.0), steps: int = 1000, fill: float = 0.5,
+                     spacing: float = 2.5):
+    """A Poisson stream of n independent replica requests at `rate` per second: arrival time,
+    cubic edge L ~ U{edge}, particle count ~ U{0..np_max} capped at `fill` of the cells of edge
+    `spacing` in the box (spaced_particles then keeps every pair at least spacing / 2 apart),
+    coupling g (times the mean density 1) ~ U[g_rho], friction gamma ~ U[gamma], and a seed
+    for the replica's inputs."""
+    g = rng(seed)
+    t = np.cumsum(g.exponential(1.0 / rate, size=n))
+    out = []
+    for k in range(n):
+        L = int(g.integers(edge[0], edge[1] + 1))
+        cap = int(fill * int(L // spacing) ** 3)
+        out.append(dict(rid=k, arrival=float(t[k]), edge=L, np=min(int(g.integers(0, np_max + 1)), cap),
+                        g=float(g.uniform(*g_rho)), gamma=float(g.uniform(*gamma)), steps=steps,
+                        seed=int(g.integers(0, 2**31 - 1))))
+    return out
