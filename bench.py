@@ -52,6 +52,9 @@ WORKLOADS = {
                                       "2e4 solvation-coupled point particles (kappa_A=-0.001, kappa_B=-0.002, gamma=1, "
                                       "m=200, kT=0.01), WCA, mean density 78.4 per component, g=0.0214"),
     "noise_32": (32, 64, "32^3 two-component LB FP32, rho=1+-0.01, g=1.4, 64 friction-coupled particles, WCA"),
+    "replicas_24": (0, 0, "24 independent replicas of the serving distribution (edge 16..128, 0..5000 particles, "
+                          "g rho 1.2..2.1 from a coexistence slab, gamma 0.1..2) advanced together in shared "
+                          "graph-captured launches, autotuned"),
 }
 
 
@@ -157,7 +160,47 @@ def build_workload(name: str, seed: int, edge_override: int = 0):
     return dims, rA.astype(np.float32), rB.astype(np.float32), x, types, kT, g
 
 
+def run_batch(args):
+    """The batched step: one batch of 24 replicas of the serving distribution, K steps in
+    graph-captured shared launches after autotuning; value = site updates per second."""
+    import torch
+    from paper_1306_0788_gb300 import inputs, serving
+    from paper_1306_0788_gb300 import lbmd as L
+    torch.cuda.set_device(0)
+    reqs = inputs.serving_requests(args.replicas, rate=1.0, seed=2025, steps=args.steps + args.warmup + 10)
+    sites = sum(r["edge"] ** 3 for r in reqs)
+    with serving.Server(max_slots=64, chunk=25) as srv:
+        b = srv.batch
+        slots = [serving.admit(b, r) for r in reqs]
+        L.lbmd_batch_step(b, args.warmup)
+        L.lbmd_batch_poll(b, 64)
+        cfg, ms = L.lbmd_batch_tune(b)
+        L.lbmd_batch_step(b, 3)
+        L.lbmd_batch_poll(b, 64)
+        n0 = L.lbmd_batch_launch_count(b)
+        sampler = ClockSampler(0)
+        sampler.start()
+        time.sleep(0.3)
+        t0 = time.perf_counter()
+        L.lbmd_batch_step(b, args.steps)
+        st = L.lbmd_batch_poll(b, 64)
+        dt = time.perf_counter() - t0
+        clocks = sampler.stop()
+        launches = L.lbmd_batch_launch_count(b) - n0
+        failed = int((st[slots] == L.LBMD_SLOT_FAILED).sum())
+    out = {"metric": METRIC, "value": round(sites * args.steps / dt / 1e6, 3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 5),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "replicas_%d" % len(reqs), "description": WORKLOADS["replicas_24"][2].replace("24", str(len(reqs)), 1), "replicas": len(reqs),
+                      "sites": sites, "particles": sum(r["np"] for r in reqs), "tuned": cfg,
+                      "tuned_kernel_ms": ms, "timing": "host wall clock around lbmd_batch_step + lbmd_batch_poll"},
+           "gpu_launches": int(launches), "clocks": clocks, "state_ok": failed == 0}
+    print(json.dumps(out), flush=True)
+
+
 def run_cuda(args):
+    if args.workload == "replicas_24":
+        return run_batch(args)
     import torch
     from paper_1306_0788_gb300 import lbmd as L
 
@@ -405,12 +448,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--replicas", type=int, default=24, help="replicas of the replicas_24 workload")
     ap.add_argument("--serving", type=int, default=200,
                     help="replicas in the serving stream measured after the main run (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
+        if args.workload == "replicas_24":
+            ap.error("the oracle arm times the single-lattice workloads")
         run_reference(args)
     else:
         run_cuda(args)

@@ -297,7 +297,7 @@ int lbmd_batch_set_config(lbmd_batch *batch, int tile_sites, int grid_moments, i
 int lbmd_batch_get_config(const lbmd_batch *batch, int cfg[5]);
 
 /* Autotuner: times the lattice kernels over the current replicas for tiles of 256, 1024 and
- * 4096 sites, density-pass grids of 2/4/8 blocks per SM and update variants (register budget
+ * 4096 sites, density-pass grids of 2/3/4 blocks per SM and update variants (register budget
  * of 3 blocks per SM with grids of 1/2/3 blocks per SM, of 2 blocks per SM with 1/2), keeps
  * the fastest, and returns it in cfg[5] and the two kernel times in ms[2] (either may be
  * NULL).  The state of the replicas is unchanged.  Needs at least one initialised replica. */

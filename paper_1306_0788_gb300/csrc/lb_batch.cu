@@ -67,43 +67,74 @@ struct BatchDev {
 
 // ------------------------------------------------------------------ lattice kernels
 
-template <class T>
-__global__ void __launch_bounds__(kBThreads) kb_moments(const BatchDev *__restrict__ B) {
-  const int ntiles = B->ntiles, ts = B->tile_sites;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int slot = B->tile_slot[t];
-    if (B->left[slot] <= 0) continue;
-    const RepDev &R = B->rep[slot];
-    const long long base = (long long)(t - B->lay[slot].tile0) * ts;
-    const long long N = R.P.N;
-    const T *fin = static_cast<const T *>(R.pop[B->state[slot].cur]);
-    float *jp = R.P.np > 0 ? R.jp : nullptr;
-    for (int k = threadIdx.x; k < ts; k += kBThreads) {
-      const long long s = base + k;
-      if (s >= N) break;
-      site::moments<T>(R.P, s, fin, R.rest, R.rho, jp);
-    }
-  }
-}
-
 // tuning != 0: time the update without side effects on the state -- no particle coupling (the
 // sorted particle arrays are only valid inside a step) and, with 16-bit storage, the FP32 rest
 // populations are not written (f_0 goes to the output buffer, which is scratch between steps).
-// Per-block copy of what the update of one replica's tile needs.  Kept in shared memory (and
-// re-read there for every site) so that it takes no registers across the update.
+// Per-block copy of what the kernels need for one replica's tile.  Kept in shared memory (and
+// re-read there for every site) so that it takes no registers across the site update and is
+// not reloaded from global memory after every store.
 template <class T>
 struct TileCtx {
   StepParams P;
   const T *fin;
   T *fout;
-  const float *rho, *rest_in;
+  const float *rest_in;
   float *rest_out;
+  float *rho, *jp;
   unsigned *err;
-  const int *row_start;
-  long long base;
-  ParticleArrays pa;  // the sorted particles of the batch
+  const int *row_start;  // the replica's rows in the shared row space; NULL: no particle coupling
+  long long base;        // first site of the tile
+  ParticleArrays pa;     // the sorted particles of the batch
   ParticleForces pf;
 };
+
+// Fill c for tile t of `slot` (all threads call it; the parameters are copied when the slot
+// changes).  Ends with a barrier: c is ready for every thread.
+template <class T>
+__device__ __forceinline__ void load_tile(TileCtx<T> &c, const BatchDev *__restrict__ B, int t, int slot, int &have,
+                                          int tuning) {
+  __syncthreads();  // every thread is done with the previous tile
+  if (slot != have) {
+    const int *src = reinterpret_cast<const int *>(&B->rep[slot].P);
+    int *dst = reinterpret_cast<int *>(&c.P);
+    for (int k = threadIdx.x; k < (int)(sizeof(StepParams) / sizeof(int)); k += kBThreads) dst[k] = src[k];
+  }
+  if (threadIdx.x == 0) {
+    const RepDev &R = B->rep[slot];
+    const RepLayout &L = B->lay[slot];
+    const int cur = B->state[slot].cur;
+    c.fin = static_cast<const T *>(R.pop[cur]);
+    c.fout = static_cast<T *>(R.pop[cur ^ 1]);
+    c.rest_in = R.rest;
+    c.rest_out = tuning ? nullptr : R.rest;
+    c.rho = R.rho;
+    c.jp = R.P.np > 0 ? R.jp : nullptr;
+    c.err = &B->state[slot].err;
+    c.row_start = (!tuning && R.P.np > 0) ? B->row_start + L.row0 : nullptr;
+    c.base = (long long)(t - L.tile0) * B->tile_sites;
+    c.pa = B->S;
+    c.pf = B->pf;
+  }
+  __syncthreads();
+  have = slot;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBThreads, 4) kb_moments(const BatchDev *__restrict__ B) {
+  __shared__ TileCtx<T> c;
+  const int ts = B->tile_sites;
+  int have = -1;
+  for (int t = blockIdx.x; t < B->ntiles; t += gridDim.x) {
+    const int slot = B->tile_slot[t];
+    if (B->left[slot] <= 0) continue;  // uniform across the block
+    load_tile(c, B, t, slot, have, 0);
+    for (int k = threadIdx.x; k < ts; k += kBThreads) {
+      const long long s = c.base + k;
+      if (s >= c.P.N) break;
+      site::moments<T>(c.P, s, c.fin, c.rest_in, c.rho, c.jp);
+    }
+  }
+}
 
 // kMinBlocks: blocks per SM the register budget is sized for (3: 80 registers, some spilled; 2:
 // up to 128 registers, none spilled) -- the autotuner picks.
@@ -115,29 +146,7 @@ __global__ void __launch_bounds__(kBThreads, kMinBlocks) kb_collide(const BatchD
   for (int t = blockIdx.x; t < B->ntiles; t += gridDim.x) {
     const int slot = B->tile_slot[t];
     if (B->left[slot] <= 0) continue;  // uniform across the block
-    __syncthreads();                   // every thread is done with the previous tile
-    if (slot != have) {
-      const int *src = reinterpret_cast<const int *>(&B->rep[slot].P);
-      int *dst = reinterpret_cast<int *>(&c.P);
-      for (int k = threadIdx.x; k < (int)(sizeof(StepParams) / sizeof(int)); k += kBThreads) dst[k] = src[k];
-    }
-    if (threadIdx.x == 0) {
-      const RepDev &R = B->rep[slot];
-      const RepLayout &L = B->lay[slot];
-      const int cur = B->state[slot].cur;
-      c.fin = static_cast<const T *>(R.pop[cur]);
-      c.fout = static_cast<T *>(R.pop[cur ^ 1]);
-      c.rho = R.rho;
-      c.rest_in = R.rest;
-      c.rest_out = tuning ? nullptr : R.rest;
-      c.err = &B->state[slot].err;
-      c.row_start = (!tuning && R.P.np > 0) ? B->row_start + L.row0 : nullptr;
-      c.base = (long long)(t - L.tile0) * ts;
-      c.pa = B->S;
-      c.pf = B->pf;
-    }
-    __syncthreads();
-    have = slot;
+    load_tile(c, B, t, slot, have, tuning);
     for (int k = threadIdx.x; k < ts; k += kBThreads) {
       const long long s = c.base + k;
       if (s >= c.P.N) break;
@@ -1213,7 +1222,7 @@ int lbmd_batch_tune(lbmd_batch *b, int cfg[5], double ms[2]) {
     return t / kReps;
   };
   const int tiles[] = {256, 1024, 4096};
-  const int gms[] = {2, 4, 8};
+  const int gms[] = {2, 3, 4};
   static const int gcs_v[][2] = {{3, 1}, {3, 2}, {3, 3}, {2, 1}, {2, 2}};  // (blocks per SM budget, grid / SMs)
   const int *gcs[] = {gcs_v[0], gcs_v[1], gcs_v[2], gcs_v[3], gcs_v[4]};
   float best = 1e30f, best_m = 0.f, best_c = 0.f;

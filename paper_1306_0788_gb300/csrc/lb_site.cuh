@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "lbmd_internal.cuh"
 
 namespace lbmd {
@@ -16,6 +18,9 @@ namespace site {
 // enc / dec convert between the FP32 value and the stored element.
 template <class T>
 struct Pop;
+// 16-bit storage keeps the rest populations apart, in FP32; FP32 storage has none
+template <class T>
+constexpr bool kSplitRest = !std::is_same<T, float>::value;
 template <>
 struct Pop<float> {
   static __device__ __forceinline__ float enc(float v, float) { return v; }
@@ -64,12 +69,15 @@ struct Coord {
   int x, y, z;
 };
 
+// (x, y, z) of site s = (z ny + y) nx + x; s < 2^32 (19 N < 2^32 is enforced)
 __device__ __forceinline__ Coord site_coord(const StepParams &P, long long s) {
+  const uint32_t s32 = (uint32_t)s;
+  const uint32_t t = fast_div(s32, P.divx);  // z ny + y
+  const uint32_t z = fast_div(t, P.divy);
   Coord c;
-  c.x = (int)(s % P.nx);
-  const long long t = s / P.nx;
-  c.y = (int)(t % P.ny);
-  c.z = (int)(t / P.ny);
+  c.x = (int)(s32 - t * (uint32_t)P.nx);
+  c.y = (int)(t - z * (uint32_t)P.ny);
+  c.z = (int)z;
   return c;
 }
 
@@ -131,8 +139,9 @@ __device__ __forceinline__ void moments(const StepParams &P, long long s, const 
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
-    const float a = (i == 0 && rest) ? __ldg(rest + s32) : Pop<T>::ld(fin + src, pop_shift(P, 0, i));
-    const float b = (i == 0 && rest) ? __ldg(rest + N32 + s32) : Pop<T>::ld(finB + src, pop_shift(P, 1, i));
+    const bool r0 = kSplitRest<T> && i == 0 && rest;
+    const float a = r0 ? __ldg(rest + s32) : Pop<T>::ld(fin + src, pop_shift(P, 0, i));
+    const float b = r0 ? __ldg(rest + N32 + s32) : Pop<T>::ld(finB + src, pop_shift(P, 1, i));
     rA += a;
     rB += b;
     jx += kCx[i] * (a + b);
@@ -212,7 +221,7 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, const 
     fA[i] = Pop<T>::ld(fin + src, pop_shift(P, 0, i));
     fB[i] = Pop<T>::ld(finB + src, pop_shift(P, 1, i));
   }
-  if (rest_in) {  // 16-bit storage: the rest populations are kept in FP32
+  if (kSplitRest<T> && rest_in) {  // 16-bit storage: the rest populations are kept in FP32
     fA[0] = __ldg(rest_in + s32);
     fB[0] = __ldg(rest_in + N32 + s32);
   }
@@ -273,7 +282,7 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, const 
     }
   }
   T *foutB = fout + (size_t)kQ * N32;
-  if (rest_out) {
+  if (kSplitRest<T> && rest_out) {
     // 16-bit storage: each moving population is rounded on store; the FP32 rest population takes
     // the rounding error of the node's 18 others, so the node's total (and the total mass of each
     // component) is the one of the collision up to FP32 rounding instead of drifting each step.

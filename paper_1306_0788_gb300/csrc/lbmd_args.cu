@@ -32,6 +32,8 @@ void fill_step_params(const lbmd_params *prm, StepParams &P) {
   P.nz = prm->nz;
   P.nrows = prm->ny * prm->nz;
   P.N = (long long)prm->nx * prm->ny * prm->nz;
+  P.divx = make_fastdiv((uint32_t)prm->nx);
+  P.divy = make_fastdiv((uint32_t)prm->ny);
   P.inv_tau = (float)(1.0 / prm->tau_r);
   P.force_pref = (float)(1.0 - 0.5 / prm->tau_r);
   P.gAB = (float)prm->g_AB;

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "fastdiv.h"
 #include "lbmd.h"
 
 namespace lbmd {
@@ -49,6 +50,7 @@ struct StepParams {
   int nx, ny, nz;
   int nrows;             // ny * nz
   long long N;           // nx * ny * nz
+  FastDiv divx, divy;    // division by nx and by ny (site index -> coordinates)
   float inv_tau;         // 1 / tau_r
   float force_pref;      // 1 - 1/(2 tau_r)  (the (2 + lambda)/2 factor of the forcing term)
   float gAB, gBA;
