@@ -31,7 +31,7 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes per node moved by k_collide (dram__bytes_read + dram__bytes_write of one ncu capture
 # of the 128^3 case of this workload, scaled per node; profiles/k_collide_slab_droplets_256.md).
 # None while k_collide has changed since the last capture.
-COLLIDE_TRAFFIC_BYTES_PER_NODE = None
+COLLIDE_TRAFFIC_BYTES_PER_NODE = 290.0
 
 # The slab/droplet workload uses the density scale of the paper's ferrofluid example (Sec. 4.5):
 # mean density 78.4 per component with g = 0.0214 (g rho = 1.68).  Bulk coexistence of F_bulk
@@ -136,6 +136,22 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(seconds: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time (every rank passes its own); the job finishes when it does."""
+    if dist is None:
+        return float(seconds)
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Units processed by all ranks (independent replicas: the same work on each) per second of
+    the slowest rank."""
+    return world * units_per_rank / seconds_max
 
 
 def build_workload(name: str, seed: int, edge_override: int = 0):
@@ -259,10 +275,7 @@ def run_cuda(args):
         L.lbmd_sync(ctx)
     except L.LbmdError:
         state_ok = False
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist, "cuda")
 
     # end-to-end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -288,10 +301,8 @@ def run_cuda(args):
         t_e2e = time.perf_counter() - t0
         h2d = (2 * N * 4 + npart * (6 * 8 + 4)) / args.steps
         d2h = (5 * N * 4 + npart * 9 * 8) / args.steps
-        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": round(world * N * args.steps / float(tt.item()) / 1e6, 3), "unit": UNIT,
+        e2e = {"value": round(whole_job_rate(N * args.steps, world, max_over_ranks(t_e2e, dist, "cuda")) / 1e6, 3),
+               "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "status": int(rc),
                "what": "lbmd_init_fluid + lbmd_set_particles (pinned host) + lbmd_step(K) + "
                        "lbmd_get_fields + lbmd_get_particles (pinned host), wall clock"}
@@ -301,7 +312,7 @@ def run_cuda(args):
     bps = algorithmic_bytes_per_site(args.storage)
     avg_kernel_ms = k_ms / max(k_n, 1)
     achieved = bps * N / (avg_kernel_ms * 1e-3) / 1e9
-    value = world * N * args.steps / (ms_max * 1e-3) / 1e6
+    value = whole_job_rate(N * args.steps, world, ms_max * 1e-3) / 1e6
     if rank == 0:
         out = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
