@@ -59,6 +59,8 @@ def _load():
                                       ctypes.c_double, ctypes.c_double] + [ctypes.c_void_p] * 4
         _lib.orc_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                      ctypes.c_void_p]
+        _lib.orc_fluid_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]
+        _lib.orc_mode_basis.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     return _lib
 
 
@@ -116,6 +118,20 @@ def normals(seed: int, step: int, pid: int) -> np.ndarray:
     return out
 
 
+def mode_basis():
+    """(e [19, 19] with e[k, i] = e_k(c_i), b [19] = sum_i w_i e_ki^2): the MRT mode basis."""
+    e, b = np.zeros((Q, Q)), np.zeros(Q)
+    _load().orc_mode_basis(_ptr(e), _ptr(b))
+    return e, b
+
+
+def fluid_normals(seed: int, step: int, site: int) -> np.ndarray:
+    """The 36 unit normals of one node and step of the fluctuating MRT collision."""
+    out = np.zeros(36)
+    _load().orc_fluid_normals(seed, step, site, _ptr(out))
+    return out
+
+
 def fs_geometry(d) -> np.ndarray:
     out = np.zeros(3)
     _load().orc_fs_geometry(_ptr(_f64(d)), _ptr(out))
@@ -123,6 +139,7 @@ def fs_geometry(d) -> np.ndarray:
 
 
 PAIR_WCA, PAIR_DH, BOND_FENE, BOND_HARMONIC = 0, 1, 2, 3
+COLLISION_BGK, COLLISION_MRT = 0, 1
 
 
 def pair_energy(kind: int, p0: float, p1: float, p2: float, r: float) -> float:
@@ -164,7 +181,9 @@ class _OrcSystem(ctypes.Structure):
                 ("dh_lB", ctypes.c_double), ("dh_kappa", ctypes.c_double), ("dh_rc", ctypes.c_double),
                 ("np", ctypes.c_int), ("type", ctypes.c_void_p), ("q", ctypes.c_void_p),
                 ("pid", ctypes.c_void_p), ("nbonds", ctypes.c_int), ("bonds", ctypes.c_void_p),
-                ("bond_kind", ctypes.c_int), ("bond_k", ctypes.c_double), ("bond_r", ctypes.c_double)]
+                ("bond_kind", ctypes.c_int), ("bond_k", ctypes.c_double), ("bond_r", ctypes.c_double),
+                ("collision", ctypes.c_int), ("lam_bulk", ctypes.c_double), ("lam_mom", ctypes.c_double),
+                ("lam_ghost", ctypes.c_double)]
 
 
 class _OrcTrace(ctypes.Structure):
@@ -201,6 +220,12 @@ class System:
     bond_kind: int = BOND_FENE
     bond_k: float = 0.0
     bond_r: float = 1.0
+    # collision: COLLISION_BGK, or COLLISION_MRT (fluctuating when kT > 0) with the bulk,
+    # component-momentum and kinetic eigenvalues (None: -1/tau_r, the shear one)
+    collision: int = 0
+    lam_bulk: float = None
+    lam_mom: float = None
+    lam_ghost: float = None
 
     def _struct(self):
         keep = []
@@ -227,6 +252,11 @@ class System:
         s.nbonds = int(len(self.bonds))
         s.bonds = arr(self.bonds, np.int32)
         s.bond_kind, s.bond_k, s.bond_r = int(self.bond_kind), float(self.bond_k), float(self.bond_r)
+        ls = -1.0 / self.tau_r
+        s.collision = int(self.collision)
+        s.lam_bulk = ls if self.lam_bulk is None else float(self.lam_bulk)
+        s.lam_mom = ls if self.lam_mom is None else float(self.lam_mom)
+        s.lam_ghost = ls if self.lam_ghost is None else float(self.lam_ghost)
         return s, keep
 
 

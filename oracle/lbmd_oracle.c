@@ -40,6 +40,25 @@
  *       SC'11) and the Box-Muller transform.
  *   R10 D3Q19 order: 0; +x,-x,+y,-y,+z,-z; then the xy, xz, yz diagonals with
  *       opposite directions adjacent.
+ *   R13 Fluctuating MRT (Eq. MODES, appendix): mode basis = the orthogonal polynomials of
+ *       Duenweg, Schiller and Ladd in c (the paper's citation for its mode space); eigenvalues
+ *       lambda_M (component momenta), lambda_b (bulk), lambda_s = -1/tau_r (shear), lambda_g
+ *       (kinetic modes); m*_k = m^eq_k + (1 + lambda_k)(m_k - m^eq_k) + m^g_k + phi_k r_k with
+ *       m^eq, m^g the projections of f^eq and of the forcing term.  Noise amplitudes from the
+ *       equilibrium mode variances <m_k^2> = (kT/c_s^2) rho_z b_k (b_k = sum_i w_i e_ki^2):
+ *       phi = sqrt((kT/c_s^2) rho_z b_k (1 - (1+lambda_k)^2)) for the stress and kinetic modes,
+ *       one Gaussian per component; the momentum modes share one Gaussian per direction with
+ *       opposite signs for A and B (Sec. 2), amplitude sqrt(kT (rho_A rho_B / rho)
+ *       (1 - (1+lambda_M)^2)), the equilibrium variance of the interdiffusion flux
+ *       (rho_B j_A - rho_A j_B) / rho of two ideal components.  Gaussians from Philox4x32-10
+ *       with counter (site, step low, step high, 0x464c0000 + k), k = 0..8, Box-Muller on both
+ *       uniform pairs of each draw: normals 0-2 are the momentum ones (x, y, z), 3-17 the
+ *       modes 4-18 of A, 18-32 those of B.
+ *   R14 Bulk viscosity of that collision: eta_b = -(2/3) rho c_s^2 (1/lambda_b + 1/2), from the
+ *       trace equation of the Chapman-Enskog expansion with the traceless shear stress of
+ *       Eq. (comp_Pi); Eq. (TRANSPORTCOEFF) prints it without the 2/3 (which at BGK would
+ *       contradict the known eta_b = 2/3 eta_s of D3Q19).  Nothing in the collision depends on
+ *       this reading; only the pin of the sound damping does.
  */
 #include <math.h>
 #include <stdint.h>
@@ -182,6 +201,64 @@ void orc_normals(uint64_t seed, uint64_t step, uint32_t id, double *n) {
   n[2] = b * cos(two_pi * u[3]);
 }
 
+/* Mode basis (R13): e_k(c_i) for k = 0..18 -- density; momentum x, y, z; bulk c^2 - 1; the
+ * five shear modes 3c_x^2 - c^2, c_y^2 - c_z^2, c_x c_y, c_y c_z, c_z c_x; the kinetic modes
+ * (3c^2 - 5) c_a, (c_y^2 - c_z^2) c_x, (c_z^2 - c_x^2) c_y, (c_x^2 - c_y^2) c_z, 3c^4 - 6c^2 + 1,
+ * (2c^2 - 3)(3c_x^2 - c^2), (2c^2 - 3)(c_y^2 - c_z^2).  e has layout [k][i]; b_k = sum_i w_i e_ki^2. */
+static double orc_mode_poly(int k, const int *c) {
+  const double x = c[0], y = c[1], z = c[2], c2 = x * x + y * y + z * z;
+  switch (k) {
+    case 0: return 1.0;
+    case 1: return x;
+    case 2: return y;
+    case 3: return z;
+    case 4: return c2 - 1.0;
+    case 5: return 3.0 * x * x - c2;
+    case 6: return y * y - z * z;
+    case 7: return x * y;
+    case 8: return y * z;
+    case 9: return z * x;
+    case 10: return (3.0 * c2 - 5.0) * x;
+    case 11: return (3.0 * c2 - 5.0) * y;
+    case 12: return (3.0 * c2 - 5.0) * z;
+    case 13: return (y * y - z * z) * x;
+    case 14: return (z * z - x * x) * y;
+    case 15: return (x * x - y * y) * z;
+    case 16: return 3.0 * c2 * c2 - 6.0 * c2 + 1.0;
+    case 17: return (2.0 * c2 - 3.0) * (3.0 * x * x - c2);
+    case 18: return (2.0 * c2 - 3.0) * (y * y - z * z);
+  }
+  return 0.0;
+}
+
+void orc_mode_basis(double *e, double *b) {
+  for (int k = 0; k < ORC_Q; ++k) {
+    b[k] = 0.0;
+    for (int i = 0; i < ORC_Q; ++i) {
+      e[k * ORC_Q + i] = orc_mode_poly(k, orc_c[i]);
+      b[k] += orc_w(i) * e[k * ORC_Q + i] * e[k * ORC_Q + i];
+    }
+  }
+}
+
+/* The 36 unit normals of one node and step for the fluid noise (R13). */
+void orc_fluid_normals(uint64_t seed, uint64_t step, uint32_t site, double *n) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  const double two_pi = 6.283185307179586;
+  for (uint32_t k = 0; k < 9; ++k) {
+    uint32_t ctr[4] = {site, (uint32_t)step, (uint32_t)(step >> 32), 0x464c0000u + k};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    double u[4];
+    for (int j = 0; j < 4; ++j) u[j] = ((double)(r[j] >> 8) + 0.5) / 16777216.0;
+    double a = sqrt(-2.0 * log(u[0])), bb = sqrt(-2.0 * log(u[2]));
+    n[4 * k + 0] = a * cos(two_pi * u[1]);
+    n[4 * k + 1] = a * sin(two_pi * u[1]);
+    n[4 * k + 2] = bb * cos(two_pi * u[3]);
+    n[4 * k + 3] = bb * sin(two_pi * u[3]);
+  }
+}
+
 /* Geometric factor of Eq. (solvation_lambda) for one particle seen from one node, readings R8:
  *   sum over the 18 neighbours r' = r + c_i of Theta[d_hat . c_hat_i] c_i / |c_i|^2,
  * with d = r_particle - r and Theta(x) = 1 for 0 < x < 1.  By Cauchy-Schwarz d_hat . c_hat <= 1
@@ -265,6 +342,8 @@ typedef struct {
   const int *bonds;      /* [nbonds][2] */
   int bond_kind;         /* 2 = FENE, 3 = harmonic */
   double bond_k, bond_r;
+  int collision;         /* 0 = BGK (R3), 1 = fluctuating MRT (R13) */
+  double lam_bulk, lam_mom, lam_ghost; /* MRT eigenvalues; the shear one is -1/tau_r */
 } orc_system;
 
 typedef struct {         /* optional outputs, each may be NULL */
@@ -443,8 +522,14 @@ int orc_step(const orc_system *sys, double *f, double *x, double *v, uint64_t st
   }
 
   /* 7. Collision with forcing (Eqs. EQ:LBapp, collis, feq, momentum_definition and the
-   * forcing term), BGK reading R3, then 8. streaming f(r + c_i, t+1) = f*(r, t). */
+   * forcing term), BGK reading R3 or fluctuating MRT (Eq. MODES, reading R13), then
+   * 8. streaming f(r + c_i, t+1) = f*(r, t). */
   const double lam = -1.0 / sys->tau_r;
+  const int mrt = sys->collision == 1;
+  double E[ORC_Q * ORC_Q], bk[ORC_Q], lk[ORC_Q];
+  orc_mode_basis(E, bk);
+  for (int k = 0; k < ORC_Q; ++k)
+    lk[k] = k == 0 ? 0.0 : k <= 3 ? sys->lam_mom : k == 4 ? sys->lam_bulk : k <= 9 ? lam : sys->lam_ghost;
   for (long zz = 0; zz < dim[2]; ++zz)
     for (long yy = 0; yy < dim[1]; ++yy)
       for (long xx = 0; xx < dim[0]; ++xx) {
@@ -460,15 +545,52 @@ int orc_step(const orc_system *sys, double *f, double *x, double *v, uint64_t st
         if (tr && tr->g)
           for (int z = 0; z < 2; ++z)
             for (int a = 0; a < 3; ++a) tr->g[3 * (z * N + s) + a] = gz[z][a];
+        double nrm[36];
+        if (mrt && sys->kT > 0.0) orc_fluid_normals(sys->seed, step, (uint32_t)s, nrm);
         for (int z = 0; z < 2; ++z) {
-          double feq[ORC_Q], dg[ORC_Q];
+          double feq[ORC_Q], dg[ORC_Q], fstar[ORC_Q];
           orc_feq(rho[z * N + s], u, feq);
-          orc_forcing(gz[z], u, lam, lam, lam, dg);
+          if (!mrt) {
+            orc_forcing(gz[z], u, lam, lam, lam, dg);
+            for (int i = 0; i < ORC_Q; ++i) {
+              double fi = f[((long)z * ORC_Q + i) * N + s];
+              fstar[i] = fi + lam * (fi - feq[i]) + dg[i];
+            }
+          } else {
+            /* modes m_k = sum_i e_ki f_i, their equilibria and forcing moments, Eq. MODES */
+            orc_forcing(gz[z], u, sys->lam_mom, lam, sys->lam_bulk, dg);
+            double ms[ORC_Q];
+            for (int k = 0; k < ORC_Q; ++k) {
+              double m = 0.0, meq = 0.0, mg = 0.0;
+              for (int i = 0; i < ORC_Q; ++i) {
+                m += E[k * ORC_Q + i] * f[((long)z * ORC_Q + i) * N + s];
+                meq += E[k * ORC_Q + i] * feq[i];
+                mg += E[k * ORC_Q + i] * dg[i];
+              }
+              double noise = 0.0;
+              if (sys->kT > 0.0 && k > 0) {
+                const double rz = rho[z * N + s];
+                if (k <= 3) {
+                  double rr = rho[s] * rho[N + s] / r;
+                  double phi = sqrt(sys->kT * rr * (1.0 - (1.0 + lk[k]) * (1.0 + lk[k])));
+                  noise = (z == 0 ? 1.0 : -1.0) * phi * nrm[k - 1];
+                } else {
+                  double phi = sqrt(sys->kT / ORC_CS2 * rz * bk[k] * (1.0 - (1.0 + lk[k]) * (1.0 + lk[k])));
+                  noise = phi * nrm[3 + 15 * z + (k - 4)];
+                }
+              }
+              ms[k] = meq + (1.0 + lk[k]) * (m - meq) + mg + noise;
+            }
+            /* back to populations: f*_i = w_i sum_k e_ki m*_k / b_k */
+            for (int i = 0; i < ORC_Q; ++i) {
+              double acc = 0.0;
+              for (int k = 0; k < ORC_Q; ++k) acc += E[k * ORC_Q + i] * ms[k] / bk[k];
+              fstar[i] = orc_w(i) * acc;
+            }
+          }
           for (int i = 0; i < ORC_Q; ++i) {
-            double fi = f[((long)z * ORC_Q + i) * N + s];
-            double fstar = fi + lam * (fi - feq[i]) + dg[i];
             long dst = orc_site(dim, xx + orc_c[i][0], yy + orc_c[i][1], zz + orc_c[i][2]);
-            fnew[((long)z * ORC_Q + i) * N + dst] = fstar;
+            fnew[((long)z * ORC_Q + i) * N + dst] = fstar[i];
           }
         }
       }
