@@ -60,6 +60,10 @@ extern "C" {
 #define LBMD_STORAGE_FP16_SHIFTED 1
 #define LBMD_STORAGE_BF16_SHIFTED 2
 
+/* collision operator (lbmd_params.collision) */
+#define LBMD_COLLISION_BGK 0 /* every relaxation eigenvalue -1/tau_r; no fluid noise */
+#define LBMD_COLLISION_MRT 1 /* Eq. MODES: per-mode eigenvalues, Gaussian mode noise at kT > 0 */
+
 /* bonded interactions */
 #define LBMD_BOND_FENE 2     /* U = -(k R0^2 / 2) ln(1 - (r/R0)^2) (Kremer-Grest form) */
 #define LBMD_BOND_HARMONIC 3 /* U = (k/2) (r - d)^2 (Sec. 4.3, 4.4) */
@@ -81,7 +85,15 @@ typedef struct lbmd_ctx lbmd_ctx;
  * the isotropy weights w_i.  kT: thermal energy of the particle noise (Eq. NEWTON).
  * dt: particle time step, must equal the lattice time step 1.  storage: LBMD_STORAGE_*.
  * rho0_A, rho0_B: shift reference of the 16-bit storages (ignored for FP32).  seed: key
- * of the counter-based particle noise. */
+ * of the counter-based particle and fluid noise.
+ * collision: LBMD_COLLISION_BGK, or LBMD_COLLISION_MRT -- the collision of Eq. MODES in the
+ * mode space of the orthogonal D3Q19 polynomials of Duenweg, Schiller and Ladd: the shear
+ * modes relax with lambda_s = -1/tau_r, the bulk mode with lambda_bulk, each component's
+ * momentum with lambda_mom (interdiffusion, mu = -(1/lambda_mom + 1/2)), the nine kinetic
+ * modes with lambda_ghost, every eigenvalue in (-2, 0); at kT > 0 each mode receives
+ * Gaussian noise with the amplitude that gives equipartition at temperature kT, the momentum
+ * noise of A and B being one random number with opposite signs (Sec. 2).  The lambda_* are
+ * ignored with BGK. */
 typedef struct {
   int nx, ny, nz;
   double tau_r;
@@ -91,6 +103,8 @@ typedef struct {
   int storage;
   double rho0_A, rho0_B;
   uint64_t seed;
+  int collision;
+  double lambda_bulk, lambda_mom, lambda_ghost;
 } lbmd_params;
 
 /* Per particle type: kappa_A, kappa_B of Eq. (solvation_kappa), lambda_A, lambda_B of
@@ -109,7 +123,7 @@ typedef struct {
  * cudaStream_t (may be NULL).  Allocates both population buffers; fails with
  * LBMD_E_NOMEM if they do not fit.  *warnings (may be NULL) receives LBMD_WARN_* bits.
  * Errors: LBMD_E_INVALID_ARG for sizes < 1, tau_r <= 1/2, dt != 1, unknown storage,
- * negative rho0. */
+ * negative rho0, unknown collision, an MRT eigenvalue outside (-2, 0). */
 int lbmd_create(const lbmd_params *params, void *stream, lbmd_ctx **out, unsigned *warnings);
 
 /* Destroy a context and free its device memory (NULL is ignored). */
@@ -306,7 +320,7 @@ int lbmd_batch_tune(lbmd_batch *batch, int cfg[5], double ms[2]);
 /* Budget and use in bytes, number of occupied slots, slot count (any pointer may be NULL). */
 int lbmd_batch_info(const lbmd_batch *batch, size_t *budget, size_t *used, int *occupied, int *max_slots);
 
-/* Kernel launches issued by lbmd_batch_step so far (host-side count, 13 per step). */
+/* Kernel launches issued by lbmd_batch_step so far (host-side count, 14 per step). */
 int64_t lbmd_batch_launch_count(const lbmd_batch *batch);
 
 /* Message of the last failure of a batch call (NULL: of lbmd_batch_create). */

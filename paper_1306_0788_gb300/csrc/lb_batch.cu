@@ -84,6 +84,7 @@ struct TileCtx {
   unsigned *err;
   const int *row_start;  // the replica's rows in the shared row space; NULL: no particle coupling
   long long base;        // first site of the tile
+  unsigned long long step;  // the replica's step count (noise counter)
   ParticleArrays pa;     // the sorted particles of the batch
   ParticleForces pf;
 };
@@ -112,6 +113,7 @@ __device__ __forceinline__ void load_tile(TileCtx<T> &c, const BatchDev *__restr
     c.err = &B->state[slot].err;
     c.row_start = (!tuning && R.P.np > 0) ? B->row_start + L.row0 : nullptr;
     c.base = (long long)(t - L.tile0) * B->tile_sites;
+    c.step = B->state[slot].step;
     c.pa = B->S;
     c.pf = B->pf;
   }
@@ -138,24 +140,27 @@ __global__ void __launch_bounds__(kBThreads, 4) kb_moments(const BatchDev *__res
 
 // kMinBlocks: blocks per SM the register budget is sized for (3: 80 registers, some spilled; 2:
 // up to 128 registers, none spilled) -- the autotuner picks.
-template <class T, int kMinBlocks>
+// kMRT: this launch updates the replicas with the fluctuating MRT collision (and skips the BGK
+// ones); the step runs both, each with its own register budget.
+template <class T, int kMinBlocks, bool kMRT>
 __global__ void __launch_bounds__(kBThreads, kMinBlocks) kb_collide(const BatchDev *__restrict__ B, int tuning) {
   __shared__ TileCtx<T> c;
   const int ts = B->tile_sites;
   int have = -1;
   for (int t = blockIdx.x; t < B->ntiles; t += gridDim.x) {
     const int slot = B->tile_slot[t];
-    if (B->left[slot] <= 0) continue;  // uniform across the block
+    // uniform across the block
+    if (B->left[slot] <= 0 || (B->rep[slot].P.collision == LBMD_COLLISION_MRT) != kMRT) continue;
     load_tile(c, B, t, slot, have, tuning);
     for (int k = threadIdx.x; k < ts; k += kBThreads) {
       const long long s = c.base + k;
       if (s >= c.P.N) break;
       if (c.row_start)
-        site::collide<T, true>(c.P, s, c.fin, c.fout, c.rho, c.pa, c.pf, CellIndex{c.row_start}, c.err, c.rest_in,
-                               c.rest_out);
+        site::collide<T, true, kMRT>(c.P, s, c.step, c.fin, c.fout, c.rho, c.pa, c.pf, CellIndex{c.row_start},
+                                     c.err, c.rest_in, c.rest_out);
       else
-        site::collide<T, false>(c.P, s, c.fin, c.fout, c.rho, c.pa, c.pf, CellIndex{nullptr}, c.err, c.rest_in,
-                                c.rest_out);
+        site::collide<T, false, kMRT>(c.P, s, c.step, c.fin, c.fout, c.rho, c.pa, c.pf, CellIndex{nullptr},
+                                      c.err, c.rest_in, c.rest_out);
     }
   }
 }
@@ -713,13 +718,15 @@ void launch_batched_moments(lbmd_batch *b, int grid) {
   });
 }
 
+// The BGK replicas with the tuned shape, then the MRT ones (two blocks of 256 per SM).
 void launch_batched_collide(lbmd_batch *b, int grid, int min_blocks, int tuning) {
   with_batch_storage(b->storage, [&](auto t) {
     using T = std::remove_pointer_t<decltype(t)>;
     if (min_blocks == 2)
-      kb_collide<T, 2><<<grid, kBThreads, 0, b->st>>>(b->d_batch, tuning);
+      kb_collide<T, 2, false><<<grid, kBThreads, 0, b->st>>>(b->d_batch, tuning);
     else
-      kb_collide<T, 3><<<grid, kBThreads, 0, b->st>>>(b->d_batch, tuning);
+      kb_collide<T, 3, false><<<grid, kBThreads, 0, b->st>>>(b->d_batch, tuning);
+    kb_collide<T, 2, true><<<2 * b->sms, kBThreads, 0, b->st>>>(b->d_batch, tuning);
   });
 }
 
@@ -740,7 +747,7 @@ void enqueue_step(lbmd_batch *b) {
   kb_integrate<<<gp, kBPThreads, 0, b->st>>>(B);
   kb_advance<<<1, 256, 0, b->st>>>(B);
 }
-constexpr int kLaunchesPerStep = 13;
+constexpr int kLaunchesPerStep = 14;
 
 void drop_graphs(lbmd_batch *b) {
   for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);

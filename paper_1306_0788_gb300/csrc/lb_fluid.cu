@@ -76,16 +76,17 @@ __global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const T *__res
   moments(P, s, fin, rest, rho, jp);
 }
 
-// The lattice update of one step at every site (site::collide).
-template <class T, bool kParticles>
-__global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const T *__restrict__ fin,
-                                                    T *__restrict__ fout, const float *__restrict__ rho,
-                                                    ParticleArrays pa, ParticleForces pf, CellIndex ci,
-                                                    unsigned *err, const float *__restrict__ rest_in,
-                                                    float *__restrict__ rest_out) {
+// The lattice update of one step at every site (site::collide; with kMRT the fluctuating MRT
+// collision, whose mode transforms take the register budget of two blocks per SM).
+template <class T, bool kParticles, bool kMRT>
+__global__ void __launch_bounds__(kBlock, kMRT ? 2 : 3) k_collide(StepParams P, const T *__restrict__ fin,
+                                                                  T *__restrict__ fout, const float *__restrict__ rho,
+                                                                  ParticleArrays pa, ParticleForces pf, CellIndex ci,
+                                                                  unsigned *err, const float *__restrict__ rest_in,
+                                                                  float *__restrict__ rest_out) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.N) return;
-  collide<T, kParticles>(P, s, fin, fout, rho, pa, pf, ci, err, rest_in, rest_out);
+  collide<T, kParticles, kMRT>(P, s, P.step, fin, fout, rho, pa, pf, ci, err, rest_in, rest_out);
 }
 
 // rho_A, rho_B and u = (j' + g^SC/2)/rho at the current step (for readback).
@@ -222,10 +223,15 @@ void launch_collide(const StepParams &P, const void *fin, void *fout, float *res
     using T = std::remove_pointer_t<decltype(t)>;
     const T *a = static_cast<const T *>(fin);
     T *b = static_cast<T *>(fout);
-    if (P.np > 0)
-      k_collide<T, true><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
+    const bool mrt = P.collision == LBMD_COLLISION_MRT;
+    if (P.np > 0 && mrt)
+      k_collide<T, true, true><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
+    else if (P.np > 0)
+      k_collide<T, true, false><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
+    else if (mrt)
+      k_collide<T, false, true><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
     else
-      k_collide<T, false><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
+      k_collide<T, false, false><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
   });
 }
 void launch_fields(const StepParams &P, const void *store, const float *rest, const float *rho, float *rhoA,

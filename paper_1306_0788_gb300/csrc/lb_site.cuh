@@ -9,6 +9,7 @@
 
 #include <type_traits>
 
+#include "lb_modes.h"
 #include "lbmd_internal.cuh"
 
 namespace lbmd {
@@ -199,13 +200,156 @@ __device__ __forceinline__ void gather_coupling(const StepParams &P, int x, int 
   }
 }
 
+// ------------------------------------------------------------------ fluctuating MRT
+
+// Unit normals 4k .. 4k+3 of the fluid noise at one site and step: Philox4x32-10 (Salmon et
+// al., SC'11) with counter (site, step low, step high, 0x464c0000 + k) and key = seed, uniforms
+// from the top 24 bits, Box-Muller on both uniform pairs.
+__device__ __forceinline__ float4 fluid_normals4(unsigned long long seed, unsigned long long step, unsigned site,
+                                                 unsigned k) {
+  const uint4 r = philox4x32_10(make_uint4(site, (unsigned)step, (unsigned)(step >> 32), 0x464c0000u + k),
+                                make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+  const float sc = 1.f / 16777216.f;
+  const float u0 = ((float)(r.x >> 8) + 0.5f) * sc, u1 = ((float)(r.y >> 8) + 0.5f) * sc;
+  const float u2 = ((float)(r.z >> 8) + 0.5f) * sc, u3 = ((float)(r.w >> 8) + 0.5f) * sc;
+  const float a = sqrtf(-2.f * logf(u0)), b = sqrtf(-2.f * logf(u2));
+  float s1, c1, s3, c3;
+  sincospif(2.f * u1, &s1, &c1);
+  sincospif(2.f * u3, &s3, &c3);
+  return make_float4(a * c1, a * s1, b * c3, b * s3);
+}
+
+// Eq. MODES for one component: modes m_k = sum_i e_k(c_i) f_i (lb_modes.h), each relaxed toward
+// its equilibrium value with factor 1 + lambda_k, plus the moment of the forcing term and the
+// noise nz[k]; back to populations f_i = w_i sum_k e_k(c_i) m_k / b_k.  The equilibrium moments
+// of f^eq(rho_z, u) are rho_z u (momentum), rho_z u u (stress), 0 (kinetic); those of the
+// forcing term are (2 + lambda_M)/2 g, and G for the stress (appendix), 0 for the kinetic modes.
+__device__ __forceinline__ void mrt_component(const StepParams &P, float f[kQ], float rz, float ux, float uy,
+                                              float uz, float3 g, const float nz[kQ]) {
+  float m[kQ];
+#pragma unroll
+  for (int k = 0; k < kQ; ++k) {
+    float a = 0.f;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const int e = mode_poly(k, kCx[i], kCy[i], kCz[i]);
+      if (e == 1)
+        a += f[i];
+      else if (e == -1)
+        a -= f[i];
+      else if (e != 0)
+        a += (float)e * f[i];
+    }
+    m[k] = a;
+  }
+  const float uu = ux * ux + uy * uy + uz * uz, ug = ux * g.x + uy * g.y + uz * g.z;
+  const float meq[10] = {rz,
+                         rz * ux,
+                         rz * uy,
+                         rz * uz,
+                         rz * uu,
+                         rz * (3.f * ux * ux - uu),
+                         rz * (uy * uy - uz * uz),
+                         rz * ux * uy,
+                         rz * uy * uz,
+                         rz * uz * ux};
+  const float mg[10] = {0.f,
+                        P.force[1] * g.x,
+                        P.force[2] * g.y,
+                        P.force[3] * g.z,
+                        P.force[4] * ug,
+                        P.force[5] * (3.f * ux * g.x - ug),
+                        P.force[6] * (uy * g.y - uz * g.z),
+                        P.force[7] * (ux * g.y + uy * g.x),
+                        P.force[8] * (uy * g.z + uz * g.y),
+                        P.force[9] * (uz * g.x + ux * g.z)};
+#pragma unroll
+  for (int k = 1; k < kQ; ++k) {
+    if (k < 10)
+      m[k] = meq[k] + P.relax[k] * (m[k] - meq[k]) + mg[k] + nz[k];
+    else
+      m[k] = P.relax[k] * m[k] + nz[k];
+  }
+  // moving populations from the modes; the rest population takes what the node's density
+  // (unchanged by the collision) leaves, so that the FP32 weights, whose sum is not exactly 1,
+  // do not bias the mass every step
+  float moving = 0.f;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k < kQ; ++k) {
+      const int e = mode_poly(k, kCx[i], kCy[i], kCz[i]);
+      if (e != 0) a += ((float)e * 9.f / (float)mode_norm9(k)) * m[k];
+    }
+    f[i] = kW[i] * a;
+    moving += f[i];
+  }
+  f[0] = m[0] - moving;
+}
+
+// The collision of both components with the fluctuating MRT operator.  With noise: the three
+// momentum normals are shared by A (+) and B (-), amplitude over sqrt(rho_A rho_B / rho); the
+// stress and kinetic modes take normals 3-17 (A) and 18-32 (B) of the site's 36.
+__device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long long step, unsigned site,
+                                           float fA[kQ], float fB[kQ], float rA, float rB, float ux, float uy,
+                                           float uz, float3 gA, float3 gB) {
+  float nz[kQ];
+#pragma unroll
+  for (int k = 0; k < kQ; ++k) nz[k] = 0.f;
+  float rmx = 0.f, rmy = 0.f, rmz = 0.f, b0 = 0.f, b1 = 0.f, am = 0.f;
+  if (P.fluct) {
+    am = P.noise[1] * sqrtf(rA * rB / (rA + rB));
+    const float sA = sqrtf(rA);
+    float4 q = fluid_normals4(P.seed, step, site, 0);
+    rmx = q.x; rmy = q.y; rmz = q.z;
+    nz[1] = am * rmx; nz[2] = am * rmy; nz[3] = am * rmz;
+    nz[4] = P.noise[4] * sA * q.w;
+#pragma unroll
+    for (int c = 1; c <= 3; ++c) {
+      q = fluid_normals4(P.seed, step, site, c);
+      const int k = 4 * c + 1;
+      nz[k] = P.noise[k] * sA * q.x;
+      nz[k + 1] = P.noise[k + 1] * sA * q.y;
+      nz[k + 2] = P.noise[k + 2] * sA * q.z;
+      nz[k + 3] = P.noise[k + 3] * sA * q.w;
+    }
+    q = fluid_normals4(P.seed, step, site, 4);
+    nz[17] = P.noise[17] * sA * q.x;
+    nz[18] = P.noise[18] * sA * q.y;
+    b0 = q.z;
+    b1 = q.w;
+  }
+  mrt_component(P, fA, rA, ux, uy, uz, gA, nz);
+  if (P.fluct) {
+    const float sB = sqrtf(rB);
+    nz[1] = -am * rmx; nz[2] = -am * rmy; nz[3] = -am * rmz;
+    nz[4] = P.noise[4] * sB * b0;
+    nz[5] = P.noise[5] * sB * b1;
+#pragma unroll
+    for (int c = 5; c <= 7; ++c) {
+      const float4 q = fluid_normals4(P.seed, step, site, c);
+      const int k = 4 * c - 14;
+      nz[k] = P.noise[k] * sB * q.x;
+      nz[k + 1] = P.noise[k + 1] * sB * q.y;
+      nz[k + 2] = P.noise[k + 2] * sB * q.z;
+      nz[k + 3] = P.noise[k + 3] * sB * q.w;
+    }
+    const float4 q = fluid_normals4(P.seed, step, site, 8);
+    nz[18] = P.noise[18] * sB * q.x;
+  }
+  mrt_component(P, fB, rB, ux, uy, uz, gB, nz);
+}
+
 // The lattice update of one step at site s: pull, densities and momentum, Shan-Chen force
 // (Eq. SCforce with psi = rho, g_AA = g_BB = 0), fluid-side solvation force and momentum
 // return from the particles (Sec. 2), barycentric velocity (Eq. momentum_definition), BGK
-// collision with forcing for both components, write.  With 16-bit storage rest_in / rest_out
-// are the FP32 rest populations (rest_out may be NULL: then f_0 is stored with the others).
-template <class T, bool kParticles>
-__device__ __forceinline__ void collide(const StepParams &P, long long s, const T *__restrict__ fin,
+// collision with forcing for both components (BGK, or with kMRT the fluctuating MRT of Eq. MODES,
+// `step` being the noise counter), write.  With 16-bit storage rest_in / rest_out are the FP32
+// rest populations (rest_out may be NULL: then f_0 is stored with the others).
+template <class T, bool kParticles, bool kMRT = false>
+__device__ __forceinline__ void collide(const StepParams &P, long long s, unsigned long long step,
+                                        const T *__restrict__ fin,
                                         T *__restrict__ fout, const float *__restrict__ rho,
                                         const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci,
                                         unsigned *err, const float *__restrict__ rest_in,
@@ -254,9 +398,11 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, const 
   const float ux = (jx + 0.5f * (gA.x + gB.x)) * rinv;
   const float uy = (jy + 0.5f * (gA.y + gB.y)) * rinv;
   const float uz = (jz + 0.5f * (gA.z + gB.z)) * rinv;
-  // BGK + forcing, f* = (1 - 1/tau) f + (1/tau) f^eq + Delta^g, per pair of opposite directions
-  // (c_j = -c_i): f^eq and Delta^g split into parts even and odd in c.
-  {
+  if (kMRT) {
+    mrt_update(P, step, s32, fA, fB, rA, rB, ux, uy, uz, gA, gB);
+  } else {
+    // BGK + forcing, f* = (1 - 1/tau) f + (1/tau) f^eq + Delta^g, per pair of opposite directions
+    // (c_j = -c_i): f^eq and Delta^g split into parts even and odd in c.
     const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
     const float ugA3 = 3.f * (ux * gA.x + uy * gA.y + uz * gA.z);
     const float ugB3 = 3.f * (ux * gB.x + uy * gB.y + uz * gB.z);

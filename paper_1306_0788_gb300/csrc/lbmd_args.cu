@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "lb_modes.h"
 #include "lbmd_internal.cuh"
 
 namespace lbmd {
@@ -22,6 +23,11 @@ int check_params(const lbmd_params *prm, std::string &why) {
     return why = "unknown storage", LBMD_E_INVALID_ARG;
   if (!(prm->rho0_A >= 0.0) || !(prm->rho0_B >= 0.0) || !std::isfinite(prm->rho0_A) || !std::isfinite(prm->rho0_B))
     return why = "rho0_A, rho0_B must be finite and >= 0", LBMD_E_INVALID_ARG;
+  if (prm->collision != LBMD_COLLISION_BGK && prm->collision != LBMD_COLLISION_MRT)
+    return why = "unknown collision", LBMD_E_INVALID_ARG;
+  if (prm->collision == LBMD_COLLISION_MRT)
+    for (double l : {prm->lambda_bulk, prm->lambda_mom, prm->lambda_ghost})
+      if (!(l > -2.0 && l < 0.0)) return why = "MRT eigenvalues must lie in (-2, 0)", LBMD_E_INVALID_ARG;
   return LBMD_OK;
 }
 
@@ -45,6 +51,22 @@ void fill_step_params(const lbmd_params *prm, StepParams &P) {
   P.seed = prm->seed;
   P.ntypes = 0;
   P.bond_kind = LBMD_BOND_FENE;
+  // fluctuating MRT factors (Eq. MODES): eigenvalue per mode, forcing moments of the paper's
+  // forcing term, noise amplitudes from the equilibrium mode variances (kT/c_s^2) rho_z b_k
+  P.collision = prm->collision;
+  const bool mrt = prm->collision == LBMD_COLLISION_MRT;
+  P.fluct = mrt && prm->kT > 0.0;
+  const double ls = -1.0 / prm->tau_r;
+  const double lb = mrt ? prm->lambda_bulk : ls, lm = mrt ? prm->lambda_mom : ls, lg = mrt ? prm->lambda_ghost : ls;
+  for (int k = 0; k < kQ; ++k) {
+    const double l = k == 0 ? 0.0 : k <= 3 ? lm : k == 4 ? lb : k <= 9 ? ls : lg;
+    P.relax[k] = (float)(1.0 + l);
+    P.force[k] = (float)(k == 0 ? 0.0 : k <= 3 ? 0.5 * (2.0 + lm) : k == 4 ? 2.0 + lb : k <= 6 ? 2.0 + ls
+                                        : k <= 9 ? 0.5 * (2.0 + ls) : 0.0);
+    const double keep = 1.0 - (1.0 + l) * (1.0 + l);
+    const double bk = mode_norm9(k) / 9.0;
+    P.noise[k] = (float)(k == 0 ? 0.0 : k <= 3 ? std::sqrt(prm->kT * keep) : std::sqrt(3.0 * prm->kT * bk * keep));
+  }
 }
 
 unsigned param_warnings(const lbmd_params *prm) {

@@ -62,6 +62,13 @@ struct StepParams {
   int bond_kind;
   float bond_k, bond_r;
   int reach;             // cells to scan for pair forces: ceil(max interaction range)
+  // fluctuating MRT (collision == LBMD_COLLISION_MRT): per mode k, relax[k] = 1 + lambda_k,
+  // force[k] the factor of the forcing moment ((2 + lambda)/2 for the momenta, 2 + lambda for
+  // the bulk and the normal shear modes, (2 + lambda)/2 for the off-diagonal ones), noise[k]
+  // the amplitude over sqrt(rho_z) (over sqrt(rho_A rho_B / rho) for the momenta, k = 1..3)
+  int collision;
+  bool fluct;            // kT > 0: draw the mode noise
+  float relax[kQ], force[kQ], noise[kQ];
   unsigned long long seed, step;
   TypeParams types[LBMD_MAX_TYPES];
   PairParams pairs[LBMD_MAX_TYPES * LBMD_MAX_TYPES];

@@ -37,6 +37,8 @@ LBMD_WARN_VISCOSITY = 1 << 1
 LBMD_WARN_BOLTZMANN = 1 << 2
 LBMD_WARN_ASYMMETRIC_G = 1 << 3
 LBMD_MAX_TYPES = 8
+LBMD_COLLISION_BGK = 0
+LBMD_COLLISION_MRT = 1
 LBMD_SLOT_EMPTY = 0
 LBMD_SLOT_ACTIVE = 1
 LBMD_SLOT_DONE = 2
@@ -67,7 +69,9 @@ class lbmd_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("tau_r", ctypes.c_double), ("g_AB", ctypes.c_double), ("g_BA", ctypes.c_double),
                 ("kT", ctypes.c_double), ("dt", ctypes.c_double), ("storage", ctypes.c_int),
-                ("rho0_A", ctypes.c_double), ("rho0_B", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("rho0_A", ctypes.c_double), ("rho0_B", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("collision", ctypes.c_int), ("lambda_bulk", ctypes.c_double), ("lambda_mom", ctypes.c_double),
+                ("lambda_ghost", ctypes.c_double)]
 
 
 class lbmd_ptype(ctypes.Structure):
@@ -421,8 +425,12 @@ def lbmd_batch_last_error(b) -> str:
 
 
 def params(dims, tau_r=1.0, g_AB=0.0, g_BA=None, kT=0.0, seed=0, storage=LBMD_STORAGE_FP32,
-           rho0=(0.0, 0.0)) -> lbmd_params:
-    """Convenience constructor of lbmd_params (dims = (nx, ny, nz))."""
+           rho0=(0.0, 0.0), collision=LBMD_COLLISION_BGK, lambda_bulk=None, lambda_mom=None,
+           lambda_ghost=None) -> lbmd_params:
+    """Convenience constructor of lbmd_params (dims = (nx, ny, nz)); MRT eigenvalues left as
+    None take the shear value -1/tau_r."""
     nx, ny, nz = dims
+    ls = -1.0 / tau_r
+    pick = lambda v: ls if v is None else v  # noqa: E731
     return lbmd_params(nx, ny, nz, tau_r, g_AB, g_AB if g_BA is None else g_BA, kT, 1.0, storage,
-                       rho0[0], rho0[1], seed)
+                       rho0[0], rho0[1], seed, collision, pick(lambda_bulk), pick(lambda_mom), pick(lambda_ghost))

@@ -32,6 +32,10 @@ class Case:
     bond_kind: int = 2
     bond_k: float = 0.0
     bond_r: float = 1.0
+    collision: int = 0  # 0 BGK, 1 fluctuating MRT
+    lam_bulk: float = None
+    lam_mom: float = None
+    lam_ghost: float = None
 
     def fields32(self):
         return (self.rhoA.astype(np.float32), self.rhoB.astype(np.float32),
@@ -66,7 +70,8 @@ def oracle_system(c: Case) -> oracle.System:
                          lam=lam, gamma=gamma, mass=mass, wca_eps=eps, wca_sig=sig, dh_lB=c.dh[0],
                          dh_kappa=c.dh[1], dh_rc=c.dh[2], type=np.asarray(c.ptype, dtype=np.int32), q=q,
                          bonds=np.asarray(c.bonds, dtype=np.int32).reshape(-1, 2), bond_kind=c.bond_kind,
-                         bond_k=c.bond_k, bond_r=c.bond_r)
+                         bond_k=c.bond_k, bond_r=c.bond_r, collision=c.collision, lam_bulk=c.lam_bulk,
+                         lam_mom=c.lam_mom, lam_ghost=c.lam_ghost)
 
 
 def run_oracle(c: Case, nsteps: int, trace_last: bool = False):
@@ -85,7 +90,8 @@ def run_oracle(c: Case, nsteps: int, trace_last: bool = False):
 
 def make_gpu(c: Case, stream=None):
     from paper_1306_0788_gb300 import lbmd as L
-    ctx, _ = L.lbmd_create(L.params(c.dims, tau_r=c.tau_r, g_AB=c.g, kT=c.kT, seed=c.seed), stream)
+    ctx, _ = L.lbmd_create(L.params(c.dims, tau_r=c.tau_r, g_AB=c.g, kT=c.kT, seed=c.seed, collision=c.collision,
+                                    lambda_bulk=c.lam_bulk, lambda_mom=c.lam_mom, lambda_ghost=c.lam_ghost), stream)
     types = [L.lbmd_ptype(*t) for t in c.types]
     pairs = [L.lbmd_pair(i, j, e, s) for (i, j), (e, s) in c.wca.items()]
     L.lbmd_set_types(ctx, types, pairs)

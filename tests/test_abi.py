@@ -65,3 +65,14 @@ def test_batch_create_rejects_invalid_arguments_without_device(storage, max_slot
         lbmd.lbmd_batch_create(0, storage, max_slots)
     assert e.value.code == lbmd.LBMD_E_INVALID_ARG
     assert lbmd.lbmd_batch_last_error(None)
+
+
+@pytest.mark.parametrize("field,value", [("collision", 5), ("lambda_bulk", 0.0), ("lambda_mom", -2.0),
+                                         ("lambda_ghost", 0.3)])
+def test_create_rejects_invalid_collision_without_device(field, value):
+    from paper_1306_0788_gb300 import lbmd
+    p = lbmd.params((4, 4, 4), collision=lbmd.LBMD_COLLISION_MRT)
+    setattr(p, field, value)
+    with pytest.raises(lbmd.LbmdError) as e:
+        lbmd.lbmd_create(p)
+    assert e.value.code == lbmd.LBMD_E_INVALID_ARG

@@ -30,7 +30,9 @@ def L():
 def add_case(b, c: Case, total: int, np_max=None, storage=0, rho0=(0.0, 0.0)):
     lb = L()
     slot, _ = lb.lbmd_batch_add(b, lb.params(c.dims, tau_r=c.tau_r, g_AB=c.g, kT=c.kT, seed=c.seed, storage=storage,
-                                             rho0=rho0), c.n if np_max is None else np_max, total)
+                                             rho0=rho0, collision=c.collision, lambda_bulk=c.lam_bulk,
+                                             lambda_mom=c.lam_mom, lambda_ghost=c.lam_ghost),
+                                c.n if np_max is None else np_max, total)
     lb.lbmd_batch_set_types(b, slot, [lb.lbmd_ptype(*t) for t in c.types],
                             [lb.lbmd_pair(i, j, e, s) for (i, j), (e, s) in c.wca.items()])
     if c.dh[0] != 0.0:
@@ -287,5 +289,35 @@ def test_batch_argument_errors():
         with pytest.raises(lb.LbmdError) as e:
             add_case(b, c, 5)  # both slots taken
         assert e.value.code == lb.LBMD_E_NOMEM
+    finally:
+        lb.lbmd_batch_destroy(b)
+
+
+def test_batch_mixing_bgk_and_fluctuating_mrt_replicas():
+    """MRT replicas (with fluid noise) and BGK replicas in one batch: each matches the oracle,
+    and the MRT one is bit-identical alone and in the mix."""
+    lb = L()
+    eigs = dict(collision=1, lam_bulk=-1.5, lam_mom=-0.7, lam_ghost=-1.2)
+    m1 = coupled_case((12, 10, 14), 24, seed=5, g=1.3, kT=0.002)
+    for k, v in eigs.items():
+        setattr(m1, k, v)
+    m2 = fluid_case((9, 7, 5), seed=8, tau=0.8)
+    m2.kT, m2.seed = 1e-4, 44
+    for k, v in eigs.items():
+        setattr(m2, k, v)
+    bg = coupled_case((7, 11, 6), 6, seed=9, g=0.9)
+    b = lb.lbmd_batch_create(0, 0, 8)
+    try:
+        slots = [add_case(b, c, 10) for c in (bg, m1, m2)]
+        lb.lbmd_batch_step(b, 3)
+        lb.lbmd_batch_step(b, 7)
+        st = lb.lbmd_batch_poll(b, 8)
+        for c, s in zip((bg, m1, m2), slots):
+            assert st[s] == lb.LBMD_SLOT_DONE
+            fg, xg, _, _ = read(b, s, c)
+            fo, xo, _, _ = run_oracle(c, 10)
+            assert pop_error(fg, fo) <= POP_TOL
+            assert position_error(xg, xo, c.x, c.dims) <= POS_TOL
+        assert same(read(b, slots[1], m1), run_alone(m1, 10))
     finally:
         lb.lbmd_batch_destroy(b)

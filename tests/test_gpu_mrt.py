@@ -1,0 +1,95 @@
+"""Fluctuating MRT collision (Eq. MODES) of the CUDA path against the FP64 oracle.
+
+Both sides draw the fluid noise from the same counter-based generator (Philox4x32-10, one
+counter per site and step), so noisy runs are compared pointwise with the parity tolerances:
+populations 1e-5 after 10 steps, positions 1e-4 after 100 steps.  The full-size test checks a
+property that holds at any size: equipartition of the density and momentum fluctuations.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import Case, make_gpu, noisy_fluid, pop_error, position_error, run_gpu, run_oracle
+
+from test_gpu_parity import coupled_case
+
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-5
+POS_TOL = 1e-4
+EIGS = dict(collision=1, lam_bulk=-1.5, lam_mom=-0.7, lam_ghost=-1.2)
+
+
+@pytest.mark.parametrize("kT", [0.0, 1e-4])
+@pytest.mark.parametrize("dims,tau", [((12, 10, 9), 0.8), ((5, 7, 3), 1.3)])
+def test_mrt_fluid_populations_10_steps(kT, dims, tau):
+    rA, rB = noisy_fluid(dims, amp=0.03, seed=31)
+    c = Case(dims=dims, tau_r=tau, g=1.3, kT=kT, seed=17, rhoA=rA, rhoB=rB, **EIGS)
+    fg, *_ = run_gpu(c, 10)
+    fo, *_ = run_oracle(c, 10)
+    assert pop_error(fg, fo) <= POP_TOL
+
+
+def test_mrt_equal_eigenvalues_match_bgk_path():
+    """With every eigenvalue -1/tau_r and kT = 0 the MRT kernel computes the BGK update."""
+    dims = (9, 8, 7)
+    rA, rB = noisy_fluid(dims, amp=0.03, seed=32)
+    bgk = Case(dims=dims, tau_r=0.9, g=1.2, rhoA=rA, rhoB=rB)
+    mrt = Case(dims=dims, tau_r=0.9, g=1.2, rhoA=rA, rhoB=rB, collision=1)
+    fb, *_ = run_gpu(bgk, 10)
+    fm, *_ = run_gpu(mrt, 10)
+    assert pop_error(fm, fb.astype(np.float64)) <= 2e-6
+
+
+def test_mrt_coupled_10_steps_with_fluid_and_particle_noise():
+    c = coupled_case((12, 10, 14), 24, seed=5, g=1.3, kT=0.002)
+    for k, v in EIGS.items():
+        setattr(c, k, v)
+    fg, xg, _, Fg = run_gpu(c, 10)
+    fo, xo, _, tr = run_oracle(c, 10, trace_last=True)
+    assert pop_error(fg, fo) <= POP_TOL
+    assert position_error(xg, xo, c.x, c.dims) <= POS_TOL
+    Fo = tr["f_total"]
+    assert np.abs(Fg - Fo).max() <= 1e-4 * max(np.abs(Fo).max(), 1e-3)
+
+
+def test_mrt_particles_100_steps():
+    c = coupled_case((20, 18, 16), 30, seed=21, kT=0.002, min_dist=2.5)
+    for k, v in EIGS.items():
+        setattr(c, k, v)
+    fg, xg, _, _ = run_gpu(c, 100)
+    fo, xo, _, _ = run_oracle(c, 100)
+    assert position_error(xg, xo, c.x, c.dims) <= POS_TOL
+    assert pop_error(fg, fo) <= 1e-4
+
+
+@pytest.mark.parametrize("rhoA,rhoB", [(1.0, 1.0), (1.5, 0.5)])
+def test_mrt_equipartition_at_96_cubed(rhoA, rhoB):
+    """At 96^3 (0.9 M nodes), after 300 steps at kT = 1e-4 and g = 0: per-node variance of
+    rho_z = (kT/c_s^2) rho_z, no A-B correlation, total momentum variance kT rho per
+    direction -- within 2 %.  Mass and momentum from the FP64 diagnostics: the FP32 update
+    keeps each node's density exactly up to rounding, whose bias with noise and unequal
+    densities reaches ~3e-6 of the denser component in 300 steps (a float32 emulation of the
+    same arithmetic on the host shows the same); the stated bound is 1e-5."""
+    from paper_1306_0788_gb300 import lbmd as L
+    dims = (96, 96, 96)
+    kT = 1e-4
+    c = Case(dims=dims, tau_r=0.8, g=0.0, kT=kT, seed=3, rhoA=np.full(dims[::-1], rhoA),
+             rhoB=np.full(dims[::-1], rhoB), **EIGS)
+    ctx = make_gpu(c)
+    try:
+        L.lbmd_step(ctx, 10)  # the first collisions move the FP32 equilibrium's mass by ~1e-6
+        d0 = L.lbmd_diagnostics(ctx)
+        L.lbmd_step(ctx, 290)
+        a, b, u = L.lbmd_get_fields(ctx, c.shape)
+        d1 = L.lbmd_diagnostics(ctx)
+    finally:
+        L.lbmd_destroy(ctx)
+    da, db = a.astype(np.float64) - rhoA, b.astype(np.float64) - rhoB
+    ea, eb = 3 * kT * rhoA, 3 * kT * rhoB
+    assert abs((da * da).mean() / ea - 1) < 0.02
+    assert abs((db * db).mean() / eb - 1) < 0.02
+    assert abs((da * db).mean()) < 0.02 * np.sqrt(ea * eb)
+    j = u.astype(np.float64) * (a + b)[..., None]  # g = 0: u = j / rho
+    assert abs((j * j).mean() / (kT * (rhoA + rhoB)) - 1) < 0.02
+    assert abs(d1[0] / d0[0] - 1) < 1e-5 and abs(d1[1] / d0[1] - 1) < 1e-5
+    assert np.abs(d1[2:5]).max() < 1e-6 * d0[0]
