@@ -237,7 +237,9 @@ def run_cuda(args):
     npart = len(x)
     N = dims[0] * dims[1] * dims[2]
     rho0 = (float(rA.mean()), float(rB.mean()))  # shift reference of the 16-bit storages
-    prm = L.params(dims, tau_r=1.0, g_AB=g_ab, kT=kT, seed=42 + rank, storage=STORAGES[args.storage][0], rho0=rho0)
+    mrt = args.collision == "mrt"
+    prm = L.params(dims, tau_r=1.0, g_AB=g_ab, kT=kT, seed=42 + rank, storage=STORAGES[args.storage][0], rho0=rho0,
+                   collision=L.LBMD_COLLISION_MRT if mrt else L.LBMD_COLLISION_BGK)
     ctx, _ = L.lbmd_create(prm, stream)
     L.lbmd_set_types(ctx, [L.lbmd_ptype(*t) for t in types], [L.lbmd_pair(0, 0, 1.0, 1.0)])
     L.lbmd_init_fluid(ctx, rA, rB)
@@ -324,14 +326,17 @@ def run_cuda(args):
                        "description": WORKLOADS[args.workload][2],
                        "lattice": list(dims), "particles": npart, "tau_r": 1.0, "g_AB": g_ab, "kT": kT,
                        "storage": args.storage,
+                       "collision": ("fluctuating MRT (Eq. MODES), eigenvalues -1, fluid noise at kT"
+                                     if mrt else "BGK"),
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (N * 152 / 1e9)
                        if N * 152 > 129e6 else "L2-resident lattice (latency regime)"},
-            "roofline": {"bound": "hbm", "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + BGK/forcing, both components)",
+            "roofline": {"bound": "hbm", "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + %s/forcing, "
+                                                   "both components)" % ("MRT + noise" if mrt else "BGK"),
                          "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_site": bps,
                          "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,
-                         "traffic": (None if COLLIDE_TRAFFIC_BYTES_PER_NODE is None or args.storage != "fp32"
+                         "traffic": (None if COLLIDE_TRAFFIC_BYTES_PER_NODE is None or args.storage != "fp32" or mrt
                                      else int(COLLIDE_TRAFFIC_BYTES_PER_NODE * N))},
             "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks, "state_ok": state_ok,
         }
@@ -456,6 +461,8 @@ def main():
     ap.add_argument("--edge", type=int, default=0, help="override the lattice edge (profiling of smaller cases)")
     ap.add_argument("--storage", choices=sorted(STORAGES), default="fp32",
                     help="population storage: FP32, or FP16 / BF16 shifted by w_i rho0 (FP32 arithmetic)")
+    ap.add_argument("--collision", choices=["bgk", "mrt"], default="bgk",
+                    help="BGK, or the fluctuating MRT collision with fluid noise at the workload's kT")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -204,7 +204,9 @@ __device__ __forceinline__ void gather_coupling(const StepParams &P, int x, int 
 
 // Unit normals 4k .. 4k+3 of the fluid noise at one site and step: Philox4x32-10 (Salmon et
 // al., SC'11) with counter (site, step low, step high, 0x464c0000 + k) and key = seed, uniforms
-// from the top 24 bits, Box-Muller on both uniform pairs.
+// from the top 24 bits, Box-Muller on both uniform pairs.  The logarithm and the sine / cosine
+// are the hardware approximations (absolute error ~1e-6 on a normal, far below what the
+// populations can resolve); the generator's integer stream is exact.
 __device__ __forceinline__ float4 fluid_normals4(unsigned long long seed, unsigned long long step, unsigned site,
                                                  unsigned k) {
   const uint4 r = philox4x32_10(make_uint4(site, (unsigned)step, (unsigned)(step >> 32), 0x464c0000u + k),
@@ -212,10 +214,11 @@ __device__ __forceinline__ float4 fluid_normals4(unsigned long long seed, unsign
   const float sc = 1.f / 16777216.f;
   const float u0 = ((float)(r.x >> 8) + 0.5f) * sc, u1 = ((float)(r.y >> 8) + 0.5f) * sc;
   const float u2 = ((float)(r.z >> 8) + 0.5f) * sc, u3 = ((float)(r.w >> 8) + 0.5f) * sc;
-  const float a = sqrtf(-2.f * logf(u0)), b = sqrtf(-2.f * logf(u2));
+  const float a = sqrtf(-2.f * __logf(u0)), b = sqrtf(-2.f * __logf(u2));
+  const float two_pi = 6.28318530717958647692f;
   float s1, c1, s3, c3;
-  sincospif(2.f * u1, &s1, &c1);
-  sincospif(2.f * u3, &s3, &c3);
+  __sincosf(two_pi * u1, &s1, &c1);
+  __sincosf(two_pi * u3, &s3, &c3);
   return make_float4(a * c1, a * s1, b * c3, b * s3);
 }
 
@@ -224,21 +227,34 @@ __device__ __forceinline__ float4 fluid_normals4(unsigned long long seed, unsign
 // noise nz[k]; back to populations f_i = w_i sum_k e_k(c_i) m_k / b_k.  The equilibrium moments
 // of f^eq(rho_z, u) are rho_z u (momentum), rho_z u u (stress), 0 (kinetic); those of the
 // forcing term are (2 + lambda_M)/2 g, and G for the stress (appendix), 0 for the kinetic modes.
+// Directions come in opposite pairs (2p + 1, 2p + 2) and every e_k is even or odd in c, so both
+// transforms work on the pair sums and differences: half the arithmetic of the plain sums.
+__device__ __host__ constexpr bool mode_even(int k) { return k == 0 || (k >= 4 && k <= 9) || k >= 16; }
+
 __device__ __forceinline__ void mrt_component(const StepParams &P, float f[kQ], float rz, float ux, float uy,
                                               float uz, float3 g, const float nz[kQ]) {
+  constexpr int kPairs = (kQ - 1) / 2;
+  float sp[kPairs], dp[kPairs];
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    sp[p] = f[2 * p + 1] + f[2 * p + 2];
+    dp[p] = f[2 * p + 1] - f[2 * p + 2];
+  }
   float m[kQ];
 #pragma unroll
   for (int k = 0; k < kQ; ++k) {
-    float a = 0.f;
+    float a = mode_even(k) ? (float)mode_poly(k, 0, 0, 0) * f[0] : 0.f;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
+    for (int p = 0; p < kPairs; ++p) {
+      const int i = 2 * p + 1;
       const int e = mode_poly(k, kCx[i], kCy[i], kCz[i]);
+      const float v = mode_even(k) ? sp[p] : dp[p];
       if (e == 1)
-        a += f[i];
+        a += v;
       else if (e == -1)
-        a -= f[i];
+        a -= v;
       else if (e != 0)
-        a += (float)e * f[i];
+        a += (float)e * v;
     }
     m[k] = a;
   }
@@ -263,29 +279,40 @@ __device__ __forceinline__ void mrt_component(const StepParams &P, float f[kQ], 
                         P.force[7] * (ux * g.y + uy * g.x),
                         P.force[8] * (uy * g.z + uz * g.y),
                         P.force[9] * (uz * g.x + ux * g.z)};
+  // relaxed modes, scaled by 1 / b_k for the way back
 #pragma unroll
-  for (int k = 1; k < kQ; ++k) {
-    if (k < 10)
-      m[k] = meq[k] + P.relax[k] * (m[k] - meq[k]) + mg[k] + nz[k];
+  for (int k = 0; k < kQ; ++k) {
+    float v;
+    if (k == 0)
+      v = m[0];
+    else if (k < 10)
+      v = meq[k] + P.relax[k] * (m[k] - meq[k]) + mg[k] + nz[k];
     else
-      m[k] = P.relax[k] * m[k] + nz[k];
+      v = P.relax[k] * m[k] + nz[k];
+    m[k] = v * (9.f / (float)mode_norm9(k));
   }
   // moving populations from the modes; the rest population takes what the node's density
   // (unchanged by the collision) leaves, so that the FP32 weights, whose sum is not exactly 1,
   // do not bias the mass every step
   float moving = 0.f;
 #pragma unroll
-  for (int i = 1; i < kQ; ++i) {
-    float a = 0.f;
+  for (int p = 0; p < kPairs; ++p) {
+    const int i = 2 * p + 1;
+    float even = 0.f, odd = 0.f;
 #pragma unroll
     for (int k = 0; k < kQ; ++k) {
       const int e = mode_poly(k, kCx[i], kCy[i], kCz[i]);
-      if (e != 0) a += ((float)e * 9.f / (float)mode_norm9(k)) * m[k];
+      if (e == 0) continue;
+      if (mode_even(k))
+        even += (float)e * m[k];
+      else
+        odd += (float)e * m[k];
     }
-    f[i] = kW[i] * a;
-    moving += f[i];
+    f[i] = kW[i] * (even + odd);
+    f[i + 1] = kW[i] * (even - odd);
+    moving += f[i] + f[i + 1];
   }
-  f[0] = m[0] - moving;
+  f[0] = rz - moving;
 }
 
 // The collision of both components with the fluctuating MRT operator.  With noise: the three
