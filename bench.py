@@ -32,6 +32,13 @@ HBM_FALLBACK_GBS = 6800.0
 # of the 128^3 case of this workload, scaled per node; profiles/k_collide_slab_droplets_256.md).
 # None while k_collide has changed since the last capture.
 COLLIDE_TRAFFIC_BYTES_PER_NODE = 290.0
+# The fluctuating MRT update is bound by instruction issue, not by HBM: warp instructions per
+# node of k_collide<float, true, true> (smsp__inst_executed.sum / nodes of one ncu capture of the
+# 128^3 case, profiles/k_collide_mrt_slab_droplets_256.md), and the issue peak of the GPU: one
+# warp instruction per cycle per scheduler, 4 schedulers per SM, 152 SMs, at the SM clock.
+MRT_WARP_INSTR_PER_NODE = 85.42
+MRT_TRAFFIC_BYTES_PER_NODE = 290.7  # DRAM bytes per node of the same capture
+SMS, SCHEDULERS_PER_SM = 152, 4
 
 # The slab/droplet workload uses the density scale of the paper's ferrofluid example (Sec. 4.5):
 # mean density 78.4 per component with g = 0.0214 (g rho = 1.68).  Bulk coexistence of F_bulk
@@ -314,6 +321,19 @@ def run_cuda(args):
     bps = algorithmic_bytes_per_site(args.storage)
     avg_kernel_ms = k_ms / max(k_n, 1)
     achieved = bps * N / (avg_kernel_ms * 1e-3) / 1e9
+    if mrt:
+        clk = clocks.get("sm_mhz") or 2070.0
+        issue_peak = SMS * SCHEDULERS_PER_SM * clk * 1e6
+        issued = MRT_WARP_INSTR_PER_NODE * N / (avg_kernel_ms * 1e-3)
+        roofline = {"bound": "alu", "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + fluctuating "
+                                              "MRT with Philox noise, both components)",
+                    "achieved": round(issued / 1e12, 4), "peak": round(issue_peak / 1e12, 4),
+                    "peak_kind": "derived: 152 SMs x 4 schedulers x 1 warp instruction per cycle x the median SM "
+                                 "clock under load", "unit": "T warp-instructions/s",
+                    "frac": round(issued / issue_peak, 4), "instructions_per_node": MRT_WARP_INSTR_PER_NODE,
+                    "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,
+                    "hbm_frac": round(achieved / peak, 4),
+                    "traffic": int(MRT_TRAFFIC_BYTES_PER_NODE * N) if args.storage == "fp32" else None}
     value = whole_job_rate(N * args.steps, world, ms_max * 1e-3) / 1e6
     if rank == 0:
         out = {
@@ -331,8 +351,9 @@ def run_cuda(args):
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (N * 152 / 1e9)
                        if N * 152 > 129e6 else "L2-resident lattice (latency regime)"},
-            "roofline": {"bound": "hbm", "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + %s/forcing, "
-                                                   "both components)" % ("MRT + noise" if mrt else "BGK"),
+            "roofline": roofline if mrt else {
+                         "bound": "hbm", "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + BGK/forcing, "
+                                                   "both components)",
                          "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_site": bps,
                          "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,
