@@ -183,7 +183,7 @@ class _OrcSystem(ctypes.Structure):
                 ("pid", ctypes.c_void_p), ("nbonds", ctypes.c_int), ("bonds", ctypes.c_void_p),
                 ("bond_kind", ctypes.c_int), ("bond_k", ctypes.c_double), ("bond_r", ctypes.c_double),
                 ("collision", ctypes.c_int), ("lam_bulk", ctypes.c_double), ("lam_mom", ctypes.c_double),
-                ("lam_ghost", ctypes.c_double)]
+                ("lam_ghost", ctypes.c_double), ("md_substeps", ctypes.c_int)]
 
 
 class _OrcTrace(ctypes.Structure):
@@ -226,6 +226,7 @@ class System:
     lam_bulk: float = None
     lam_mom: float = None
     lam_ghost: float = None
+    md_substeps: int = 1  # particle substeps per lattice step (reading R15)
 
     def _struct(self):
         keep = []
@@ -257,6 +258,7 @@ class System:
         s.lam_bulk = ls if self.lam_bulk is None else float(self.lam_bulk)
         s.lam_mom = ls if self.lam_mom is None else float(self.lam_mom)
         s.lam_ghost = ls if self.lam_ghost is None else float(self.lam_ghost)
+        s.md_substeps = int(self.md_substeps)
         return s, keep
 
 

@@ -54,6 +54,14 @@
  *       with counter (site, step low, step high, 0x464c0000 + k), k = 0..8, Box-Muller on both
  *       uniform pairs of each draw: normals 0-2 are the momentum ones (x, y, z), 3-17 the
  *       modes 4-18 of A, 18-32 those of B.
+ *   R15 MD sub-stepping (Sec. 3, gamma dt / m << 1): with K = md_substeps > 1 the particle
+ *       forces, the momentum return and the particle update (steps 5, 6 and 9 below) run K
+ *       times with dt / K while the fluid fields of the step stay frozen: the coupling velocity
+ *       field u_cpl and the node gradients are those of step 4, the fluid-side solvation force
+ *       and its reaction on the particles those of x(n); the friction noise of substep k draws
+ *       with the counter step K + k and has the amplitude sqrt(2 kT gamma K / dt); the momentum
+ *       return of every substep is spread with that substep's trilinear weights and divided by
+ *       K, and the collision uses the sum.  K = 1 is the step above.
  *   R14 Bulk viscosity of that collision: eta_b = -(2/3) rho c_s^2 (1/lambda_b + 1/2), from the
  *       trace equation of the Chapman-Enskog expansion with the traceless shear stress of
  *       Eq. (comp_Pi); Eq. (TRANSPORTCOEFF) prints it without the 2/3 (which at BGK would
@@ -344,6 +352,7 @@ typedef struct {
   double bond_k, bond_r;
   int collision;         /* 0 = BGK (R3), 1 = fluctuating MRT (R13) */
   double lam_bulk, lam_mom, lam_ghost; /* MRT eigenvalues; the shear one is -1/tau_r */
+  int md_substeps;       /* K >= 1 particle substeps per lattice step (R15) */
 } orc_system;
 
 typedef struct {         /* optional outputs, each may be NULL */
@@ -380,8 +389,8 @@ static void orc_trilinear(const int *dim, const double *x, long *cell, double *f
  * [2][19][nz][ny][nx]; x, v are [np][3] and are advanced in place.  Returns 0, or -1 if a
  * density is non-positive, -2 if a FENE bond is stretched beyond R0.  Steps follow the
  * order: densities and momentum, Shan-Chen force, fluid-side solvation force, coupling
- * velocity, particle forces, momentum return, collision with forcing, streaming, particle
- * update. */
+ * velocity, particle forces, momentum return, particle update (these three once per particle
+ * substep, reading R15), collision with forcing, streaming. */
 int orc_step(const orc_system *sys, double *f, double *x, double *v, uint64_t step, orc_trace *tr) {
   const int *dim = sys->dim;
   const long N = (long)dim[0] * dim[1] * dim[2];
@@ -445,6 +454,15 @@ int orc_step(const orc_system *sys, double *f, double *x, double *v, uint64_t st
                                                  ffs[3 * s + a] + ffs[3 * (N + s) + a])) / r;
   }
 
+  /* Steps 5, 6 and 9 run once per particle substep (reading R15; K = 1: once, with dt). */
+  const int K = sys->md_substeps > 1 ? sys->md_substeps : 1;
+  const double dts = sys->dt / K, wK = 1.0 / K;
+  for (int sub = 0; sub < K; ++sub) {
+  if (sub > 0) {
+    memset(pu, 0, sizeof(double) * 9 * np);   /* pu, pgA, pgB */
+    memset(pf_pair, 0, sizeof(double) * 6 * np); /* pf_pair, pf_bond */
+  }
+
   /* 5. Particle forces at x(n), v(n): friction and noise (Eq. NEWTON), solvation
    * (Eq. solvation_kappa, reading R6), pair forces (WCA, DH) and bonds. */
   for (int p = 0; p < np; ++p) {
@@ -461,8 +479,8 @@ int orc_step(const orc_system *sys, double *f, double *x, double *v, uint64_t st
     double noise[3] = {0.0, 0.0, 0.0};
     if (sys->kT > 0.0) {
       double nrm[3];
-      orc_normals(sys->seed, step, (uint32_t)sys->pid[p], nrm);
-      double amp = sqrt(2.0 * sys->kT * sys->gamma[t] / sys->dt);
+      orc_normals(sys->seed, step * (uint64_t)K + (uint64_t)sub, (uint32_t)sys->pid[p], nrm);
+      double amp = sqrt(2.0 * sys->kT * sys->gamma[t] / dts);
       for (int a = 0; a < 3; ++a) noise[a] = amp * nrm[a];
     }
     for (int a = 0; a < 3; ++a) {
@@ -515,11 +533,27 @@ int orc_step(const orc_system *sys, double *f, double *x, double *v, uint64_t st
       double r = rho[s] + rho[N + s];
       double sA = rho[s] / r, sB = rho[N + s] / r;
       for (int a = 0; a < 3; ++a) {
-        gcp[3 * s + a] += w[k] * (-sA * pf_fric[3 * p + a] - pf_psA[3 * p + a]);
-        gcp[3 * (N + s) + a] += w[k] * (-sB * pf_fric[3 * p + a] - pf_psB[3 * p + a]);
+        gcp[3 * s + a] += wK * (w[k] * (-sA * pf_fric[3 * p + a] - pf_psA[3 * p + a]));
+        gcp[3 * (N + s) + a] += wK * (w[k] * (-sB * pf_fric[3 * p + a] - pf_psB[3 * p + a]));
       }
     }
   }
+
+  /* 9. Particle update (reading R9) with the substep dt / K (reading R15); the collision
+   * below does not depend on the particle state any more. */
+  for (int p = 0; p < np; ++p) {
+    int t = sys->type[p];
+    for (int a = 0; a < 3; ++a) {
+      double F = pf_fric[3 * p + a] + pf_psA[3 * p + a] + pf_psB[3 * p + a] + pf_fs[3 * p + a] +
+                 pf_pair[3 * p + a] + pf_bond[3 * p + a];
+      pf_tot[3 * p + a] = F;
+      v[3 * p + a] += F * dts / sys->mass[t];
+      x[3 * p + a] += v[3 * p + a] * dts;
+      x[3 * p + a] -= dim[a] * floor(x[3 * p + a] / dim[a]);
+      if (x[3 * p + a] >= dim[a]) x[3 * p + a] = 0.0;
+    }
+  }
+  }  /* substeps */
 
   /* 7. Collision with forcing (Eqs. EQ:LBapp, collis, feq, momentum_definition and the
    * forcing term), BGK reading R3 or fluctuating MRT (Eq. MODES, reading R13), then
@@ -595,20 +629,6 @@ int orc_step(const orc_system *sys, double *f, double *x, double *v, uint64_t st
         }
       }
   memcpy(f, fnew, sizeof(double) * 2 * ORC_Q * N);
-
-  /* 9. Particle update (reading R9). */
-  for (int p = 0; p < np; ++p) {
-    int t = sys->type[p];
-    for (int a = 0; a < 3; ++a) {
-      double F = pf_fric[3 * p + a] + pf_psA[3 * p + a] + pf_psB[3 * p + a] + pf_fs[3 * p + a] +
-                 pf_pair[3 * p + a] + pf_bond[3 * p + a];
-      pf_tot[3 * p + a] = F;
-      v[3 * p + a] += F * sys->dt / sys->mass[t];
-      x[3 * p + a] += v[3 * p + a] * sys->dt;
-      x[3 * p + a] -= dim[a] * floor(x[3 * p + a] / dim[a]);
-      if (x[3 * p + a] >= dim[a]) x[3 * p + a] = 0.0;
-    }
-  }
 
   if (tr) {
     if (tr->rho) memcpy(tr->rho, rho, sizeof(double) * 2 * N);
