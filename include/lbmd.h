@@ -52,6 +52,7 @@ extern "C" {
 #define LBMD_E_UNIMPLEMENTED (-7)
 #define LBMD_E_BOND_BROKEN (-8) /* FENE bond stretched to or beyond R0 */
 #define LBMD_E_STATE (-9)       /* call out of order (e.g. step before init_fluid) */
+#define LBMD_E_PARTICLE_TOO_FAST (-10) /* md_substeps > 1: a particle crossed more than one cell in one step */
 
 /* population storage: FP32, or 16-bit (IEEE half or bfloat16) holding the shifted value
  * f_zi - w_i rho0_z (lbmd_params.rho0_A / rho0_B); collisions always compute in FP32 and the
@@ -93,7 +94,13 @@ typedef struct lbmd_ctx lbmd_ctx;
  * modes with lambda_ghost, every eigenvalue in (-2, 0); at kT > 0 each mode receives
  * Gaussian noise with the amplitude that gives equipartition at temperature kT, the momentum
  * noise of A and B being one random number with opposite signs (Sec. 2).  The lambda_* are
- * ignored with BGK. */
+ * ignored with BGK.
+ * md_substeps: K >= 1 particle substeps per lattice step (Sec. 3: gamma dt / m << 1 and stiff
+ * pair forces need a particle step below the lattice one): forces, momentum return and
+ * particle update run K times with dt / K while the fluid fields of the step stay frozen,
+ * and the collision takes the average momentum return.  K > 1 requires every particle to
+ * stay within one cell of where the step started (else LBMD_E_PARTICLE_TOO_FAST); batches
+ * take K = 1 only. */
 typedef struct {
   int nx, ny, nz;
   double tau_r;
@@ -105,6 +112,7 @@ typedef struct {
   uint64_t seed;
   int collision;
   double lambda_bulk, lambda_mom, lambda_ghost;
+  int md_substeps;
 } lbmd_params;
 
 /* Per particle type: kappa_A, kappa_B of Eq. (solvation_kappa), lambda_A, lambda_B of
@@ -123,7 +131,8 @@ typedef struct {
  * cudaStream_t (may be NULL).  Allocates both population buffers; fails with
  * LBMD_E_NOMEM if they do not fit.  *warnings (may be NULL) receives LBMD_WARN_* bits.
  * Errors: LBMD_E_INVALID_ARG for sizes < 1, tau_r <= 1/2, dt != 1, unknown storage,
- * negative rho0, unknown collision, an MRT eigenvalue outside (-2, 0). */
+ * negative rho0, unknown collision, an MRT eigenvalue outside (-2, 0), md_substeps outside
+ * [1, 256]. */
 int lbmd_create(const lbmd_params *params, void *stream, lbmd_ctx **out, unsigned *warnings);
 
 /* Destroy a context and free its device memory (NULL is ignored). */

@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kBPThreads) kb_couple(const BatchDev *__restri
     if (B->left[slot] <= 0) continue;
     const RepDev &R = B->rep[slot];
     const CellIndex ci{B->row_start + B->lay[slot].row0};
-    site::couple(R.P, B->state[slot].step, p, B->S, ci, R.rho, R.jp, B->pf);
+    site::couple(R.P, B->state[slot].step, p, B->S, B->S, ci, R.rho, R.jp, B->pf);
   }
 }
 
@@ -879,6 +879,7 @@ int lbmd_batch_add(lbmd_batch *b, const lbmd_params *prm, int np_max, int64_t to
   int r = check_params(prm, why);
   if (r) return bfail(b, r, why);
   if (prm->storage != b->storage) return bfail(b, LBMD_E_INVALID_ARG, "replica storage differs from the batch's");
+  if (prm->md_substeps != 1) return bfail(b, LBMD_E_INVALID_ARG, "batches take md_substeps = 1 only");
   if (np_max < 0 || total_steps < 0) return bfail(b, LBMD_E_INVALID_ARG, "np_max and total_steps must be >= 0");
   StepParams P;
   fill_step_params(prm, P);

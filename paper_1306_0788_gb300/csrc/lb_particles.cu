@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kPBlock) k_couple(StepParams P, ParticleArrays
                                                     ParticleForces pf) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P.np) return;
-  site::couple(P, P.step, p, pa, ci, rho, jp, pf);
+  site::couple(P, P.step, p, pa, pa, ci, rho, jp, pf);
 }
 
 // Pair and bonded forces of every particle (site::pairs).
@@ -156,6 +156,55 @@ __global__ void k_integrate(StepParams P, ParticleArrays pa, ParticleForces pf, 
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P.np) return;
   site::integrate(P, p, pa, pa, pf, err);
+}
+
+// ------------------------------------------------------------------ MD sub-stepping
+
+// Coupling forces of substep `sub` at the particles' current positions C (in the order of the
+// step's sorted list S, whose fluid-side solvation force stays frozen), then the substep's
+// reaction record: position, friction and solvation forces over K, and the substep index in
+// the cell's w (the fluid-side solvation force is taken from substep 0's records only).
+__global__ void __launch_bounds__(kPBlock) k_couple_sub(StepParams P, ParticleArrays C, ParticleArrays S,
+                                                        CellIndex ci, const float *__restrict__ rho,
+                                                        const float *__restrict__ jp, ParticleForces pf, int sub,
+                                                        ReactionRecords rec) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P.np) return;
+  site::couple(P, P.step, p, C, S, ci, rho, jp, pf, sub == 0);
+  const float invK = 1.f / (float)P.substeps;
+  const int r = sub * P.np + p;
+  const int4 c = C.cell[p];
+  rec.cell[r] = make_int4(c.x, c.y, c.z, c.w | (sub << 8));
+  rec.frac[r] = C.frac[p];
+  rec.key[r] = sub * P.np + C.pid[p];
+  const float4 a = pf.fric[p], b = pf.psA[p], d = pf.psB[p];
+  rec.fric[r] = make_float4(a.x * invK, a.y * invK, a.z * invK, 0.f);
+  rec.psA[r] = make_float4(b.x * invK, b.y * invK, b.z * invK, 0.f);
+  rec.psB[r] = make_float4(d.x * invK, d.y * invK, d.z * invK, 0.f);
+}
+
+// Particle update of one substep (P.dt = dt / K), in place, and the check that each particle
+// is still within one cell of where the step started (the cell list of the step relies on it).
+__global__ void k_integrate_sub(StepParams P, ParticleArrays C, ParticleArrays S, ParticleForces pf, unsigned *err) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P.np) return;
+  site::integrate(P, p, C, C, pf, err);
+  const int4 a = C.cell[p], b = S.cell[p];
+  const int dx = site::min_image_cells(a.x - b.x, P.nx), dy = site::min_image_cells(a.y - b.y, P.ny),
+            dz = site::min_image_cells(a.z - b.z, P.nz);
+  if (dx > 1 || dx < -1 || dy > 1 || dy < -1 || dz > 1 || dz < -1) atomicOr(err, kErrTooFast);
+}
+
+__global__ void k_rec_permute(int n, const int *__restrict__ perm, ReactionRecords src, ReactionRecords dst) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int p = perm[j];
+  dst.cell[j] = src.cell[p];
+  dst.frac[j] = src.frac[p];
+  dst.key[j] = src.key[p];
+  dst.fric[j] = src.fric[p];
+  dst.psA[j] = src.psA[p];
+  dst.psB[j] = src.psB[p];
 }
 
 constexpr int kMomBlock = 256;
@@ -217,6 +266,19 @@ void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, c
 void launch_integrate(const StepParams &P, const ParticleArrays &pa, const ParticleForces &pf, unsigned *err,
                       cudaStream_t st) {
   k_integrate<<<pgrid(P.np), kPBlock, 0, st>>>(P, pa, pf, err);
+}
+void launch_couple_sub(const StepParams &P, const ParticleArrays &C, const ParticleArrays &S, CellIndex ci,
+                       const float *rho, const float *jp, const ParticleForces &pf, int sub,
+                       const ReactionRecords &rec, cudaStream_t st) {
+  k_couple_sub<<<pgrid(P.np), kPBlock, 0, st>>>(P, C, S, ci, rho, jp, pf, sub, rec);
+}
+void launch_integrate_sub(const StepParams &P, const ParticleArrays &C, const ParticleArrays &S,
+                          const ParticleForces &pf, unsigned *err, cudaStream_t st) {
+  k_integrate_sub<<<pgrid(P.np), kPBlock, 0, st>>>(P, C, S, pf, err);
+}
+void launch_rec_permute(int n, const int *perm, const ReactionRecords &src, const ReactionRecords &dst,
+                        cudaStream_t st) {
+  k_rec_permute<<<pgrid(n), kPBlock, 0, st>>>(n, perm, src, dst);
 }
 void launch_particle_momentum(const StepParams &P, const ParticleArrays &pa, double *partial, int nblocks,
                               cudaStream_t st) {

@@ -159,7 +159,9 @@ __device__ __forceinline__ void moments(const StepParams &P, long long s, const 
 
 // Fluid-side solvation force (Eq. solvation_lambda) and momentum return (Sec. 2) gathered at
 // node (x, y, z) from the particles of the 8 unit cells having that node as a corner.
-// ci.row_start is indexed by this lattice's row (z * ny + y); pa, pf by the sorted slot.
+// ci.row_start is indexed by this lattice's row (z * ny + y); pa, pf by the sorted slot.  The
+// cell's w holds the particle type in its low byte and, for the reaction records of MD
+// sub-stepping, the substep index above it.
 __device__ __forceinline__ void gather_coupling(const StepParams &P, int x, int y, int z, float rA, float rB,
                                                 const ParticleArrays &pa, const ParticleForces &pf,
                                                 CellIndex ci, bool with_momentum, float3 &gA, float3 &gB) {
@@ -180,9 +182,11 @@ __device__ __forceinline__ void gather_coupling(const StepParams &P, int x, int 
           const int cx = ox ? (x == 0 ? P.nx - 1 : x - 1) : x;
           if (c.x != cx) continue;
           const float4 fr = __ldg(pa.frac + q);
-          const TypeParams &T = P.types[c.w];
+          const TypeParams &T = P.types[c.w & 0xff];
           const float dx = fr.x - ox, dy = fr.y - oy, dz = fr.z - oz;
-          if (T.lam[0] != 0.f || T.lam[1] != 0.f) {
+          // entries of later particle substeps (c.w >> 8 > 0) carry momentum only: the
+          // fluid-side solvation force comes from the positions at the start of the step
+          if ((c.w >> 8) == 0 && (T.lam[0] != 0.f || T.lam[1] != 0.f)) {
             const float3 geo = fs_geometry(dx, dy, dz);
             const float a = -T.lam[0] * rA, b = -T.lam[1] * rB;
             gA.x += a * geo.x; gA.y += a * geo.y; gA.z += a * geo.z;
@@ -512,12 +516,17 @@ __device__ __forceinline__ NodeState node_state(const StepParams &P, const float
 // particle's cell; friction + noise (Eq. NEWTON), solvation (Eq. solvation_kappa) and the
 // reaction of the particle's own fluid-side solvation force (Eq. solvation_lambda).  `step`
 // is this lattice's step counter (the noise counter).
+// `self` holds the particle's own state; `list` and ci the sorted particles whose fluid-side
+// solvation force enters the coupling velocity (the same arrays, except in the later particle
+// substeps, which keep the list of the step's start).  with_fsr: compute the reaction of the
+// particle's own fluid-side solvation force (else keep the value in pf.fsr).
 __device__ __forceinline__ void couple(const StepParams &P, unsigned long long step, int p,
-                                       const ParticleArrays &pa, CellIndex ci, const float *__restrict__ rho,
-                                       const float *__restrict__ jp, const ParticleForces &pf) {
-  const int4 c = pa.cell[p];
-  const float4 fr = pa.frac[p];
-  const float4 v = pa.vel[p];
+                                       const ParticleArrays &self, const ParticleArrays &list, CellIndex ci,
+                                       const float *__restrict__ rho, const float *__restrict__ jp,
+                                       const ParticleForces &pf, bool with_fsr = true) {
+  const int4 c = self.cell[p];
+  const float4 fr = self.frac[p];
+  const float4 v = self.vel[p];
   const TypeParams &T = P.types[c.w];
   float3 up = make_float3(0.f, 0.f, 0.f), gA = up, gB = up, fsr = up;
   for (int k = 0; k < 8; ++k) {
@@ -528,7 +537,7 @@ __device__ __forceinline__ void couple(const StepParams &P, unsigned long long s
     const NodeState n = node_state(P, rho, X, Y, Z);
     float3 fA = make_float3(-P.gAB * n.rA * n.SB.x, -P.gAB * n.rA * n.SB.y, -P.gAB * n.rA * n.SB.z);
     float3 fB = make_float3(-P.gBA * n.rB * n.SA.x, -P.gBA * n.rB * n.SA.y, -P.gBA * n.rB * n.SA.z);
-    gather_coupling(P, X, Y, Z, n.rA, n.rB, pa, pf, ci, false, fA, fB);
+    gather_coupling(P, X, Y, Z, n.rA, n.rB, list, pf, ci, false, fA, fB);
     const long long s = site_index(P, X, Y, Z);
     const float rinv = 1.f / (n.rA + n.rB);
     const float w = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
@@ -537,7 +546,7 @@ __device__ __forceinline__ void couple(const StepParams &P, unsigned long long s
     up.z += w * (__ldg(jp + 2 * P.N + s) + 0.5f * (fA.z + fB.z)) * rinv;
     gA.x += w * n.SA.x; gA.y += w * n.SA.y; gA.z += w * n.SA.z;
     gB.x += w * n.SB.x; gB.y += w * n.SB.y; gB.z += w * n.SB.z;
-    if (T.lam[0] != 0.f || T.lam[1] != 0.f) {
+    if (with_fsr && (T.lam[0] != 0.f || T.lam[1] != 0.f)) {
       const float3 geo = fs_geometry(fr.x - ox, fr.y - oy, fr.z - oz);
       const float a = T.lam[0] * n.rA + T.lam[1] * n.rB;
       fsr.x += a * geo.x; fsr.y += a * geo.y; fsr.z += a * geo.z;
@@ -545,15 +554,16 @@ __device__ __forceinline__ void couple(const StepParams &P, unsigned long long s
   }
   float3 R = make_float3(0.f, 0.f, 0.f);
   if (T.noise_amp > 0.f) {
-    const float3 nn = particle_normals(P.seed, step, (unsigned)pa.pid[p]);
-    R = make_float3(T.noise_amp * nn.x, T.noise_amp * nn.y, T.noise_amp * nn.z);
+    const float3 nn = particle_normals(P.seed, step, (unsigned)self.pid[p]);
+    const float amp = T.noise_amp * P.noise_scale;
+    R = make_float3(amp * nn.x, amp * nn.y, amp * nn.z);
   }
   pf.fric[p] = make_float4(-T.gamma * (v.x - up.x) + R.x, -T.gamma * (v.y - up.y) + R.y,
                            -T.gamma * (v.z - up.z) + R.z, 0.f);
   const float kA = -T.kappa[0] / kCs2, kB = -T.kappa[1] / kCs2;
   pf.psA[p] = make_float4(kA * gA.x, kA * gA.y, kA * gA.z, 0.f);
   pf.psB[p] = make_float4(kB * gB.x, kB * gB.y, kB * gB.z, 0.f);
-  pf.fsr[p] = make_float4(fsr.x, fsr.y, fsr.z, 0.f);
+  if (with_fsr) pf.fsr[p] = make_float4(fsr.x, fsr.y, fsr.z, 0.f);
 }
 
 __device__ __forceinline__ int min_image_cells(int d, int n) {

@@ -31,6 +31,10 @@ struct lbmd_ctx {
   int *row_bsum = nullptr;  // block sums of the row scan
   int *bond_start = nullptr, *bond_other = nullptr;
   int nbonds = 0, bond_np = 0;  // bonds index particles 0..bond_np-1
+  // MD sub-stepping: momentum-return records per (substep, particle), unsorted and sorted
+  ReactionRecords rec[2]{};
+  int *rec_row_of = nullptr, *rec_perm = nullptr;
+  long long rec_cap = 0;
   unsigned *err = nullptr;
   double *diag_partial = nullptr, *diag_out = nullptr;
   int diag_blocks = 0;
@@ -92,6 +96,9 @@ int map_device_error(lbmd_ctx *c, unsigned bits) {
   if (bits & kErrNegDensity) return fail(c, LBMD_E_NEGATIVE_DENSITY, "negative fluid density");
   if (bits & kErrBond) return fail(c, LBMD_E_BOND_BROKEN, "FENE bond stretched to or beyond R0");
   if (bits & kErrParticle) return fail(c, LBMD_E_NONFINITE, "particle position out of range");
+  if (bits & kErrTooFast)
+    return fail(c, LBMD_E_PARTICLE_TOO_FAST,
+                "with md_substeps > 1 a particle moved more than one cell away within one lattice step");
   return LBMD_OK;
 }
 
@@ -101,6 +108,38 @@ int sync_and_check(lbmd_ctx *c) {
   CK(cudaMemcpy(&bits, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read error word");
   c->sticky |= bits;
   return map_device_error(c, c->sticky);
+}
+
+void free_records(lbmd_ctx *c) {
+  for (int b = 0; b < 2; ++b) {
+    dfree(c->rec[b].cell); dfree(c->rec[b].frac); dfree(c->rec[b].key);
+    dfree(c->rec[b].fric); dfree(c->rec[b].psA); dfree(c->rec[b].psB);
+  }
+  dfree(c->rec_row_of); dfree(c->rec_perm);
+  c->rec_cap = 0;
+}
+
+int ensure_records(lbmd_ctx *c, long long n) {
+  if (n <= c->rec_cap) return LBMD_OK;
+  free_records(c);
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    ReactionRecords &r = c->rec[b];
+    if ((e = dalloc(&r.cell, n)) != cudaSuccess || (e = dalloc(&r.frac, n)) != cudaSuccess ||
+        (e = dalloc(&r.key, n)) != cudaSuccess || (e = dalloc(&r.fric, n)) != cudaSuccess ||
+        (e = dalloc(&r.psA, n)) != cudaSuccess)
+      break;
+    e = dalloc(&r.psB, n);
+  }
+  if (e == cudaSuccess) e = dalloc(&c->rec_row_of, n);
+  if (e == cudaSuccess) e = dalloc(&c->rec_perm, n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_records(c);
+    return fail(c, LBMD_E_NOMEM, std::string("sub-stepping records: ") + cudaGetErrorString(e));
+  }
+  c->rec_cap = n;
+  return LBMD_OK;
 }
 
 void free_particles(lbmd_ctx *c) {
@@ -125,6 +164,62 @@ int sort_particles(lbmd_ctx *c) {
   launch_permute(P.np, c->perm, c->pa[c->pcur], c->pa[1 - c->pcur], c->slot_of_id, c->st);
   c->pcur = 1 - c->pcur;
   return launched(c, "particle sort", 8);
+}
+
+}  // namespace
+
+namespace {
+
+// MD sub-stepping of one lattice step (K = P.substeps > 1): the sorted particles S of the step's
+// start stay frozen (cell list, fluid-side solvation force); a working copy C takes K substeps
+// of coupling forces (writing one momentum-return record per particle and substep), pair
+// forces over S's rows with one more cell of reach, and updates of dt / K; the records are
+// then sorted by row for the update's node-side gather.  On return C is the particle state and
+// (pa, pf, ci) describe the records.
+int substep_particles(lbmd_ctx *c, ParticleArrays &pa, ParticleForces &pf, CellIndex &ci) {
+  const StepParams &P = c->P;
+  const int K = P.substeps, np = P.np;
+  const long long nrec = (long long)K * np;
+  if (nrec > 0x7fffffffLL) return fail(c, LBMD_E_INVALID_ARG, "md_substeps x particles exceeds 2^31");
+  int r = ensure_records(c, nrec);
+  if (r) return r;
+  const ParticleArrays &S = c->pa[c->pcur];
+  const ParticleArrays &C = c->pa[1 - c->pcur];
+  CK(cudaMemcpyAsync(C.cell, S.cell, sizeof(int4) * np, cudaMemcpyDeviceToDevice, c->st), "copy particles");
+  CK(cudaMemcpyAsync(C.frac, S.frac, sizeof(float4) * np, cudaMemcpyDeviceToDevice, c->st), "copy particles");
+  CK(cudaMemcpyAsync(C.vel, S.vel, sizeof(float4) * np, cudaMemcpyDeviceToDevice, c->st), "copy particles");
+  CK(cudaMemcpyAsync(C.pid, S.pid, sizeof(int) * np, cudaMemcpyDeviceToDevice, c->st), "copy particles");
+  const CellIndex rows{c->row_start};
+  for (int sub = 0; sub < K; ++sub) {
+    StepParams Q = P;
+    Q.step = P.step * (unsigned long long)K + (unsigned long long)sub;
+    Q.dt = P.dt / (float)K;
+    launch_couple_sub(Q, C, S, rows, c->rho, c->jp, c->pf, sub, c->rec[0], c->st);
+    StepParams Qp = Q;
+    Qp.reach = P.reach + 1;  // particles may have left their row by one cell
+    launch_pairs(Qp, C, rows, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf, c->err,
+                 c->st);
+    launch_integrate_sub(Q, C, S, c->pf, c->err, c->st);
+    if ((r = launched(c, "particle substep", 3))) return r;
+  }
+  // sort the records by (row, x cell, substep * np + id): the same counting sort as particles
+  StepParams R = P;
+  R.np = (int)nrec;
+  const ParticleArrays view{c->rec[0].cell, c->rec[0].frac, nullptr, c->rec[0].key};
+  CK(cudaMemsetAsync(c->row_count, 0, sizeof(int) * (P.nrows + 1), c->st), "memset rows");
+  launch_bin(R, view, c->rec_row_of, c->row_count, c->err, c->st);
+  launch_scan_rows(P.nrows, c->row_count, c->row_start, c->row_cursor, c->row_bsum, c->st);
+  launch_scatter(R.np, c->rec_row_of, c->row_cursor, c->rec_perm, c->st);
+  launch_row_sort(R, c->row_start, view, c->rec_perm, c->st);
+  launch_rec_permute(R.np, c->rec_perm, c->rec[0], c->rec[1], c->st);
+  if ((r = launched(c, "record sort", 7))) return r;
+  pa = ParticleArrays{c->rec[1].cell, c->rec[1].frac, nullptr, c->rec[1].key};
+  pf = c->pf;
+  pf.fric = c->rec[1].fric;
+  pf.psA = c->rec[1].psA;
+  pf.psB = c->rec[1].psB;
+  ci = CellIndex{c->row_start};
+  return LBMD_OK;
 }
 
 }  // namespace
@@ -184,6 +279,7 @@ void lbmd_destroy(lbmd_ctx *c) {
   dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho); dfree(c->jp); dfree(c->err); dfree(c->rest);
   dfree(c->diag_partial); dfree(c->diag_out);
   free_particles(c);
+  free_records(c);
   dfree(c->row_count); dfree(c->row_start); dfree(c->row_cursor); dfree(c->row_bsum);
   dfree(c->bond_start); dfree(c->bond_other);
   for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
@@ -385,7 +481,13 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
     // densities (and j' for the particle coupling) of this step's populations
     launch_moments(P, fin, c->rest, c->rho, P.np > 0 ? c->jp : nullptr, c->st);
     if ((r = launched(c, "moments"))) return r;
-    if (P.np > 0) {
+    const bool sub = P.np > 0 && P.substeps > 1;
+    ParticleArrays gpa = c->pa[c->pcur];  // what the update gathers the momentum return from
+    ParticleForces gpf = c->pf;
+    CellIndex gci = ci;
+    if (sub) {
+      if ((r = substep_particles(c, gpa, gpf, gci))) return r;
+    } else if (P.np > 0) {
       launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
       launch_pairs(P, c->pa[c->pcur], ci, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf,
                    c->err, c->st);
@@ -401,13 +503,15 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
       }
       CK(cudaEventRecord(c->ev[c->ev_used], c->st), "event");
     }
-    launch_collide(P, fin, fout, c->rest, c->rho, c->pa[c->pcur], c->pf, ci, c->err, c->st);
+    launch_collide(P, fin, fout, c->rest, c->rho, gpa, gpf, gci, c->err, c->st);
     if ((r = launched(c, "collide"))) return r;
     if (c->prof) {
       CK(cudaEventRecord(c->ev[c->ev_used + 1], c->st), "event");
       c->ev_used += 2;
     }
-    if (P.np > 0) {
+    if (sub) {
+      c->pcur = 1 - c->pcur;  // the working copy that took the substeps is the particle state
+    } else if (P.np > 0) {
       launch_integrate(P, c->pa[c->pcur], c->pf, c->err, c->st);
       if ((r = launched(c, "integrate"))) return r;
     }

@@ -23,6 +23,7 @@ int check_params(const lbmd_params *prm, std::string &why) {
     return why = "unknown storage", LBMD_E_INVALID_ARG;
   if (!(prm->rho0_A >= 0.0) || !(prm->rho0_B >= 0.0) || !std::isfinite(prm->rho0_A) || !std::isfinite(prm->rho0_B))
     return why = "rho0_A, rho0_B must be finite and >= 0", LBMD_E_INVALID_ARG;
+  if (prm->md_substeps < 1 || prm->md_substeps > 256) return why = "md_substeps must be in [1, 256]", LBMD_E_INVALID_ARG;
   if (prm->collision != LBMD_COLLISION_BGK && prm->collision != LBMD_COLLISION_MRT)
     return why = "unknown collision", LBMD_E_INVALID_ARG;
   if (prm->collision == LBMD_COLLISION_MRT)
@@ -53,6 +54,8 @@ void fill_step_params(const lbmd_params *prm, StepParams &P) {
   P.bond_kind = LBMD_BOND_FENE;
   // fluctuating MRT factors (Eq. MODES): eigenvalue per mode, forcing moments of the paper's
   // forcing term, noise amplitudes from the equilibrium mode variances (kT/c_s^2) rho_z b_k
+  P.substeps = prm->md_substeps;
+  P.noise_scale = (float)std::sqrt((double)prm->md_substeps);
   P.collision = prm->collision;
   const bool mrt = prm->collision == LBMD_COLLISION_MRT;
   P.fluct = mrt && prm->kT > 0.0;

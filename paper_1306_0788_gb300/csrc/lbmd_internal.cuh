@@ -31,6 +31,7 @@ constexpr unsigned kErrNegDensity = 1u << 0;
 constexpr unsigned kErrNonFinite = 1u << 1;
 constexpr unsigned kErrBond = 1u << 2;
 constexpr unsigned kErrParticle = 1u << 3;
+constexpr unsigned kErrTooFast = 1u << 4;  // a particle left its cell's neighbourhood within one sub-stepped step
 
 struct TypeParams {
   float kappa[2];   // Eq. (solvation_kappa)
@@ -68,6 +69,10 @@ struct StepParams {
   // the amplitude over sqrt(rho_z) (over sqrt(rho_A rho_B / rho) for the momenta, k = 1..3)
   int collision;
   bool fluct;            // kT > 0: draw the mode noise
+  // MD sub-stepping: K particle substeps per lattice step; the particle noise amplitude of a
+  // substep is that of dt times sqrt(K) (noise_scale, 1 for K = 1)
+  int substeps;
+  float noise_scale;
   float relax[kQ], force[kQ], noise[kQ];
   unsigned long long seed, step;
   TypeParams types[LBMD_MAX_TYPES];
@@ -90,6 +95,16 @@ struct ParticleForces {
   float4 *fsr;    // reaction of the fluid-side solvation force (minus what the particle exerts)
   float4 *pair;   // WCA + screened Coulomb + bonds
   float4 *total;  // sum, written by the integrator
+};
+
+// Momentum-return records of MD sub-stepping, one per particle and substep: position (cell with
+// type | substep << 8 in w, fraction), a unique sort key (substep * np + id), and the friction
+// and solvation forces divided by the number of substeps.
+struct ReactionRecords {
+  int4 *cell;
+  float4 *frac;
+  int *key;
+  float4 *fric, *psA, *psB;
 };
 
 struct CellIndex {
@@ -214,5 +229,13 @@ void launch_integrate(const StepParams &P, const ParticleArrays &pa, const Parti
                       unsigned *err, cudaStream_t st);
 void launch_particle_momentum(const StepParams &P, const ParticleArrays &pa, double *partial, int nblocks,
                               cudaStream_t st);
+// MD sub-stepping (lb_particles.cu)
+void launch_couple_sub(const StepParams &P, const ParticleArrays &C, const ParticleArrays &S, CellIndex ci,
+                       const float *rho, const float *jp, const ParticleForces &pf, int sub,
+                       const ReactionRecords &rec, cudaStream_t st);
+void launch_integrate_sub(const StepParams &P, const ParticleArrays &C, const ParticleArrays &S,
+                          const ParticleForces &pf, unsigned *err, cudaStream_t st);
+void launch_rec_permute(int n, const int *perm, const ReactionRecords &src, const ReactionRecords &dst,
+                        cudaStream_t st);
 
 }  // namespace lbmd

@@ -26,6 +26,7 @@ LBMD_E_TIMEOUT = -6
 LBMD_E_UNIMPLEMENTED = -7
 LBMD_E_BOND_BROKEN = -8
 LBMD_E_STATE = -9
+LBMD_E_PARTICLE_TOO_FAST = -10
 
 LBMD_STORAGE_FP32 = 0
 LBMD_STORAGE_FP16_SHIFTED = 1
@@ -71,7 +72,7 @@ class lbmd_params(ctypes.Structure):
                 ("kT", ctypes.c_double), ("dt", ctypes.c_double), ("storage", ctypes.c_int),
                 ("rho0_A", ctypes.c_double), ("rho0_B", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("collision", ctypes.c_int), ("lambda_bulk", ctypes.c_double), ("lambda_mom", ctypes.c_double),
-                ("lambda_ghost", ctypes.c_double)]
+                ("lambda_ghost", ctypes.c_double), ("md_substeps", ctypes.c_int)]
 
 
 class lbmd_ptype(ctypes.Structure):
@@ -426,11 +427,12 @@ def lbmd_batch_last_error(b) -> str:
 
 def params(dims, tau_r=1.0, g_AB=0.0, g_BA=None, kT=0.0, seed=0, storage=LBMD_STORAGE_FP32,
            rho0=(0.0, 0.0), collision=LBMD_COLLISION_BGK, lambda_bulk=None, lambda_mom=None,
-           lambda_ghost=None) -> lbmd_params:
+           lambda_ghost=None, md_substeps=1) -> lbmd_params:
     """Convenience constructor of lbmd_params (dims = (nx, ny, nz)); MRT eigenvalues left as
     None take the shear value -1/tau_r."""
     nx, ny, nz = dims
     ls = -1.0 / tau_r
     pick = lambda v: ls if v is None else v  # noqa: E731
     return lbmd_params(nx, ny, nz, tau_r, g_AB, g_AB if g_BA is None else g_BA, kT, 1.0, storage,
-                       rho0[0], rho0[1], seed, collision, pick(lambda_bulk), pick(lambda_mom), pick(lambda_ghost))
+                       rho0[0], rho0[1], seed, collision, pick(lambda_bulk), pick(lambda_mom), pick(lambda_ghost),
+                       md_substeps)

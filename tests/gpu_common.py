@@ -36,6 +36,7 @@ class Case:
     lam_bulk: float = None
     lam_mom: float = None
     lam_ghost: float = None
+    md_substeps: int = 1
 
     def fields32(self):
         return (self.rhoA.astype(np.float32), self.rhoB.astype(np.float32),
@@ -71,7 +72,7 @@ def oracle_system(c: Case) -> oracle.System:
                          dh_kappa=c.dh[1], dh_rc=c.dh[2], type=np.asarray(c.ptype, dtype=np.int32), q=q,
                          bonds=np.asarray(c.bonds, dtype=np.int32).reshape(-1, 2), bond_kind=c.bond_kind,
                          bond_k=c.bond_k, bond_r=c.bond_r, collision=c.collision, lam_bulk=c.lam_bulk,
-                         lam_mom=c.lam_mom, lam_ghost=c.lam_ghost)
+                         lam_mom=c.lam_mom, lam_ghost=c.lam_ghost, md_substeps=c.md_substeps)
 
 
 def run_oracle(c: Case, nsteps: int, trace_last: bool = False):
@@ -91,7 +92,8 @@ def run_oracle(c: Case, nsteps: int, trace_last: bool = False):
 def make_gpu(c: Case, stream=None):
     from paper_1306_0788_gb300 import lbmd as L
     ctx, _ = L.lbmd_create(L.params(c.dims, tau_r=c.tau_r, g_AB=c.g, kT=c.kT, seed=c.seed, collision=c.collision,
-                                    lambda_bulk=c.lam_bulk, lambda_mom=c.lam_mom, lambda_ghost=c.lam_ghost), stream)
+                                    lambda_bulk=c.lam_bulk, lambda_mom=c.lam_mom, lambda_ghost=c.lam_ghost,
+                                    md_substeps=c.md_substeps), stream)
     types = [L.lbmd_ptype(*t) for t in c.types]
     pairs = [L.lbmd_pair(i, j, e, s) for (i, j), (e, s) in c.wca.items()]
     L.lbmd_set_types(ctx, types, pairs)

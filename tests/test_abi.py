@@ -76,3 +76,12 @@ def test_create_rejects_invalid_collision_without_device(field, value):
     with pytest.raises(lbmd.LbmdError) as e:
         lbmd.lbmd_create(p)
     assert e.value.code == lbmd.LBMD_E_INVALID_ARG
+
+
+@pytest.mark.parametrize("k", [0, 257])
+def test_create_rejects_invalid_substeps_without_device(k):
+    from paper_1306_0788_gb300 import lbmd
+    p = lbmd.params((4, 4, 4), md_substeps=k)
+    with pytest.raises(lbmd.LbmdError) as e:
+        lbmd.lbmd_create(p)
+    assert e.value.code == lbmd.LBMD_E_INVALID_ARG
