@@ -270,3 +270,17 @@ def test_full_size_256_tiled_against_16_oracle():
     xg = xg.reshape(R ** 3, n0, 3) - shifts[:, None, :]
     for t in range(0, R ** 3, 997):
         assert position_error(xg[t], xo, x0, small) <= POS_TOL
+
+
+def test_single_solvation_force_variant():
+    """kappa = 0, lambda != 0 (the per-node momentum-conserving scheme with one solvation
+    force): populations and positions against the oracle after 30 steps in an interface."""
+    dims = (8, 8, 24)
+    rA, rB, _ = inputs.slab_and_droplets(dims, 1.9, 0.1, n_drops=0, width=3.0, seed=1)
+    x = inputs.random_particles(12, dims, 2.0, seed=4)
+    c = Case(dims=dims, g=1.68, rhoA=rA, rhoB=rB, x=x, v=np.zeros((12, 3)), ptype=np.zeros(12, dtype=np.int32),
+             types=[(0.0, 0.0, 0.02, -0.01, 0.2, 5.0)])
+    fg, xg, _, _ = run_gpu(c, 30)
+    fo, xo, _, _ = run_oracle(c, 30)
+    assert pop_error(fg, fo) <= 3e-5
+    assert position_error(xg, xo, c.x, c.dims) <= POS_TOL
