@@ -59,6 +59,11 @@ WORKLOADS = {
                                       "2e4 solvation-coupled point particles (kappa_A=-0.001, kappa_B=-0.002, gamma=1, "
                                       "m=200, kT=0.01), WCA, mean density 78.4 per component, g=0.0214"),
     "noise_32": (32, 64, "32^3 two-component LB FP32, rho=1+-0.01, g=1.4, 64 friction-coupled particles, WCA"),
+    "chains_512": (512, 50000, "512^3 two-component LB FP32 demixing from 50/50 noise (mean density 78.4 per "
+                                "component, g rho 1.4), 1000 bead-spring chains of 50 beads (FENE k=30 kT R0=1.5 plus WCA "
+                                "eps=kT, charges +1 / -1 by chain, screened Coulomb lB=1 kappa_D=1/4 rc=3), friction + "
+                                "solvation "
+                                "(kappa_A = -kappa_B = -5e-4 kT, lambda_A = 0.01 kT), m=100, kT=0.01"),
     "replicas_24": (0, 0, "24 independent replicas of the serving distribution (edge 16..128, 0..5000 particles, "
                           "g rho 1.2..2.1 from a coexistence slab, gamma 0.1..2) advanced together in shared "
                           "graph-captured launches, autotuned"),
@@ -161,13 +166,41 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
     return world * units_per_rank / seconds_max
 
 
+# Chains of the 512^3 workload, with the interactions of the paper's polyelectrolyte example
+# (Sec. 4.4) stated in units of kT: WCA with sigma = 1 and eps = kT between every pair, screened
+# Coulomb with Bjerrum length 1 (prefactor lB kT), screening length 4 and a 3-cell cut-off,
+# Kremer-Grest FENE bonds (k = 30 kT, R0 = 1.5) for the chain connectivity, solvation couplings
+# kappa_A = -kappa_B = -5e-4 kT and lambda_A = 0.01 kT.  Beads of mass 100 (gamma dt / m = 0.01,
+# Sec. 3); their contacts at a few kT stay far inside the explicit integrator's stability range
+# at dt = 1, so one particle update per lattice step (--md-substeps raises it).
+CHAIN_LEN, CHAIN_MASS, CHAIN_KT = 50, 100.0, 0.01
+G_CHAINS = 1.4 / RHO_SCALE
+
+
+def chain_model(kT: float = CHAIN_KT):
+    """Particle type (kappa_A, kappa_B, lambda_A, lambda_B, gamma, mass), WCA (eps, sigma),
+    screened Coulomb (lB kT, kappa_D, rc) and FENE (k, R0) of the chains workload."""
+    return dict(type=(-5e-4 * kT, 5e-4 * kT, 0.01 * kT, 0.0, 1.0, CHAIN_MASS), wca=(kT, 1.0),
+                dh=(1.0 * kT, 0.25, 3.0), fene=(30.0 * kT, 1.5))
+
+
 def build_workload(name: str, seed: int, edge_override: int = 0):
+    """dims, rho_A, rho_B, positions, types, kT, g and a dict of extras (bonds, charges,
+    screened Coulomb, substeps) of a bench workload."""
     from paper_1306_0788_gb300 import inputs
     edge, npart, _ = WORKLOADS[name]
     if edge_override:
         npart = max(1, int(round(npart * (edge_override / edge) ** 3)))
         edge = edge_override
     dims = (edge, edge, edge)
+    extra = {}
+    if name == "chains_512":
+        rA, rB = inputs.uniform_noise(dims, RHO_SCALE, 0.01 * RHO_SCALE, seed=seed)
+        nch = max(2, npart // CHAIN_LEN)
+        x, bonds, q = inputs.bead_spring_chains(nch, CHAIN_LEN, dims, bond=0.97, seed=seed + 1, min_dist=1.0)
+        cm = chain_model()
+        extra = dict(bonds=bonds, q=q, dh=cm["dh"], fene=cm["fene"], wca=cm["wca"])
+        return dims, rA.astype(np.float32), rB.astype(np.float32), x, [cm["type"]], CHAIN_KT, G_CHAINS, extra
     if name == "slab_droplets_256":
         rA, rB, drops = inputs.slab_and_droplets(dims, RHO_HI, RHO_LO, n_drops=8, r_min=edge / 32,
                                                  r_max=edge / 8, width=4.0, seed=seed)
@@ -180,7 +213,7 @@ def build_workload(name: str, seed: int, edge_override: int = 0):
         types = [(0.0, 0.0, 0.0, 0.0, 1.0, 1.0)]
         kT, g = 1e-4, G_NOISE
     x = inputs.random_particles(npart, dims, 2 ** (1 / 6), seed=seed + 1)
-    return dims, rA.astype(np.float32), rB.astype(np.float32), x, types, kT, g
+    return dims, rA.astype(np.float32), rB.astype(np.float32), x, types, kT, g, extra
 
 
 def run_batch(args):
@@ -240,17 +273,22 @@ def run_cuda(args):
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
 
-    dims, rA, rB, x, types, kT, g_ab = build_workload(args.workload, seed=1234 + rank, edge_override=args.edge)
+    dims, rA, rB, x, types, kT, g_ab, extra = build_workload(args.workload, seed=1234 + rank, edge_override=args.edge)
     npart = len(x)
     N = dims[0] * dims[1] * dims[2]
     rho0 = (float(rA.mean()), float(rB.mean()))  # shift reference of the 16-bit storages
     mrt = args.collision == "mrt"
     prm = L.params(dims, tau_r=1.0, g_AB=g_ab, kT=kT, seed=42 + rank, storage=STORAGES[args.storage][0], rho0=rho0,
-                   collision=L.LBMD_COLLISION_MRT if mrt else L.LBMD_COLLISION_BGK)
+                   collision=L.LBMD_COLLISION_MRT if mrt else L.LBMD_COLLISION_BGK,
+                   md_substeps=args.md_substeps)
     ctx, _ = L.lbmd_create(prm, stream)
-    L.lbmd_set_types(ctx, [L.lbmd_ptype(*t) for t in types], [L.lbmd_pair(0, 0, 1.0, 1.0)])
+    L.lbmd_set_types(ctx, [L.lbmd_ptype(*t) for t in types], [L.lbmd_pair(0, 0, *extra.get("wca", (1.0, 1.0)))])
+    if "dh" in extra:
+        L.lbmd_set_debye_hueckel(ctx, *extra["dh"])
     L.lbmd_init_fluid(ctx, rA, rB)
-    L.lbmd_set_particles(ctx, x, np.zeros_like(x), np.zeros(npart, dtype=np.int32))
+    L.lbmd_set_particles(ctx, x, np.zeros_like(x), np.zeros(npart, dtype=np.int32), extra.get("q"))
+    if "bonds" in extra:
+        L.lbmd_set_bonds(ctx, extra["bonds"], L.LBMD_BOND_FENE, *extra["fene"])
 
     def barrier():
         torch.cuda.synchronize()
@@ -302,13 +340,14 @@ def run_cuda(args):
         barrier()
         t0 = time.perf_counter()
         rc = lib.lbmd_init_fluid(ctx, p(hA), p(hB), None)
-        rc |= lib.lbmd_set_particles(ctx, npart, p(hx), p(hv), p(ht), None)
+        hq = pin(np.asarray(extra["q"], dtype=np.float64)) if "q" in extra else None
+        rc |= lib.lbmd_set_particles(ctx, npart, p(hx), p(hv), p(ht), None if hq is None else p(hq))
         rc |= lib.lbmd_step(ctx, args.steps)
         rc |= lib.lbmd_get_fields(ctx, p(outA), p(outB), p(outU))
         rc |= lib.lbmd_get_particles(ctx, p(ox), p(ov), p(of))
         barrier()
         t_e2e = time.perf_counter() - t0
-        h2d = (2 * N * 4 + npart * (6 * 8 + 4)) / args.steps
+        h2d = (2 * N * 4 + npart * (6 * 8 + 4 + (8 if "q" in extra else 0))) / args.steps
         d2h = (5 * N * 4 + npart * 9 * 8) / args.steps
         e2e = {"value": round(whole_job_rate(N * args.steps, world, max_over_ranks(t_e2e, dist, "cuda")) / 1e6, 3),
                "unit": UNIT,
@@ -343,6 +382,7 @@ def run_cuda(args):
             "dtype": "f32" if args.storage == "fp32" else "f32 arithmetic, %s shifted population storage" % args.storage,
             "data": "synthetic",
             "config": {"workload": args.workload + ("" if not args.edge else "@%d" % args.edge),
+                       "md_substeps": args.md_substeps, "bonds": int(len(extra.get("bonds", []))),
                        "description": WORKLOADS[args.workload][2],
                        "lattice": list(dims), "particles": npart, "tau_r": 1.0, "g_AB": g_ab, "kT": kT,
                        "storage": args.storage,
@@ -364,7 +404,7 @@ def run_cuda(args):
         if world == 1 and args.serving > 0:
             out["serving"] = run_serving(args.serving)
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
+            out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds, md_substeps=args.md_substeps)
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()
@@ -404,35 +444,49 @@ def run_serving(n_requests: int, load: float = 0.8, chunk: int = 25, seed: int =
     return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in info.items()}
 
 
-def oracle_sample(workload: str, edge: int, seed: int):
+def oracle_sample(workload: str, edge: int, seed: int, md_substeps: int = 1):
     """A bounded sample of the workload for the CPU oracle: an edge^3 box with the same
-    particle density and the same fluid recipe."""
+    particle density (at least one whole chain for the chains workload) and the same fluid
+    recipe and interactions."""
     import oracle
     from paper_1306_0788_gb300 import inputs
     full_edge, npart_full, _ = WORKLOADS[workload]
     dims = (edge, edge, edge)
     n = max(1, int(round(npart_full * (edge / full_edge) ** 3)))
-    if workload == "slab_droplets_256":
+    extra = {}
+    if workload == "chains_512":
+        rA, rB = inputs.uniform_noise(dims, RHO_SCALE, 0.01 * RHO_SCALE, seed=seed)
+        cm = chain_model()
+        nch = max(1, int(round(n / CHAIN_LEN)))
+        x, bonds, q = inputs.bead_spring_chains(nch, CHAIN_LEN, dims, bond=0.97, seed=seed + 1, min_dist=1.0)
+        n = len(x)
+        ka, kb, la, lb, _, m = cm["type"]
+        kap, lam, kT, g, eps = np.array([[ka, kb]]), np.array([[la, lb]]), CHAIN_KT, G_CHAINS, cm["wca"][0]
+        extra = dict(q=np.asarray(q, dtype=np.float64), bonds=np.asarray(bonds, dtype=np.int32), bond_k=cm["fene"][0],
+                     bond_r=cm["fene"][1], dh_lB=cm["dh"][0], dh_kappa=cm["dh"][1], dh_rc=cm["dh"][2])
+    elif workload == "slab_droplets_256":
         rA, rB, _ = inputs.slab_and_droplets(dims, RHO_HI, RHO_LO, n_drops=1, r_min=edge / 8, r_max=edge / 8,
                                              width=4.0, seed=seed)
-        kap, kT, g, m = np.array([[-0.001, -0.002]]), 0.01, G_COUPLING, PARTICLE_MASS
+        kap, lam, kT, g, m, eps = np.array([[-0.001, -0.002]]), np.zeros((1, 2)), 0.01, G_COUPLING, PARTICLE_MASS, 1.0
     else:
         rA, rB = inputs.uniform_noise(dims, 1.0, 0.01, seed=seed)
-        kap, kT, g, m = np.zeros((1, 2)), 1e-4, G_NOISE, 1.0
-    x = inputs.random_particles(n, dims, 2 ** (1 / 6), seed=seed + 1)
+        kap, lam, kT, g, m, eps = np.zeros((1, 2)), np.zeros((1, 2)), 1e-4, G_NOISE, 1.0, 1.0
+    if workload != "chains_512":
+        x = inputs.random_particles(n, dims, 2 ** (1 / 6), seed=seed + 1)
+        extra = dict(q=np.zeros(n))
     s = oracle.System(dims=dims, tau_r=1.0, g_AB=g, g_BA=g, kT=kT, seed=42,
-                      kappa=kap, lam=np.zeros((1, 2)), gamma=np.ones(1), mass=np.array([m]),
-                      wca_eps=np.ones((1, 1)), wca_sig=np.ones((1, 1)), type=np.zeros(n, dtype=np.int32),
-                      q=np.zeros(n))
+                      kappa=kap, lam=lam, gamma=np.ones(1), mass=np.array([m]),
+                      wca_eps=np.full((1, 1), eps), wca_sig=np.ones((1, 1)), type=np.zeros(n, dtype=np.int32),
+                      md_substeps=md_substeps, **extra)
     f = oracle.init_equilibrium(rA.astype(np.float32).astype(np.float64), rB.astype(np.float32).astype(np.float64))
     return s, f, x.copy(), np.zeros((n, 3)), n
 
 
-def cpu_baseline(workload: str, budget_s: float = 15.0, edge: int = 32):
+def cpu_baseline(workload: str, budget_s: float = 15.0, edge: int = 32, md_substeps: int = 1):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample (edge^3 with the
     workload's particle density), timed for about budget_s seconds."""
     import oracle
-    s, f, x, v, n = oracle_sample(workload, edge, seed=7)
+    s, f, x, v, n = oracle_sample(workload, edge, seed=7, md_substeps=md_substeps)
     oracle.step(s, f, x, v, 0)  # load and warm
     steps = 0
     t0 = time.perf_counter()
@@ -453,7 +507,7 @@ def run_reference(args):
     # size the sample so that warm-up + K steps take about two minutes at ~0.3 MLUPS
     sites = max(8 ** 3, min(32 ** 3, int(0.3e6 * 120.0 / max(args.steps + args.warmup, 1))))
     edge = max(8, int(round(sites ** (1 / 3))))
-    s, f, x, v, n = oracle_sample(args.workload, edge, seed=7)
+    s, f, x, v, n = oracle_sample(args.workload, edge, seed=7, md_substeps=args.md_substeps)
     for k in range(args.warmup):
         oracle.step(s, f, x, v, k)
     t0 = time.perf_counter()
@@ -484,6 +538,7 @@ def main():
                     help="population storage: FP32, or FP16 / BF16 shifted by w_i rho0 (FP32 arithmetic)")
     ap.add_argument("--collision", choices=["bgk", "mrt"], default="bgk",
                     help="BGK, or the fluctuating MRT collision with fluid noise at the workload's kT")
+    ap.add_argument("--md-substeps", type=int, default=1, help="particle substeps per lattice step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -77,8 +77,9 @@ __global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const T *__res
 }
 
 // The lattice update of one step at every site (site::collide; with kMRT the fluctuating MRT
-// collision, whose mode transforms take the register budget of two blocks per SM).
-template <class T, bool kParticles, bool kMRT>
+// collision, whose mode transforms take the register budget of two blocks per SM; with
+// kBisect the gather over the sub-stepping reaction records).
+template <class T, bool kParticles, bool kMRT, bool kBisect = false>
 __global__ void __launch_bounds__(kBlock, kMRT ? 2 : 3) k_collide(StepParams P, const T *__restrict__ fin,
                                                                   T *__restrict__ fout, const float *__restrict__ rho,
                                                                   ParticleArrays pa, ParticleForces pf, CellIndex ci,
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(kBlock, kMRT ? 2 : 3) k_collide(StepParams P, 
                                                                   float *__restrict__ rest_out) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.N) return;
-  collide<T, kParticles, kMRT>(P, s, P.step, fin, fout, rho, pa, pf, ci, err, rest_in, rest_out);
+  collide<T, kParticles, kMRT, kBisect>(P, s, P.step, fin, fout, rho, pa, pf, ci, err, rest_in, rest_out);
 }
 
 // rho_A, rho_B and u = (j' + g^SC/2)/rho at the current step (for readback).
@@ -224,7 +225,12 @@ void launch_collide(const StepParams &P, const void *fin, void *fout, float *res
     const T *a = static_cast<const T *>(fin);
     T *b = static_cast<T *>(fout);
     const bool mrt = P.collision == LBMD_COLLISION_MRT;
-    if (P.np > 0 && mrt)
+    const bool records = P.np > 0 && P.substeps > 1;
+    if (records && mrt)
+      k_collide<T, true, true, true><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
+    else if (records)
+      k_collide<T, true, false, true><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
+    else if (P.np > 0 && mrt)
       k_collide<T, true, true><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
     else if (P.np > 0)
       k_collide<T, true, false><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);

@@ -161,12 +161,36 @@ __device__ __forceinline__ void moments(const StepParams &P, long long s, const 
 // node (x, y, z) from the particles of the 8 unit cells having that node as a corner.
 // ci.row_start is indexed by this lattice's row (z * ny + y); pa, pf by the sorted slot.  The
 // cell's w holds the particle type in its low byte and, for the reaction records of MD
-// sub-stepping, the substep index above it.
+// sub-stepping, the substep index above it.  A row is sorted by x cell; with kBisect the
+// node's two cells are found in it by bisection (the K records per particle of sub-stepping
+// make rows of hundreds of entries), otherwise the row is scanned once (short rows: the
+// plain scan keeps the update's register budget).
+template <bool kBisect = false>
 __device__ __forceinline__ void gather_coupling(const StepParams &P, int x, int y, int z, float rA, float rB,
                                                 const ParticleArrays &pa, const ParticleForces &pf,
                                                 CellIndex ci, bool with_momentum, float3 &gA, float3 &gB) {
   const float rinv = 1.f / (rA + rB);
   const float sA = rA * rinv, sB = rB * rinv;
+  // one particle (or reaction record) q in the cell whose corner offset from it is (ox, oy, oz)
+  auto add = [&](int q, int ox, int oy, int oz, int w) {
+    const float4 fr = __ldg(pa.frac + q);
+    const TypeParams &T = P.types[w & 0xff];
+    const float dx = fr.x - ox, dy = fr.y - oy, dz = fr.z - oz;
+    // entries of later particle substeps (w >> 8 > 0) carry momentum only: the fluid-side
+    // solvation force comes from the positions at the start of the step
+    if ((w >> 8) == 0 && (T.lam[0] != 0.f || T.lam[1] != 0.f)) {
+      const float3 geo = fs_geometry(dx, dy, dz);
+      const float a = -T.lam[0] * rA, b = -T.lam[1] * rB;
+      gA.x += a * geo.x; gA.y += a * geo.y; gA.z += a * geo.z;
+      gB.x += b * geo.x; gB.y += b * geo.y; gB.z += b * geo.z;
+    }
+    if (with_momentum) {
+      const float wt = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
+      const float4 ff = __ldg(pf.fric + q), pA = __ldg(pf.psA + q), pB = __ldg(pf.psB + q);
+      gA.x += wt * (-sA * ff.x - pA.x); gA.y += wt * (-sA * ff.y - pA.y); gA.z += wt * (-sA * ff.z - pA.z);
+      gB.x += wt * (-sB * ff.x - pB.x); gB.y += wt * (-sB * ff.y - pB.y); gB.z += wt * (-sB * ff.z - pB.z);
+    }
+  };
 #pragma unroll
   for (int oz = 0; oz < 2; ++oz) {
     const int cz = oz ? (z == 0 ? P.nz - 1 : z - 1) : z;
@@ -175,28 +199,31 @@ __device__ __forceinline__ void gather_coupling(const StepParams &P, int x, int 
       const int cy = oy ? (y == 0 ? P.ny - 1 : y - 1) : y;
       const int row = cz * P.ny + cy;
       const int q0 = __ldg(ci.row_start + row), q1 = __ldg(ci.row_start + row + 1);
-      for (int q = q0; q < q1; ++q) {
-        const int4 c = __ldg(pa.cell + q);
-#pragma unroll
+      if (kBisect) {
+        if (q0 == q1) continue;
         for (int ox = 0; ox < 2; ++ox) {
           const int cx = ox ? (x == 0 ? P.nx - 1 : x - 1) : x;
-          if (c.x != cx) continue;
-          const float4 fr = __ldg(pa.frac + q);
-          const TypeParams &T = P.types[c.w & 0xff];
-          const float dx = fr.x - ox, dy = fr.y - oy, dz = fr.z - oz;
-          // entries of later particle substeps (c.w >> 8 > 0) carry momentum only: the
-          // fluid-side solvation force comes from the positions at the start of the step
-          if ((c.w >> 8) == 0 && (T.lam[0] != 0.f || T.lam[1] != 0.f)) {
-            const float3 geo = fs_geometry(dx, dy, dz);
-            const float a = -T.lam[0] * rA, b = -T.lam[1] * rB;
-            gA.x += a * geo.x; gA.y += a * geo.y; gA.z += a * geo.z;
-            gB.x += b * geo.x; gB.y += b * geo.y; gB.z += b * geo.z;
+          int lo = q0, hi = q1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(&pa.cell[mid].x) < cx)
+              lo = mid + 1;
+            else
+              hi = mid;
           }
-          if (with_momentum) {
-            const float w = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
-            const float4 ff = __ldg(pf.fric + q), pA = __ldg(pf.psA + q), pB = __ldg(pf.psB + q);
-            gA.x += w * (-sA * ff.x - pA.x); gA.y += w * (-sA * ff.y - pA.y); gA.z += w * (-sA * ff.z - pA.z);
-            gB.x += w * (-sB * ff.x - pB.x); gB.y += w * (-sB * ff.y - pB.y); gB.z += w * (-sB * ff.z - pB.z);
+          for (int q = lo; q < q1; ++q) {
+            const int4 c = __ldg(pa.cell + q);
+            if (c.x != cx) break;
+            add(q, ox, oy, oz, c.w);
+          }
+        }
+      } else {
+        for (int q = q0; q < q1; ++q) {
+          const int4 c = __ldg(pa.cell + q);
+#pragma unroll
+          for (int ox = 0; ox < 2; ++ox) {
+            const int cx = ox ? (x == 0 ? P.nx - 1 : x - 1) : x;
+            if (c.x == cx) add(q, ox, oy, oz, c.w);
           }
         }
       }
@@ -378,7 +405,7 @@ __device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long lo
 // collision with forcing for both components (BGK, or with kMRT the fluctuating MRT of Eq. MODES,
 // `step` being the noise counter), write.  With 16-bit storage rest_in / rest_out are the FP32
 // rest populations (rest_out may be NULL: then f_0 is stored with the others).
-template <class T, bool kParticles, bool kMRT = false>
+template <class T, bool kParticles, bool kMRT = false, bool kBisect = false>
 __device__ __forceinline__ void collide(const StepParams &P, long long s, unsigned long long step,
                                         const T *__restrict__ fin,
                                         T *__restrict__ fout, const float *__restrict__ rho,
@@ -422,7 +449,7 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
   }
   float3 gA = make_float3(-P.gAB * rA * SBx, -P.gAB * rA * SBy, -P.gAB * rA * SBz);
   float3 gB = make_float3(-P.gBA * rB * SAx, -P.gBA * rB * SAy, -P.gBA * rB * SAz);
-  if (kParticles) gather_coupling(P, c.x, c.y, c.z, rA, rB, pa, pf, ci, true, gA, gB);
+  if (kParticles) gather_coupling<kBisect>(P, c.x, c.y, c.z, rA, rB, pa, pf, ci, true, gA, gB);
   const float r = rA + rB;
   if (!(rA > 0.f) || !(rB > 0.f) || !isfinite(r)) atomicOr(err, isfinite(r) ? kErrNegDensity : kErrNonFinite);
   const float rinv = 1.f / r;
