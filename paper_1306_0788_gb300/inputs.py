@@ -85,6 +85,16 @@ def slab_and_droplets(dims, rho_hi: float, rho_lo: float, n_drops: int = 8,
     return rA, rB, drops
 
 
+def flat_slab(dims, rho_hi: float, rho_lo: float, width: float = 2.0):
+    """A-rich slab occupying nz/4 <= z < 3 nz/4 (two flat interfaces normal to z, at z =
+    nz/4 - 1/2 and 3 nz/4 - 1/2), B-rich elsewhere, tanh profiles of the given width."""
+    nx, ny, nz = dims
+    z = np.arange(nz, dtype=np.float64) + 0.5
+    dist = np.minimum(z - nz / 4.0, 3 * nz / 4.0 - z)
+    phiA = _tanh_profile(dist, width)[:, None, None] * np.ones((nz, ny, nx))
+    return rho_lo + (rho_hi - rho_lo) * phiA, rho_hi - (rho_hi - rho_lo) * phiA
+
+
 def disk(dims, radius: float, rho_hi: float, rho_lo: float, width: float = 2.0):
     """A-rich cylinder (axis along z) of the given radius at the centre of the x-y plane."""
     nx, ny, nz = dims
