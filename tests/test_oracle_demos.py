@@ -140,3 +140,47 @@ def test_strong_preference_detaches_from_the_interface(slab):
     F = probe_forces(slab, (1.0, 0.0), zs)
     assert stable_zero(zs, F, 3 * LZ / 4 - 0.5) is None
     assert (F >= -1e-15).all()
+
+
+def _demixing_run(lam, steps, dims=(32, 32, 2), n=100, seed=3):
+    """The single-fluid example of Sec. 3 on the oracle: two identical uncoupled components at
+    rho = 1 each, particles with kappa = 0.05, the given lambda on both components, WCA with
+    eps = 0.1 k_BT and sigma = 0.7, gamma = 1, m = 10, k_BT = 1e-5."""
+    kT = 1e-5
+    nx, ny, nz = dims
+    x = inputs.random_particles(n, dims, 0.7, seed=seed)
+    v = np.zeros_like(x)
+    f = oracle.init_equilibrium(np.ones((nz, ny, nx)), np.ones((nz, ny, nx)))
+    s = oracle.System(dims=dims, tau_r=1.0, kT=kT, seed=seed + 1, kappa=np.array([[0.05, 0.05]]),
+                      lam=np.array([[lam, lam]]), gamma=np.ones(1), mass=np.array([10.0]),
+                      wca_eps=np.full((1, 1), 0.1 * kT), wca_sig=np.full((1, 1), 0.7),
+                      type=np.zeros(n, dtype=np.int32), q=np.zeros(n))
+    for k in range(steps):
+        assert oracle.step(s, f, x, v, k)[0] == 0
+    return x, f.sum(1).sum(0)
+
+
+def _block_stats(x, rho, dims, block=8):
+    nx, ny, _ = dims
+    c, _, _ = np.histogram2d(np.mod(x[:, 1], ny), np.mod(x[:, 0], nx), bins=(ny // block, nx // block),
+                             range=[[0, ny], [0, nx]])
+    r = rho.mean(0).reshape(ny // block, block, nx // block, block).mean(axis=(1, 3))
+    return c, r
+
+
+def test_depleting_particles_gather_in_fluid_poor_domains():
+    """Sec. 3, single-fluid example: particles that push the fluid away (lambda > 0 in Eq.
+    solvation_lambda as printed) and move down density gradients (kappa > 0) gather where the
+    fluid is thin -- block particle counts anti-correlate with the fluid density and spread
+    beyond independent placement -- while the fluid stays positive there; with kappa alone
+    (lambda = 0) the fluid, uniform at the start, gives the particles no force to gather by."""
+    dims = (32, 32, 2)
+    x, rho = _demixing_run(0.01, 1500, dims)
+    c, r = _block_stats(x, rho, dims)
+    assert np.corrcoef(c.ravel(), r.ravel())[0, 1] < -0.7
+    assert c.var() / c.mean() > 1.5
+    assert rho.min() > 0.5 * 2.0
+    x0, rho0 = _demixing_run(0.0, 1500, dims)
+    assert np.abs(rho0 - 2.0).max() < 0.05 * (2.0 - rho.min())  # only friction stirs it
+    c0, _ = _block_stats(x0, rho0, dims)
+    assert c0.var() / c0.mean() < c.var() / c.mean()
