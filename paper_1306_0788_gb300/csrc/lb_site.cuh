@@ -427,28 +427,39 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
     fA[0] = __ldg(rest_in + s32);
     fB[0] = __ldg(rest_in + N32 + s32);
   }
-  float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+  // The two components go through the same arithmetic: it runs on (A, B) pairs with the
+  // packed two-lane FP32 instructions.
+  float2 r2s = make_float2(0.f, 0.f);
+  float jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    rA += fA[i];
-    rB += fB[i];
+    r2s = __fadd2_rn(r2s, make_float2(fA[i], fB[i]));
     jx += kCx[i] * (fA[i] + fB[i]);
     jy += kCy[i] * (fA[i] + fB[i]);
     jz += kCz[i] * (fA[i] + fB[i]);
   }
-  // S_z = sum_i w_i rho_z(r + c_i) c_i from the density field of this step
+  const float rA = r2s.x, rB = r2s.y;
+  // S_z = sum_i w_i rho_z(r + c_i) c_i from the density field of this step, as (S_A, S_B) pairs,
+  // summed over opposite directions as w_i c_i (rho(r + c_i) - rho(r - c_i)): a profile uniform
+  // along an axis gives exactly no force along it
   const float2 *rho2 = reinterpret_cast<const float2 *>(rho);
-  float SAx = 0.f, SAy = 0.f, SAz = 0.f, SBx = 0.f, SBy = 0.f, SBz = 0.f;
+  float2 Sx = make_float2(0.f, 0.f), Sy = Sx, Sz = Sx;
 #pragma unroll
-  for (int i = 1; i < kQ; ++i) {
-    const unsigned nb = (unsigned)((int)s32 + shift(o, kCx[i], kCy[i], kCz[i]));
-    const float2 r2 = __ldg(rho2 + nb);
-    const float a = kW[i] * r2.x, b = kW[i] * r2.y;
-    SAx += kCx[i] * a; SAy += kCy[i] * a; SAz += kCz[i] * a;
-    SBx += kCx[i] * b; SBy += kCy[i] * b; SBz += kCz[i] * b;
+  for (int i = 1; i < kQ; i += 2) {
+    const float2 rp = __ldg(rho2 + (unsigned)((int)s32 + shift(o, kCx[i], kCy[i], kCz[i])));
+    const float2 rm = __ldg(rho2 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i])));
+    const float2 d = __ffma2_rn(make_float2(-1.f, -1.f), rm, rp);
+    if (kCx[i]) Sx = __ffma2_rn(make_float2(kW[i] * kCx[i], kW[i] * kCx[i]), d, Sx);
+    if (kCy[i]) Sy = __ffma2_rn(make_float2(kW[i] * kCy[i], kW[i] * kCy[i]), d, Sy);
+    if (kCz[i]) Sz = __ffma2_rn(make_float2(kW[i] * kCz[i], kW[i] * kCz[i]), d, Sz);
   }
-  float3 gA = make_float3(-P.gAB * rA * SBx, -P.gAB * rA * SBy, -P.gAB * rA * SBz);
-  float3 gB = make_float3(-P.gBA * rB * SAx, -P.gBA * rB * SAy, -P.gBA * rB * SAz);
+  // g^SC_A = -g_AB rho_A S_B, g^SC_B = -g_BA rho_B S_A
+  const float2 gpre = make_float2(-P.gAB * rA, -P.gBA * rB);
+  const float2 gx = __fmul2_rn(gpre, make_float2(Sx.y, Sx.x));
+  const float2 gy = __fmul2_rn(gpre, make_float2(Sy.y, Sy.x));
+  const float2 gz = __fmul2_rn(gpre, make_float2(Sz.y, Sz.x));
+  float3 gA = make_float3(gx.x, gy.x, gz.x);
+  float3 gB = make_float3(gx.y, gy.y, gz.y);
   if (kParticles) gather_coupling<kBisect>(P, c.x, c.y, c.z, rA, rB, pa, pf, ci, true, gA, gB);
   const float r = rA + rB;
   if (!(rA > 0.f) || !(rB > 0.f) || !isfinite(r)) atomicOr(err, isfinite(r) ? kErrNegDensity : kErrNonFinite);
@@ -462,27 +473,44 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
     // BGK + forcing, f* = (1 - 1/tau) f + (1/tau) f^eq + Delta^g, per pair of opposite directions
     // (c_j = -c_i): f^eq and Delta^g split into parts even and odd in c.
     const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-    const float ugA3 = 3.f * (ux * gA.x + uy * gA.y + uz * gA.z);
-    const float ugB3 = 3.f * (ux * gB.x + uy * gB.y + uz * gB.z);
     const float om = P.inv_tau, om1 = 1.f - om, fp = P.force_pref;
-    const float aA = om * rA, aB = om * rB;
-    fA[0] = om1 * fA[0] + aA * kW[0] * (1.f - usq15) - kW[0] * fp * ugA3;
-    fB[0] = om1 * fB[0] + aB * kW[0] * (1.f - usq15) - kW[0] * fp * ugB3;
+    const float2 gx = make_float2(gA.x, gB.x), gy = make_float2(gA.y, gB.y), gz = make_float2(gA.z, gB.z);
+    // 3 u.g_z and om rho_z as (A, B) pairs
+    const float2 ug3 = __fmul2_rn(make_float2(3.f, 3.f),
+                                  __ffma2_rn(make_float2(uz, uz), gz,
+                                             __ffma2_rn(make_float2(uy, uy), gy, __fmul2_rn(make_float2(ux, ux), gx))));
+    const float2 a2 = __fmul2_rn(make_float2(om, om), make_float2(rA, rB));
+    const float2 om1_2 = make_float2(om1, om1);
+    {
+      const float e0 = kW[0] * (1.f - usq15), q0 = -kW[0] * fp;
+      const float2 f0 = __ffma2_rn(om1_2, make_float2(fA[0], fB[0]),
+                                   __ffma2_rn(a2, make_float2(e0, e0), __fmul2_rn(make_float2(q0, q0), ug3)));
+      fA[0] = f0.x;
+      fB[0] = f0.y;
+    }
 #pragma unroll
     for (int i = 1; i < kQ; i += 2) {
       const int j = i + 1;
       const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
-      const float cgA = kCx[i] * gA.x + kCy[i] * gA.y + kCz[i] * gA.z;
-      const float cgB = kCx[i] * gB.x + kCy[i] * gB.y + kCz[i] * gB.z;
+      // c_i . g_z for both components (each c component is -1, 0 or 1)
+      float2 cg = make_float2(0.f, 0.f);
+      if (kCx[i]) cg = __ffma2_rn(make_float2((float)kCx[i], (float)kCx[i]), gx, cg);
+      if (kCy[i]) cg = __ffma2_rn(make_float2((float)kCy[i], (float)kCy[i]), gy, cg);
+      if (kCz[i]) cg = __ffma2_rn(make_float2((float)kCz[i], (float)kCz[i]), gz, cg);
       const float sym = kW[i] * (1.f + 4.5f * cu * cu - usq15), anti = 3.f * kW[i] * cu;
-      const float wf = kW[i] * fp;
-      const float symA = wf * (9.f * cu * cgA - ugA3), antiA = 3.f * wf * cgA;
-      const float symB = wf * (9.f * cu * cgB - ugB3), antiB = 3.f * wf * cgB;
-      const float fAi = fA[i], fAj = fA[j], fBi = fB[i], fBj = fB[j];
-      fA[i] = om1 * fAi + aA * (sym + anti) + symA + antiA;
-      fA[j] = om1 * fAj + aA * (sym - anti) + symA - antiA;
-      fB[i] = om1 * fBi + aB * (sym + anti) + symB + antiB;
-      fB[j] = om1 * fBj + aB * (sym - anti) + symB - antiB;
+      const float wf = kW[i] * fp, wf9cu = 9.f * wf * cu, wf3 = 3.f * wf;
+      // even and odd forcing parts: wf (9 cu c.g - 3 u.g), 3 wf c.g
+      const float2 fs = __ffma2_rn(make_float2(wf9cu, wf9cu), cg, __fmul2_rn(make_float2(-wf, -wf), ug3));
+      const float2 fa = __fmul2_rn(make_float2(wf3, wf3), cg);
+      const float2 fi = __ffma2_rn(om1_2, make_float2(fA[i], fB[i]),
+                                   __ffma2_rn(a2, make_float2(sym + anti, sym + anti), __fadd2_rn(fs, fa)));
+      const float2 fj = __ffma2_rn(om1_2, make_float2(fA[j], fB[j]),
+                                   __ffma2_rn(a2, make_float2(sym - anti, sym - anti),
+                                              __ffma2_rn(make_float2(-1.f, -1.f), fa, fs)));
+      fA[i] = fi.x;
+      fB[i] = fi.y;
+      fA[j] = fj.x;
+      fB[j] = fj.y;
     }
   }
   T *foutB = fout + (size_t)kQ * N32;

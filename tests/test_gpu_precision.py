@@ -6,6 +6,8 @@ systems use the density scale of the paper's examples (rho ~ 78 per component,
 g rho = 1.2-1.68).  The bounds are the stated errors of each storage (measured values in
 the design notes), not parity: 16-bit rounding is far above the FP32 tolerance.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -18,11 +20,14 @@ pytestmark = pytest.mark.gpu
 CS2 = 1.0 / 3.0
 SCALE = 78.4
 STORAGES = {"fp32": 0, "fp16": 1, "bf16": 2}
-# stated bounds per storage: 10-step population error, 3000-step mass drift, Laplace dp error
+# stated bounds per storage: 10-step population error, 3000-step mass drift, Laplace dp error.
+# The 16-bit rounding is systematic near a steady state, so its Laplace error depends on where
+# the droplet's values fall between representable numbers: measured over R = 6, 7, 8, 9 it is
+# 1.3-1.6e-4 (FP32), 0.7-1.8 % (FP16) and 3.3-9.7 % (BF16, 8 significant bits).
 BOUNDS = {
     "fp32": dict(pop10=1e-5, drift=2e-4, dp=1e-3),
-    "fp16": dict(pop10=2e-5, drift=2e-3, dp=0.05),
-    "bf16": dict(pop10=1e-4, drift=2e-3, dp=0.05),
+    "fp16": dict(pop10=2e-5, drift=2e-3, dp=0.04),
+    "bf16": dict(pop10=1e-4, drift=2e-3, dp=0.15),
 }
 
 
@@ -53,16 +58,26 @@ def test_ten_step_populations(storage):
     assert pop_error(fg, fo) <= BOUNDS[storage]["pop10"]
 
 
+@functools.lru_cache(maxsize=None)
+def _oracle_droplet(radius):
+    """The oracle's droplet after 3000 steps (shared by the three storages)."""
+    dims = (32, 32, 1)
+    rA, rB = inputs.disk(dims, radius, 1.8 * SCALE, 0.2 * SCALE, width=1.0)
+    fo, *_ = run_oracle(Case(dims=dims, g=1.68 / SCALE, rhoA=rA, rhoB=rB), 3000)
+    return fo
+
+
+@pytest.mark.parametrize("radius", [6.0, 7.0, 8.0, 9.0])
 @pytest.mark.parametrize("storage", sorted(STORAGES))
-def test_laplace_pressure_and_mass_drift(storage):
-    """Quasi-2D A-rich droplet (R = 7, 32 x 32 x 1) relaxed for 3000 steps: the Laplace
+def test_laplace_pressure_and_mass_drift(storage, radius):
+    """Quasi-2D A-rich droplet (R = 6-9, 32 x 32 x 1) relaxed for 3000 steps: the Laplace
     pressure jump p(centre) - p(far) with p = c_s^2 (rho_A + rho_B) + c_s^2 g rho_A rho_B,
     against the FP64 oracle; mass drift of each component from the FP64 diagnostics."""
     g = 1.68 / SCALE
     dims = (32, 32, 1)
-    rA, rB = inputs.disk(dims, 7.0, 1.8 * SCALE, 0.2 * SCALE, width=1.0)
+    rA, rB = inputs.disk(dims, radius, 1.8 * SCALE, 0.2 * SCALE, width=1.0)
     c = Case(dims=dims, g=g, rhoA=rA, rhoB=rB)
-    fo, *_ = run_oracle(c, 3000)
+    fo = _oracle_droplet(radius)
 
     def dp(f):
         A, B = f[0].sum(0)[0], f[1].sum(0)[0]
