@@ -24,6 +24,9 @@ template <class T>
 constexpr bool kSplitRest = !std::is_same<T, float>::value;
 template <>
 struct Pop<float> {
+  static __device__ __forceinline__ float enc_raw(float v) { return v; }
+  static __device__ __forceinline__ float dec_raw(float e) { return e; }
+  static __device__ __forceinline__ float ld_raw(const float *p) { return __ldg(p); }
   static __device__ __forceinline__ float enc(float v, float) { return v; }
   static __device__ __forceinline__ float dec(float e, float) { return e; }
   static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
@@ -32,6 +35,10 @@ struct Pop<float> {
 };
 template <>
 struct Pop<__half> {
+  // raw: the stored (shifted) value itself, f - w_i rho0
+  static __device__ __forceinline__ __half enc_raw(float v) { return __float2half_rn(v); }
+  static __device__ __forceinline__ float dec_raw(__half e) { return __half2float(e); }
+  static __device__ __forceinline__ float ld_raw(const __half *p) { return __half2float(__ldg(p)); }
   static __device__ __forceinline__ __half enc(float v, float sh) { return __float2half_rn(v - sh); }
   static __device__ __forceinline__ float dec(__half e, float sh) { return __half2float(e) + sh; }
   static __device__ __forceinline__ float ld(const __half *p, float sh) { return dec(__ldg(p), sh); }
@@ -40,6 +47,9 @@ struct Pop<__half> {
 };
 template <>
 struct Pop<__nv_bfloat16> {
+  static __device__ __forceinline__ __nv_bfloat16 enc_raw(float v) { return __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ float dec_raw(__nv_bfloat16 e) { return __bfloat162float(e); }
+  static __device__ __forceinline__ float ld_raw(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
   static __device__ __forceinline__ __nv_bfloat16 enc(float v, float sh) { return __float2bfloat16_rn(v - sh); }
   static __device__ __forceinline__ float dec(__nv_bfloat16 e, float sh) { return __bfloat162float(e) + sh; }
   static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float sh) { return dec(__ldg(p), sh); }
@@ -48,6 +58,11 @@ struct Pop<__nv_bfloat16> {
 };
 
 __device__ __forceinline__ float pop_shift(const StepParams &P, int comp, int i) { return kW[i] * P.rho0[comp]; }
+
+// Sum of the shifts of the 18 moving populations of component comp, (1 - w_0) rho0: the density
+// of a 16-bit node is f_0 + (its 18 stored values) + this.  The update and the mass closure use
+// this same FP32 value, so that rounding it moves no mass from step to step.
+__device__ __forceinline__ float shift_sum(const StepParams &P, int comp) { return (1.f - kW[0]) * P.rho0[comp]; }
 
 // With 16-bit storage the rest population f_0 (which does not stream) is kept in an FP32 array
 // rest[2][N]; these read / write direction i of component c at site s from the right place.
@@ -136,18 +151,46 @@ __device__ __forceinline__ void moments(const StepParams &P, long long s, const 
   const NOff o = neighbour_offsets(P, c);
   const unsigned N32 = (unsigned)P.N, s32 = (unsigned)s;
   const T *finB = fin + (size_t)kQ * N32;
+  // 16-bit storage: the moving populations are summed as stored (shifted) and the shifts added
+  // once; the shifts cancel in j' (sum_i w_i c_i = 0)
+  constexpr bool kShifted = kSplitRest<T>;
   float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+  if (kShifted) {
+    // two-byte values: all 36 loads are issued before any is used, so that enough bytes are in
+    // flight per thread
+    T ea[kQ], eb[kQ];
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
-    const bool r0 = kSplitRest<T> && i == 0 && rest;
-    const float a = r0 ? __ldg(rest + s32) : Pop<T>::ld(fin + src, pop_shift(P, 0, i));
-    const float b = r0 ? __ldg(rest + N32 + s32) : Pop<T>::ld(finB + src, pop_shift(P, 1, i));
-    rA += a;
-    rB += b;
-    jx += kCx[i] * (a + b);
-    jy += kCy[i] * (a + b);
-    jz += kCz[i] * (a + b);
+    for (int i = 1; i < kQ; ++i) {
+      const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // r - c_i
+      ea[i] = __ldg(fin + src);
+      eb[i] = __ldg(finB + src);
+    }
+    rA = __ldg(rest + s32);
+    rB = __ldg(rest + N32 + s32);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+      const float a = Pop<T>::dec_raw(ea[i]), b = Pop<T>::dec_raw(eb[i]);
+      rA += a;
+      rB += b;
+      jx += kCx[i] * (a + b);
+      jy += kCy[i] * (a + b);
+      jz += kCz[i] * (a + b);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // r - c_i
+      const float a = Pop<T>::ld(fin + src, 0.f), b = Pop<T>::ld(finB + src, 0.f);
+      rA += a;
+      rB += b;
+      jx += kCx[i] * (a + b);
+      jy += kCy[i] * (a + b);
+      jz += kCz[i] * (a + b);
+    }
+  }
+  if (kShifted) {
+    rA += shift_sum(P, 0);
+    rB += shift_sum(P, 1);
   }
   reinterpret_cast<float2 *>(rho)[s] = make_float2(rA, rB);
   if (jp) {
@@ -416,14 +459,23 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
   const NOff o = neighbour_offsets(P, c);
   const unsigned N32 = (unsigned)P.N, s32 = (unsigned)s;
   const T *finB = fin + (size_t)kQ * N32;
+  // 16-bit storage with the BGK update: the moving populations stay shifted (f - w_i rho0, as
+  // stored) through the update, the shifts folded into its constants, and the FP32 rest
+  // population closes the node's mass
+  constexpr bool kShifted = kSplitRest<T> && !kMRT;
   float fA[kQ], fB[kQ];
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
-    fA[i] = Pop<T>::ld(fin + src, pop_shift(P, 0, i));
-    fB[i] = Pop<T>::ld(finB + src, pop_shift(P, 1, i));
+    if (kShifted && i > 0) {
+      fA[i] = Pop<T>::ld_raw(fin + src);
+      fB[i] = Pop<T>::ld_raw(finB + src);
+    } else if (!kSplitRest<T> || i > 0) {
+      fA[i] = Pop<T>::ld(fin + src, pop_shift(P, 0, i));
+      fB[i] = Pop<T>::ld(finB + src, pop_shift(P, 1, i));
+    }
   }
-  if (kSplitRest<T> && rest_in) {  // 16-bit storage: the rest populations are kept in FP32
+  if (kSplitRest<T>) {  // 16-bit storage: the rest populations are kept in FP32
     fA[0] = __ldg(rest_in + s32);
     fB[0] = __ldg(rest_in + N32 + s32);
   }
@@ -438,6 +490,7 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
     jy += kCy[i] * (fA[i] + fB[i]);
     jz += kCz[i] * (fA[i] + fB[i]);
   }
+  if (kShifted) r2s = __fadd2_rn(r2s, make_float2(shift_sum(P, 0), shift_sum(P, 1)));
   const float rA = r2s.x, rB = r2s.y;
   // S_z = sum_i w_i rho_z(r + c_i) c_i from the density field of this step, as (S_A, S_B) pairs,
   // summed over opposite directions as w_i c_i (rho(r + c_i) - rho(r - c_i)): a profile uniform
@@ -481,7 +534,7 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
                                              __ffma2_rn(make_float2(uy, uy), gy, __fmul2_rn(make_float2(ux, ux), gx))));
     const float2 a2 = __fmul2_rn(make_float2(om, om), make_float2(rA, rB));
     const float2 om1_2 = make_float2(om1, om1);
-    {
+    if (!kShifted) {  // (with 16-bit storage the rest population is set by the mass closure)
       const float e0 = kW[0] * (1.f - usq15), q0 = -kW[0] * fp;
       const float2 f0 = __ffma2_rn(om1_2, make_float2(fA[0], fB[0]),
                                    __ffma2_rn(a2, make_float2(e0, e0), __fmul2_rn(make_float2(q0, q0), ug3)));
@@ -500,7 +553,9 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
       const float sym = kW[i] * (1.f + 4.5f * cu * cu - usq15), anti = 3.f * kW[i] * cu;
       const float wf = kW[i] * fp, wf9cu = 9.f * wf * cu, wf3 = 3.f * wf;
       // even and odd forcing parts: wf (9 cu c.g - 3 u.g), 3 wf c.g
-      const float2 fs = __ffma2_rn(make_float2(wf9cu, wf9cu), cg, __fmul2_rn(make_float2(-wf, -wf), ug3));
+      float2 fs = __ffma2_rn(make_float2(wf9cu, wf9cu), cg, __fmul2_rn(make_float2(-wf, -wf), ug3));
+      // shifted storage: f~* = (1 - om) f~ + om (f^eq - w_i rho0) + Delta^g
+      if (kShifted) fs = __ffma2_rn(make_float2(-om * kW[i], -om * kW[i]), make_float2(P.rho0[0], P.rho0[1]), fs);
       const float2 fa = __fmul2_rn(make_float2(wf3, wf3), cg);
       const float2 fi = __ffma2_rn(om1_2, make_float2(fA[i], fB[i]),
                                    __ffma2_rn(a2, make_float2(sym + anti, sym + anti), __fadd2_rn(fs, fa)));
@@ -514,7 +569,23 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
     }
   }
   T *foutB = fout + (size_t)kQ * N32;
-  if (kSplitRest<T> && rest_out) {
+  if (kShifted) {
+    // store the 18 shifted values; the rest population takes what keeps the node's mass at its
+    // value before the update (the BGK update and the forcing term conserve it exactly)
+    float mA = rA - shift_sum(P, 0), mB = rB - shift_sum(P, 1);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+      const T a = Pop<T>::enc_raw(fA[i]), b = Pop<T>::enc_raw(fB[i]);
+      fout[i * N32 + s32] = a;
+      foutB[i * N32 + s32] = b;
+      mA -= Pop<T>::dec_raw(a);
+      mB -= Pop<T>::dec_raw(b);
+    }
+    if (rest_out) {
+      rest_out[s32] = mA;
+      rest_out[N32 + s32] = mB;
+    }
+  } else if (kSplitRest<T> && rest_out) {
     // 16-bit storage: each moving population is rounded on store; the FP32 rest population takes
     // the rounding error of the node's 18 others, so the node's total (and the total mass of each
     // component) is the one of the collision up to FP32 rounding instead of drifting each step.
