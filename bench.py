@@ -29,15 +29,15 @@ METRIC = "coupled 2-comp D3Q19 MLUPS & HBM-roofline %; replica p50/p99 latency"
 UNIT = "MLUPS"
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes per node moved by k_collide (dram__bytes_read + dram__bytes_write of one ncu capture
-# of the 128^3 case of this workload, scaled per node; profiles/k_collide_slab_droplets_256.md).
-# None while k_collide has changed since the last capture.
-COLLIDE_TRAFFIC_BYTES_PER_NODE = 290.0
+# of the 128^3 case of this workload, scaled per node; profiles/k_collide_slab_droplets_256.md),
+# per storage with a capture of its own.  None while k_collide has changed since the capture.
+COLLIDE_TRAFFIC_BYTES_PER_NODE = {"fp32": 290.6, "bf16": 148.1}
 # The fluctuating MRT update is bound by instruction issue, not by HBM: warp instructions per
 # node of k_collide<float, true, true> (smsp__inst_executed.sum / nodes of one ncu capture of the
 # 128^3 case, profiles/k_collide_mrt_slab_droplets_256.md), and the issue peak of the GPU: one
 # warp instruction per cycle per scheduler, 4 schedulers per SM, 152 SMs, at the SM clock.
-MRT_WARP_INSTR_PER_NODE = 85.42
-MRT_TRAFFIC_BYTES_PER_NODE = 290.7  # DRAM bytes per node of the same capture
+MRT_WARP_INSTR_PER_NODE = 80.87
+MRT_TRAFFIC_BYTES_PER_NODE = 290.6  # DRAM bytes per node of the same capture
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 # The slab/droplet workload uses the density scale of the paper's ferrofluid example (Sec. 4.5):
@@ -74,11 +74,14 @@ STORAGES = {"fp32": (0, 4), "fp16": (1, 2), "bf16": (2, 2)}  # name: (LBMD_STORA
 
 
 def algorithmic_bytes_per_site(storage: str = "fp32") -> int:
-    """Algorithmic bytes per node of the collide kernel: both components' 19 populations
-    read (pull) and written once (2*19*2*b for b bytes per stored value: 304 in FP32, 152 in
-    16-bit storage), plus the node's two FP32 densities of the Shan-Chen stencil (8; the
-    neighbours' come from cache)."""
-    return 2 * 19 * 2 * STORAGES[storage][1] + 8
+    """Algorithmic bytes per node of the collide kernel: both components' populations read
+    (pull) and written once, plus the node's two FP32 densities of the Shan-Chen stencil (8; the
+    neighbours' come from cache).  FP32: 2*19*4*2 + 8 = 312.  16-bit storage: the 18 moving
+    populations in 2 bytes and the rest population in FP32, 2*(18*2 + 4)*2 + 8 = 168."""
+    b = STORAGES[storage][1]
+    if b == 4:
+        return 2 * 19 * 4 * 2 + 8
+    return 2 * (18 * b + 4) * 2 + 8
 
 
 def measured_hbm_peak():
@@ -363,16 +366,19 @@ def run_cuda(args):
     if mrt:
         clk = clocks.get("sm_mhz") or 2070.0
         issue_peak = SMS * SCHEDULERS_PER_SM * clk * 1e6
-        issued = MRT_WARP_INSTR_PER_NODE * N / (avg_kernel_ms * 1e-3)
+        issued = None if MRT_WARP_INSTR_PER_NODE is None else MRT_WARP_INSTR_PER_NODE * N / (avg_kernel_ms * 1e-3)
         roofline = {"bound": "alu", "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + fluctuating "
                                               "MRT with Philox noise, both components)",
-                    "achieved": round(issued / 1e12, 4), "peak": round(issue_peak / 1e12, 4),
+                    "achieved": None if issued is None else round(issued / 1e12, 4),
+                    "peak": round(issue_peak / 1e12, 4),
                     "peak_kind": "derived: 152 SMs x 4 schedulers x 1 warp instruction per cycle x the median SM "
                                  "clock under load", "unit": "T warp-instructions/s",
-                    "frac": round(issued / issue_peak, 4), "instructions_per_node": MRT_WARP_INSTR_PER_NODE,
+                    "frac": None if issued is None else round(issued / issue_peak, 4),
+                    "instructions_per_node": MRT_WARP_INSTR_PER_NODE,
                     "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,
                     "hbm_frac": round(achieved / peak, 4),
-                    "traffic": int(MRT_TRAFFIC_BYTES_PER_NODE * N) if args.storage == "fp32" else None}
+                    "traffic": (int(MRT_TRAFFIC_BYTES_PER_NODE * N)
+                                if args.storage == "fp32" and MRT_TRAFFIC_BYTES_PER_NODE is not None else None)}
     value = whole_job_rate(N * args.steps, world, ms_max * 1e-3) / 1e6
     if rank == 0:
         out = {
@@ -397,8 +403,8 @@ def run_cuda(args):
                          "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_site": bps,
                          "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,
-                         "traffic": (None if COLLIDE_TRAFFIC_BYTES_PER_NODE is None or args.storage != "fp32" or mrt
-                                     else int(COLLIDE_TRAFFIC_BYTES_PER_NODE * N))},
+                         "traffic": (None if args.storage not in COLLIDE_TRAFFIC_BYTES_PER_NODE
+                                     else int(COLLIDE_TRAFFIC_BYTES_PER_NODE[args.storage] * N))},
             "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks, "state_ok": state_ok,
         }
         if world == 1 and args.serving > 0:
