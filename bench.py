@@ -233,7 +233,11 @@ def run_batch(args):
         slots = [serving.admit(b, r) for r in reqs]
         L.lbmd_batch_step(b, args.warmup)
         L.lbmd_batch_poll(b, 64)
-        cfg, ms = L.lbmd_batch_tune(b)
+        if args.batch_config:  # a fixed launch shape instead of the autotuner's (profiling)
+            L.lbmd_batch_set_config(b, *args.batch_config)
+            cfg, ms = L.lbmd_batch_get_config(b), None
+        else:
+            cfg, ms = L.lbmd_batch_tune(b)
         L.lbmd_batch_step(b, 3)
         L.lbmd_batch_poll(b, 64)
         n0 = L.lbmd_batch_launch_count(b)
@@ -549,6 +553,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--replicas", type=int, default=24, help="replicas of the replicas_24 workload")
+    ap.add_argument("--batch-config", type=lambda v: [int(t) for t in v.split(",")], default=None,
+                    help="tile_sites,grid_moments,grid_collide,collide_blocks: fixed batch launch shape, no autotuning")
     ap.add_argument("--serving", type=int, default=200,
                     help="replicas in the serving stream measured after the main run (0 = skip)")
     args = ap.parse_args()
