@@ -25,10 +25,12 @@ STORAGES = {"fp32": 0, "fp16": 1, "bf16": 2}
 # the droplet's values fall between representable numbers: measured over R = 6, 7, 8, 9 it is
 # 1.3-1.6e-4 (FP32), 0.4-1.2 % (FP16) and 1.6-19 % (BF16, 8 significant bits).  The FP32 rest
 # population closes each node's mass, so the 16-bit drift (7e-7 to 8e-5) stays within FP32's.
+# Particle MSD over 1000 steps (the particles' noise is the same on both sides, so the fluid's
+# rounding is all that separates them): measured 7.5e-8 (FP32), 7.1e-8 (FP16), 9.2e-7 (BF16).
 BOUNDS = {
-    "fp32": dict(pop10=1e-5, drift=2e-4, dp=1e-3),
-    "fp16": dict(pop10=2e-5, drift=3e-4, dp=0.04),
-    "bf16": dict(pop10=1e-4, drift=3e-4, dp=0.25),
+    "fp32": dict(pop10=1e-5, drift=2e-4, dp=1e-3, msd=1e-6),
+    "fp16": dict(pop10=2e-5, drift=3e-4, dp=0.04, msd=1e-6),
+    "bf16": dict(pop10=1e-4, drift=3e-4, dp=0.25, msd=1e-5),
 }
 
 
@@ -88,3 +90,77 @@ def test_laplace_pressure_and_mass_drift(storage, radius):
     fg, drift = _gpu(c, 3000, storage, (float(rA.mean()), float(rB.mean())))
     assert abs(dp(fg) - dp(fo)) <= BOUNDS[storage]["dp"] * abs(dp(fo))
     assert drift <= BOUNDS[storage]["drift"]
+
+
+MSD_TIMES = (100, 200, 500, 1000)
+
+
+def _unwrapped_track(step_fn, x0, dims, times):
+    """Positions read after each interval, unwrapped by the minimum image of each interval's
+    displacement (intervals of 100 steps move a particle far less than half the box)."""
+    L = np.asarray(dims, dtype=np.float64)
+    prev, disp, out, t = x0.copy(), np.zeros_like(x0), {}, 0
+    for T in times:
+        while t < T:
+            x = step_fn(100)
+            d = x - prev
+            disp += d - L * np.round(d / L)
+            prev, t = x, t + 100
+        out[T] = float((disp ** 2).sum(1).mean())
+    return out
+
+
+def _msd_case():
+    dims = (16, 16, 16)
+    rA, rB = inputs.uniform_noise(dims, SCALE, 0.01 * SCALE, seed=5)
+    x = inputs.random_particles(100, dims, 2 ** (1 / 6), seed=6)
+    return Case(dims=dims, g=0.5 / SCALE, kT=0.01, seed=11, rhoA=rA, rhoB=rB, x=x, v=np.zeros_like(x),
+                ptype=np.zeros(len(x), dtype=np.int32), types=[(0.0, 0.0, 0.0, 0.0, 1.0, 200.0)])
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_msd():
+    import oracle
+    from gpu_common import oracle_system
+    c = _msd_case()
+    a, b, _ = c.fields32()
+    f = oracle.init_equilibrium(a.astype(np.float64), b.astype(np.float64))
+    x, v = c.x.copy(), c.v.copy()
+    s = oracle_system(c)
+    state = {"k": 0}
+
+    def step(n):
+        for _ in range(n):
+            assert oracle.step(s, f, x, v, state["k"])[0] == 0
+            state["k"] += 1
+        return x.copy()
+
+    return _unwrapped_track(step, c.x, c.dims, MSD_TIMES)
+
+
+@pytest.mark.parametrize("storage", sorted(STORAGES))
+def test_particle_msd(storage):
+    """Mean-square displacement of 100 thermal particles (k_BT = 0.01, gamma = 1, m = 200, friction
+    noise from the same counter-based generator on both sides) in a stable mixture at the paper's
+    density scale, 16^3, over 1000 steps: each storage against the FP64 oracle."""
+    from paper_1306_0788_gb300 import lbmd as L
+    c = _msd_case()
+    rA, rB, _ = c.fields32()
+    ctx, _ = L.lbmd_create(L.params(c.dims, tau_r=c.tau_r, g_AB=c.g, kT=c.kT, seed=c.seed,
+                                    storage=STORAGES[storage], rho0=(float(rA.mean()), float(rB.mean()))))
+    try:
+        L.lbmd_set_types(ctx, [L.lbmd_ptype(*t) for t in c.types], [])
+        L.lbmd_init_fluid(ctx, rA, rB)
+        L.lbmd_set_particles(ctx, c.x, c.v, c.ptype)
+
+        def step(n):
+            L.lbmd_step(ctx, n)
+            return L.lbmd_get_particles(ctx, c.n)[0]
+
+        msd_g = _unwrapped_track(step, c.x, c.dims, MSD_TIMES)
+    finally:
+        L.lbmd_destroy(ctx)
+    msd_o = _oracle_msd()
+    errs = {t: abs(msd_g[t] / msd_o[t] - 1) for t in MSD_TIMES}
+    print("MSD", storage, {t: (round(msd_o[t], 4), float("%.3e" % errs[t])) for t in MSD_TIMES})
+    assert max(errs.values()) <= BOUNDS[storage]["msd"]
