@@ -329,7 +329,8 @@ int lbmd_batch_tune(lbmd_batch *batch, int cfg[5], double ms[2]);
 /* Budget and use in bytes, number of occupied slots, slot count (any pointer may be NULL). */
 int lbmd_batch_info(const lbmd_batch *batch, size_t *budget, size_t *used, int *occupied, int *max_slots);
 
-/* Kernel launches issued by lbmd_batch_step so far (host-side count, 14 per step). */
+/* Kernel launches issued by lbmd_batch_step so far (host-side count: 13 per step, 14 when the
+ * batch holds replicas of both collisions). */
 int64_t lbmd_batch_launch_count(const lbmd_batch *batch);
 
 /* Message of the last failure of a batch call (NULL: of lbmd_batch_create). */

@@ -437,7 +437,10 @@ struct lbmd_batch {
   // launch shape (autotuned)
   int tile_sites = 1024, grid_moments = 0, grid_collide = 0, grid_particles = 0;
   int collide_blocks = 3;  // register budget of the update kernel: blocks per SM
-  std::map<int, cudaGraphExec_t> graphs;  // by steps per graph
+  // collisions among the replicas of the tables: bit 0 BGK, bit 1 MRT (the update launches only
+  // the variants in use)
+  int mix = 0;
+  std::map<int, cudaGraphExec_t> graphs;  // by steps per graph and mix: 4 n + mix
   int64_t launches = 0;
   std::string msg;
 };
@@ -692,6 +695,8 @@ int repack(lbmd_batch *b) {
        "upload replicas");
   int r = build_tiles(b, act);
   if (r) return r;
+  b->mix = 0;
+  for (int s : act) b->mix |= b->slots[s].P.collision == LBMD_COLLISION_MRT ? 2 : 1;
   b->hb.nrep = (int)act.size();
   b->hb.np = np;
   b->hb.nrows = nrows;
@@ -718,19 +723,29 @@ void launch_batched_moments(lbmd_batch *b, int grid) {
   });
 }
 
-// The BGK replicas with the tuned shape, then the MRT ones (two blocks of 256 per SM).
-void launch_batched_collide(lbmd_batch *b, int grid, int min_blocks, int tuning) {
+// The BGK replicas with the tuned shape, then the MRT ones (two blocks of 256 per SM); a variant
+// no replica uses is not launched.  Returns the number of launches.
+int launch_batched_collide(lbmd_batch *b, int grid, int min_blocks, int tuning) {
+  int n = 0;
   with_batch_storage(b->storage, [&](auto t) {
     using T = std::remove_pointer_t<decltype(t)>;
-    if (min_blocks == 2)
-      kb_collide<T, 2, false><<<grid, kBThreads, 0, b->st>>>(b->d_batch, tuning);
-    else
-      kb_collide<T, 3, false><<<grid, kBThreads, 0, b->st>>>(b->d_batch, tuning);
-    kb_collide<T, 2, true><<<2 * b->sms, kBThreads, 0, b->st>>>(b->d_batch, tuning);
+    if (b->mix & 1) {
+      if (min_blocks == 2)
+        kb_collide<T, 2, false><<<grid, kBThreads, 0, b->st>>>(b->d_batch, tuning);
+      else
+        kb_collide<T, 3, false><<<grid, kBThreads, 0, b->st>>>(b->d_batch, tuning);
+      ++n;
+    }
+    if (b->mix & 2) {
+      kb_collide<T, 2, true><<<2 * b->sms, kBThreads, 0, b->st>>>(b->d_batch, tuning);
+      ++n;
+    }
   });
+  return n;
 }
 
-void enqueue_step(lbmd_batch *b) {
+// Enqueues one step; returns the number of kernel launches.
+int enqueue_step(lbmd_batch *b) {
   const BatchDev *B = b->d_batch;
   const int gp = b->grid_particles;
   kb_bin<<<gp, kBPThreads, 0, b->st>>>(B);
@@ -743,34 +758,40 @@ void enqueue_step(lbmd_batch *b) {
   launch_batched_moments(b, b->grid_moments);
   kb_couple<<<gp, kBPThreads, 0, b->st>>>(B);
   kb_pairs<<<gp, kBPThreads, 0, b->st>>>(B);
-  launch_batched_collide(b, b->grid_collide, b->collide_blocks, 0);
+  const int nc = launch_batched_collide(b, b->grid_collide, b->collide_blocks, 0);
   kb_integrate<<<gp, kBPThreads, 0, b->st>>>(B);
   kb_advance<<<1, 256, 0, b->st>>>(B);
+  return 12 + nc;
 }
-constexpr int kLaunchesPerStep = 14;
 
 void drop_graphs(lbmd_batch *b) {
   for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
   b->graphs.clear();
 }
 
-int graph_for(lbmd_batch *b, int n, cudaGraphExec_t *out) {
-  auto it = b->graphs.find(n);
+// The graph of n steps for the current mix of collisions (captured once per n and mix);
+// *launches receives its kernel launches.
+int graph_for(lbmd_batch *b, int n, cudaGraphExec_t *out, int *launches) {
+  const int key = 4 * n + b->mix;
+  auto it = b->graphs.find(key);
+  int per_step = 0;
   if (it != b->graphs.end()) {
     *out = it->second;
+    *launches = n * (12 + ((b->mix & 1) != 0) + ((b->mix & 2) != 0));
     return LBMD_OK;
   }
   cudaGraph_t g = nullptr;
   BK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal), "begin capture");
-  for (int k = 0; k < n; ++k) enqueue_step(b);
+  for (int k = 0; k < n; ++k) per_step = enqueue_step(b);
   cudaError_t e = cudaStreamEndCapture(b->st, &g);
   if (e != cudaSuccess) return bcuda(b, e, "end capture");
   cudaGraphExec_t x = nullptr;
   e = cudaGraphInstantiate(&x, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return bcuda(b, e, "instantiate graph");
-  b->graphs[n] = x;
+  b->graphs[key] = x;
   *out = x;
+  *launches = n * per_step;
   return LBMD_OK;
 }
 
@@ -1031,13 +1052,17 @@ int lbmd_batch_step(lbmd_batch *b, int nsteps) {
   constexpr int kMaxGraphSteps = 16;
   const int chunk = std::min(most, kMaxGraphSteps);
   cudaGraphExec_t g = nullptr;
-  if ((r = graph_for(b, chunk, &g))) return r;
-  for (int k = 0; k + chunk <= most; k += chunk) BK(cudaGraphLaunch(g, b->st), "graph launch");
-  if (most % chunk) {
-    if ((r = graph_for(b, most % chunk, &g))) return r;
+  int nl = 0;
+  if ((r = graph_for(b, chunk, &g, &nl))) return r;
+  for (int k = 0; k + chunk <= most; k += chunk) {
     BK(cudaGraphLaunch(g, b->st), "graph launch");
+    b->launches += nl;
   }
-  b->launches += (int64_t)kLaunchesPerStep * most;
+  if (most % chunk) {
+    if ((r = graph_for(b, most % chunk, &g, &nl))) return r;
+    BK(cudaGraphLaunch(g, b->st), "graph launch");
+    b->launches += nl;
+  }
   return LBMD_OK;
 }
 
