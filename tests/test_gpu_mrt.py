@@ -93,3 +93,34 @@ def test_mrt_equipartition_at_96_cubed(rhoA, rhoB):
     assert abs((j * j).mean() / (kT * (rhoA + rhoB)) - 1) < 0.02
     assert abs(d1[0] / d0[0] - 1) < 1e-5 and abs(d1[1] / d0[1] - 1) < 1e-5
     assert np.abs(d1[2:5]).max() < 1e-6 * d0[0]
+
+
+@pytest.mark.parametrize("kT", [0.0, 1e-3])
+@pytest.mark.parametrize("storage,bound", [(1, 2e-5), (2, 1e-4)])
+def test_mrt_with_16bit_storage(storage, bound, kT):
+    """The fluctuating MRT update on FP16 (1) / BF16 (2) shifted storage at the paper's density
+    scale (rho ~ 78 per component): populations after 10 steps against the FP64 oracle within
+    the storage's stated 10-step bound, and each component's mass after 300 steps within 3e-4
+    (the FP32 rest population absorbs the rounding of the 18 stored values)."""
+    from paper_1306_0788_gb300 import inputs
+    from paper_1306_0788_gb300 import lbmd as L
+    scale = 78.4
+    dims = (12, 10, 9)
+    rA, rB = inputs.uniform_noise(dims, scale, 0.01 * scale, seed=33)
+    c = Case(dims=dims, tau_r=0.9, g=1.3 / scale, kT=kT, seed=19, rhoA=rA, rhoB=rB, **EIGS)
+    fo, *_ = run_oracle(c, 10)
+    a, b, _ = c.fields32()
+    ctx, _ = L.lbmd_create(L.params(dims, tau_r=c.tau_r, g_AB=c.g, kT=kT, seed=c.seed, storage=storage,
+                                    rho0=(float(a.mean()), float(b.mean())), collision=1, lambda_bulk=c.lam_bulk,
+                                    lambda_mom=c.lam_mom, lambda_ghost=c.lam_ghost))
+    try:
+        L.lbmd_init_fluid(ctx, a, b)
+        d0 = L.lbmd_diagnostics(ctx)
+        L.lbmd_step(ctx, 10)
+        fg = np.stack([L.lbmd_get_populations(ctx, 0, c.shape), L.lbmd_get_populations(ctx, 1, c.shape)])
+        L.lbmd_step(ctx, 290)
+        d1 = L.lbmd_diagnostics(ctx)
+    finally:
+        L.lbmd_destroy(ctx)
+    assert pop_error(fg.astype(np.float64), fo) <= bound
+    assert abs(d1[0] / d0[0] - 1) < 3e-4 and abs(d1[1] / d0[1] - 1) < 3e-4
