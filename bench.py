@@ -36,8 +36,8 @@ COLLIDE_TRAFFIC_BYTES_PER_NODE = {"fp32": 290.6, "bf16": 148.1}
 # node of k_collide<float, true, true> (smsp__inst_executed.sum / nodes of one ncu capture of the
 # 128^3 case, profiles/k_collide_mrt_slab_droplets_256.md), and the issue peak of the GPU: one
 # warp instruction per cycle per scheduler, 4 schedulers per SM, 152 SMs, at the SM clock.
-MRT_WARP_INSTR_PER_NODE = 80.87
-MRT_TRAFFIC_BYTES_PER_NODE = 290.6  # DRAM bytes per node of the same capture
+MRT_WARP_INSTR_PER_NODE = 83.19
+MRT_TRAFFIC_BYTES_PER_NODE = 291.7  # DRAM bytes per node of the same capture
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 # The slab/droplet workload uses the density scale of the paper's ferrofluid example (Sec. 4.5):

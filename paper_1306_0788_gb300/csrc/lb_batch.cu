@@ -723,8 +723,9 @@ void launch_batched_moments(lbmd_batch *b, int grid) {
   });
 }
 
-// The BGK replicas with the tuned shape, then the MRT ones (two blocks of 256 per SM); a variant
-// no replica uses is not launched.  Returns the number of launches.
+// The BGK replicas with the tuned shape, then the MRT ones (two blocks of 256 per SM: at three the
+// tile context spills heavily); a variant no replica uses is not launched.  Returns the number of
+// launches.
 int launch_batched_collide(lbmd_batch *b, int grid, int min_blocks, int tuning) {
   int n = 0;
   with_batch_storage(b->storage, [&](auto t) {

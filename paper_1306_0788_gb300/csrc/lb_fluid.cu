@@ -77,10 +77,11 @@ __global__ void __launch_bounds__(kBlock) k_moments(StepParams P, const T *__res
 }
 
 // The lattice update of one step at every site (site::collide; with kMRT the fluctuating MRT
-// collision, whose mode transforms take the register budget of two blocks per SM; with
-// kBisect the gather over the sub-stepping reaction records).
+// collision, whose mode transforms spill a few registers at this budget of three blocks per SM
+// but run faster than without spills at two; with kBisect the gather over the sub-stepping
+// reaction records).
 template <class T, bool kParticles, bool kMRT, bool kBisect = false>
-__global__ void __launch_bounds__(kBlock, kMRT ? 2 : 3) k_collide(StepParams P, const T *__restrict__ fin,
+__global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const T *__restrict__ fin,
                                                                   T *__restrict__ fout, const float *__restrict__ rho,
                                                                   ParticleArrays pa, ParticleForces pf, CellIndex ci,
                                                                   unsigned *err, const float *__restrict__ rest_in,
