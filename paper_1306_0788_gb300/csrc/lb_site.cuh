@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cstring>
 #include <type_traits>
 
 #include "lb_modes.h"
@@ -57,7 +58,45 @@ struct Pop<__nv_bfloat16> {
   static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float sh) { *p = enc(v, sh); }
 };
 
+// 16-bit storage holds both components' values of a direction at a node in one 32-bit word,
+// A in the low half: dec gives (A, B) as floats, enc rounds an (A, B) pair into a word.
+template <class T>
+struct Pair16;
+template <>
+struct Pair16<__half> {
+  static __device__ __forceinline__ float2 dec(unsigned w) {
+    __half2 h;
+    memcpy(&h, &w, 4);
+    return __half22float2(h);
+  }
+  static __device__ __forceinline__ unsigned enc(float2 v) {
+    const __half2 h = __floats2half2_rn(v.x, v.y);
+    unsigned w;
+    memcpy(&w, &h, 4);
+    return w;
+  }
+};
+template <>
+struct Pair16<__nv_bfloat16> {
+  static __device__ __forceinline__ float2 dec(unsigned w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+  }
+  static __device__ __forceinline__ unsigned enc(float2 v) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+    unsigned w;
+    memcpy(&w, &h, 4);
+    return w;
+  }
+};
+
 __device__ __forceinline__ float pop_shift(const StepParams &P, int comp, int i) { return kW[i] * P.rho0[comp]; }
+
+// Element index of direction i of component c at site s: FP32 storage [2][19][N]; 16-bit
+// storage [19][N][2] (the (A, B) pair of a direction in one 32-bit word).
+template <class T>
+__device__ __forceinline__ long long pop_elem(const StepParams &P, int c, int i, long long s) {
+  return kSplitRest<T> ? ((long long)i * P.N + s) * 2 + c : ((long long)c * kQ + i) * P.N + s;
+}
 
 // Sum of the shifts of the 18 moving populations of component comp, (1 - w_0) rho0: the density
 // of a 16-bit node is f_0 + (its 18 stored values) + this.  The update and the mass closure use
@@ -70,7 +109,7 @@ template <class T>
 __device__ __forceinline__ float pop_read(const StepParams &P, const T *buf, const float *rest, int c, int i,
                                           long long s) {
   if (i == 0 && rest) return rest[(long long)c * P.N + s];
-  return Pop<T>::rd(buf + ((long long)c * kQ + i) * P.N + s, kW[i] * P.rho0[c]);
+  return Pop<T>::rd(buf + pop_elem<T>(P, c, i, s), kW[i] * P.rho0[c]);
 }
 template <class T>
 __device__ __forceinline__ void pop_write(const StepParams &P, T *buf, float *rest, int c, int i, long long s,
@@ -78,7 +117,7 @@ __device__ __forceinline__ void pop_write(const StepParams &P, T *buf, float *re
   if (i == 0 && rest)
     rest[(long long)c * P.N + s] = v;
   else
-    Pop<T>::st(buf + ((long long)c * kQ + i) * P.N + s, v, kW[i] * P.rho0[c]);
+    Pop<T>::st(buf + pop_elem<T>(P, c, i, s), v, kW[i] * P.rho0[c]);
 }
 
 struct Coord {
@@ -155,26 +194,24 @@ __device__ __forceinline__ void moments(const StepParams &P, long long s, const 
   // once; the shifts cancel in j' (sum_i w_i c_i = 0)
   constexpr bool kShifted = kSplitRest<T>;
   float rA = 0.f, rB = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-  if (kShifted) {
-    // two-byte values: all 36 loads are issued before any is used, so that enough bytes are in
-    // flight per thread
-    T ea[kQ], eb[kQ];
+  if constexpr (kShifted) {
+    // one 32-bit word per direction holds the (A, B) pair; all 18 loads are issued before any is
+    // used, so that enough bytes are in flight per thread
+    const unsigned *win = reinterpret_cast<const unsigned *>(fin);
+    unsigned w[kQ];
 #pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-      const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // r - c_i
-      ea[i] = __ldg(fin + src);
-      eb[i] = __ldg(finB + src);
-    }
+    for (int i = 1; i < kQ; ++i)
+      w[i] = __ldg(win + i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i])));  // r - c_i
     rA = __ldg(rest + s32);
     rB = __ldg(rest + N32 + s32);
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
-      const float a = Pop<T>::dec_raw(ea[i]), b = Pop<T>::dec_raw(eb[i]);
-      rA += a;
-      rB += b;
-      jx += kCx[i] * (a + b);
-      jy += kCy[i] * (a + b);
-      jz += kCz[i] * (a + b);
+      const float2 v = Pair16<T>::dec(w[i]);
+      rA += v.x;
+      rB += v.y;
+      jx += kCx[i] * (v.x + v.y);
+      jy += kCy[i] * (v.x + v.y);
+      jz += kCz[i] * (v.x + v.y);
     }
   } else {
 #pragma unroll
@@ -464,20 +501,26 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
   // population closes the node's mass
   constexpr bool kShifted = kSplitRest<T> && !kMRT;
   float fA[kQ], fB[kQ];
+  if constexpr (kSplitRest<T>) {
+    // 16-bit storage: one 32-bit word per direction holds the (A, B) pair; the rest populations
+    // are kept in FP32
+    const unsigned *win = reinterpret_cast<const unsigned *>(fin);
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
-    if (kShifted && i > 0) {
-      fA[i] = Pop<T>::ld_raw(fin + src);
-      fB[i] = Pop<T>::ld_raw(finB + src);
-    } else if (!kSplitRest<T> || i > 0) {
-      fA[i] = Pop<T>::ld(fin + src, pop_shift(P, 0, i));
-      fB[i] = Pop<T>::ld(finB + src, pop_shift(P, 1, i));
+    for (int i = 1; i < kQ; ++i) {
+      const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
+      const float2 v = Pair16<T>::dec(__ldg(win + src));
+      fA[i] = kShifted ? v.x : v.x + pop_shift(P, 0, i);
+      fB[i] = kShifted ? v.y : v.y + pop_shift(P, 1, i);
     }
-  }
-  if (kSplitRest<T>) {  // 16-bit storage: the rest populations are kept in FP32
     fA[0] = __ldg(rest_in + s32);
     fB[0] = __ldg(rest_in + N32 + s32);
+  } else {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
+      fA[i] = Pop<T>::ld(fin + src, 0.f);
+      fB[i] = Pop<T>::ld(finB + src, 0.f);
+    }
   }
   // The two components go through the same arithmetic: it runs on (A, B) pairs with the
   // packed two-lane FP32 instructions.
@@ -568,44 +611,45 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
       fB[j] = fj.y;
     }
   }
-  T *foutB = fout + (size_t)kQ * N32;
-  if (kShifted) {
-    // store the 18 shifted values; the rest population takes what keeps the node's mass at its
-    // value before the update (the BGK update and the forcing term conserve it exactly)
-    float mA = rA - shift_sum(P, 0), mB = rB - shift_sum(P, 1);
+  if constexpr (kSplitRest<T>) {
+    unsigned *wout = reinterpret_cast<unsigned *>(fout);
+    if (kShifted) {
+      // store the 18 shifted (A, B) pairs; the rest population takes what keeps the node's mass
+      // at its value before the update (the BGK update and the forcing term conserve it exactly)
+      float2 m = make_float2(rA - shift_sum(P, 0), rB - shift_sum(P, 1));
 #pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-      const T a = Pop<T>::enc_raw(fA[i]), b = Pop<T>::enc_raw(fB[i]);
-      fout[i * N32 + s32] = a;
-      foutB[i * N32 + s32] = b;
-      mA -= Pop<T>::dec_raw(a);
-      mB -= Pop<T>::dec_raw(b);
-    }
-    if (rest_out) {
-      rest_out[s32] = mA;
-      rest_out[N32 + s32] = mB;
-    }
-  } else if (kSplitRest<T> && rest_out) {
-    // 16-bit storage: each moving population is rounded on store; the FP32 rest population takes
-    // the rounding error of the node's 18 others, so the node's total (and the total mass of each
-    // component) is the one of the collision up to FP32 rounding instead of drifting each step.
-    float eA = 0.f, eB = 0.f;
+      for (int i = 1; i < kQ; ++i) {
+        const unsigned w = Pair16<T>::enc(make_float2(fA[i], fB[i]));
+        wout[i * N32 + s32] = w;
+        m = __ffma2_rn(make_float2(-1.f, -1.f), Pair16<T>::dec(w), m);
+      }
+      if (rest_out) {
+        rest_out[s32] = m.x;
+        rest_out[N32 + s32] = m.y;
+      }
+    } else {
+      // MRT: each moving population is rounded on store as f - w_i rho0; the FP32 rest population
+      // takes the rounding error of the node's 18 others, so the node's total (and each
+      // component's mass) is the one of the collision up to FP32 rounding
+      float2 e = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-      const auto a = Pop<T>::enc(fA[i], pop_shift(P, 0, i));
-      const auto b = Pop<T>::enc(fB[i], pop_shift(P, 1, i));
-      fout[i * N32 + s32] = a;
-      foutB[i * N32 + s32] = b;
-      eA += fA[i] - Pop<T>::dec(a, pop_shift(P, 0, i));
-      eB += fB[i] - Pop<T>::dec(b, pop_shift(P, 1, i));
+      for (int i = 1; i < kQ; ++i) {
+        const float2 v = make_float2(fA[i] - pop_shift(P, 0, i), fB[i] - pop_shift(P, 1, i));
+        const unsigned w = Pair16<T>::enc(v);
+        wout[i * N32 + s32] = w;
+        e = __fadd2_rn(e, __ffma2_rn(make_float2(-1.f, -1.f), Pair16<T>::dec(w), v));
+      }
+      if (rest_out) {
+        rest_out[s32] = fA[0] + e.x;
+        rest_out[N32 + s32] = fB[0] + e.y;
+      }
     }
-    rest_out[s32] = fA[0] + eA;
-    rest_out[N32 + s32] = fB[0] + eB;
   } else {
+    T *foutB = fout + (size_t)kQ * N32;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      Pop<T>::st(fout + (i * N32 + s32), fA[i], pop_shift(P, 0, i));
-      Pop<T>::st(foutB + (i * N32 + s32), fB[i], pop_shift(P, 1, i));
+      fout[i * N32 + s32] = fA[i];
+      foutB[i * N32 + s32] = fB[i];
     }
   }
 }
