@@ -91,11 +91,11 @@ struct Pair16<__nv_bfloat16> {
 
 __device__ __forceinline__ float pop_shift(const StepParams &P, int comp, int i) { return kW[i] * P.rho0[comp]; }
 
-// Element index of direction i of component c at site s: FP32 storage [2][19][N]; 16-bit
-// storage [19][N][2] (the (A, B) pair of a direction in one 32-bit word).
+// Element index of direction i of component c at site s: [19][N][2], the (A, B) pair of a
+// direction at a node side by side (one 8-byte word in FP32, one 4-byte word in 16 bits).
 template <class T>
 __device__ __forceinline__ long long pop_elem(const StepParams &P, int c, int i, long long s) {
-  return kSplitRest<T> ? ((long long)i * P.N + s) * 2 + c : ((long long)c * kQ + i) * P.N + s;
+  return ((long long)i * P.N + s) * 2 + c;
 }
 
 // Sum of the shifts of the 18 moving populations of component comp, (1 - w_0) rho0: the density
@@ -189,7 +189,6 @@ __device__ __forceinline__ void moments(const StepParams &P, long long s, const 
   const Coord c = site_coord(P, s);
   const NOff o = neighbour_offsets(P, c);
   const unsigned N32 = (unsigned)P.N, s32 = (unsigned)s;
-  const T *finB = fin + (size_t)kQ * N32;
   // 16-bit storage: the moving populations are summed as stored (shifted) and the shifts added
   // once; the shifts cancel in j' (sum_i w_i c_i = 0)
   constexpr bool kShifted = kSplitRest<T>;
@@ -214,15 +213,15 @@ __device__ __forceinline__ void moments(const StepParams &P, long long s, const 
       jz += kCz[i] * (v.x + v.y);
     }
   } else {
+    const float2 *fin2 = reinterpret_cast<const float2 *>(fin);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // r - c_i
-      const float a = Pop<T>::ld(fin + src, 0.f), b = Pop<T>::ld(finB + src, 0.f);
-      rA += a;
-      rB += b;
-      jx += kCx[i] * (a + b);
-      jy += kCy[i] * (a + b);
-      jz += kCz[i] * (a + b);
+      const float2 v = __ldg(fin2 + i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i])));  // r - c_i
+      rA += v.x;
+      rB += v.y;
+      jx += kCx[i] * (v.x + v.y);
+      jy += kCy[i] * (v.x + v.y);
+      jz += kCz[i] * (v.x + v.y);
     }
   }
   if (kShifted) {
@@ -495,7 +494,6 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
   const Coord c = site_coord(P, s);
   const NOff o = neighbour_offsets(P, c);
   const unsigned N32 = (unsigned)P.N, s32 = (unsigned)s;
-  const T *finB = fin + (size_t)kQ * N32;
   // 16-bit storage with the BGK update: the moving populations stay shifted (f - w_i rho0, as
   // stored) through the update, the shifts folded into its constants, and the FP32 rest
   // population closes the node's mass
@@ -515,11 +513,13 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
     fA[0] = __ldg(rest_in + s32);
     fB[0] = __ldg(rest_in + N32 + s32);
   } else {
+    // FP32 storage: one 8-byte word per direction holds the (A, B) pair
+    const float2 *fin2 = reinterpret_cast<const float2 *>(fin);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
-      fA[i] = Pop<T>::ld(fin + src, 0.f);
-      fB[i] = Pop<T>::ld(finB + src, 0.f);
+      const float2 v = __ldg(fin2 + i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i])));  // pull r - c_i
+      fA[i] = v.x;
+      fB[i] = v.y;
     }
   }
   // The two components go through the same arithmetic: it runs on (A, B) pairs with the
@@ -645,12 +645,9 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
       }
     }
   } else {
-    T *foutB = fout + (size_t)kQ * N32;
+    float2 *fout2 = reinterpret_cast<float2 *>(fout);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      fout[i * N32 + s32] = fA[i];
-      foutB[i * N32 + s32] = fB[i];
-    }
+    for (int i = 0; i < kQ; ++i) fout2[i * N32 + s32] = make_float2(fA[i], fB[i]);
   }
 }
 
