@@ -31,13 +31,13 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes per node moved by k_collide (dram__bytes_read + dram__bytes_write of one ncu capture
 # of the 128^3 case of this workload, scaled per node; profiles/k_collide_slab_droplets_256.md),
 # per storage with a capture of its own.  None while k_collide has changed since the capture.
-COLLIDE_TRAFFIC_BYTES_PER_NODE = {"bf16": 147.2}
+COLLIDE_TRAFFIC_BYTES_PER_NODE = {"fp32": 290.0, "bf16": 147.2}
 # The fluctuating MRT update is bound by instruction issue, not by HBM: warp instructions per
 # node of k_collide<float, true, true> (smsp__inst_executed.sum / nodes of one ncu capture of the
 # 128^3 case, profiles/k_collide_mrt_slab_droplets_256.md), and the issue peak of the GPU: one
 # warp instruction per cycle per scheduler, 4 schedulers per SM, 152 SMs, at the SM clock.
-MRT_WARP_INSTR_PER_NODE = None  # re-measured with the interleaved layout
-MRT_TRAFFIC_BYTES_PER_NODE = None  # DRAM bytes per node of the same capture
+MRT_WARP_INSTR_PER_NODE = 80.71
+MRT_TRAFFIC_BYTES_PER_NODE = 290.9  # DRAM bytes per node of the same capture
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 # The slab/droplet workload uses the density scale of the paper's ferrofluid example (Sec. 4.5):
