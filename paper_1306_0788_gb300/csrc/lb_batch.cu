@@ -411,6 +411,10 @@ size_t particle_bytes(const StepParams &P, int np_max) {
 struct lbmd_batch {
   int dev = 0, sms = 0;
   cudaStream_t st = nullptr;
+  // the particle sort and the pair forces run on a side stream beside the density pass (joined
+  // into st within every captured step; see enqueue_step)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_sorted = nullptr, ev_pairs = nullptr;
   bool own_stream = false;
   size_t budget = 0, used = 0;
   int storage = 0;
@@ -746,20 +750,30 @@ int launch_batched_collide(lbmd_batch *b, int grid, int min_blocks, int tuning) 
 }
 
 // Enqueues one step; returns the number of kernel launches.
+// The particle sort and the pair forces depend on the particles only: they run on the side
+// stream beside the density pass, forked from st at the start of the step and joined before the
+// coupling (sorted rows) and before the particle update (pair forces).
 int enqueue_step(lbmd_batch *b) {
   const BatchDev *B = b->d_batch;
   const int gp = b->grid_particles;
-  kb_bin<<<gp, kBPThreads, 0, b->st>>>(B);
-  kb_scan_partial<<<gp, site::kScanThreads, 0, b->st>>>(B);
-  kb_scan_top<<<1, site::kScanThreads, 0, b->st>>>(B);
-  kb_scan_final<<<gp, site::kScanThreads, 0, b->st>>>(B);
-  kb_scatter<<<gp, kBPThreads, 0, b->st>>>(B);
-  kb_row_sort<<<gp, kBPThreads, 0, b->st>>>(B);
-  kb_permute<<<gp, kBPThreads, 0, b->st>>>(B);
+  cudaStream_t sd = b->side;
+  cudaEventRecord(b->ev_fork, b->st);
+  cudaStreamWaitEvent(sd, b->ev_fork, 0);
+  kb_bin<<<gp, kBPThreads, 0, sd>>>(B);
+  kb_scan_partial<<<gp, site::kScanThreads, 0, sd>>>(B);
+  kb_scan_top<<<1, site::kScanThreads, 0, sd>>>(B);
+  kb_scan_final<<<gp, site::kScanThreads, 0, sd>>>(B);
+  kb_scatter<<<gp, kBPThreads, 0, sd>>>(B);
+  kb_row_sort<<<gp, kBPThreads, 0, sd>>>(B);
+  kb_permute<<<gp, kBPThreads, 0, sd>>>(B);
+  cudaEventRecord(b->ev_sorted, sd);
   launch_batched_moments(b, b->grid_moments);
+  cudaStreamWaitEvent(b->st, b->ev_sorted, 0);
   kb_couple<<<gp, kBPThreads, 0, b->st>>>(B);
-  kb_pairs<<<gp, kBPThreads, 0, b->st>>>(B);
+  kb_pairs<<<gp, kBPThreads, 0, sd>>>(B);
+  cudaEventRecord(b->ev_pairs, sd);
   const int nc = launch_batched_collide(b, b->grid_collide, b->collide_blocks, 0);
+  cudaStreamWaitEvent(b->st, b->ev_pairs, 0);
   kb_integrate<<<gp, kBPThreads, 0, b->st>>>(B);
   kb_advance<<<1, 256, 0, b->st>>>(B);
   return 12 + nc;
@@ -821,6 +835,10 @@ void lbmd_batch_destroy(lbmd_batch *b) {
   cudaFree(b->d_rep); cudaFree(b->d_state); cudaFree(b->d_lay); cudaFree(b->d_left); cudaFree(b->d_rep_slot);
   cudaFree(b->d_batch); cudaFree(b->diag_partial); cudaFree(b->diag_out);
   if (b->own_stream) cudaStreamDestroy(b->st);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_sorted) cudaEventDestroy(b->ev_sorted);
+  if (b->ev_pairs) cudaEventDestroy(b->ev_pairs);
   delete b;
 }
 
@@ -840,6 +858,10 @@ int lbmd_batch_create(size_t mem_budget, int storage, int max_slots, void *strea
   } else {
     b->st = (cudaStream_t)stream;
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_sorted, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_pairs, cudaEventDisableTiming);
   size_t free_b = 0, total_b = 0;
   if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
   if (e == cudaSuccess) {

@@ -13,6 +13,12 @@ using namespace lbmd;
 struct lbmd_ctx {
   lbmd_params prm{};
   cudaStream_t st = nullptr;
+  // the particle sort and the pair forces depend on the particles only, so they run on a side
+  // stream beside the density pass: side waits for the previous step's update (ev_int), st waits
+  // for the sort before the coupling (ev_sorted) and for the pair forces before the update of
+  // the particles (ev_pairs); every step ends on st
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_int = nullptr, ev_sorted = nullptr, ev_pairs = nullptr;
   int dev = 0;
   StepParams P{};
   unsigned char *pop[2] = {nullptr, nullptr};  // population buffers, element type P.storage
@@ -154,14 +160,14 @@ void free_particles(lbmd_ctx *c) {
   c->cap = 0;
 }
 
-int sort_particles(lbmd_ctx *c) {
+int sort_particles(lbmd_ctx *c, cudaStream_t st) {
   const StepParams &P = c->P;
-  CK(cudaMemsetAsync(c->row_count, 0, sizeof(int) * (P.nrows + 1), c->st), "memset rows");
-  launch_bin(P, c->pa[c->pcur], c->row_of, c->row_count, c->err, c->st);
-  launch_scan_rows(P.nrows, c->row_count, c->row_start, c->row_cursor, c->row_bsum, c->st);
-  launch_scatter(P.np, c->row_of, c->row_cursor, c->perm, c->st);
-  launch_row_sort(P, c->row_start, c->pa[c->pcur], c->perm, c->st);
-  launch_permute(P.np, c->perm, c->pa[c->pcur], c->pa[1 - c->pcur], c->slot_of_id, c->st);
+  CK(cudaMemsetAsync(c->row_count, 0, sizeof(int) * (P.nrows + 1), st), "memset rows");
+  launch_bin(P, c->pa[c->pcur], c->row_of, c->row_count, c->err, st);
+  launch_scan_rows(P.nrows, c->row_count, c->row_start, c->row_cursor, c->row_bsum, st);
+  launch_scatter(P.np, c->row_of, c->row_cursor, c->perm, st);
+  launch_row_sort(P, c->row_start, c->pa[c->pcur], c->perm, st);
+  launch_permute(P.np, c->perm, c->pa[c->pcur], c->pa[1 - c->pcur], c->slot_of_id, st);
   c->pcur = 1 - c->pcur;
   return launched(c, "particle sort", 8);
 }
@@ -258,6 +264,14 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
     return fail(nullptr, e == cudaErrorMemoryAllocation ? LBMD_E_NOMEM : LBMD_E_CUDA,
                 std::string("device allocation: ") + cudaGetErrorString(e));
   }
+  if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_int, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_sorted, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_pairs, cudaEventDisableTiming)) != cudaSuccess) {
+    cudaGetLastError();
+    lbmd_destroy(c);
+    return fail(nullptr, LBMD_E_CUDA, std::string("stream / event creation: ") + cudaGetErrorString(e));
+  }
   c->diag_blocks = fluid_sum_blocks(P);
   if ((e = dalloc(&c->diag_partial, (size_t)5 * c->diag_blocks)) != cudaSuccess ||
       (e = dalloc(&c->diag_out, 8)) != cudaSuccess ||
@@ -276,6 +290,13 @@ void lbmd_destroy(lbmd_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->dev);
   if (c->st) cudaStreamSynchronize(c->st);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_int) cudaEventDestroy(c->ev_int);
+  if (c->ev_sorted) cudaEventDestroy(c->ev_sorted);
+  if (c->ev_pairs) cudaEventDestroy(c->ev_pairs);
   dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho); dfree(c->jp); dfree(c->err); dfree(c->rest);
   dfree(c->diag_partial); dfree(c->diag_out);
   free_particles(c);
@@ -417,7 +438,7 @@ int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, con
     CK(cudaMemcpyAsync(c->pa[0].vel, hv.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, c->st), "upload");
     CK(cudaMemcpyAsync(c->pa[0].pid, hid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st), "upload");
     CK(cudaMemsetAsync(c->pf.total, 0, sizeof(float4) * n, c->st), "memset");
-    int r = sort_particles(c);
+    int r = sort_particles(c, c->st);
     if (r) return r;
   }
   CK(cudaStreamSynchronize(c->st), "sync");
@@ -477,20 +498,30 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
     const void *fin = c->pop[c->cur];
     void *fout = c->pop[1 - c->cur];
     int r;
-    if (P.np > 0 && (r = sort_particles(c))) return r;
+    const bool sub = P.np > 0 && P.substeps > 1;
+    const bool overlap = P.np > 0 && !sub;
+    if (overlap) {
+      CK(cudaEventRecord(c->ev_int, c->st), "event");
+      CK(cudaStreamWaitEvent(c->side, c->ev_int, 0), "stream wait");
+      if ((r = sort_particles(c, c->side))) return r;
+      CK(cudaEventRecord(c->ev_sorted, c->side), "event");
+    } else if (P.np > 0 && (r = sort_particles(c, c->st))) {
+      return r;
+    }
     // densities (and j' for the particle coupling) of this step's populations
     launch_moments(P, fin, c->rest, c->rho, P.np > 0 ? c->jp : nullptr, c->st);
     if ((r = launched(c, "moments"))) return r;
-    const bool sub = P.np > 0 && P.substeps > 1;
     ParticleArrays gpa = c->pa[c->pcur];  // what the update gathers the momentum return from
     ParticleForces gpf = c->pf;
     CellIndex gci = ci;
     if (sub) {
       if ((r = substep_particles(c, gpa, gpf, gci))) return r;
     } else if (P.np > 0) {
+      CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
       launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
       launch_pairs(P, c->pa[c->pcur], ci, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf,
-                   c->err, c->st);
+                   c->err, c->side);
+      CK(cudaEventRecord(c->ev_pairs, c->side), "event");
       if ((r = launched(c, "particle forces", 2))) return r;
     }
     if (c->prof) {
@@ -512,6 +543,7 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
     if (sub) {
       c->pcur = 1 - c->pcur;  // the working copy that took the substeps is the particle state
     } else if (P.np > 0) {
+      CK(cudaStreamWaitEvent(c->st, c->ev_pairs, 0), "stream wait");
       launch_integrate(P, c->pa[c->pcur], c->pf, c->err, c->st);
       if ((r = launched(c, "integrate"))) return r;
     }
