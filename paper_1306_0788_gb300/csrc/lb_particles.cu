@@ -10,7 +10,7 @@ namespace {
 
 constexpr int kPBlock = 128;
 
-inline unsigned pgrid(int n) { return (unsigned)((n + kPBlock - 1) / kPBlock); }
+inline unsigned pgrid(long long n) { return (unsigned)((n + kPBlock - 1) / kPBlock); }
 
 // Lattice row (z, y) of each particle and the row histogram.
 __global__ void k_bin(StepParams P, ParticleArrays pa, int *__restrict__ row_of, int *__restrict__ row_count,
@@ -135,9 +135,11 @@ __global__ void k_permute(int np, const int *__restrict__ perm, ParticleArrays s
 __global__ void __launch_bounds__(kPBlock) k_couple(StepParams P, ParticleArrays pa, CellIndex ci,
                                                     const float *__restrict__ rho, const float *__restrict__ jp,
                                                     ParticleForces pf) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  // 8 lanes per particle (site::couple8): the group of a particle returns together
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (int)(t >> 3), k = (int)(t & 7);
   if (p >= P.np) return;
-  site::couple(P, P.step, p, pa, pa, ci, rho, jp, pf);
+  site::couple8(P, P.step, p, k, 0xFFu << (threadIdx.x & 24), pa, ci, rho, jp, pf);
 }
 
 // Pair and bonded forces of every particle (site::pairs).
@@ -256,7 +258,7 @@ void launch_permute(int np, const int *perm, const ParticleArrays &src, const Pa
 }
 void launch_couple(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho, const float *jp,
                    const ParticleForces &pf, cudaStream_t st) {
-  k_couple<<<pgrid(P.np), kPBlock, 0, st>>>(P, pa, ci, rho, jp, pf);
+  k_couple<<<pgrid(8LL * P.np), kPBlock, 0, st>>>(P, pa, ci, rho, jp, pf);
 }
 void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const int *bond_start,
                   const int *bond_other, const int *slot_of_id, const ParticleForces &pf, unsigned *err,

@@ -678,11 +678,66 @@ __device__ __forceinline__ NodeState node_state(const StepParams &P, const float
   return n;
 }
 
-// Coupling forces on particle p (Sec. 2): the coupling velocity u_cpl = (j' + (g^SC + F^fs)/2)/rho
+// Coupling forces on a particle (Sec. 2): the coupling velocity u_cpl = (j' + (g^SC + F^fs)/2)/rho
 // and the node gradients S/c_s^2 are interpolated trilinearly from the 8 corners of the
 // particle's cell; friction + noise (Eq. NEWTON), solvation (Eq. solvation_kappa) and the
 // reaction of the particle's own fluid-side solvation force (Eq. solvation_lambda).  `step`
 // is this lattice's step counter (the noise counter).
+//
+// The interpolated sums of one particle: coupling velocity, node gradients S_A, S_B and the
+// reaction of its own fluid-side solvation force.
+struct CoupleSums {
+  float3 up, gA, gB, fsr;
+};
+
+// Contribution of corner k (offset (k & 1, k >> 1 & 1, k >> 2 & 1)) of the particle's cell.
+__device__ __forceinline__ void couple_corner(const StepParams &P, int k, int4 c, float4 fr, const TypeParams &T,
+                                              const ParticleArrays &list, CellIndex ci,
+                                              const float *__restrict__ rho, const float *__restrict__ jp,
+                                              const ParticleForces &pf, bool with_fsr, CoupleSums &S) {
+  const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
+  const int X = c.x + ox == P.nx ? 0 : c.x + ox;
+  const int Y = c.y + oy == P.ny ? 0 : c.y + oy;
+  const int Z = c.z + oz == P.nz ? 0 : c.z + oz;
+  const NodeState n = node_state(P, rho, X, Y, Z);
+  float3 fA = make_float3(-P.gAB * n.rA * n.SB.x, -P.gAB * n.rA * n.SB.y, -P.gAB * n.rA * n.SB.z);
+  float3 fB = make_float3(-P.gBA * n.rB * n.SA.x, -P.gBA * n.rB * n.SA.y, -P.gBA * n.rB * n.SA.z);
+  gather_coupling(P, X, Y, Z, n.rA, n.rB, list, pf, ci, false, fA, fB);
+  const long long s = site_index(P, X, Y, Z);
+  const float rinv = 1.f / (n.rA + n.rB);
+  const float w = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
+  S.up.x += w * (__ldg(jp + s) + 0.5f * (fA.x + fB.x)) * rinv;
+  S.up.y += w * (__ldg(jp + P.N + s) + 0.5f * (fA.y + fB.y)) * rinv;
+  S.up.z += w * (__ldg(jp + 2 * P.N + s) + 0.5f * (fA.z + fB.z)) * rinv;
+  S.gA.x += w * n.SA.x; S.gA.y += w * n.SA.y; S.gA.z += w * n.SA.z;
+  S.gB.x += w * n.SB.x; S.gB.y += w * n.SB.y; S.gB.z += w * n.SB.z;
+  if (with_fsr && (T.lam[0] != 0.f || T.lam[1] != 0.f)) {
+    const float3 geo = fs_geometry(fr.x - ox, fr.y - oy, fr.z - oz);
+    const float a = T.lam[0] * n.rA + T.lam[1] * n.rB;
+    S.fsr.x += a * geo.x; S.fsr.y += a * geo.y; S.fsr.z += a * geo.z;
+  }
+}
+
+// Forces from the sums: friction + noise (Eq. NEWTON), solvation (Eq. solvation_kappa), the
+// reaction of the fluid-side solvation force.
+__device__ __forceinline__ void couple_finish(const StepParams &P, unsigned long long step, int p,
+                                              const ParticleArrays &self, const ParticleForces &pf, bool with_fsr,
+                                              const TypeParams &T, float4 v, const CoupleSums &S) {
+  float3 R = make_float3(0.f, 0.f, 0.f);
+  if (T.noise_amp > 0.f) {
+    const float3 nn = particle_normals(P.seed, step, (unsigned)self.pid[p]);
+    const float amp = T.noise_amp * P.noise_scale;
+    R = make_float3(amp * nn.x, amp * nn.y, amp * nn.z);
+  }
+  pf.fric[p] = make_float4(-T.gamma * (v.x - S.up.x) + R.x, -T.gamma * (v.y - S.up.y) + R.y,
+                           -T.gamma * (v.z - S.up.z) + R.z, 0.f);
+  const float kA = -T.kappa[0] / kCs2, kB = -T.kappa[1] / kCs2;
+  pf.psA[p] = make_float4(kA * S.gA.x, kA * S.gA.y, kA * S.gA.z, 0.f);
+  pf.psB[p] = make_float4(kB * S.gB.x, kB * S.gB.y, kB * S.gB.z, 0.f);
+  if (with_fsr) pf.fsr[p] = make_float4(S.fsr.x, S.fsr.y, S.fsr.z, 0.f);
+}
+
+// Coupling forces on particle p (Sec. 2), one thread: the 8 corners in turn.
 // `self` holds the particle's own state; `list` and ci the sorted particles whose fluid-side
 // solvation force enters the coupling velocity (the same arrays, except in the later particle
 // substeps, which keep the list of the step's start).  with_fsr: compute the reaction of the
@@ -693,46 +748,30 @@ __device__ __forceinline__ void couple(const StepParams &P, unsigned long long s
                                        const ParticleForces &pf, bool with_fsr = true) {
   const int4 c = self.cell[p];
   const float4 fr = self.frac[p];
-  const float4 v = self.vel[p];
   const TypeParams &T = P.types[c.w];
-  float3 up = make_float3(0.f, 0.f, 0.f), gA = up, gB = up, fsr = up;
-  for (int k = 0; k < 8; ++k) {
-    const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
-    const int X = c.x + ox == P.nx ? 0 : c.x + ox;
-    const int Y = c.y + oy == P.ny ? 0 : c.y + oy;
-    const int Z = c.z + oz == P.nz ? 0 : c.z + oz;
-    const NodeState n = node_state(P, rho, X, Y, Z);
-    float3 fA = make_float3(-P.gAB * n.rA * n.SB.x, -P.gAB * n.rA * n.SB.y, -P.gAB * n.rA * n.SB.z);
-    float3 fB = make_float3(-P.gBA * n.rB * n.SA.x, -P.gBA * n.rB * n.SA.y, -P.gBA * n.rB * n.SA.z);
-    gather_coupling(P, X, Y, Z, n.rA, n.rB, list, pf, ci, false, fA, fB);
-    const long long s = site_index(P, X, Y, Z);
-    const float rinv = 1.f / (n.rA + n.rB);
-    const float w = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
-    up.x += w * (__ldg(jp + s) + 0.5f * (fA.x + fB.x)) * rinv;
-    up.y += w * (__ldg(jp + P.N + s) + 0.5f * (fA.y + fB.y)) * rinv;
-    up.z += w * (__ldg(jp + 2 * P.N + s) + 0.5f * (fA.z + fB.z)) * rinv;
-    gA.x += w * n.SA.x; gA.y += w * n.SA.y; gA.z += w * n.SA.z;
-    gB.x += w * n.SB.x; gB.y += w * n.SB.y; gB.z += w * n.SB.z;
-    if (with_fsr && (T.lam[0] != 0.f || T.lam[1] != 0.f)) {
-      const float3 geo = fs_geometry(fr.x - ox, fr.y - oy, fr.z - oz);
-      const float a = T.lam[0] * n.rA + T.lam[1] * n.rB;
-      fsr.x += a * geo.x; fsr.y += a * geo.y; fsr.z += a * geo.z;
-    }
-  }
-  float3 R = make_float3(0.f, 0.f, 0.f);
-  if (T.noise_amp > 0.f) {
-    const float3 nn = particle_normals(P.seed, step, (unsigned)self.pid[p]);
-    const float amp = T.noise_amp * P.noise_scale;
-    R = make_float3(amp * nn.x, amp * nn.y, amp * nn.z);
-  }
-  pf.fric[p] = make_float4(-T.gamma * (v.x - up.x) + R.x, -T.gamma * (v.y - up.y) + R.y,
-                           -T.gamma * (v.z - up.z) + R.z, 0.f);
-  const float kA = -T.kappa[0] / kCs2, kB = -T.kappa[1] / kCs2;
-  pf.psA[p] = make_float4(kA * gA.x, kA * gA.y, kA * gA.z, 0.f);
-  pf.psB[p] = make_float4(kB * gB.x, kB * gB.y, kB * gB.z, 0.f);
-  if (with_fsr) pf.fsr[p] = make_float4(fsr.x, fsr.y, fsr.z, 0.f);
+  CoupleSums S{};
+  for (int k = 0; k < 8; ++k) couple_corner(P, k, c, fr, T, list, ci, rho, jp, pf, with_fsr, S);
+  couple_finish(P, step, p, self, pf, with_fsr, T, self.vel[p], S);
 }
 
+// The same with 8 lanes per particle: lane k of a group of 8 consecutive lanes takes corner k,
+// the sums are added over the group by shuffles (mask: the group's lanes), and lane 0 writes
+// the forces.  Every lane of the group must call it with the same p.
+__device__ __forceinline__ void couple8(const StepParams &P, unsigned long long step, int p, int k, unsigned mask,
+                                        const ParticleArrays &pa, CellIndex ci, const float *__restrict__ rho,
+                                        const float *__restrict__ jp, const ParticleForces &pf) {
+  const int4 c = pa.cell[p];
+  const float4 fr = pa.frac[p];
+  const TypeParams &T = P.types[c.w];
+  CoupleSums S{};
+  couple_corner(P, k, c, fr, T, pa, ci, rho, jp, pf, true, S);
+  float *x = &S.up.x;  // the 12 sums, contiguous
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1)
+#pragma unroll
+    for (int q = 0; q < 12; ++q) x[q] += __shfl_xor_sync(mask, x[q], off);
+  if (k == 0) couple_finish(P, step, p, pa, pf, true, T, pa.vel[p], S);
+}
 __device__ __forceinline__ int min_image_cells(int d, int n) {
   d = wrapi(d, n);
   return 2 * d > n ? d - n : d;

@@ -14,7 +14,8 @@ def test_served_replicas_equal_alone_runs_and_admission_waits_for_memory():
     from paper_1306_0788_gb300 import lbmd as L
     from paper_1306_0788_gb300 import serving
 
-    reqs = inputs.serving_requests(10, rate=200.0, seed=5, edge=(16, 28), np_max=300, steps=60)
+    # all ten arrive at once (whatever the service speed) and together need more than the budget
+    reqs = inputs.serving_requests(10, rate=1e6, seed=5, edge=(16, 28), np_max=300, steps=60)
     biggest = max(r["edge"] for r in reqs)
     # a budget of about three of the largest replicas: admission has to wait for memory
     with serving.Server(max_slots=16, chunk=7) as probe:
