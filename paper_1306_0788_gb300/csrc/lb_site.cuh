@@ -16,8 +16,10 @@
 namespace lbmd {
 namespace site {
 
-// Load / store of one population value; `shift` = w_i rho0_z (ignored for FP32 storage).
-// enc / dec convert between the FP32 value and the stored element.
+// Read / write of one population value by the element-wise kernels (initialisation, exchange
+// with the host, fields, sums); `shift` = w_i rho0_z (ignored for FP32 storage).  enc / dec
+// convert between the FP32 value and the stored element.  The update and the density pass load
+// and store whole (A, B) words instead (Pair16 below for 16-bit storage).
 template <class T>
 struct Pop;
 // 16-bit storage keeps the rest populations apart, in FP32; FP32 storage has none
@@ -25,35 +27,22 @@ template <class T>
 constexpr bool kSplitRest = !std::is_same<T, float>::value;
 template <>
 struct Pop<float> {
-  static __device__ __forceinline__ float enc_raw(float v) { return v; }
-  static __device__ __forceinline__ float dec_raw(float e) { return e; }
-  static __device__ __forceinline__ float ld_raw(const float *p) { return __ldg(p); }
   static __device__ __forceinline__ float enc(float v, float) { return v; }
   static __device__ __forceinline__ float dec(float e, float) { return e; }
-  static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
   static __device__ __forceinline__ float rd(const float *p, float) { return *p; }
   static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
 };
 template <>
 struct Pop<__half> {
-  // raw: the stored (shifted) value itself, f - w_i rho0
-  static __device__ __forceinline__ __half enc_raw(float v) { return __float2half_rn(v); }
-  static __device__ __forceinline__ float dec_raw(__half e) { return __half2float(e); }
-  static __device__ __forceinline__ float ld_raw(const __half *p) { return __half2float(__ldg(p)); }
   static __device__ __forceinline__ __half enc(float v, float sh) { return __float2half_rn(v - sh); }
   static __device__ __forceinline__ float dec(__half e, float sh) { return __half2float(e) + sh; }
-  static __device__ __forceinline__ float ld(const __half *p, float sh) { return dec(__ldg(p), sh); }
   static __device__ __forceinline__ float rd(const __half *p, float sh) { return dec(*p, sh); }
   static __device__ __forceinline__ void st(__half *p, float v, float sh) { *p = enc(v, sh); }
 };
 template <>
 struct Pop<__nv_bfloat16> {
-  static __device__ __forceinline__ __nv_bfloat16 enc_raw(float v) { return __float2bfloat16_rn(v); }
-  static __device__ __forceinline__ float dec_raw(__nv_bfloat16 e) { return __bfloat162float(e); }
-  static __device__ __forceinline__ float ld_raw(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
   static __device__ __forceinline__ __nv_bfloat16 enc(float v, float sh) { return __float2bfloat16_rn(v - sh); }
   static __device__ __forceinline__ float dec(__nv_bfloat16 e, float sh) { return __bfloat162float(e) + sh; }
-  static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float sh) { return dec(__ldg(p), sh); }
   static __device__ __forceinline__ float rd(const __nv_bfloat16 *p, float sh) { return dec(*p, sh); }
   static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float sh) { *p = enc(v, sh); }
 };
