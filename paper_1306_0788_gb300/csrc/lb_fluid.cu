@@ -1,10 +1,12 @@
 // lb_fluid.cu -- lattice kernels of the coupled Shan-Chen LB / MD step (sm_103a).
 //
-// Storage: populations of both components in one buffer [2][19][nz][ny][nx] (structure of
-// arrays, x fastest).  The buffer holds the post-collision values f*(r, t-1) at their source
-// node; a kernel "pulls" f_i(r, t) = f*_i(r - c_i, t-1), so reads are coalesced along x
-// (shifted by at most one element) and writes are fully coalesced.  Element type: FP32, or a
-// 16-bit type (FP16, BF16) holding the shifted value f_i - w_i rho0_z; all arithmetic is FP32.
+// Storage: populations of both components in one buffer [19][nz][ny][nx][2] (structure of
+// arrays over directions and sites, x fastest, the (A, B) pair of a direction at a node side by
+// side, loaded and stored as one word).  The buffer holds the post-collision values f*(r, t-1)
+// at their source node; a kernel "pulls" f_i(r, t) = f*_i(r - c_i, t-1), so reads are
+// coalesced along x (shifted by at most one node) and writes are fully coalesced.  Element
+// type: FP32, or a 16-bit type (FP16, BF16) holding the shifted value f_i - w_i rho0_z with the
+// rest populations apart in FP32; all arithmetic is FP32.
 #include <type_traits>
 
 #include "lb_site.cuh"
