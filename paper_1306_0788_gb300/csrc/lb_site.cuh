@@ -472,7 +472,8 @@ __device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long lo
 // return from the particles (Sec. 2), barycentric velocity (Eq. momentum_definition), BGK
 // collision with forcing for both components (BGK, or with kMRT the fluctuating MRT of Eq. MODES,
 // `step` being the noise counter), write.  With 16-bit storage rest_in / rest_out are the FP32
-// rest populations (rest_out may be NULL: then f_0 is stored with the others).
+// rest populations (rest_out may be NULL, in the autotuner's trial launches: no rest population
+// is written then).
 template <class T, bool kParticles, bool kMRT = false, bool kBisect = false>
 __device__ __forceinline__ void collide(const StepParams &P, long long s, unsigned long long step,
                                         const T *__restrict__ fin,
