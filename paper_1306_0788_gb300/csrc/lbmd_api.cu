@@ -200,11 +200,17 @@ int substep_particles(lbmd_ctx *c, ParticleArrays &pa, ParticleForces &pf, CellI
     StepParams Q = P;
     Q.step = P.step * (unsigned long long)K + (unsigned long long)sub;
     Q.dt = P.dt / (float)K;
-    launch_couple_sub(Q, C, S, rows, c->rho, c->jp, c->pf, sub, c->rec[0], c->st);
+    // the pair forces (side stream) and the coupling read the same positions and write
+    // different forces; the update of the substep waits for both
+    CK(cudaEventRecord(c->ev_int, c->st), "event");
+    CK(cudaStreamWaitEvent(c->side, c->ev_int, 0), "stream wait");
     StepParams Qp = Q;
     Qp.reach = P.reach + 1;  // particles may have left their row by one cell
     launch_pairs(Qp, C, rows, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf, c->err,
-                 c->st);
+                 c->side);
+    CK(cudaEventRecord(c->ev_pairs, c->side), "event");
+    launch_couple_sub(Q, C, S, rows, c->rho, c->jp, c->pf, sub, c->rec[0], c->st);
+    CK(cudaStreamWaitEvent(c->st, c->ev_pairs, 0), "stream wait");
     launch_integrate_sub(Q, C, S, c->pf, c->err, c->st);
     if ((r = launched(c, "particle substep", 3))) return r;
   }
@@ -499,14 +505,11 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
     void *fout = c->pop[1 - c->cur];
     int r;
     const bool sub = P.np > 0 && P.substeps > 1;
-    const bool overlap = P.np > 0 && !sub;
-    if (overlap) {
+    if (P.np > 0) {  // the particle sort runs beside the density pass
       CK(cudaEventRecord(c->ev_int, c->st), "event");
       CK(cudaStreamWaitEvent(c->side, c->ev_int, 0), "stream wait");
       if ((r = sort_particles(c, c->side))) return r;
       CK(cudaEventRecord(c->ev_sorted, c->side), "event");
-    } else if (P.np > 0 && (r = sort_particles(c, c->st))) {
-      return r;
     }
     // densities (and j' for the particle coupling) of this step's populations
     launch_moments(P, fin, c->rest, c->rho, P.np > 0 ? c->jp : nullptr, c->st);
@@ -515,6 +518,7 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
     ParticleForces gpf = c->pf;
     CellIndex gci = ci;
     if (sub) {
+      CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
       if ((r = substep_particles(c, gpa, gpf, gci))) return r;
     } else if (P.np > 0) {
       CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
