@@ -319,14 +319,18 @@ __global__ void __launch_bounds__(kBPThreads) kb_couple(const BatchDev *__restri
   }
 }
 
+// 8 lanes per particle (site::pairs8); the 8 lanes of a particle stay together through the loop
 __global__ void __launch_bounds__(kBPThreads) kb_pairs(const BatchDev *__restrict__ B) {
   const int np = B->np;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+  const int k = threadIdx.x & 7;
+  const unsigned mask = 0xFFu << (threadIdx.x & 24);
+  const int stride = (gridDim.x * blockDim.x) >> 3;
+  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 3; p < np; p += stride) {
     const int slot = B->pslot[p];
     if (B->left[slot] <= 0) continue;
     const RepDev &R = B->rep[slot];
     const CellIndex ci{B->row_start + B->lay[slot].row0};
-    site::pairs(R.P, p, B->S, ci, nullptr, nullptr, nullptr, B->pf, &B->state[slot].err);
+    site::pairs8(R.P, p, k, mask, B->S, ci, nullptr, nullptr, nullptr, B->pf, &B->state[slot].err);
   }
 }
 

@@ -148,9 +148,11 @@ __global__ void __launch_bounds__(kPBlock) k_pairs(StepParams P, ParticleArrays 
                                                    const int *__restrict__ bond_other,
                                                    const int *__restrict__ slot_of_id, ParticleForces pf,
                                                    unsigned *err) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  // 8 lanes per particle (site::pairs8): the group of a particle returns together
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (int)(t >> 3), k = (int)(t & 7);
   if (p >= P.np) return;
-  site::pairs(P, p, pa, ci, bond_start, bond_other, slot_of_id, pf, err);
+  site::pairs8(P, p, k, 0xFFu << (threadIdx.x & 24), pa, ci, bond_start, bond_other, slot_of_id, pf, err);
 }
 
 // Particle update in place (site::integrate).
@@ -263,7 +265,7 @@ void launch_couple(const StepParams &P, const ParticleArrays &pa, CellIndex ci, 
 void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const int *bond_start,
                   const int *bond_other, const int *slot_of_id, const ParticleForces &pf, unsigned *err,
                   cudaStream_t st) {
-  k_pairs<<<pgrid(P.np), kPBlock, 0, st>>>(P, pa, ci, bond_start, bond_other, slot_of_id, pf, err);
+  k_pairs<<<pgrid(8LL * P.np), kPBlock, 0, st>>>(P, pa, ci, bond_start, bond_other, slot_of_id, pf, err);
 }
 void launch_integrate(const StepParams &P, const ParticleArrays &pa, const ParticleForces &pf, unsigned *err,
                       cudaStream_t st) {

@@ -767,93 +767,120 @@ __device__ __forceinline__ int min_image_cells(int d, int n) {
   return 2 * d > n ? d - n : d;
 }
 
-// Short-range pair forces on particle p (WCA, Sec. 4.1; screened Coulomb, Sec. 4.4) over the
-// rows within `reach` cells, and bonded forces from its own bond list (bond_start indexed by
+// Short-range pair forces (WCA, Sec. 4.1; screened Coulomb, Sec. 4.4) over the rows within
+// `reach` cells of a particle, and bonded forces from its own bond list (bond_start indexed by
 // the particle id, bond_other holding ids, slot_of_id mapping ids to sorted slots; NULL
 // bond_start = no bonds).  Each particle computes its own force (pairs are visited from both
 // ends): no atomics, fixed order.
-__device__ __forceinline__ void pairs(const StepParams &P, int p, const ParticleArrays &pa, CellIndex ci,
-                                      const int *__restrict__ bond_start, const int *__restrict__ bond_other,
-                                      const int *__restrict__ slot_of_id, const ParticleForces &pf,
-                                      unsigned *err) {
+//
+// Pair forces on particle p from the particles of one lattice row of the cell index (-dU/dr),
+// accumulated into F.
+__device__ __forceinline__ void pair_row(const StepParams &P, int p, int4 c, float4 fr, int row, bool allx,
+                                         const ParticleArrays &pa, CellIndex ci, float3 &F) {
+  const int m = P.reach;
+  const float Lx = (float)P.nx, Ly = (float)P.ny, Lz = (float)P.nz;
+  const int q0 = ci.row_start[row], q1 = ci.row_start[row + 1];
+  for (int q = q0; q < q1; ++q) {
+    if (q == p) continue;
+    const int4 cq = pa.cell[q];
+    const int dcx = min_image_cells(c.x - cq.x, P.nx);
+    if (!allx && (dcx > m || dcx < -m)) continue;
+    const float4 fq = pa.frac[q];
+    float dx = (float)dcx + (fr.x - fq.x);
+    float dy_ = (float)min_image_cells(c.y - cq.y, P.ny) + (fr.y - fq.y);
+    float dz_ = (float)min_image_cells(c.z - cq.z, P.nz) + (fr.z - fq.z);
+    dx -= Lx * rintf(dx / Lx);
+    dy_ -= Ly * rintf(dy_ / Ly);
+    dz_ -= Lz * rintf(dz_ / Lz);
+    const float r2 = dx * dx + dy_ * dy_ + dz_ * dz_;
+    float fscal = 0.f;  // -dU/dr / r
+    const PairParams &pp = P.pairs[c.w * LBMD_MAX_TYPES + cq.w];
+    if (pp.eps > 0.f && r2 < pp.rc2) {
+      const float sr2 = pp.sigma2 / r2;
+      const float sr6 = sr2 * sr2 * sr2;
+      fscal += 24.f * pp.eps * (2.f * sr6 * sr6 - sr6) / r2;
+    }
+    const float qq = fr.w * fq.w;
+    if (P.dh_lB != 0.f && qq != 0.f && r2 < P.dh_rc2) {
+      const float r = sqrtf(r2);
+      fscal += qq * P.dh_lB * expf(-P.dh_kappa * r) * (1.f / r2 + P.dh_kappa / r) / r;
+    }
+    F.x += fscal * dx;
+    F.y += fscal * dy_;
+    F.z += fscal * dz_;
+  }
+}
+
+// Bond forces on particle p (FENE or harmonic), accumulated into F; a FENE bond stretched to
+// its maximum sets kErrBond.
+__device__ __forceinline__ void bond_forces(const StepParams &P, int p, int4 c, float4 fr, const ParticleArrays &pa,
+                                            const int *__restrict__ bond_start, const int *__restrict__ bond_other,
+                                            const int *__restrict__ slot_of_id, unsigned *err, float3 &F) {
+  const float Lx = (float)P.nx, Ly = (float)P.ny, Lz = (float)P.nz;
+  const int id = pa.pid[p];
+  for (int b = bond_start[id]; b < bond_start[id + 1]; ++b) {
+    const int q = slot_of_id[bond_other[b]];
+    const int4 cq = pa.cell[q];
+    const float4 fq = pa.frac[q];
+    float dx = (float)min_image_cells(c.x - cq.x, P.nx) + (fr.x - fq.x);
+    float dy_ = (float)min_image_cells(c.y - cq.y, P.ny) + (fr.y - fq.y);
+    float dz_ = (float)min_image_cells(c.z - cq.z, P.nz) + (fr.z - fq.z);
+    dx -= Lx * rintf(dx / Lx);
+    dy_ -= Ly * rintf(dy_ / Ly);
+    dz_ -= Lz * rintf(dz_ / Lz);
+    const float r2 = dx * dx + dy_ * dy_ + dz_ * dz_;
+    float fscal;
+    if (P.bond_kind == LBMD_BOND_FENE) {
+      const float x2 = r2 / (P.bond_r * P.bond_r);
+      if (!(x2 < 1.f)) {
+        atomicOr(err, kErrBond);
+        continue;
+      }
+      fscal = -P.bond_k / (1.f - x2);
+    } else {
+      const float r = sqrtf(r2);
+      fscal = r > 0.f ? -P.bond_k * (r - P.bond_r) / r : 0.f;
+    }
+    F.x += fscal * dx;
+    F.y += fscal * dy_;
+    F.z += fscal * dz_;
+  }
+}
+
+// Pair and bonded forces of particle p with 8 lanes per particle: lane k of a group of 8
+// consecutive lanes scans the rows k, k + 8, ... of the (2 reach + 1)^2 rows around the
+// particle (the whole axis where the lattice is narrower), the forces are added over the group
+// by shuffles (mask: the group's lanes), lane 0 adds the bonds and writes.  Every lane of the
+// group must call it with the same p.
+__device__ __forceinline__ void pairs8(const StepParams &P, int p, int k, unsigned mask, const ParticleArrays &pa,
+                                       CellIndex ci, const int *__restrict__ bond_start,
+                                       const int *__restrict__ bond_other, const int *__restrict__ slot_of_id,
+                                       const ParticleForces &pf, unsigned *err) {
   const int4 c = pa.cell[p];
   const float4 fr = pa.frac[p];
   float3 F = make_float3(0.f, 0.f, 0.f);
   const int m = P.reach;
-  const bool allz = 2 * m + 1 >= P.nz, ally = 2 * m + 1 >= P.ny, allx = 2 * m + 1 >= P.nx;
-  const int z0 = allz ? 0 : -m, z1 = allz ? P.nz - 1 : m;
-  const int y0 = ally ? 0 : -m, y1 = ally ? P.ny - 1 : m;
-  const float Lx = (float)P.nx, Ly = (float)P.ny, Lz = (float)P.nz;
   if (m > 0) {
-    for (int dz = z0; dz <= z1; ++dz) {
+    const bool allz = 2 * m + 1 >= P.nz, ally = 2 * m + 1 >= P.ny, allx = 2 * m + 1 >= P.nx;
+    const int z0 = allz ? 0 : -m, nzw = allz ? P.nz : 2 * m + 1;
+    const int y0 = ally ? 0 : -m, nyw = ally ? P.ny : 2 * m + 1;
+    for (int w = k; w < nzw * nyw; w += 8) {
+      const int dz = z0 + w / nyw, dy = y0 + w % nyw;
       const int cz = allz ? dz : wrapi(c.z + dz, P.nz);
-      for (int dy = y0; dy <= y1; ++dy) {
-        const int cy = ally ? dy : wrapi(c.y + dy, P.ny);
-        const int row = cz * P.ny + cy;
-        const int q0 = ci.row_start[row], q1 = ci.row_start[row + 1];
-        for (int q = q0; q < q1; ++q) {
-          if (q == p) continue;
-          const int4 cq = pa.cell[q];
-          const int dcx = min_image_cells(c.x - cq.x, P.nx);
-          if (!allx && (dcx > m || dcx < -m)) continue;
-          const float4 fq = pa.frac[q];
-          float dx = (float)dcx + (fr.x - fq.x);
-          float dy_ = (float)min_image_cells(c.y - cq.y, P.ny) + (fr.y - fq.y);
-          float dz_ = (float)min_image_cells(c.z - cq.z, P.nz) + (fr.z - fq.z);
-          dx -= Lx * rintf(dx / Lx);
-          dy_ -= Ly * rintf(dy_ / Ly);
-          dz_ -= Lz * rintf(dz_ / Lz);
-          const float r2 = dx * dx + dy_ * dy_ + dz_ * dz_;
-          float fscal = 0.f;  // -dU/dr / r
-          const PairParams &pp = P.pairs[c.w * LBMD_MAX_TYPES + cq.w];
-          if (pp.eps > 0.f && r2 < pp.rc2) {
-            const float sr2 = pp.sigma2 / r2;
-            const float sr6 = sr2 * sr2 * sr2;
-            fscal += 24.f * pp.eps * (2.f * sr6 * sr6 - sr6) / r2;
-          }
-          const float qq = fr.w * fq.w;
-          if (P.dh_lB != 0.f && qq != 0.f && r2 < P.dh_rc2) {
-            const float r = sqrtf(r2);
-            fscal += qq * P.dh_lB * expf(-P.dh_kappa * r) * (1.f / r2 + P.dh_kappa / r) / r;
-          }
-          F.x += fscal * dx;
-          F.y += fscal * dy_;
-          F.z += fscal * dz_;
-        }
-      }
+      const int cy = ally ? dy : wrapi(c.y + dy, P.ny);
+      pair_row(P, p, c, fr, cz * P.ny + cy, allx, pa, ci, F);
     }
   }
-  if (bond_start) {
-    const int id = pa.pid[p];
-    for (int b = bond_start[id]; b < bond_start[id + 1]; ++b) {
-      const int q = slot_of_id[bond_other[b]];
-      const int4 cq = pa.cell[q];
-      const float4 fq = pa.frac[q];
-      float dx = (float)min_image_cells(c.x - cq.x, P.nx) + (fr.x - fq.x);
-      float dy_ = (float)min_image_cells(c.y - cq.y, P.ny) + (fr.y - fq.y);
-      float dz_ = (float)min_image_cells(c.z - cq.z, P.nz) + (fr.z - fq.z);
-      dx -= Lx * rintf(dx / Lx);
-      dy_ -= Ly * rintf(dy_ / Ly);
-      dz_ -= Lz * rintf(dz_ / Lz);
-      const float r2 = dx * dx + dy_ * dy_ + dz_ * dz_;
-      float fscal;
-      if (P.bond_kind == LBMD_BOND_FENE) {
-        const float x2 = r2 / (P.bond_r * P.bond_r);
-        if (!(x2 < 1.f)) {
-          atomicOr(err, kErrBond);
-          continue;
-        }
-        fscal = -P.bond_k / (1.f - x2);
-      } else {
-        const float r = sqrtf(r2);
-        fscal = r > 0.f ? -P.bond_k * (r - P.bond_r) / r : 0.f;
-      }
-      F.x += fscal * dx;
-      F.y += fscal * dy_;
-      F.z += fscal * dz_;
-    }
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1) {
+    F.x += __shfl_xor_sync(mask, F.x, off);
+    F.y += __shfl_xor_sync(mask, F.y, off);
+    F.z += __shfl_xor_sync(mask, F.z, off);
   }
-  pf.pair[p] = make_float4(F.x, F.y, F.z, 0.f);
+  if (k == 0) {
+    if (bond_start) bond_forces(P, p, c, fr, pa, bond_start, bond_other, slot_of_id, err, F);
+    pf.pair[p] = make_float4(F.x, F.y, F.z, 0.f);
+  }
 }
 
 // Particle update of slot p: v += F dt / m, x += v dt, periodic wrap kept as (cell,
