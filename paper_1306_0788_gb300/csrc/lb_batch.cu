@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kBPThreads) kb_couple(const BatchDev *__restri
     if (B->left[slot] <= 0) continue;
     const RepDev &R = B->rep[slot];
     const CellIndex ci{B->row_start + B->lay[slot].row0};
-    site::couple8(R.P, B->state[slot].step, p, k, mask, B->S, ci, R.rho, R.jp, B->pf);
+    site::couple8(R.P, B->state[slot].step, p, k, mask, B->S, B->S, ci, R.rho, R.jp, B->pf);
   }
 }
 

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kPBlock) k_couple(StepParams P, ParticleArrays
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = (int)(t >> 3), k = (int)(t & 7);
   if (p >= P.np) return;
-  site::couple8(P, P.step, p, k, 0xFFu << (threadIdx.x & 24), pa, ci, rho, jp, pf);
+  site::couple8(P, P.step, p, k, 0xFFu << (threadIdx.x & 24), pa, pa, ci, rho, jp, pf);
 }
 
 // Pair and bonded forces of every particle (site::pairs).
@@ -172,9 +172,12 @@ __global__ void __launch_bounds__(kPBlock) k_couple_sub(StepParams P, ParticleAr
                                                         CellIndex ci, const float *__restrict__ rho,
                                                         const float *__restrict__ jp, ParticleForces pf, int sub,
                                                         ReactionRecords rec) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  // 8 lanes per particle (site::couple8); lane 0, which wrote the forces, writes the records
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (int)(t >> 3), k = (int)(t & 7);
   if (p >= P.np) return;
-  site::couple(P, P.step, p, C, S, ci, rho, jp, pf, sub == 0);
+  site::couple8(P, P.step, p, k, 0xFFu << (threadIdx.x & 24), C, S, ci, rho, jp, pf, sub == 0);
+  if (k != 0) return;
   const float invK = 1.f / (float)P.substeps;
   const int r = sub * P.np + p;
   const int4 c = C.cell[p];
@@ -274,7 +277,7 @@ void launch_integrate(const StepParams &P, const ParticleArrays &pa, const Parti
 void launch_couple_sub(const StepParams &P, const ParticleArrays &C, const ParticleArrays &S, CellIndex ci,
                        const float *rho, const float *jp, const ParticleForces &pf, int sub,
                        const ReactionRecords &rec, cudaStream_t st) {
-  k_couple_sub<<<pgrid(P.np), kPBlock, 0, st>>>(P, C, S, ci, rho, jp, pf, sub, rec);
+  k_couple_sub<<<pgrid(8LL * P.np), kPBlock, 0, st>>>(P, C, S, ci, rho, jp, pf, sub, rec);
 }
 void launch_integrate_sub(const StepParams &P, const ParticleArrays &C, const ParticleArrays &S,
                           const ParticleForces &pf, unsigned *err, cudaStream_t st) {

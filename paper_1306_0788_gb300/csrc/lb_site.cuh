@@ -727,40 +727,28 @@ __device__ __forceinline__ void couple_finish(const StepParams &P, unsigned long
   if (with_fsr) pf.fsr[p] = make_float4(S.fsr.x, S.fsr.y, S.fsr.z, 0.f);
 }
 
-// Coupling forces on particle p (Sec. 2), one thread: the 8 corners in turn.
+// Coupling forces on particle p with 8 lanes per particle: lane k of a group of 8 consecutive
+// lanes takes corner k, the sums are added over the group by shuffles (mask: the group's
+// lanes), and lane 0 writes the forces.  Every lane of the group must call it with the same p.
 // `self` holds the particle's own state; `list` and ci the sorted particles whose fluid-side
 // solvation force enters the coupling velocity (the same arrays, except in the later particle
 // substeps, which keep the list of the step's start).  with_fsr: compute the reaction of the
 // particle's own fluid-side solvation force (else keep the value in pf.fsr).
-__device__ __forceinline__ void couple(const StepParams &P, unsigned long long step, int p,
-                                       const ParticleArrays &self, const ParticleArrays &list, CellIndex ci,
-                                       const float *__restrict__ rho, const float *__restrict__ jp,
-                                       const ParticleForces &pf, bool with_fsr = true) {
+__device__ __forceinline__ void couple8(const StepParams &P, unsigned long long step, int p, int k, unsigned mask,
+                                        const ParticleArrays &self, const ParticleArrays &list, CellIndex ci,
+                                        const float *__restrict__ rho, const float *__restrict__ jp,
+                                        const ParticleForces &pf, bool with_fsr = true) {
   const int4 c = self.cell[p];
   const float4 fr = self.frac[p];
   const TypeParams &T = P.types[c.w];
   CoupleSums S{};
-  for (int k = 0; k < 8; ++k) couple_corner(P, k, c, fr, T, list, ci, rho, jp, pf, with_fsr, S);
-  couple_finish(P, step, p, self, pf, with_fsr, T, self.vel[p], S);
-}
-
-// The same with 8 lanes per particle: lane k of a group of 8 consecutive lanes takes corner k,
-// the sums are added over the group by shuffles (mask: the group's lanes), and lane 0 writes
-// the forces.  Every lane of the group must call it with the same p.
-__device__ __forceinline__ void couple8(const StepParams &P, unsigned long long step, int p, int k, unsigned mask,
-                                        const ParticleArrays &pa, CellIndex ci, const float *__restrict__ rho,
-                                        const float *__restrict__ jp, const ParticleForces &pf) {
-  const int4 c = pa.cell[p];
-  const float4 fr = pa.frac[p];
-  const TypeParams &T = P.types[c.w];
-  CoupleSums S{};
-  couple_corner(P, k, c, fr, T, pa, ci, rho, jp, pf, true, S);
+  couple_corner(P, k, c, fr, T, list, ci, rho, jp, pf, with_fsr, S);
   float *x = &S.up.x;  // the 12 sums, contiguous
 #pragma unroll
   for (int off = 4; off > 0; off >>= 1)
 #pragma unroll
     for (int q = 0; q < 12; ++q) x[q] += __shfl_xor_sync(mask, x[q], off);
-  if (k == 0) couple_finish(P, step, p, pa, pf, true, T, pa.vel[p], S);
+  if (k == 0) couple_finish(P, step, p, self, pf, with_fsr, T, self.vel[p], S);
 }
 __device__ __forceinline__ int min_image_cells(int d, int n) {
   d = wrapi(d, n);
