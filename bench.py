@@ -289,6 +289,7 @@ def run_cuda(args):
                    collision=L.LBMD_COLLISION_MRT if mrt else L.LBMD_COLLISION_BGK,
                    md_substeps=args.md_substeps)
     ctx, _ = L.lbmd_create(prm, stream)
+    L.lbmd_set_graphs(ctx, args.launch == "graph")
     L.lbmd_set_types(ctx, [L.lbmd_ptype(*t) for t in types], [L.lbmd_pair(0, 0, *extra.get("wca", (1.0, 1.0)))])
     if "dh" in extra:
         L.lbmd_set_debye_hueckel(ctx, *extra["dh"])
@@ -302,10 +303,11 @@ def run_cuda(args):
         if dist is not None:
             dist.barrier()
 
-    # warm-up
+    # warm-up (with the update's timing events on, so that the graphs replayed in the timed
+    # region are recorded here)
+    L.lbmd_profile_enable(ctx, True)
     L.lbmd_step(ctx, args.warmup)
     barrier()
-    L.lbmd_profile_enable(ctx, True)
     L.lbmd_profile_read(ctx, reset=True)
     launches0 = L.lbmd_launch_count(ctx)
     sampler = ClockSampler(dev)
@@ -395,7 +397,7 @@ def run_cuda(args):
                        "md_substeps": args.md_substeps, "bonds": int(len(extra.get("bonds", []))),
                        "description": WORKLOADS[args.workload][2],
                        "lattice": list(dims), "particles": npart, "tau_r": 1.0, "g_AB": g_ab, "kT": kT,
-                       "storage": args.storage,
+                       "storage": args.storage, "launch": args.launch,
                        "collision": ("fluctuating MRT (Eq. MODES), eigenvalues -1, fluid noise at kT"
                                      if mrt else "BGK"),
                        "parallelism": "replicas" if world > 1 else "single",
@@ -549,6 +551,8 @@ def main():
     ap.add_argument("--collision", choices=["bgk", "mrt"], default="bgk",
                     help="BGK, or the fluctuating MRT collision with fluid noise at the workload's kT")
     ap.add_argument("--md-substeps", type=int, default=1, help="particle substeps per lattice step")
+    ap.add_argument("--launch", choices=["graph", "stream"], default="graph",
+                    help="lbmd_step launch mode: replayed two-step graphs, or every kernel one by one")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

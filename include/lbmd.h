@@ -175,6 +175,21 @@ int lbmd_set_bonds(lbmd_ctx *ctx, int nb, const int *pairs, int kind, double k, 
  * call. */
 int lbmd_step(lbmd_ctx *ctx, int nsteps);
 
+/* Launch mode of lbmd_step (no counterpart in the paper: a property of the GPU code).  With
+ * on != 0 (the default) lbmd_step takes its steps two at a time by replaying a CUDA graph of
+ * two coupled steps, recorded at the first such call for the current buffers on a private
+ * stream and launched into the context stream; an odd last step is launched directly.  The
+ * results are bit-identical to on = 0, where every kernel is launched one by one; the graph
+ * saves the launch latency that dominates small lattices.  The particle kernels read their noise
+ * counter from a device-resident step base; the fluctuating MRT update gets its counter written
+ * into its graph nodes before each replay (where those nodes are not recognised, the context
+ * falls back to launches one by one).  Every setter (types, Debye-Hueckel,
+ * fluid, populations, particles, bonds, profiling) drops the recorded graphs; recording
+ * allocates nothing while it runs (the sub-stepping records are allocated first).  Returns
+ * LBMD_E_INVALID_ARG for a NULL context; errors of recording surface at the next lbmd_step as
+ * LBMD_E_CUDA. */
+int lbmd_set_graphs(lbmd_ctx *ctx, int on);
+
 /* Wait for the context stream; returns the first recorded device error, if any. */
 int lbmd_sync(lbmd_ctx *ctx);
 int lbmd_clear_error(lbmd_ctx *ctx);
@@ -202,7 +217,8 @@ int64_t lbmd_step_count(const lbmd_ctx *ctx);
 int lbmd_profile_enable(lbmd_ctx *ctx, int on);
 int lbmd_profile_read(lbmd_ctx *ctx, double *ms, int64_t *launches, int reset);
 
-/* Number of kernel launches issued by lbmd_step so far (host-side count). */
+/* Number of kernel launches issued by lbmd_step so far (host-side count; a graph replay counts
+ * the kernels it holds, the step counter's own one-thread kernels included). */
 int64_t lbmd_launch_count(const lbmd_ctx *ctx);
 
 /* Total mass of each component and fluid momentum -- the same FP64 sums as out[0..4] of

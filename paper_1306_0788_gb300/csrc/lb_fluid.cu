@@ -243,6 +243,40 @@ void launch_collide(const StepParams &P, const void *fin, void *fout, float *res
       k_collide<T, false, false><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
   });
 }
+
+template <class T>
+bool is_noisy_update_of(const void *fn) {
+  return fn == reinterpret_cast<const void *>(&k_collide<T, true, true, true>) ||
+         fn == reinterpret_cast<const void *>(&k_collide<T, true, true>) ||
+         fn == reinterpret_cast<const void *>(&k_collide<T, false, true>);
+}
+
+bool is_noisy_update(const void *fn) {
+  return is_noisy_update_of<float>(fn) || is_noisy_update_of<__half>(fn) || is_noisy_update_of<__nv_bfloat16>(fn);
+}
+
+template <class... A>
+constexpr int arity(void (*)(A...)) {
+  return (int)sizeof...(A);
+}
+
+cudaError_t set_update_step(cudaGraphExec_t exec, cudaGraphNode_t node, unsigned long long step) {
+  constexpr int kArgs = arity(&k_collide<float, false, true>);
+  cudaKernelNodeParams kp;
+  cudaError_t e = cudaGraphKernelNodeGetParams(node, &kp);
+  if (e != cudaSuccess) return e;
+  if (!is_noisy_update(kp.func) || !kp.kernelParams) return cudaErrorInvalidValue;
+  StepParams P;
+  std::memcpy(&P, kp.kernelParams[0], sizeof(P));  // the node's own copy of the parameters
+  P.step = step;
+  void *args[kArgs];
+  for (int k = 0; k < kArgs; ++k) args[k] = kp.kernelParams[k];
+  args[0] = &P;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  return cudaGraphExecKernelNodeSetParams(exec, node, &kp);  // copies the values
+}
+
 void launch_fields(const StepParams &P, const void *store, const float *rest, const float *rho, float *rhoA,
                    float *rhoB, float *u, cudaStream_t st) {
   with_storage(P, [&](auto t) {
@@ -263,6 +297,19 @@ void launch_fluid_sums(const StepParams &P, const void *store, const float *rest
 }
 void launch_finish_sums(const double *partial, int nblocks, int nvals, double *out, cudaStream_t st) {
   k_finish_sums<<<1, 32, 0, st>>>(partial, nblocks, nvals, out);
+}
+
+// The step base of replayed step graphs (one thread: a write, or an increment at the end of a
+// replay, ordered after every launch of the replay that reads it).
+__global__ void k_set_step(unsigned long long *base, unsigned long long value) { *base = value; }
+__global__ void k_advance_step(unsigned long long *base, unsigned long long n) { *base += n; }
+
+void launch_set_step(unsigned long long *base, unsigned long long value, cudaStream_t st) {
+  k_set_step<<<1, 1, 0, st>>>(base, value);
+}
+
+void launch_advance_step(unsigned long long *base, unsigned long long n, cudaStream_t st) {
+  k_advance_step<<<1, 1, 0, st>>>(base, n);
 }
 
 }  // namespace lbmd

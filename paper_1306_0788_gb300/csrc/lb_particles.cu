@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kPBlock) k_couple(StepParams P, ParticleArrays
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = (int)(t >> 3), k = (int)(t & 7);
   if (p >= P.np) return;
-  site::couple8(P, P.step, p, k, 0xFFu << (threadIdx.x & 24), pa, pa, ci, rho, jp, pf);
+  site::couple8(P, noise_step(P, P.step), p, k, 0xFFu << (threadIdx.x & 24), pa, pa, ci, rho, jp, pf);
 }
 
 // Pair and bonded forces of every particle (site::pairs).
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kPBlock) k_couple_sub(StepParams P, ParticleAr
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = (int)(t >> 3), k = (int)(t & 7);
   if (p >= P.np) return;
-  site::couple8(P, P.step, p, k, 0xFFu << (threadIdx.x & 24), C, S, ci, rho, jp, pf, sub == 0);
+  site::couple8(P, noise_step(P, P.step), p, k, 0xFFu << (threadIdx.x & 24), C, S, ci, rho, jp, pf, sub == 0);
   if (k != 0) return;
   const float invK = 1.f / (float)P.substeps;
   const int r = sub * P.np + p;

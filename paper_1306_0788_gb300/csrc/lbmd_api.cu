@@ -10,6 +10,24 @@
 
 using namespace lbmd;
 
+namespace {
+constexpr int kGraphSteps = 2;  // steps per replayed graph: both buffer pairs return to their start
+
+// A recorded sequence of kGraphSteps coupled steps (lbmd_set_graphs).
+struct StepGraph {
+  cudaGraph_t graph = nullptr;  // kept for the event nodes' handles
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;                            // kernels per replay
+  cudaGraphNode_t ev_node[2 * kGraphSteps] = {};  // k_collide timing events, retargeted per replay
+  // the noisy MRT update of each step: its node and the counter offset it was recorded with
+  // (its counter is patched per replay; see is_noisy_update)
+  cudaGraphNode_t upd_node[kGraphSteps] = {};
+  unsigned long long upd_off[kGraphSteps] = {};
+  int n_upd = 0;
+};
+constexpr int kGraphUnavailable = 1;  // record_steps: take the steps one by one instead
+}  // namespace
+
 struct lbmd_ctx {
   lbmd_params prm{};
   cudaStream_t st = nullptr;
@@ -53,6 +71,16 @@ struct lbmd_ctx {
   size_t ev_used = 0;
   double prof_ms = 0.0;
   int64_t prof_launches = 0;
+  // replayed step graphs: recorded on gst (never on the caller's stream, which may carry other
+  // work), one per parity of (cur, pcur) at the replay's start, launched into st; the kernels
+  // read their noise counter's base from step_base, which holds dev_step once the work
+  // enqueued so far has run (-1: not known)
+  bool graphs = true;
+  cudaStream_t gst = nullptr;
+  StepGraph graph[2][2];
+  unsigned long long *step_base = nullptr;
+  int64_t dev_step = -1;
+  cudaEvent_t ph[2 * kGraphSteps] = {};  // stand-ins for the timing events while recording
 };
 
 namespace {
@@ -199,6 +227,7 @@ int substep_particles(lbmd_ctx *c, ParticleArrays &pa, ParticleForces &pf, CellI
   for (int sub = 0; sub < K; ++sub) {
     StepParams Q = P;
     Q.step = P.step * (unsigned long long)K + (unsigned long long)sub;
+    Q.step_mul = (unsigned long long)K;
     Q.dt = P.dt / (float)K;
     // the pair forces (side stream) and the coupling read the same positions and write
     // different forces; the update of the substep waits for both
@@ -231,6 +260,185 @@ int substep_particles(lbmd_ctx *c, ParticleArrays &pa, ParticleForces &pf, CellI
   pf.psA = c->rec[1].psA;
   pf.psB = c->rec[1].psB;
   ci = CellIndex{c->row_start};
+  return LBMD_OK;
+}
+
+// Timing events of k_collide (lbmd_profile_enable): the pool holds at least n unused ones.
+int reserve_events(lbmd_ctx *c, size_t n) {
+  while (c->ev.size() < c->ev_used + n) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e), "event");
+    c->ev.push_back(e);
+  }
+  return LBMD_OK;
+}
+
+// One coupled step on st and side.  `step` is the noise counter the kernels get: the lattice
+// step, or, while a graph is recorded, the step's offset in it (the kernels add the base).
+// t0, t1 (or null): events recorded around the lattice update, with `flags`.
+int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t1, unsigned flags) {
+  StepParams &P = c->P;
+  P.step = step;
+  const CellIndex ci{c->row_start};
+  const void *fin = c->pop[c->cur];
+  void *fout = c->pop[1 - c->cur];
+  int r;
+  const bool sub = P.np > 0 && P.substeps > 1;
+  if (P.np > 0) {  // the particle sort runs beside the density pass
+    CK(cudaEventRecord(c->ev_int, c->st), "event");
+    CK(cudaStreamWaitEvent(c->side, c->ev_int, 0), "stream wait");
+    if ((r = sort_particles(c, c->side))) return r;
+    CK(cudaEventRecord(c->ev_sorted, c->side), "event");
+  }
+  // densities (and j' for the particle coupling) of this step's populations
+  launch_moments(P, fin, c->rest, c->rho, P.np > 0 ? c->jp : nullptr, c->st);
+  if ((r = launched(c, "moments"))) return r;
+  ParticleArrays gpa = c->pa[c->pcur];  // what the update gathers the momentum return from
+  ParticleForces gpf = c->pf;
+  CellIndex gci = ci;
+  if (sub) {
+    CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
+    if ((r = substep_particles(c, gpa, gpf, gci))) return r;
+  } else if (P.np > 0) {
+    CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
+    launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
+    launch_pairs(P, c->pa[c->pcur], ci, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf,
+                 c->err, c->side);
+    CK(cudaEventRecord(c->ev_pairs, c->side), "event");
+    if ((r = launched(c, "particle forces", 2))) return r;
+  }
+  if (t0) CK(cudaEventRecordWithFlags(t0, c->st, flags), "event");
+  launch_collide(P, fin, fout, c->rest, c->rho, gpa, gpf, gci, c->err, c->st);
+  if ((r = launched(c, "collide"))) return r;
+  if (t1) CK(cudaEventRecordWithFlags(t1, c->st, flags), "event");
+  if (sub) {
+    c->pcur = 1 - c->pcur;  // the working copy that took the substeps is the particle state
+  } else if (P.np > 0) {
+    CK(cudaStreamWaitEvent(c->st, c->ev_pairs, 0), "stream wait");
+    launch_integrate(P, c->pa[c->pcur], c->pf, c->err, c->st);
+    if ((r = launched(c, "integrate"))) return r;
+  }
+  c->cur = 1 - c->cur;
+  c->steps++;
+  return LBMD_OK;
+}
+
+void drop_graphs(lbmd_ctx *c) {
+  for (auto &row : c->graph)
+    for (StepGraph &g : row) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);  // a launch in flight completes first
+      if (g.graph) cudaGraphDestroy(g.graph);
+      g = StepGraph{};
+    }
+}
+
+// Records kGraphSteps steps from the current buffers into g: on the private stream gst, with
+// the noise counters relative to the device-resident step base, the base advanced at the end.
+// Nothing runs; the context's host state is left as it was.
+int record_steps(lbmd_ctx *c, StepGraph &g) {
+  const StepParams &P = c->P;
+  int r;
+  if (P.np > 0 && P.substeps > 1 && (r = ensure_records(c, (long long)P.substeps * P.np)))
+    return r;  // no allocation while recording
+  if (!c->gst) CK(cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking), "graph stream");
+  if (!c->step_base) CK(dalloc(&c->step_base, 1), "alloc step base");
+  if (c->prof)
+    for (cudaEvent_t &e : c->ph)
+      if (!e) CK(cudaEventCreate(&e), "event");
+  const int cur0 = c->cur, pcur0 = c->pcur;
+  const int64_t steps0 = c->steps, launches0 = c->launches;
+  cudaStream_t user = c->st;
+  CK(cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal), "begin capture");
+  c->st = c->gst;
+  c->P.step_base = c->step_base;
+  r = LBMD_OK;
+  for (int j = 0; j < kGraphSteps && !r; ++j)
+    r = one_step(c, (unsigned long long)j, c->prof ? c->ph[2 * j] : nullptr, c->prof ? c->ph[2 * j + 1] : nullptr,
+                 cudaEventRecordExternal);
+  if (!r) {
+    launch_advance_step(c->step_base, kGraphSteps, c->gst);
+    r = launched(c, "step counter");
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->gst, &graph);
+  const bool back = c->cur == cur0 && c->pcur == pcur0;
+  c->st = user;
+  c->P.step_base = nullptr;
+  c->cur = cur0;
+  c->pcur = pcur0;
+  c->steps = steps0;
+  g.launches = c->launches - launches0;
+  c->launches = launches0;
+  if (r || e != cudaSuccess || !back) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (r) return r;
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+    return fail(c, LBMD_E_STATE, "recorded steps do not return to their buffers");
+  }
+  g.graph = graph;
+  cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  const bool noisy = c->P.collision == LBMD_COLLISION_MRT && c->P.fluct;
+  if (ei == cudaSuccess && (c->prof || noisy)) {  // find the timing stand-ins and the noisy updates
+    size_t n = 0;
+    ei = cudaGraphGetNodes(graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (ei == cudaSuccess) ei = cudaGraphGetNodes(graph, nodes.data(), &n);
+    for (size_t k = 0; k < n && ei == cudaSuccess; ++k) {
+      cudaGraphNodeType t;
+      if ((ei = cudaGraphNodeGetType(nodes[k], &t)) != cudaSuccess) break;
+      if (t == cudaGraphNodeTypeEventRecord) {
+        cudaEvent_t ev = nullptr;
+        if ((ei = cudaGraphEventRecordNodeGetEvent(nodes[k], &ev)) != cudaSuccess) break;
+        for (int q = 0; q < 2 * kGraphSteps; ++q)
+          if (ev == c->ph[q]) g.ev_node[q] = nodes[k];
+      } else if (t == cudaGraphNodeTypeKernel && noisy) {
+        cudaKernelNodeParams kp;
+        if ((ei = cudaGraphKernelNodeGetParams(nodes[k], &kp)) != cudaSuccess) break;
+        if (!is_noisy_update(kp.func) || !kp.kernelParams || g.n_upd == kGraphSteps) continue;
+        StepParams Q;
+        std::memcpy(&Q, kp.kernelParams[0], sizeof(Q));
+        g.upd_node[g.n_upd] = nodes[k];
+        g.upd_off[g.n_upd++] = Q.step;
+      }
+    }
+    for (int q = 0; q < 2 * kGraphSteps && ei == cudaSuccess && c->prof; ++q)
+      if (!g.ev_node[q]) ei = cudaErrorInvalidValue;
+  }
+  if (ei != cudaSuccess) {
+    drop_graphs(c);
+    cudaGetLastError();
+    return cuda_fail(c, ei, "graph instantiation");
+  }
+  if (noisy && g.n_upd != kGraphSteps) {  // the update's nodes were not recognised
+    drop_graphs(c);
+    c->graphs = false;
+    return kGraphUnavailable;
+  }
+  return LBMD_OK;
+}
+
+// kGraphSteps steps by one launch of the graph recorded for the current buffers.
+int replay_steps(lbmd_ctx *c) {
+  StepGraph &g = c->graph[c->cur][c->pcur];
+  int r;
+  if (!g.exec && (r = record_steps(c, g))) return r;
+  if (c->dev_step != c->steps) {  // steps were taken without the graph since it last ran
+    launch_set_step(c->step_base, (unsigned long long)c->steps, c->st);
+    if ((r = launched(c, "step counter"))) return r;
+  }
+  if (c->prof) {
+    if ((r = reserve_events(c, 2 * kGraphSteps))) return r;
+    for (int q = 0; q < 2 * kGraphSteps; ++q)
+      CK(cudaGraphExecEventRecordNodeSetEvent(g.exec, g.ev_node[q], c->ev[c->ev_used + q]), "timing event");
+  }
+  for (int q = 0; q < g.n_upd; ++q)
+    CK(set_update_step(g.exec, g.upd_node[q], (unsigned long long)c->steps + g.upd_off[q]), "update counter");
+  CK(cudaGraphLaunch(g.exec, c->st), "graph launch");
+  if (c->prof) c->ev_used += 2 * kGraphSteps;
+  c->launches += g.launches;
+  c->steps += kGraphSteps;
+  c->dev_step = c->steps;
   return LBMD_OK;
 }
 
@@ -303,6 +511,11 @@ void lbmd_destroy(lbmd_ctx *c) {
   if (c->ev_int) cudaEventDestroy(c->ev_int);
   if (c->ev_sorted) cudaEventDestroy(c->ev_sorted);
   if (c->ev_pairs) cudaEventDestroy(c->ev_pairs);
+  drop_graphs(c);
+  if (c->gst) cudaStreamDestroy(c->gst);
+  for (cudaEvent_t e : c->ph)
+    if (e) cudaEventDestroy(e);
+  dfree(c->step_base);
   dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho); dfree(c->jp); dfree(c->err); dfree(c->rest);
   dfree(c->diag_partial); dfree(c->diag_out);
   free_particles(c);
@@ -316,6 +529,7 @@ void lbmd_destroy(lbmd_ctx *c) {
 int lbmd_set_types(lbmd_ctx *c, int ntypes, const lbmd_ptype *types, int npairs, const lbmd_pair *pairs,
                    unsigned *warnings) {
   if (!c) return LBMD_E_INVALID_ARG;
+  drop_graphs(c);  // every setter: the recorded steps hold the old parameters and buffers
   if (warnings) *warnings = 0;
   unsigned w = 0;
   std::string why;
@@ -328,6 +542,7 @@ int lbmd_set_types(lbmd_ctx *c, int ntypes, const lbmd_ptype *types, int npairs,
 
 int lbmd_set_debye_hueckel(lbmd_ctx *c, double lB, double kappa_D, double rc) {
   if (!c) return LBMD_E_INVALID_ARG;
+  drop_graphs(c);
   std::string why;
   const int r = apply_debye_hueckel(c->P, lB, kappa_D, rc, why);
   return r ? fail(c, r, why) : LBMD_OK;
@@ -336,6 +551,7 @@ int lbmd_set_debye_hueckel(lbmd_ctx *c, double lB, double kappa_D, double rc) {
 int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const float *u) {
   if (!c || !rhoA || !rhoB) return c ? fail(c, LBMD_E_INVALID_ARG, "null density") : LBMD_E_INVALID_ARG;
   cudaSetDevice(c->dev);
+  drop_graphs(c);
   const long long N = c->P.N;
   for (long long s = 0; s < N; ++s)
     if (!(rhoA[s] > 0.f) || !(rhoB[s] > 0.f) || !std::isfinite(rhoA[s]) || !std::isfinite(rhoB[s]))
@@ -362,6 +578,7 @@ int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const flo
 int lbmd_set_populations(lbmd_ctx *c, int comp, const float *f) {
   if (!c || !f || comp < 0 || comp > 1) return c ? fail(c, LBMD_E_INVALID_ARG, "bad arguments") : LBMD_E_INVALID_ARG;
   cudaSetDevice(c->dev);
+  drop_graphs(c);
   float *stage = reinterpret_cast<float *>(c->pop[1 - c->cur]);
   CK(cudaMemcpyAsync(stage, f, sizeof(float) * kQ * (size_t)c->P.N, cudaMemcpyHostToDevice, c->st), "upload f");
   launch_restream(c->P, stage, comp, c->pop[c->cur], c->rest, c->st);
@@ -389,6 +606,7 @@ int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, con
   if (n < 0 || (n > 0 && (!x || !v || !type))) return fail(c, LBMD_E_INVALID_ARG, "bad particle arrays");
   if (n > 0 && !c->types_set) return fail(c, LBMD_E_STATE, "set the particle types first");
   cudaSetDevice(c->dev);
+  drop_graphs(c);
   StepParams &P = c->P;
   std::vector<int4> hc;
   std::vector<float4> hf, hv;
@@ -453,6 +671,7 @@ int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, con
 
 int lbmd_set_bonds(lbmd_ctx *c, int nb, const int *pairs, int kind, double k, double r) {
   if (!c) return LBMD_E_INVALID_ARG;
+  drop_graphs(c);
   if (nb < 0 || (nb > 0 && !pairs)) return fail(c, LBMD_E_INVALID_ARG, "bad bond list");
   if (kind != LBMD_BOND_FENE && kind != LBMD_BOND_HARMONIC) return fail(c, LBMD_E_INVALID_ARG, "unknown bond kind");
   if (nb > 0 && (!(k >= 0.0) || !(r > 0.0 || kind == LBMD_BOND_HARMONIC)))
@@ -496,64 +715,32 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
   cudaSetDevice(c->dev);
   if (c->nbonds > 0 && c->bond_np != c->np)
     return fail(c, LBMD_E_STATE, "bonds refer to a different particle set; call lbmd_set_bonds again");
-  StepParams &P = c->P;
-  P.np = c->np;
-  const CellIndex ci{c->row_start};
-  for (int s = 0; s < nsteps; ++s) {
-    P.step = (unsigned long long)c->steps;
-    const void *fin = c->pop[c->cur];
-    void *fout = c->pop[1 - c->cur];
-    int r;
-    const bool sub = P.np > 0 && P.substeps > 1;
-    if (P.np > 0) {  // the particle sort runs beside the density pass
-      CK(cudaEventRecord(c->ev_int, c->st), "event");
-      CK(cudaStreamWaitEvent(c->side, c->ev_int, 0), "stream wait");
-      if ((r = sort_particles(c, c->side))) return r;
-      CK(cudaEventRecord(c->ev_sorted, c->side), "event");
-    }
-    // densities (and j' for the particle coupling) of this step's populations
-    launch_moments(P, fin, c->rest, c->rho, P.np > 0 ? c->jp : nullptr, c->st);
-    if ((r = launched(c, "moments"))) return r;
-    ParticleArrays gpa = c->pa[c->pcur];  // what the update gathers the momentum return from
-    ParticleForces gpf = c->pf;
-    CellIndex gci = ci;
-    if (sub) {
-      CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
-      if ((r = substep_particles(c, gpa, gpf, gci))) return r;
-    } else if (P.np > 0) {
-      CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
-      launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
-      launch_pairs(P, c->pa[c->pcur], ci, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf,
-                   c->err, c->side);
-      CK(cudaEventRecord(c->ev_pairs, c->side), "event");
-      if ((r = launched(c, "particle forces", 2))) return r;
-    }
-    if (c->prof) {
-      if (c->ev_used + 2 > c->ev.size()) {
-        cudaEvent_t a, b;
-        CK(cudaEventCreate(&a), "event");
-        CK(cudaEventCreate(&b), "event");
-        c->ev.push_back(a);
-        c->ev.push_back(b);
+  c->P.np = c->np;
+  int s = 0, r;
+  if (c->graphs)
+    for (; s + kGraphSteps <= nsteps; s += kGraphSteps)
+      if ((r = replay_steps(c))) {
+        if (r != kGraphUnavailable) return r;
+        break;
       }
-      CK(cudaEventRecord(c->ev[c->ev_used], c->st), "event");
-    }
-    launch_collide(P, fin, fout, c->rest, c->rho, gpa, gpf, gci, c->err, c->st);
-    if ((r = launched(c, "collide"))) return r;
+  for (; s < nsteps; ++s) {
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (c->prof) {
-      CK(cudaEventRecord(c->ev[c->ev_used + 1], c->st), "event");
-      c->ev_used += 2;
+      if ((r = reserve_events(c, 2))) return r;
+      t0 = c->ev[c->ev_used];
+      t1 = c->ev[c->ev_used + 1];
     }
-    if (sub) {
-      c->pcur = 1 - c->pcur;  // the working copy that took the substeps is the particle state
-    } else if (P.np > 0) {
-      CK(cudaStreamWaitEvent(c->st, c->ev_pairs, 0), "stream wait");
-      launch_integrate(P, c->pa[c->pcur], c->pf, c->err, c->st);
-      if ((r = launched(c, "integrate"))) return r;
-    }
-    c->cur = 1 - c->cur;
-    c->steps++;
+    if ((r = one_step(c, (unsigned long long)c->steps, t0, t1, cudaEventRecordDefault))) return r;
+    if (c->prof) c->ev_used += 2;
   }
+  return LBMD_OK;
+}
+
+int lbmd_set_graphs(lbmd_ctx *c, int on) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  cudaSetDevice(c->dev);
+  drop_graphs(c);
+  c->graphs = on != 0;
   return LBMD_OK;
 }
 
@@ -654,6 +841,7 @@ int64_t lbmd_launch_count(const lbmd_ctx *c) { return c ? c->launches : -1; }
 
 int lbmd_profile_enable(lbmd_ctx *c, int on) {
   if (!c) return LBMD_E_INVALID_ARG;
+  if (c->prof != (on != 0)) drop_graphs(c);  // profiled graphs carry the timing events
   c->prof = on != 0;
   return LBMD_OK;
 }

@@ -55,6 +55,7 @@ void fill_step_params(const lbmd_params *prm, StepParams &P) {
   // fluctuating MRT factors (Eq. MODES): eigenvalue per mode, forcing moments of the paper's
   // forcing term, noise amplitudes from the equilibrium mode variances (kT/c_s^2) rho_z b_k
   P.substeps = prm->md_substeps;
+  P.step_mul = 1;
   P.noise_scale = (float)std::sqrt((double)prm->md_substeps);
   P.collision = prm->collision;
   const bool mrt = prm->collision == LBMD_COLLISION_MRT;

@@ -75,6 +75,11 @@ struct StepParams {
   float noise_scale;
   float relax[kQ], force[kQ], noise[kQ];
   unsigned long long seed, step;
+  // replayed step graphs: the particle kernels' noise counter is step + *step_base * step_mul,
+  // the device-resident base being the lattice step at the replay's start (null: step alone);
+  // the lattice update keeps its counter in `step` (patched into its graph node per replay)
+  const unsigned long long *step_base;
+  unsigned long long step_mul;
   TypeParams types[LBMD_MAX_TYPES];
   PairParams pairs[LBMD_MAX_TYPES * LBMD_MAX_TYPES];
 };
@@ -114,6 +119,11 @@ struct CellIndex {
 __host__ __device__ __forceinline__ int wrapi(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;
+}
+
+// The noise counter of a particle kernel given its own counter `step` (StepParams::step_base).
+__device__ __forceinline__ unsigned long long noise_step(const StepParams &P, unsigned long long step) {
+  return P.step_base ? step + *P.step_base * P.step_mul : step;
 }
 
 __device__ __forceinline__ long long site_index(const StepParams &P, int x, int y, int z) {
@@ -208,6 +218,15 @@ void launch_fields(const StepParams &P, const void *store, const float *rest, co
 void launch_fluid_sums(const StepParams &P, const void *store, const float *rest, double *partial, int nblocks,
                        cudaStream_t st);
 void launch_finish_sums(const double *partial, int nblocks, int nvals, double *out, cudaStream_t st);
+// Replayed step graphs.  The lattice update with the fluctuating MRT collision draws its noise
+// with the counter in its parameter bank (a counter read from memory would hold a register pair
+// through the update and spill): is_noisy_update tells its kernels, set_update_step writes the
+// counter into a node of an instantiated graph.  The particle kernels read the device-resident
+// step base, set or advanced by the two launches below.
+bool is_noisy_update(const void *fn);
+cudaError_t set_update_step(cudaGraphExec_t exec, cudaGraphNode_t node, unsigned long long step);
+void launch_set_step(unsigned long long *base, unsigned long long value, cudaStream_t st);
+void launch_advance_step(unsigned long long *base, unsigned long long n, cudaStream_t st);
 int fluid_sum_blocks(const StepParams &P);
 
 // particles (lb_particles.cu)

@@ -48,7 +48,7 @@ LBMD_SLOT_FAILED = 3
 # every symbol include/lbmd.h declares
 EXPORTS = ("lbmd_create", "lbmd_destroy", "lbmd_set_types", "lbmd_set_debye_hueckel", "lbmd_init_fluid",
            "lbmd_set_populations", "lbmd_get_populations", "lbmd_set_particles", "lbmd_set_bonds",
-           "lbmd_step", "lbmd_sync", "lbmd_clear_error", "lbmd_get_fields", "lbmd_get_particles",
+           "lbmd_step", "lbmd_set_graphs", "lbmd_sync", "lbmd_clear_error", "lbmd_get_fields", "lbmd_get_particles",
            "lbmd_diagnostics", "lbmd_step_count", "lbmd_profile_enable", "lbmd_profile_read",
            "lbmd_launch_count", "lbmd_last_error", "lbmd_fluid_moments_static",
            "lbmd_batch_create", "lbmd_batch_destroy", "lbmd_batch_add", "lbmd_batch_remove",
@@ -103,6 +103,7 @@ def _load():
         "lbmd_set_particles": (I, [P, I, P, P, P, P]),
         "lbmd_set_bonds": (I, [P, I, P, I, D, D]),
         "lbmd_step": (I, [P, I]),
+        "lbmd_set_graphs": (I, [P, I]),
         "lbmd_sync": (I, [P]),
         "lbmd_clear_error": (I, [P]),
         "lbmd_get_fields": (I, [P, P, P, P]),
@@ -232,6 +233,10 @@ def lbmd_set_bonds(ctx, pairs, kind: int, k: float, r: float) -> None:
 
 def lbmd_step(ctx, nsteps: int) -> None:
     _check(ctx, _lib.lbmd_step(ctx, nsteps))
+
+
+def lbmd_set_graphs(ctx, on: bool) -> None:
+    _check(ctx, _lib.lbmd_set_graphs(ctx, int(bool(on))))
 
 
 def lbmd_sync(ctx) -> None:

@@ -37,6 +37,8 @@ class Case:
     lam_mom: float = None
     lam_ghost: float = None
     md_substeps: int = 1
+    storage: int = 0  # LBMD_STORAGE_* (the CUDA path only)
+    rho0: tuple = (0.0, 0.0)  # shift reference of the 16-bit storages
 
     def fields32(self):
         return (self.rhoA.astype(np.float32), self.rhoB.astype(np.float32),
@@ -93,7 +95,7 @@ def make_gpu(c: Case, stream=None):
     from paper_1306_0788_gb300 import lbmd as L
     ctx, _ = L.lbmd_create(L.params(c.dims, tau_r=c.tau_r, g_AB=c.g, kT=c.kT, seed=c.seed, collision=c.collision,
                                     lambda_bulk=c.lam_bulk, lambda_mom=c.lam_mom, lambda_ghost=c.lam_ghost,
-                                    md_substeps=c.md_substeps), stream)
+                                    md_substeps=c.md_substeps, storage=c.storage, rho0=c.rho0), stream)
     types = [L.lbmd_ptype(*t) for t in c.types]
     pairs = [L.lbmd_pair(i, j, e, s) for (i, j), (e, s) in c.wca.items()]
     L.lbmd_set_types(ctx, types, pairs)
