@@ -131,6 +131,81 @@ __global__ void k_permute(int np, const int *__restrict__ perm, ParticleArrays s
   slot_of_id[id] = j;
 }
 
+// The whole counting sort of a small system in one block: the steps of k_bin ... k_permute
+// (histogram with the same range check, exclusive scan, scatter, order by (x cell, id) within a
+// row, permutation) with the counts and the permutation in shared memory, one launch instead of
+// a chain of seven that a step of a small lattice would wait for.  The order is unique, so the
+// result is that of the chain.
+constexpr int kSortSmallRows = 4096, kSortSmallNp = 2048;
+
+__global__ void __launch_bounds__(kScanThreads) k_sort_small(StepParams P, ParticleArrays src, ParticleArrays dst,
+                                                             int *__restrict__ start, int *__restrict__ slot_of_id,
+                                                             unsigned *err) {
+  __shared__ int count[kSortSmallRows];  // histogram, then the scatter cursors (= row ends)
+  __shared__ int row_of[kSortSmallNp];
+  __shared__ int perm[kSortSmallNp];
+  __shared__ int wt[kScanThreads / 32];
+  const int np = P.np, nrows = P.nrows;
+  for (int r = threadIdx.x; r < nrows; r += kScanThreads) count[r] = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < np; p += kScanThreads) {
+    int4 c = src.cell[p];
+    if (c.x < 0 || c.x >= P.nx || c.y < 0 || c.y >= P.ny || c.z < 0 || c.z >= P.nz) {
+      atomicOr(err, kErrParticle);  // cannot happen for states written by this library
+      c.x = wrapi(c.x, P.nx); c.y = wrapi(c.y, P.ny); c.z = wrapi(c.z, P.nz);
+      src.cell[p] = c;
+    }
+    const int row = c.z * P.ny + c.y;
+    row_of[p] = row;
+    atomicAdd(&count[row], 1);
+  }
+  __syncthreads();
+  const int per = (nrows + kScanThreads - 1) / kScanThreads;  // consecutive rows of a thread
+  const int b = threadIdx.x * per;
+  int sum = 0;
+  for (int k = 0; k < per; ++k)
+    if (b + k < nrows) sum += count[b + k];
+  int total;
+  int run = block_exclusive_scan(sum, wt, total);
+  for (int k = 0; k < per; ++k)
+    if (b + k < nrows) {
+      const int n = count[b + k];
+      start[b + k] = run;
+      count[b + k] = run;
+      run += n;
+    }
+  if (threadIdx.x == 0) start[nrows] = total;
+  __syncthreads();
+  for (int p = threadIdx.x; p < np; p += kScanThreads) perm[atomicAdd(&count[row_of[p]], 1)] = p;
+  __syncthreads();
+  for (int r = threadIdx.x; r < nrows; r += kScanThreads) {  // row r holds slots [end of r-1, end of r)
+    const int b0 = r == 0 ? 0 : count[r - 1], e0 = count[r];
+    for (int i = b0 + 1; i < e0; ++i) {
+      const int v = perm[i];
+      const long long kv = ((long long)src.cell[v].x << 32) | (unsigned)src.pid[v];
+      int j = i - 1;
+      while (j >= b0) {
+        const int w = perm[j];
+        const long long kw = ((long long)src.cell[w].x << 32) | (unsigned)src.pid[w];
+        if (kw <= kv) break;
+        perm[j + 1] = w;
+        --j;
+      }
+      perm[j + 1] = v;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < np; j += kScanThreads) {
+    const int p = perm[j];
+    dst.cell[j] = src.cell[p];
+    dst.frac[j] = src.frac[p];
+    dst.vel[j] = src.vel[p];
+    const int id = src.pid[p];
+    dst.pid[j] = id;
+    slot_of_id[id] = j;
+  }
+}
+
 // Coupling forces of every particle (site::couple).
 __global__ void __launch_bounds__(kPBlock) k_couple(StepParams P, ParticleArrays pa, CellIndex ci,
                                                     const float *__restrict__ rho, const float *__restrict__ jp,
@@ -250,6 +325,13 @@ void launch_scan_rows(int nrows, const int *row_count, int *row_start, int *row_
   k_scan_top<<<1, kScanThreads, 0, st>>>(nb, bsum);
   k_scan_final<<<nb, kScanThreads, 0, st>>>(nrows, nb, row_count, bsum, row_start, row_cursor);
 }
+bool sort_fits_one_block(int nrows, int np) { return nrows <= kSortSmallRows && np <= kSortSmallNp; }
+
+void launch_sort_small(const StepParams &P, const ParticleArrays &src, const ParticleArrays &dst, int *row_start,
+                       int *slot_of_id, unsigned *err, cudaStream_t st) {
+  k_sort_small<<<1, kScanThreads, 0, st>>>(P, src, dst, row_start, slot_of_id, err);
+}
+
 void launch_scatter(int np, const int *row_of, int *row_cursor, int *perm, cudaStream_t st) {
   k_scatter<<<pgrid(np), kPBlock, 0, st>>>(np, row_of, row_cursor, perm);
 }

@@ -190,6 +190,11 @@ void free_particles(lbmd_ctx *c) {
 
 int sort_particles(lbmd_ctx *c, cudaStream_t st) {
   const StepParams &P = c->P;
+  if (sort_fits_one_block(P.nrows, P.np)) {
+    launch_sort_small(P, c->pa[c->pcur], c->pa[1 - c->pcur], c->row_start, c->slot_of_id, c->err, st);
+    c->pcur = 1 - c->pcur;
+    return launched(c, "particle sort");
+  }
   CK(cudaMemsetAsync(c->row_count, 0, sizeof(int) * (P.nrows + 1), st), "memset rows");
   launch_bin(P, c->pa[c->pcur], c->row_of, c->row_count, c->err, st);
   launch_scan_rows(P.nrows, c->row_count, c->row_start, c->row_cursor, c->row_bsum, st);

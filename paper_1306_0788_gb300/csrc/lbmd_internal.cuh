@@ -235,6 +235,11 @@ void launch_bin(const StepParams &P, const ParticleArrays &pa, int *row_of, int 
 int scan_blocks(int nrows);  // size of the block-sum scratch is scan_blocks(nrows) + 1
 void launch_scan_rows(int nrows, const int *row_count, int *row_start, int *row_cursor, int *bsum, cudaStream_t st);
 void launch_scatter(int np, const int *row_of, int *row_cursor, int *perm, cudaStream_t st);
+// The particle sort of a small system (nrows and np within one block's shared memory) in one
+// launch: row_start and the sorted copy dst of src, as the chain bin ... permute gives them.
+bool sort_fits_one_block(int nrows, int np);
+void launch_sort_small(const StepParams &P, const ParticleArrays &src, const ParticleArrays &dst, int *row_start,
+                       int *slot_of_id, unsigned *err, cudaStream_t st);
 void launch_row_sort(const StepParams &P, const int *row_start, const ParticleArrays &pa, int *perm,
                      cudaStream_t st);
 void launch_permute(int np, const int *perm, const ParticleArrays &src, const ParticleArrays &dst,
