@@ -1014,9 +1014,8 @@ int lbmd_batch_init_fluid(lbmd_batch *b, int slot, const float *rhoA, const floa
   if (!rhoA || !rhoB) return bfail(b, LBMD_E_INVALID_ARG, "null density");
   Slot &sl = b->slots[slot];
   const long long N = sl.P.N;
-  for (long long s = 0; s < N; ++s)
-    if (!(rhoA[s] > 0.f) || !(rhoB[s] > 0.f) || !std::isfinite(rhoA[s]) || !std::isfinite(rhoB[s]))
-      return bfail(b, LBMD_E_INVALID_ARG, "densities must be finite and > 0");
+  if (!densities_valid(rhoA, rhoB, N))
+    return bfail(b, LBMD_E_INVALID_ARG, "densities must be finite and > 0");
   if (sl.fluid_ready && (r = refresh(b))) return r;  // the current buffer
   const int cur = sl.fluid_ready ? sl.mirror.cur : 0;
   float *stage = reinterpret_cast<float *>(sl.pop[1 - cur]);

@@ -558,9 +558,8 @@ int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const flo
   cudaSetDevice(c->dev);
   drop_graphs(c);
   const long long N = c->P.N;
-  for (long long s = 0; s < N; ++s)
-    if (!(rhoA[s] > 0.f) || !(rhoB[s] > 0.f) || !std::isfinite(rhoA[s]) || !std::isfinite(rhoB[s]))
-      return fail(c, LBMD_E_INVALID_ARG, "densities must be finite and > 0");
+  if (!densities_valid(rhoA, rhoB, N))
+    return fail(c, LBMD_E_INVALID_ARG, "densities must be finite and > 0");
   // stage through the (not yet used) second population buffer
   float *stage = reinterpret_cast<float *>(c->pop[1 - c->cur]);
   const size_t bytes = sizeof(float) * (size_t)N;

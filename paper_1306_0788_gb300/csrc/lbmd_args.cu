@@ -11,6 +11,16 @@
 
 namespace lbmd {
 
+bool densities_valid(const float *rhoA, const float *rhoB, long long n) {
+  // x > 0 and x <= FLT_MAX: false for NaN, infinities, zero and negative values
+  constexpr float kMax = 3.402823466e38f;
+  unsigned ok = 1u;
+  for (long long s = 0; s < n; ++s)
+    ok &= (unsigned)(rhoA[s] > 0.f) & (unsigned)(rhoA[s] <= kMax) & (unsigned)(rhoB[s] > 0.f) &
+          (unsigned)(rhoB[s] <= kMax);
+  return ok != 0u;
+}
+
 int check_params(const lbmd_params *prm, std::string &why) {
   if (prm->nx < 1 || prm->ny < 1 || prm->nz < 1) return why = "lattice sizes must be >= 1", LBMD_E_INVALID_ARG;
   if ((double)prm->nx * prm->ny * prm->nz * kQ >= 4294967296.0)  // 32-bit population offsets

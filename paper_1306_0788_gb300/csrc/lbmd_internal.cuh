@@ -193,6 +193,8 @@ void set_context_free_error(const std::string &m);
 int check_params(const lbmd_params *prm, std::string &why);
 void fill_step_params(const lbmd_params *prm, StepParams &P);
 unsigned param_warnings(const lbmd_params *prm);
+// Every density of both fields finite and > 0 (one branch-free pass the host compiler vectorises).
+bool densities_valid(const float *rhoA, const float *rhoB, long long n);
 int apply_types(StepParams &P, double kT, double dt, int ntypes, const lbmd_ptype *types, int npairs,
                 const lbmd_pair *pairs, unsigned &warnings, std::string &why);
 int apply_debye_hueckel(StepParams &P, double lB, double kappa_D, double rc, std::string &why);

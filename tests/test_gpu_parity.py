@@ -284,3 +284,32 @@ def test_single_solvation_force_variant():
     fo, xo, _, _ = run_oracle(c, 30)
     assert pop_error(fg, fo) <= 3e-5
     assert position_error(xg, xo, c.x, c.dims) <= POS_TOL
+
+
+@pytest.mark.parametrize("bad", [0.0, -1.0, np.inf, -np.inf, np.nan])
+def test_invalid_densities_are_refused(bad):
+    """A density that is not finite and positive, at any site of either field, is refused with
+    LBMD_E_INVALID_ARG by single contexts and batches alike; a valid field is accepted after."""
+    from paper_1306_0788_gb300 import lbmd as L
+    dims = (9, 7, 5)
+    rA, rB = noisy_fluid(dims, amp=0.02, seed=4)
+    ctx, _ = L.lbmd_create(L.params(dims))
+    b = L.lbmd_batch_create(0, 0, 2)
+    try:
+        slot, _ = L.lbmd_batch_add(b, L.params(dims), 0, 10)
+        for field, site in ((0, 0), (1, dims[0] * dims[1] * dims[2] - 1), (0, 123)):
+            a, c = rA.astype(np.float32).copy(), rB.astype(np.float32).copy()
+            (a if field == 0 else c).reshape(-1)[site] = bad
+            with pytest.raises(L.LbmdError) as e:
+                L.lbmd_init_fluid(ctx, a, c)
+            assert e.value.code == L.LBMD_E_INVALID_ARG
+            with pytest.raises(L.LbmdError) as e:
+                L.lbmd_batch_init_fluid(b, slot, a, c)
+            assert e.value.code == L.LBMD_E_INVALID_ARG
+        L.lbmd_init_fluid(ctx, rA, rB)
+        L.lbmd_batch_init_fluid(b, slot, rA, rB)
+        L.lbmd_step(ctx, 2)
+        L.lbmd_sync(ctx)
+    finally:
+        L.lbmd_batch_destroy(b)
+        L.lbmd_destroy(ctx)
