@@ -85,3 +85,25 @@ def test_create_rejects_invalid_substeps_without_device(k):
     with pytest.raises(lbmd.LbmdError) as e:
         lbmd.lbmd_create(p)
     assert e.value.code == lbmd.LBMD_E_INVALID_ARG
+
+
+def test_every_entry_point_refuses_a_null_handle_without_device():
+    """Each call that takes a context or a batch returns LBMD_E_INVALID_ARG (the counters -1)
+    for a NULL handle, before touching the device; destroy(NULL) is a no-op."""
+    import ctypes
+    from paper_1306_0788_gb300 import lbmd
+    lib = lbmd._lib
+    no_handle = {"lbmd_create", "lbmd_batch_create", "lbmd_fluid_moments_static", "lbmd_last_error",
+                 "lbmd_batch_last_error", "lbmd_destroy", "lbmd_batch_destroy"}
+    checked = 0
+    for name in lbmd.EXPORTS:
+        if name in no_handle:
+            continue
+        fn = getattr(lib, name)
+        args = [0 if a in (ctypes.c_int, ctypes.c_int64, ctypes.c_size_t) else 1.0 if a is ctypes.c_double else None
+                for a in fn.argtypes]
+        assert fn(*args) == lbmd.LBMD_E_INVALID_ARG, name  # -1 for the counters too
+        checked += 1
+    assert checked >= 35
+    lib.lbmd_destroy(None)
+    lib.lbmd_batch_destroy(None)
