@@ -230,11 +230,11 @@ __global__ void __launch_bounds__(kPBlock) k_pairs(StepParams P, ParticleArrays 
   site::pairs8(P, p, k, 0xFFu << (threadIdx.x & 24), pa, ci, bond_start, bond_other, slot_of_id, pf, err);
 }
 
-// Particle update in place (site::integrate).
-__global__ void k_integrate(StepParams P, ParticleArrays pa, ParticleForces pf, unsigned *err) {
+// Particle update (site::integrate) from src into dst, in the same order (dst may be src).
+__global__ void k_integrate(StepParams P, ParticleArrays src, ParticleArrays dst, ParticleForces pf, unsigned *err) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P.np) return;
-  site::integrate(P, p, pa, pa, pf, err);
+  site::integrate(P, p, src, dst, pf, err);
 }
 
 // ------------------------------------------------------------------ MD sub-stepping
@@ -352,9 +352,9 @@ void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, c
                   cudaStream_t st) {
   k_pairs<<<pgrid(8LL * P.np), kPBlock, 0, st>>>(P, pa, ci, bond_start, bond_other, slot_of_id, pf, err);
 }
-void launch_integrate(const StepParams &P, const ParticleArrays &pa, const ParticleForces &pf, unsigned *err,
-                      cudaStream_t st) {
-  k_integrate<<<pgrid(P.np), kPBlock, 0, st>>>(P, pa, pf, err);
+void launch_integrate(const StepParams &P, const ParticleArrays &src, const ParticleArrays &dst,
+                      const ParticleForces &pf, unsigned *err, cudaStream_t st) {
+  k_integrate<<<pgrid(P.np), kPBlock, 0, st>>>(P, src, dst, pf, err);
 }
 void launch_couple_sub(const StepParams &P, const ParticleArrays &C, const ParticleArrays &S, CellIndex ci,
                        const float *rho, const float *jp, const ParticleForces &pf, int sub,

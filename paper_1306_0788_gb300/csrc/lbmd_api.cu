@@ -33,10 +33,11 @@ struct lbmd_ctx {
   cudaStream_t st = nullptr;
   // the particle sort and the pair forces depend on the particles only, so they run on a side
   // stream beside the density pass: side waits for the previous step's update (ev_int), st waits
-  // for the sort before the coupling (ev_sorted) and for the pair forces before the update of
-  // the particles (ev_pairs); every step ends on st
+  // for the sort before the coupling (ev_sorted).  The particle update waits on side for the
+  // coupling (ev_coupled) and writes the other particle buffer, beside the lattice update that
+  // gathers from this one; st waits for it (ev_pairs), so every step ends on st
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_int = nullptr, ev_sorted = nullptr, ev_pairs = nullptr;
+  cudaEvent_t ev_int = nullptr, ev_sorted = nullptr, ev_pairs = nullptr, ev_coupled = nullptr;
   int dev = 0;
   StepParams P{};
   unsigned char *pop[2] = {nullptr, nullptr};  // population buffers, element type P.storage
@@ -307,10 +308,13 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
   } else if (P.np > 0) {
     CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
     launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
+    CK(cudaEventRecord(c->ev_coupled, c->st), "event");
     launch_pairs(P, c->pa[c->pcur], ci, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf,
                  c->err, c->side);
+    CK(cudaStreamWaitEvent(c->side, c->ev_coupled, 0), "stream wait");
+    launch_integrate(P, c->pa[c->pcur], c->pa[1 - c->pcur], c->pf, c->err, c->side);
     CK(cudaEventRecord(c->ev_pairs, c->side), "event");
-    if ((r = launched(c, "particle forces", 2))) return r;
+    if ((r = launched(c, "particle forces and update", 3))) return r;
   }
   if (t0) CK(cudaEventRecordWithFlags(t0, c->st, flags), "event");
   launch_collide(P, fin, fout, c->rest, c->rho, gpa, gpf, gci, c->err, c->st);
@@ -320,8 +324,7 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
     c->pcur = 1 - c->pcur;  // the working copy that took the substeps is the particle state
   } else if (P.np > 0) {
     CK(cudaStreamWaitEvent(c->st, c->ev_pairs, 0), "stream wait");
-    launch_integrate(P, c->pa[c->pcur], c->pf, c->err, c->st);
-    if ((r = launched(c, "integrate"))) return r;
+    c->pcur = 1 - c->pcur;  // the updated copy is the particle state
   }
   c->cur = 1 - c->cur;
   c->steps++;
@@ -486,7 +489,8 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
   if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_int, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_sorted, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&c->ev_pairs, cudaEventDisableTiming)) != cudaSuccess) {
+      (e = cudaEventCreateWithFlags(&c->ev_pairs, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_coupled, cudaEventDisableTiming)) != cudaSuccess) {
     cudaGetLastError();
     lbmd_destroy(c);
     return fail(nullptr, LBMD_E_CUDA, std::string("stream / event creation: ") + cudaGetErrorString(e));
@@ -516,6 +520,7 @@ void lbmd_destroy(lbmd_ctx *c) {
   if (c->ev_int) cudaEventDestroy(c->ev_int);
   if (c->ev_sorted) cudaEventDestroy(c->ev_sorted);
   if (c->ev_pairs) cudaEventDestroy(c->ev_pairs);
+  if (c->ev_coupled) cudaEventDestroy(c->ev_coupled);
   drop_graphs(c);
   if (c->gst) cudaStreamDestroy(c->gst);
   for (cudaEvent_t e : c->ph)

@@ -251,8 +251,8 @@ void launch_couple(const StepParams &P, const ParticleArrays &pa, CellIndex ci, 
 void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const int *bond_start,
                   const int *bond_other, const int *slot_of_id, const ParticleForces &pf, unsigned *err,
                   cudaStream_t st);
-void launch_integrate(const StepParams &P, const ParticleArrays &pa, const ParticleForces &pf,
-                      unsigned *err, cudaStream_t st);
+void launch_integrate(const StepParams &P, const ParticleArrays &src, const ParticleArrays &dst,
+                      const ParticleForces &pf, unsigned *err, cudaStream_t st);
 void launch_particle_momentum(const StepParams &P, const ParticleArrays &pa, double *partial, int nblocks,
                               cudaStream_t st);
 // MD sub-stepping (lb_particles.cu)
