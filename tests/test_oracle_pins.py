@@ -596,3 +596,29 @@ def test_free_flight_integrator():
                       **_one_type(gamma=np.zeros(1)))
     oracle.step(s, f, x, v, 0)
     assert np.allclose(x[0], [0.2, 3.95, 2.25], atol=1e-14)
+
+
+def test_bonded_and_screened_coulomb_closed_forms():
+    """Values of the bond and screened-Coulomb laws at points where they have a closed form,
+    so that a factor shared by an energy and its force (which the derivative check cannot see)
+    is caught: FENE (Kremer-Grest form) U = -(k R0^2 / 2) ln(1 - (r/R0)^2), F = -k r / (1 - (r/R0)^2);
+    harmonic (Sec. 4.3) U = (k/2)(r - d)^2, F = -k (r - d); screened Coulomb (Sec. 4.4)
+    U = q_i q_j lB exp(-kappa_D r) / r inside the cut-off, F = U (1/r + kappa_D)."""
+    k, R0 = 30.0, 1.5
+    r = R0 / np.sqrt(2.0)  # (r/R0)^2 = 1/2
+    assert np.isclose(oracle.pair_energy(oracle.BOND_FENE, k, R0, 0, r), 0.5 * k * R0 ** 2 * np.log(2.0), rtol=1e-12)
+    assert np.isclose(oracle.pair_force(oracle.BOND_FENE, k, R0, 0, r), -np.sqrt(2.0) * k * R0, rtol=1e-12)
+    kh, d = 20.0, 0.8
+    assert np.isclose(oracle.pair_energy(oracle.BOND_HARMONIC, kh, d, 0, d + 0.5), kh / 8.0, rtol=1e-12)
+    assert np.isclose(oracle.pair_force(oracle.BOND_HARMONIC, kh, d, 0, d + 0.5), -kh * 0.5, rtol=1e-12)
+    assert np.isclose(oracle.pair_force(oracle.BOND_HARMONIC, kh, d, 0, d - 0.25), kh * 0.25, rtol=1e-12)
+    qqlB, kap, rc = -2.0, 0.25, 3.0
+    r = 2.0
+    u = qqlB * np.exp(-kap * r) / r
+    assert np.isclose(oracle.pair_energy(oracle.PAIR_DH, qqlB, kap, rc, r), u, rtol=1e-12)
+    assert np.isclose(oracle.pair_force(oracle.PAIR_DH, qqlB, kap, rc, r), u * (1.0 / r + kap), rtol=1e-12)
+    # WCA (Sec. 4.1), truncated at its minimum: U = 4 eps ((s/r)^12 - (s/r)^6) inside 2^(1/6) s
+    eps, s, r = 0.7, 1.1, 1.0
+    x6 = (s / r) ** 6
+    assert np.isclose(oracle.pair_energy(oracle.PAIR_WCA, eps, s, 0, r), 4 * eps * (x6 * x6 - x6), rtol=1e-12)
+    assert np.isclose(oracle.pair_force(oracle.PAIR_WCA, eps, s, 0, r), 24 * eps * (2 * x6 * x6 - x6) / r, rtol=1e-12)
