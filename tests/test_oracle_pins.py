@@ -622,3 +622,23 @@ def test_bonded_and_screened_coulomb_closed_forms():
     x6 = (s / r) ** 6
     assert np.isclose(oracle.pair_energy(oracle.PAIR_WCA, eps, s, 0, r), 4 * eps * (x6 * x6 - x6), rtol=1e-12)
     assert np.isclose(oracle.pair_force(oracle.PAIR_WCA, eps, s, 0, r), 24 * eps * (2 * x6 * x6 - x6) / r, rtol=1e-12)
+
+
+@pytest.mark.parametrize("q0,q1", [(1.0, -1.0), (1.0, 1.0), (-2.0, 0.5), (2.0, 3.0)])
+def test_two_charges_in_one_step(q0, q1):
+    """Screened Coulomb between two particles inside the step (Sec. 4.4): with the fluid
+    coupling off and the particles at rest, one step of dt = 1 gives each the velocity
+    F / m along the line between them, F = q0 q1 lB exp(-kappa_D r) (1/r^2 + kappa_D/r) (> 0
+    repulsive), the two opposite; a pair of the other sign only flips the direction."""
+    dims = (12, 12, 12)
+    f = oracle.init_equilibrium(np.ones((12, 12, 12)), np.ones((12, 12, 12)))
+    r, lB, kap, m = 2.3, 0.7, 0.25, 3.0
+    x = np.array([[4.2, 5.5, 6.1], [4.2 + r, 5.5, 6.1]])
+    v = np.zeros((2, 3))
+    s = oracle.System(dims=dims, type=np.zeros(2, dtype=np.int32), q=np.array([q0, q1]),
+                      dh_lB=lB, dh_kappa=kap, dh_rc=4.0, **_one_type(gamma=np.zeros(1), mass=np.full(1, m)))
+    st, _ = oracle.step(s, f, x, v, 0)
+    assert st == 0
+    F = q0 * q1 * lB * np.exp(-kap * r) * (1.0 / r ** 2 + kap / r)
+    assert np.allclose(v[0], [-F / m, 0.0, 0.0], rtol=1e-12, atol=1e-15)  # particle 0 sits at -x of 1
+    assert np.allclose(v[1], [F / m, 0.0, 0.0], rtol=1e-12, atol=1e-15)
