@@ -203,7 +203,7 @@ int sort_particles(lbmd_ctx *c, cudaStream_t st) {
   launch_row_sort(P, c->row_start, c->pa[c->pcur], c->perm, st);
   launch_permute(P.np, c->perm, c->pa[c->pcur], c->pa[1 - c->pcur], c->slot_of_id, st);
   c->pcur = 1 - c->pcur;
-  return launched(c, "particle sort", 8);
+  return launched(c, "particle sort", 7);  // bin, three scan passes, scatter, row order, permute
 }
 
 }  // namespace
