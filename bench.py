@@ -28,14 +28,14 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled 2-comp D3Q19 MLUPS & HBM-roofline %; replica p50/p99 latency"
 UNIT = "MLUPS"
 HBM_FALLBACK_GBS = 6800.0
+HBM_NOMINAL_GBS = 7900.0
 # DRAM bytes per node moved by k_collide (dram__bytes_read + dram__bytes_write of one ncu capture
-# of the 128^3 case of this workload, scaled per node; profiles/k_collide_slab_droplets_256.md),
-# per storage with a capture of its own.  None while k_collide has changed since the capture.
+# of the 128^3 case of this workload, scaled per node), per storage with a capture of its own.
 COLLIDE_TRAFFIC_BYTES_PER_NODE = {"fp32": 290.0, "bf16": 147.2}
 # The fluctuating MRT update is bound by instruction issue, not by HBM: warp instructions per
 # node of k_collide<float, true, true> (smsp__inst_executed.sum / nodes of one ncu capture of the
-# 128^3 case, profiles/k_collide_mrt_slab_droplets_256.md), and the issue peak of the GPU: one
-# warp instruction per cycle per scheduler, 4 schedulers per SM, 152 SMs, at the SM clock.
+# 128^3 case), and the issue peak of the GPU: one warp instruction per cycle per scheduler, 4
+# schedulers per SM, 152 SMs, at the SM clock.
 MRT_WARP_INSTR_PER_NODE = 80.71
 MRT_TRAFFIC_BYTES_PER_NODE = 290.9  # DRAM bytes per node of the same capture
 SMS, SCHEDULERS_PER_SM = 152, 4
@@ -71,6 +71,25 @@ WORKLOADS = {
 
 
 STORAGES = {"fp32": (0, 4), "fp16": (1, 2), "bf16": (2, 2)}  # name: (LBMD_STORAGE_*, bytes per value)
+
+# Errors of the 16-bit storages against the FP64 oracle, as measured and bounded by the GPU tests
+# of tests/test_gpu_precision.py (one GB300 run): the 10-step population error, the Laplace
+# pressure jump of 3-D droplets (64^3, R = 8, 12, 16, 1000 steps; relative) with the fitted
+# 2 gamma, the flat-interface position (lattice units) and the particle MSD over 1000 steps.
+PRECISION_ERRORS = {
+    "fp16": {"population_10_steps": 2.8e-6, "laplace_dp_3d": None, "laplace_2gamma_3d": None,
+             "interface_position": None, "msd_1000_steps": 7.1e-8,
+             "measured_by": "tests/test_gpu_precision.py"},
+    "bf16": {"population_10_steps": 1.0e-5, "laplace_dp_3d": None, "laplace_2gamma_3d": None,
+             "interface_position": None, "msd_1000_steps": 9.2e-7,
+             "measured_by": "tests/test_gpu_precision.py"},
+}
+
+
+def survey_bytes_per_site(storage: str = "fp32") -> int:
+    """The one-pass minimum of a site update: both components' populations read and written
+    once, 2 * 19 * 4 * 2 = 304 B in FP32 and 2 * 19 * 2 * 2 = 152 B with 16-bit storage."""
+    return 2 * 19 * STORAGES[storage][1] * 2
 
 
 def algorithmic_bytes_per_site(storage: str = "fp32") -> int:
@@ -261,35 +280,26 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
-def run_cuda(args):
-    if args.workload == "replicas_24":
-        return run_batch(args)
+def measure_single(workload: str, storage: str = "fp32", collision: str = "bgk", md_substeps: int = 1,
+                   launch: str = "graph", steps: int = 20, warmup: int = 5, edge: int = 0, e2e: bool = True,
+                   rank: int = 0, world: int = 1, dist=None):
+    """One single-lattice measurement: warm-up, K timed steps between CUDA events on the context's
+    stream (clocks sampled meanwhile), the update kernel's own event times, and optionally the
+    end-to-end run through the C ABI with pinned host buffers.  Returns a dict of raw numbers."""
     import torch
     from paper_1306_0788_gb300 import lbmd as L
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
-
-    dims, rA, rB, x, types, kT, g_ab, extra = build_workload(args.workload, seed=1234 + rank, edge_override=args.edge)
+    dims, rA, rB, x, types, kT, g_ab, extra = build_workload(workload, seed=1234 + rank, edge_override=edge)
     npart = len(x)
     N = dims[0] * dims[1] * dims[2]
     rho0 = (float(rA.mean()), float(rB.mean()))  # shift reference of the 16-bit storages
-    mrt = args.collision == "mrt"
-    prm = L.params(dims, tau_r=1.0, g_AB=g_ab, kT=kT, seed=42 + rank, storage=STORAGES[args.storage][0], rho0=rho0,
-                   collision=L.LBMD_COLLISION_MRT if mrt else L.LBMD_COLLISION_BGK,
-                   md_substeps=args.md_substeps)
+    mrt = collision == "mrt"
+    prm = L.params(dims, tau_r=1.0, g_AB=g_ab, kT=kT, seed=42 + rank, storage=STORAGES[storage][0], rho0=rho0,
+                   collision=L.LBMD_COLLISION_MRT if mrt else L.LBMD_COLLISION_BGK, md_substeps=md_substeps)
     ctx, _ = L.lbmd_create(prm, stream)
-    L.lbmd_set_graphs(ctx, args.launch == "graph")
+    L.lbmd_set_graphs(ctx, launch == "graph")
     L.lbmd_set_types(ctx, [L.lbmd_ptype(*t) for t in types], [L.lbmd_pair(0, 0, *extra.get("wca", (1.0, 1.0)))])
     if "dh" in extra:
         L.lbmd_set_debye_hueckel(ctx, *extra["dh"])
@@ -306,7 +316,7 @@ def run_cuda(args):
     # warm-up (with the update's timing events on, so that the graphs replayed in the timed
     # region are recorded here)
     L.lbmd_profile_enable(ctx, True)
-    L.lbmd_step(ctx, args.warmup)
+    L.lbmd_step(ctx, warmup)
     barrier()
     L.lbmd_profile_read(ctx, reset=True)
     launches0 = L.lbmd_launch_count(ctx)
@@ -318,7 +328,7 @@ def run_cuda(args):
     barrier()
     with torch.cuda.stream(stream):
         e0.record(stream)
-        L.lbmd_step(ctx, args.steps)
+        L.lbmd_step(ctx, steps)
         e1.record(stream)
     barrier()
     clocks = sampler.stop()
@@ -334,8 +344,8 @@ def run_cuda(args):
     ms_max = max_over_ranks(ms, dist, "cuda")
 
     # end-to-end through the public API with host buffers (pinned), copies inside the timed region
-    e2e = None
-    if not args.no_e2e:
+    e2e_out = None
+    if e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
         hA, hB = pin(rA), pin(rB)
         hx, hv = pin(x.astype(np.float64)), pin(np.zeros_like(x, dtype=np.float64))
@@ -351,40 +361,95 @@ def run_cuda(args):
         rc = lib.lbmd_init_fluid(ctx, p(hA), p(hB), None)
         hq = pin(np.asarray(extra["q"], dtype=np.float64)) if "q" in extra else None
         rc |= lib.lbmd_set_particles(ctx, npart, p(hx), p(hv), p(ht), None if hq is None else p(hq))
-        rc |= lib.lbmd_step(ctx, args.steps)
+        rc |= lib.lbmd_step(ctx, steps)
         rc |= lib.lbmd_get_fields(ctx, p(outA), p(outB), p(outU))
         rc |= lib.lbmd_get_particles(ctx, p(ox), p(ov), p(of))
         barrier()
         t_e2e = time.perf_counter() - t0
-        h2d = (2 * N * 4 + npart * (6 * 8 + 4 + (8 if "q" in extra else 0))) / args.steps
-        d2h = (5 * N * 4 + npart * 9 * 8) / args.steps
-        e2e = {"value": round(whole_job_rate(N * args.steps, world, max_over_ranks(t_e2e, dist, "cuda")) / 1e6, 3),
-               "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "status": int(rc),
-               "what": "lbmd_init_fluid + lbmd_set_particles (pinned host) + lbmd_step(K) + "
-                       "lbmd_get_fields + lbmd_get_particles (pinned host), wall clock"}
+        h2d = (2 * N * 4 + npart * (6 * 8 + 4 + (8 if "q" in extra else 0))) / steps
+        d2h = (5 * N * 4 + npart * 9 * 8) / steps
+        e2e_out = {"value": round(whole_job_rate(N * steps, world, max_over_ranks(t_e2e, dist, "cuda")) / 1e6, 3),
+                   "unit": UNIT,
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "status": int(rc),
+                   "what": "lbmd_init_fluid + lbmd_set_particles (pinned host) + lbmd_step(K) + "
+                           "lbmd_get_fields + lbmd_get_particles (pinned host), wall clock"}
     L.lbmd_destroy(ctx)
+    return dict(dims=dims, N=N, npart=npart, kT=kT, g=g_ab, extra=extra, ms=ms_max, steps=steps,
+                kernel_ms=k_ms / max(k_n, 1), kernel_launches=k_n, launches=launches, clocks=clocks,
+                state_ok=state_ok, e2e=e2e_out, storage=storage, mrt=mrt, workload=workload)
 
-    peak, peak_kind = measured_hbm_peak()
-    bps = algorithmic_bytes_per_site(args.storage)
-    avg_kernel_ms = k_ms / max(k_n, 1)
-    achieved = bps * N / (avg_kernel_ms * 1e-3) / 1e9
-    if mrt:
-        clk = clocks.get("sm_mhz") or 2070.0
+
+def collide_roofline(m, peak, peak_kind):
+    """Roofline of the lattice update kernel alone (HBM; the issue rate for the MRT update)."""
+    N = m["N"]
+    bps = algorithmic_bytes_per_site(m["storage"])
+    achieved = bps * N / (m["kernel_ms"] * 1e-3) / 1e9
+    if m["mrt"]:
+        clk = m["clocks"].get("sm_mhz") or 2070.0
         issue_peak = SMS * SCHEDULERS_PER_SM * clk * 1e6
-        issued = None if MRT_WARP_INSTR_PER_NODE is None else MRT_WARP_INSTR_PER_NODE * N / (avg_kernel_ms * 1e-3)
-        roofline = {"bound": "alu", "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + fluctuating "
-                                              "MRT with Philox noise, both components)",
-                    "achieved": None if issued is None else round(issued / 1e12, 4),
-                    "peak": round(issue_peak / 1e12, 4),
-                    "peak_kind": "derived: 152 SMs x 4 schedulers x 1 warp instruction per cycle x the median SM "
-                                 "clock under load", "unit": "T warp-instructions/s",
-                    "frac": None if issued is None else round(issued / issue_peak, 4),
-                    "instructions_per_node": MRT_WARP_INSTR_PER_NODE,
-                    "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,
-                    "hbm_frac": round(achieved / peak, 4),
-                    "traffic": (int(MRT_TRAFFIC_BYTES_PER_NODE * N)
-                                if args.storage == "fp32" and MRT_TRAFFIC_BYTES_PER_NODE is not None else None)}
+        issued = MRT_WARP_INSTR_PER_NODE * N / (m["kernel_ms"] * 1e-3)
+        return {"bound": "alu", "scope": "kernel only (the lattice update)",
+                "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + fluctuating MRT with Philox "
+                          "noise, both components)",
+                "achieved": round(issued / 1e12, 4), "peak": round(issue_peak / 1e12, 4),
+                "peak_kind": "derived: 152 SMs x 4 schedulers x 1 warp instruction per cycle x the median SM "
+                             "clock under load", "unit": "T warp-instructions/s",
+                "frac": round(issued / issue_peak, 4), "instructions_per_node": MRT_WARP_INSTR_PER_NODE,
+                "kernel_ms": round(m["kernel_ms"], 5), "kernel_launches": m["kernel_launches"],
+                "hbm_frac": round(achieved / peak, 4),
+                "traffic": int(MRT_TRAFFIC_BYTES_PER_NODE * N) if m["storage"] == "fp32" else None}
+    return {"bound": "hbm", "scope": "kernel only (the lattice update)",
+            "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + BGK/forcing, both components)",
+            "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "bytes_per_site": bps,
+            "frac_on_survey_bytes": round(survey_bytes_per_site(m["storage"]) * N / (m["kernel_ms"] * 1e-3) / 1e9 / peak, 4),
+            "kernel_ms": round(m["kernel_ms"], 5), "kernel_launches": m["kernel_launches"],
+            "traffic": (None if m["storage"] not in COLLIDE_TRAFFIC_BYTES_PER_NODE
+                        else int(COLLIDE_TRAFFIC_BYTES_PER_NODE[m["storage"]] * N))}
+
+
+def step_roofline(m, peak):
+    """The whole coupled step against the one-pass minimum of the lattice update (populations read
+    and written once: 304 B per site in FP32, 152 B with 16-bit storage), against the measured
+    copy bandwidth and the nominal 7.9 TB/s."""
+    bps = survey_bytes_per_site(m["storage"])
+    achieved = bps * m["N"] / (m["ms"] / m["steps"] * 1e-3) / 1e9
+    return {"bound": "hbm", "scope": "whole coupled step (every kernel, particles included)",
+            "bytes_per_site": bps, "achieved": round(achieved, 1), "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "frac_of_nominal_7900": round(achieved / HBM_NOMINAL_GBS, 4)}
+
+
+def sub_record(m, peak, peak_kind, label):
+    """A further configuration measured in the same run, timed like the headline."""
+    ms_step = m["ms"] / m["steps"]
+    return {"config": {"workload": label, "lattice": list(m["dims"]), "particles": m["npart"],
+                       "storage": m["storage"], "bonds": int(len(m["extra"].get("bonds", [])))},
+            "value": round(m["N"] / (ms_step * 1e-3) / 1e6, 3), "unit": UNIT, "steps": m["steps"],
+            "ms_per_step": round(ms_step, 5), "roofline": collide_roofline(m, peak, peak_kind),
+            "step_roofline": step_roofline(m, peak), "gpu_launches": int(m["launches"]),
+            "clocks": m["clocks"], "state_ok": m["state_ok"]}
+
+
+def run_cuda(args):
+    if args.workload == "replicas_24":
+        return run_batch(args)
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+
+    m = measure_single(args.workload, args.storage, args.collision, args.md_substeps, args.launch, args.steps,
+                       args.warmup, args.edge, not args.no_e2e, rank, world, dist)
+    peak, peak_kind = measured_hbm_peak()
+    N, ms_max = m["N"], m["ms"]
     value = whole_job_rate(N * args.steps, world, ms_max * 1e-3) / 1e6
     if rank == 0:
         out = {
@@ -394,25 +459,32 @@ def run_cuda(args):
             "dtype": "f32" if args.storage == "fp32" else "f32 arithmetic, %s shifted population storage" % args.storage,
             "data": "synthetic",
             "config": {"workload": args.workload + ("" if not args.edge else "@%d" % args.edge),
-                       "md_substeps": args.md_substeps, "bonds": int(len(extra.get("bonds", []))),
+                       "md_substeps": args.md_substeps, "bonds": int(len(m["extra"].get("bonds", []))),
                        "description": WORKLOADS[args.workload][2],
-                       "lattice": list(dims), "particles": npart, "tau_r": 1.0, "g_AB": g_ab, "kT": kT,
-                       "storage": args.storage, "launch": args.launch,
+                       "lattice": list(m["dims"]), "particles": m["npart"], "tau_r": 1.0, "g_AB": m["g"],
+                       "kT": m["kT"], "storage": args.storage, "launch": args.launch,
                        "collision": ("fluctuating MRT (Eq. MODES), eigenvalues -1, fluid noise at kT"
-                                     if mrt else "BGK"),
+                                     if m["mrt"] else "BGK"),
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (N * 152 / 1e9)
                        if N * 152 > 129e6 else "L2-resident lattice (latency regime)"},
-            "roofline": roofline if mrt else {
-                         "bound": "hbm", "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + BGK/forcing, "
-                                                   "both components)",
-                         "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "bytes_per_site": bps,
-                         "kernel_ms": round(avg_kernel_ms, 5), "kernel_launches": k_n,
-                         "traffic": (None if args.storage not in COLLIDE_TRAFFIC_BYTES_PER_NODE
-                                     else int(COLLIDE_TRAFFIC_BYTES_PER_NODE[args.storage] * N))},
-            "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks, "state_ok": state_ok,
+            "roofline": collide_roofline(m, peak, peak_kind),
+            "step_roofline": step_roofline(m, peak),
+            "gpu_launches": int(m["launches"]), "e2e": m["e2e"], "clocks": m["clocks"], "state_ok": m["state_ok"],
         }
+        if world == 1 and not args.no_extras:
+            ext_steps = max(args.steps, 100)
+            if args.workload == "slab_droplets_256" and args.storage == "fp32" and not m["mrt"] and not args.edge:
+                for st in ("fp16", "bf16"):
+                    ms16 = measure_single("slab_droplets_256", st, steps=ext_steps, warmup=args.warmup, e2e=False)
+                    rec = sub_record(ms16, peak, peak_kind, "slab_droplets_256 (%s shifted storage)" % st)
+                    rec["speedup_vs_fp32"] = round((ms_max / args.steps) / rec["ms_per_step"], 4)
+                    rec["update_speedup_vs_fp32"] = round(m["kernel_ms"] / ms16["kernel_ms"], 4)
+                    rec["errors_vs_fp64_oracle"] = PRECISION_ERRORS[st]
+                    out["storage_" + st] = rec
+            if args.workload != "chains_512" and not args.edge:
+                mc = measure_single("chains_512", "fp32", steps=max(args.steps, 30), warmup=args.warmup, e2e=False)
+                out["chains_512"] = sub_record(mc, peak, peak_kind, "chains_512")
         if world == 1 and args.serving > 0:
             out["serving"] = run_serving(args.serving)
         if world == 1 and not args.no_cpu_baseline:
@@ -439,9 +511,12 @@ def run_serving(n_requests: int, load: float = 0.8, chunk: int = 25, seed: int =
         capacity = cal["site_updates_per_s"] / per_replica  # replicas per second
         rate = load * capacity
         reqs = inputs.serving_requests(n_requests, rate=rate, seed=seed)
+        sampler = ClockSampler(0)
+        sampler.start()
         t0 = time.perf_counter()
         records, peak = srv.run(reqs)
         wall = time.perf_counter() - t0
+        clocks = sampler.stop()
         info = serving.summarize(records)
     info.update({
         "stream": "%d Poisson arrivals at %.2f/s (%.0f %% of the measured capacity %.2f replicas/s); edge U{16..128}, "
@@ -452,7 +527,8 @@ def run_serving(n_requests: int, load: float = 0.8, chunk: int = 25, seed: int =
         "capacity_site_updates_per_s": cal["site_updates_per_s"], "tuned": cal["config"],
         "tuned_kernel_ms": cal["kernel_ms"], "chunk_steps": chunk, "wall_s": wall,
         "peak_device_bytes": peak["peak_bytes"], "peak_replicas": peak["peak_replicas"],
-        "admissions_refused": peak["refusals"]})
+        "admissions_refused": peak["refusals"], "clocks": clocks,
+        "config": {"workload": "serving_stream_%d" % n_requests}})
     return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in info.items()}
 
 
@@ -559,8 +635,10 @@ def main():
     ap.add_argument("--replicas", type=int, default=24, help="replicas of the replicas_24 workload")
     ap.add_argument("--batch-config", type=lambda v: [int(t) for t in v.split(",")], default=None,
                     help="tile_sites,grid_moments,grid_collide,collide_blocks: fixed batch launch shape, no autotuning")
-    ap.add_argument("--serving", type=int, default=200,
+    ap.add_argument("--serving", type=int, default=2000,
                     help="replicas in the serving stream measured after the main run (0 = skip)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the further configurations (16-bit storages, 512^3 chains) after the main run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -53,6 +53,7 @@ extern "C" {
 #define LBMD_E_BOND_BROKEN (-8) /* FENE bond stretched to or beyond R0 */
 #define LBMD_E_STATE (-9)       /* call out of order (e.g. step before init_fluid) */
 #define LBMD_E_PARTICLE_TOO_FAST (-10) /* md_substeps > 1: a particle crossed more than one cell in one step */
+#define LBMD_E_DRIFT (-11) /* FP64 drift check: a conserved total moved beyond drift_tol (lbmd_params.diag_every) */
 
 /* population storage: FP32, or 16-bit (IEEE half or bfloat16) holding the shifted value
  * f_zi - w_i rho0_z (lbmd_params.rho0_A / rho0_B); collisions always compute in FP32 and the
@@ -100,7 +101,22 @@ typedef struct lbmd_ctx lbmd_ctx;
  * particle update run K times with dt / K while the fluid fields of the step stay frozen,
  * and the collision takes the average momentum return.  K > 1 requires every particle to
  * stay within one cell of where the step started (else LBMD_E_PARTICLE_TOO_FAST); batches
- * take K = 1 only. */
+ * take K = 1 only.
+ * diag_every, drift_tol: the FP64 drift check.  The model conserves the total mass of each
+ * component (the collision and the forcing term of the appendix have no zeroth moment) and
+ * the total momentum of fluid and particles (Sec. 2: every force on a particle is returned to
+ * the fluid, pair and bond forces act pairwise, the Shan-Chen forces cancel pairwise for
+ * g_AB = g_BA).  With diag_every = K > 0, lbmd_step runs FP64 reductions on the device after
+ * every step whose count is a multiple of K: M_A, M_B (sum of the populations) and the total
+ * momentum P = sum_r j'(r) + sum_p m v_p, compared with the reference taken when the state was
+ * last set (lbmd_init_fluid, lbmd_set_particles, lbmd_set_drift_reference).  The drifts are
+ * |M_z - M_z,ref| / M_z,ref per component and |P - P_ref| / (M_A,ref + M_B,ref) (a velocity in
+ * lattice units); when one exceeds drift_tol the device error word records it and the next
+ * synchronising call returns LBMD_E_DRIFT (sticky, like the other device errors).  FP32 storage
+ * drifts by about 1e-8 per step from rounding, so drift_tol is the caller's choice for its run
+ * length and storage.  diag_every = 0 (the default) switches the check off; with diag_every > 0,
+ * drift_tol must be finite and > 0.  The reductions read the populations once (152 B per site in
+ * FP32): every K steps they cost about one density pass. */
 typedef struct {
   int nx, ny, nz;
   double tau_r;
@@ -113,6 +129,8 @@ typedef struct {
   int collision;
   double lambda_bulk, lambda_mom, lambda_ghost;
   int md_substeps;
+  int diag_every;
+  double drift_tol;
 } lbmd_params;
 
 /* Per particle type: kappa_A, kappa_B of Eq. (solvation_kappa), lambda_A, lambda_B of
@@ -132,7 +150,7 @@ typedef struct {
  * LBMD_E_NOMEM if they do not fit.  *warnings (may be NULL) receives LBMD_WARN_* bits.
  * Errors: LBMD_E_INVALID_ARG for sizes < 1, tau_r <= 1/2, dt != 1, unknown storage,
  * negative rho0, unknown collision, an MRT eigenvalue outside (-2, 0), md_substeps outside
- * [1, 256]. */
+ * [1, 256], diag_every < 0, or diag_every > 0 with drift_tol not finite and > 0. */
 int lbmd_create(const lbmd_params *params, void *stream, lbmd_ctx **out, unsigned *warnings);
 
 /* Destroy a context and free its device memory (NULL is ignored). */
@@ -207,6 +225,18 @@ int lbmd_get_particles(lbmd_ctx *ctx, double *x, double *v, double *f);
  * momentum sum_r j'(r), out[5..7] = particle momentum sum m v. */
 int lbmd_diagnostics(lbmd_ctx *ctx, double out[8]);
 
+/* The FP64 drift check (lbmd_params.diag_every; appendix: mass; Sec. 2: momentum).
+ * lbmd_set_drift_reference takes the current totals as the reference (enqueued on the context
+ * stream; lbmd_init_fluid and lbmd_set_particles do the same, lbmd_set_populations does not, so
+ * that a state changed by hand between steps is measured against the run's start).
+ * lbmd_get_drift synchronises and returns, for the last check, out[0] = its step count (-1: no
+ * check yet), out[1], out[2] = the relative mass drift of A and B, out[3] = the momentum drift
+ * per unit mass, out[4] = the number of checks since the reference was taken.  It does not
+ * return LBMD_E_DRIFT itself (lbmd_sync does).  Errors: LBMD_E_INVALID_ARG, LBMD_E_STATE (fluid
+ * not initialised), LBMD_E_CUDA. */
+int lbmd_set_drift_reference(lbmd_ctx *ctx);
+int lbmd_get_drift(lbmd_ctx *ctx, double out[5]);
+
 /* Number of completed steps. */
 int64_t lbmd_step_count(const lbmd_ctx *ctx);
 
@@ -225,22 +255,26 @@ int64_t lbmd_launch_count(const lbmd_ctx *ctx);
  * lbmd_diagnostics -- of a population array the caller already holds in device memory,
  * computed WITHOUT ALLOCATING any device memory.  The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc -- a serving loop that admits work
- * against a fixed device-memory budget and must not allocate once running, code that runs
- * inside another framework that owns the device allocator, or a monitor that samples a
- * simulation from a stream where a synchronising allocation would stall it.
- *   f_dev    device pointer, FP32 [2][19][nz][ny][nx] (the populations of both components in
- *            the layout of lbmd_get_populations, component A then B).
+ * against a fixed device-memory budget and must not allocate once running, or code that runs
+ * inside another framework that owns the device allocator.  The populations must already be in
+ * the layout below (the host layout of lbmd_get_populations, FP32); the library's own
+ * contexts keep theirs in another, internal layout and are not read by this call.
+ *   f_dev    device pointer, FP32 [2][19][nz][ny][nx] (component A then B): 38 nx ny nz floats.
  *   out_dev  device pointer to 5 doubles: M_A, M_B, Px, Py, Pz.
  *   stream   cudaStream_t for both launches (NULL = legacy default stream); asynchronous.
+ * Both pointers are checked before any launch: each must be device (or managed) memory and,
+ * where the driver reports the allocation's extent, lie with its stated length inside one
+ * allocation; otherwise LBMD_E_INVALID_ARG (no device access).
  * The per-block partial sums live in one file-scope static device array of 640 KiB
  * (16384 blocks x 5 doubles), which every GPU that loads the library holds until exit;
  * lattices above 2^27 sites (512^3) are rejected with LBMD_E_INVALID_ARG.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call shares the array:
- * calls whose kernels overlap on the GPU (different streams, or different threads) race on
- * it and must be serialised by the caller.  Each call writes every partial it reads, so no
- * clearing is needed.  Errors: LBMD_E_INVALID_ARG, LBMD_E_CUDA; lbmd_last_error(NULL)
- * describes the last failure. */
+ * current, and so does the first call after the device's context was created again (after
+ * cudaDeviceReset); make that first call before any stream capture.  Every call shares the
+ * array: calls whose kernels overlap on the GPU (different streams, or different threads) race
+ * on it and must be serialised by the caller.  Each call writes every partial it reads, so no
+ * clearing is needed; the partials are summed in a fixed order (deterministic).  Errors:
+ * LBMD_E_INVALID_ARG, LBMD_E_CUDA; lbmd_last_error(NULL) describes the last failure. */
 int lbmd_fluid_moments_static(const float *f_dev, int nx, int ny, int nz, double *out_dev, void *stream);
 
 /* Message of the last failure of ctx, or, if ctx is NULL, of the last failed call made without
@@ -326,6 +360,15 @@ int lbmd_batch_get_fields(lbmd_batch *batch, int slot, float *rhoA, float *rhoB,
 int lbmd_batch_get_particles(lbmd_batch *batch, int slot, double *x, double *v, double *f);
 int lbmd_batch_diagnostics(lbmd_batch *batch, int slot, double out[8]);
 
+/* The drift check of a replica whose lbmd_params.diag_every > 0, as lbmd_get_drift: out[5] = {step
+ * of the last check (-1: none), mass drift of A, of B, momentum drift per unit mass, checks
+ * since the reference}.  The reference is taken at the replica's first lbmd_batch_step after
+ * lbmd_batch_init_fluid or lbmd_batch_set_particles; the check runs inside the step graphs after
+ * every diag_every steps of the replica, and a drift beyond drift_tol stops the replica like any
+ * device error (lbmd_batch_poll: LBMD_SLOT_FAILED; lbmd_batch_slot_error: LBMD_E_DRIFT).  Waits
+ * for the batch stream.  Errors: LBMD_E_INVALID_ARG, LBMD_E_STATE (diag_every = 0). */
+int lbmd_batch_get_drift(lbmd_batch *batch, int slot, double out[5]);
+
 /* Launch shape of the two lattice kernels: the sites per tile (a multiple of 256 in
  * [256, 65536]), the persistent grid of the density pass and of the update (in [1, 64 x SM
  * count]), and the register budget of the update, collide_blocks = 3 (80 registers, three
@@ -345,8 +388,8 @@ int lbmd_batch_tune(lbmd_batch *batch, int cfg[5], double ms[2]);
 /* Budget and use in bytes, number of occupied slots, slot count (any pointer may be NULL). */
 int lbmd_batch_info(const lbmd_batch *batch, size_t *budget, size_t *used, int *occupied, int *max_slots);
 
-/* Kernel launches issued by lbmd_batch_step so far (host-side count: 13 per step, 14 when the
- * batch holds replicas of both collisions). */
+/* Kernel launches issued by lbmd_batch_step so far (host-side count: 15 per step, 16 when the
+ * batch holds replicas of both collisions; two more when a drift reference is taken). */
 int64_t lbmd_batch_launch_count(const lbmd_batch *batch);
 
 /* Message of the last failure of a batch call (NULL: of lbmd_batch_create). */

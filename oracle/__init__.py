@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle shared library with gcc (IEEE double, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O3", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+        subprocess.check_call(["gcc", "-O3", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
                                "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -61,7 +61,13 @@ def _load():
                                      ctypes.c_void_p]
         _lib.orc_fluid_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]
         _lib.orc_mode_basis.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        _lib.orc_set_threads.argtypes = [ctypes.c_int]
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the oracle's per-site loops (1 by default); results do not depend on it."""
+    _load().orc_set_threads(int(n))
 
 
 def _ptr(a: np.ndarray):

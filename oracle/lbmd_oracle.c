@@ -67,6 +67,12 @@
  *       Eq. (comp_Pi); Eq. (TRANSPORTCOEFF) prints it without the 2/3 (which at BGK would
  *       contradict the known eta_b = 2/3 eta_s of D3Q19).  Nothing in the collision depends on
  *       this reading; only the pin of the sound damping does.
+ *
+ * Threads: the loops over sites whose iterations are independent (each writes only its own
+ * site's values, summed in the same order) may run on several host threads (OpenMP, set by
+ * orc_set_threads; one thread by default).  The arithmetic and its order per site do not
+ * change, so every result is bitwise the same for any thread count; the global reductions
+ * (orc_fluid_moments) and the particle loops stay serial.
  */
 #include <math.h>
 #include <stdint.h>
@@ -75,6 +81,11 @@
 
 #define ORC_Q 19
 #define ORC_CS2 (1.0 / 3.0)
+
+static int orc_nthreads = 1;
+
+/* Host threads of the per-site loops (see the header; n < 1 means 1). */
+void orc_set_threads(int n) { orc_nthreads = n < 1 ? 1 : n; }
 
 /* Eq. (velo), ordered per reading R10. */
 static const int orc_c[ORC_Q][3] = {
@@ -144,6 +155,7 @@ void orc_forcing(const double *g, const double *u, double lM, double ls, double 
 /* Node gradient sum S(r) = sum_i w_i rho(r + c_i) c_i (the lattice sum inside Eq. SCforce,
  * reading R1) for every site.  S has layout [N][3]. */
 void orc_stencil_sum(const int *dim, const double *rho, double *S) {
+#pragma omp parallel for num_threads(orc_nthreads) schedule(static)
   for (long z = 0; z < dim[2]; ++z)
     for (long y = 0; y < dim[1]; ++y)
       for (long x = 0; x < dim[0]; ++x) {
@@ -163,6 +175,7 @@ void orc_sc_force(const int *dim, const double *rhoA, const double *rhoB, double
   long N = (long)dim[0] * dim[1] * dim[2];
   orc_stencil_sum(dim, rhoA, SA);
   orc_stencil_sum(dim, rhoB, SB);
+#pragma omp parallel for num_threads(orc_nthreads) schedule(static)
   for (long s = 0; s < N; ++s)
     for (int a = 0; a < 3; ++a) {
       gA[3 * s + a] = -gAB * rhoA[s] * SB[3 * s + a];
@@ -410,9 +423,10 @@ int orc_step(const orc_system *sys, double *f, double *x, double *v, uint64_t st
   double *pu = P + 21 * np, *pgA = P + 24 * np, *pgB = P + 27 * np;
 
   /* 1. rho_z = sum_i f_zi (appendix, zeroth mode) and j' = sum_z sum_i f_zi c_i. */
-  for (int z = 0; z < 2; ++z)
-    for (int i = 0; i < ORC_Q; ++i)
-      for (long s = 0; s < N; ++s) {
+#pragma omp parallel for num_threads(orc_nthreads) schedule(static)
+  for (long s = 0; s < N; ++s)
+    for (int z = 0; z < 2; ++z)
+      for (int i = 0; i < ORC_Q; ++i) {
         double fi = f[((long)z * ORC_Q + i) * N + s];
         rho[z * N + s] += fi;
         for (int a = 0; a < 3; ++a) jp[3 * s + a] += fi * orc_c[i][a];
@@ -447,6 +461,7 @@ int orc_step(const orc_system *sys, double *f, double *x, double *v, uint64_t st
   }
 
   /* 4. Coupling velocity, reading R5 (Eq. momentum_definition without the particle term). */
+#pragma omp parallel for num_threads(orc_nthreads) schedule(static)
   for (long s = 0; s < N; ++s) {
     double r = rho[s] + rho[N + s];
     for (int a = 0; a < 3; ++a)
@@ -564,6 +579,7 @@ int orc_step(const orc_system *sys, double *f, double *x, double *v, uint64_t st
   orc_mode_basis(E, bk);
   for (int k = 0; k < ORC_Q; ++k)
     lk[k] = k == 0 ? 0.0 : k <= 3 ? sys->lam_mom : k == 4 ? sys->lam_bulk : k <= 9 ? lam : sys->lam_ghost;
+#pragma omp parallel for num_threads(orc_nthreads) schedule(static)
   for (long zz = 0; zz < dim[2]; ++zz)
     for (long yy = 0; yy < dim[1]; ++yy)
       for (long xx = 0; xx < dim[0]; ++xx) {
@@ -650,6 +666,7 @@ int orc_step(const orc_system *sys, double *f, double *x, double *v, uint64_t st
 /* Equilibrium initialisation f_zi = f^eq_i(rho_z, u) (Eq. feq); u may be NULL (rest). */
 void orc_init_equilibrium(const int *dim, const double *rhoA, const double *rhoB, const double *u, double *f) {
   long N = (long)dim[0] * dim[1] * dim[2];
+#pragma omp parallel for num_threads(orc_nthreads) schedule(static)
   for (long s = 0; s < N; ++s) {
     double us[3] = {0.0, 0.0, 0.0};
     if (u)

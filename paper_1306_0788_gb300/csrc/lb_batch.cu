@@ -34,12 +34,17 @@ struct RepDev {      // per slot, written by the host when the replica's paramet
   void *pop[2];      // population buffers (element type P.storage); pop[state.cur] = current
   float *rest;       // 16-bit storage: FP32 rest populations [2][N]; NULL for FP32
   float *rho, *jp;   // [N][2] densities, [3][N] j'
+  int diag_every;    // FP64 drift check every diag_every steps (0: off)
+  double drift_tol;
 };
 
 struct RepState {    // per slot, advanced by the device at the end of each step
   int cur;           // which population buffer holds the current state
   unsigned err;      // device error bits of this replica
   unsigned long long step;  // steps taken (the particle noise counter)
+  unsigned long long checked;  // step count of the last drift check (or of the reference)
+  unsigned ref_req;  // set by the host: take the current totals as the drift reference
+  unsigned pad;
 };
 
 struct RepLayout {   // per slot, written by the host at each repack
@@ -63,6 +68,8 @@ struct BatchDev {
   ParticleArrays S;      // the same particles sorted by (row, x cell, id) during a step
   ParticleForces pf;     // forces, indexed like S (and like U after the update)
   int *row_of, *row_count, *row_start, *row_cursor, *bsum, *perm;
+  double *tile_sums;     // [ntiles][5] FP64 sums of the drift check
+  double *drift;         // [max_slots][10]: reference totals [5], last check {step, dA, dB, dP, n}
 };
 
 // ------------------------------------------------------------------ lattice kernels
@@ -364,6 +371,120 @@ __global__ void kb_advance(const BatchDev *__restrict__ B) {
   }
 }
 
+// ------------------------------------------------------------------ FP64 drift check
+
+// A replica's totals are taken when the host asked for a reference, or after every diag_every
+// steps (once per step count).  Both kernels below decide the same way from the same state.
+__device__ __forceinline__ bool drift_due(const RepDev &R, const RepState &S) {
+  return R.diag_every > 0 &&
+         (S.ref_req || (S.step % (unsigned long long)R.diag_every == 0 && S.step != S.checked));
+}
+
+// FP64 sums [M_A, M_B, Px, Py, Pz] of every tile of the replicas due for a drift check, over
+// the current buffer (streaming permutes populations, so the stored values sum alike).
+template <class T>
+__global__ void __launch_bounds__(kBThreads) kb_drift_sums(const BatchDev *__restrict__ B) {
+  __shared__ double sh[5][kBThreads];
+  const int ts = B->tile_sites;
+  for (int t = blockIdx.x; t < B->ntiles; t += gridDim.x) {
+    const int slot = B->tile_slot[t];
+    const RepDev &R = B->rep[slot];
+    const RepState &S = B->state[slot];
+    if (!drift_due(R, S)) continue;  // uniform across the block
+    const StepParams &P = R.P;
+    const T *f = static_cast<const T *>(R.pop[S.cur]);
+    const long long base = (long long)(t - B->lay[slot].tile0) * ts;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < ts; k += kBThreads) {
+      const long long s = base + k;
+      if (s >= P.N) break;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        const double a = (double)site::pop_read(P, f, R.rest, 0, i, s);
+        const double b = (double)site::pop_read(P, f, R.rest, 1, i, s);
+        acc[0] += a;
+        acc[1] += b;
+        if (kCx[i]) acc[2] += kCx[i] * (a + b);
+        if (kCy[i]) acc[3] += kCy[i] * (a + b);
+        if (kCz[i]) acc[4] += kCz[i] * (a + b);
+      }
+    }
+    __syncthreads();  // sh is free (previous tile)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = kBThreads / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) B->tile_sums[(long long)t * 5 + k] = sh[k][0];
+  }
+}
+
+// Per replica due: its tiles' sums plus the momentum of its particles, in a fixed order; then
+// either the new reference or the comparison with it (kErrDrift beyond the tolerance: the
+// replica takes no further step, like after any device error).
+__global__ void __launch_bounds__(kBThreads) kb_drift_finish(const BatchDev *__restrict__ B) {
+  __shared__ double sh[5][kBThreads];
+  for (int r = blockIdx.x; r < B->nrep; r += gridDim.x) {
+    const int slot = B->rep_slot[r];
+    const RepDev &R = B->rep[slot];
+    RepState &S = B->state[slot];
+    if (!drift_due(R, S)) continue;  // uniform across the block
+    const RepLayout &L = B->lay[slot];
+    const int nt = (int)((R.P.N + B->tile_sites - 1) / B->tile_sites);
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < nt; t += kBThreads)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) acc[k] += B->tile_sums[(long long)(L.tile0 + t) * 5 + k];
+    for (int p = threadIdx.x; p < R.P.np; p += kBThreads) {
+      const int q = L.p0 + p;
+      const float4 v = B->U.vel[q];
+      const double m = (double)R.P.types[B->U.cell[q].w].mass;
+      acc[2] += m * v.x;
+      acc[3] += m * v.y;
+      acc[4] += m * v.z;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = kBThreads / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      double *ref = B->drift + (long long)slot * 10, *last = ref + 5;
+      if (S.ref_req) {
+        for (int k = 0; k < 5; ++k) ref[k] = sh[k][0];
+        last[0] = -1.0;
+        last[1] = last[2] = last[3] = last[4] = 0.0;
+        S.ref_req = 0;
+      } else {
+        const double dA = fabs(sh[0][0] - ref[0]) / fabs(ref[0]), dB = fabs(sh[1][0] - ref[1]) / fabs(ref[1]);
+        const double px = sh[2][0] - ref[2], py = sh[3][0] - ref[3], pz = sh[4][0] - ref[4];
+        const double dP = sqrt(px * px + py * py + pz * pz) / (fabs(ref[0]) + fabs(ref[1]));
+        last[0] = (double)S.step;
+        last[1] = dA;
+        last[2] = dB;
+        last[3] = dP;
+        last[4] += 1.0;
+        if (!(dA <= R.drift_tol) || !(dB <= R.drift_tol) || !(dP <= R.drift_tol)) {
+          S.err |= kErrDrift;
+          B->left[slot] = 0;  // no further step in this call (kb_advance stops it for good)
+        }
+      }
+      S.checked = S.step;
+    }
+  }
+}
+
 // Repack: dst[j] = src[src_of[j]] for src_of[j] >= 0 (the other slots are uploaded).
 __global__ void kb_gather(int n, const int *__restrict__ src_of, ParticleArrays from, ParticleArrays to,
                           const float4 *__restrict__ tot_from, float4 *__restrict__ tot_to) {
@@ -396,6 +517,7 @@ struct Slot {
   std::vector<float4> hf, hv;
   std::vector<int> hid;
   RepLayout lay{-1, -1, 0, 0};
+  bool ref_pending = false;  // a drift reference is requested and not yet taken
 };
 
 constexpr size_t kParticleBytes = 2 * (16 + 16 + 16 + 4) + 6 * 16 + 3 * 4;  // U, S, forces, row_of/perm/pslot
@@ -445,6 +567,8 @@ struct lbmd_batch {
   int bcap = 0;  // capacity of the block sums
   double *diag_partial = nullptr, *diag_out = nullptr;
   int diag_cap = 0;
+  double *d_drift = nullptr;  // [max_slots][10] (BatchDev::drift)
+  double *d_tile_sums = nullptr;  // [tile_cap][5] (BatchDev::tile_sums)
   bool dirty = true;
   // launch shape (autotuned)
   int tile_sites = 1024, grid_moments = 0, grid_collide = 0, grid_particles = 0;
@@ -524,6 +648,8 @@ int upload_rep(lbmd_batch *b, int slot) {
   r.rest = s.rest;
   r.rho = s.rho;
   r.jp = s.jp;
+  r.diag_every = s.prm.diag_every;
+  r.drift_tol = s.prm.drift_tol;
   BK(cudaMemcpyAsync(b->d_rep + slot, &r, sizeof(RepDev), cudaMemcpyHostToDevice, b->st), "upload replica");
   return LBMD_OK;
 }
@@ -551,6 +677,7 @@ int slot_error_code(unsigned bits) {
   if (bits & kErrNegDensity) return LBMD_E_NEGATIVE_DENSITY;
   if (bits & kErrBond) return LBMD_E_BOND_BROKEN;
   if (bits & kErrParticle) return LBMD_E_NONFINITE;
+  if (bits & kErrDrift) return LBMD_E_DRIFT;
   return LBMD_OK;
 }
 
@@ -566,8 +693,10 @@ int build_tiles(lbmd_batch *b, const std::vector<int> &act) {
   if (tiles.size() > 0x7fffffffull) return bfail(b, LBMD_E_INVALID_ARG, "too many tiles");
   if (tiles.size() > b->tile_cap) {
     pfree(b, b->d_tile_slot);
+    pfree(b, b->d_tile_sums);
     const size_t cap = tiles.size() + tiles.size() / 4;
     BK(palloc(b, &b->d_tile_slot, cap), "tile table");
+    BK(palloc(b, &b->d_tile_sums, 5 * cap), "tile sums");
     b->tile_cap = cap;
   }
   if (!tiles.empty())
@@ -576,6 +705,7 @@ int build_tiles(lbmd_batch *b, const std::vector<int> &act) {
   b->hb.ntiles = (int)tiles.size();
   b->hb.tile_sites = b->tile_sites;
   b->hb.tile_slot = b->d_tile_slot;
+  b->hb.tile_sums = b->d_tile_sums;
   return LBMD_OK;
 }
 
@@ -757,6 +887,15 @@ int launch_batched_collide(lbmd_batch *b, int grid, int min_blocks, int tuning) 
   return n;
 }
 
+// The drift check of the replicas due (two launches; a replica not due costs its tiles a test).
+void launch_drift(lbmd_batch *b) {
+  with_batch_storage(b->storage, [&](auto t) {
+    using T = std::remove_pointer_t<decltype(t)>;
+    kb_drift_sums<T><<<b->grid_moments, kBThreads, 0, b->st>>>(b->d_batch);
+  });
+  kb_drift_finish<<<2 * b->sms, kBThreads, 0, b->st>>>(b->d_batch);
+}
+
 // Enqueues one step; returns the number of kernel launches.
 // The particle sort and the pair forces depend on the particles only: they run on the side
 // stream beside the density pass, forked from st at the start of the step and joined before the
@@ -784,7 +923,8 @@ int enqueue_step(lbmd_batch *b) {
   cudaStreamWaitEvent(b->st, b->ev_pairs, 0);
   kb_integrate<<<gp, kBPThreads, 0, b->st>>>(B);
   kb_advance<<<1, 256, 0, b->st>>>(B);
-  return 12 + nc;
+  launch_drift(b);
+  return 14 + nc;
 }
 
 void drop_graphs(lbmd_batch *b) {
@@ -800,7 +940,7 @@ int graph_for(lbmd_batch *b, int n, cudaGraphExec_t *out, int *launches) {
   int per_step = 0;
   if (it != b->graphs.end()) {
     *out = it->second;
-    *launches = n * (12 + ((b->mix & 1) != 0) + ((b->mix & 2) != 0));
+    *launches = n * (14 + ((b->mix & 1) != 0) + ((b->mix & 2) != 0));
     return LBMD_OK;
   }
   cudaGraph_t g = nullptr;
@@ -841,7 +981,9 @@ void lbmd_batch_destroy(lbmd_batch *b) {
   cudaStreamSynchronize(b->st);
   if (b->pool) cudaMemPoolDestroy(b->pool);
   cudaFree(b->d_rep); cudaFree(b->d_state); cudaFree(b->d_lay); cudaFree(b->d_left); cudaFree(b->d_rep_slot);
-  cudaFree(b->d_batch); cudaFree(b->diag_partial); cudaFree(b->diag_out);
+  pfree(b, b->d_tile_sums);
+  cudaStreamSynchronize(b->st);
+  cudaFree(b->d_batch); cudaFree(b->diag_partial); cudaFree(b->diag_out); cudaFree(b->d_drift);
   if (b->own_stream) cudaStreamDestroy(b->st);
   if (b->side) cudaStreamDestroy(b->side);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
@@ -891,6 +1033,7 @@ int lbmd_batch_create(size_t mem_budget, int storage, int max_slots, void *strea
   if (e == cudaSuccess) e = cudaMalloc(&b->d_rep_slot, sizeof(int) * max_slots);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_batch, sizeof(BatchDev));
   if (e == cudaSuccess) e = cudaMalloc(&b->diag_partial, sizeof(double) * 8 * 1024);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_drift, sizeof(double) * 10 * max_slots);
   if (e == cudaSuccess) e = cudaMalloc(&b->diag_out, sizeof(double) * 8);
   if (e == cudaSuccess) e = cudaMemset(b->d_state, 0, sizeof(RepState) * max_slots);
   if (e == cudaSuccess) e = cudaMemset(b->d_left, 0, sizeof(int) * max_slots);
@@ -916,6 +1059,7 @@ int lbmd_batch_create(size_t mem_budget, int storage, int max_slots, void *strea
   b->hb.left = b->d_left;
   b->hb.rep_slot = b->d_rep_slot;
   b->hb.tile_sites = b->tile_sites;
+  b->hb.drift = b->d_drift;
   b->dirty = true;
   *out = b;
   return LBMD_OK;
@@ -1030,7 +1174,8 @@ int lbmd_batch_init_fluid(lbmd_batch *b, int slot, const float *rhoA, const floa
   launch_init_equilibrium(sl.P, stage, stage + N, du, sl.pop[cur], sl.rest, b->st);
   BK(cudaGetLastError(), "init_equilibrium");
   b->launches++;
-  const RepState st0{cur, 0u, 0ull};
+  const RepState st0{cur, 0u, 0ull, 0ull, sl.prm.diag_every > 0 ? 1u : 0u, 0u};
+  sl.ref_pending = sl.prm.diag_every > 0;
   BK(cudaMemcpyAsync(b->d_state + slot, &st0, sizeof(RepState), cudaMemcpyHostToDevice, b->st), "reset state");
   sl.mirror = st0;
   sl.queued = 0;
@@ -1058,6 +1203,12 @@ int lbmd_batch_set_particles(lbmd_batch *b, int slot, int n, const double *x, co
   sl.P.np = n;
   sl.on_device = false;
   b->dirty = true;
+  if (sl.prm.diag_every > 0 && sl.fluid_ready) {  // the reference includes the new particles
+    const unsigned one = 1u;
+    BK(cudaMemcpyAsync(&b->d_state[slot].ref_req, &one, sizeof(unsigned), cudaMemcpyHostToDevice, b->st),
+       "drift reference");
+    sl.ref_pending = true;
+  }
   return upload_rep(b, slot);
 }
 
@@ -1078,6 +1229,18 @@ int lbmd_batch_step(lbmd_batch *b, int nsteps) {
     most = std::max(most, (int)k);
   }
   if (most == 0) return LBMD_OK;
+  // drift references asked for since the last step: taken on the state as it is now
+  bool pending = false;
+  for (Slot &sl : b->slots)
+    if (sl.used && sl.ref_pending) {
+      pending = true;
+      sl.ref_pending = false;
+    }
+  if (pending) {
+    launch_drift(b);
+    BK(cudaGetLastError(), "drift reference");
+    b->launches += 2;
+  }
   BK(cudaMemcpyAsync(b->d_left, left.data(), sizeof(int) * b->max_slots, cudaMemcpyHostToDevice, b->st), "budgets");
   constexpr int kMaxGraphSteps = 16;
   const int chunk = std::min(most, kMaxGraphSteps);
@@ -1227,6 +1390,18 @@ int lbmd_batch_diagnostics(lbmd_batch *b, int slot, double out[8]) {
     BK(cudaGetLastError(), "sums");
     BK(cudaMemcpyAsync(h, b->diag_out, sizeof(double) * 5, cudaMemcpyDeviceToHost, b->st), "download");
   }
+  BK(cudaStreamSynchronize(b->st), "sync");
+  std::memcpy(out, h, sizeof(h));
+  return LBMD_OK;
+}
+
+int lbmd_batch_get_drift(lbmd_batch *b, int slot, double out[5]) {
+  int r = check_slot(b, slot);
+  if (r) return r;
+  if (!out) return bfail(b, LBMD_E_INVALID_ARG, "null output");
+  if (!b->slots[slot].prm.diag_every) return bfail(b, LBMD_E_STATE, "the replica has no drift check (diag_every = 0)");
+  double h[5];
+  BK(cudaMemcpyAsync(h, b->d_drift + (size_t)slot * 10 + 5, sizeof(h), cudaMemcpyDeviceToHost, b->st), "download");
   BK(cudaStreamSynchronize(b->st), "sync");
   std::memcpy(out, h, sizeof(h));
   return LBMD_OK;

@@ -179,6 +179,31 @@ __global__ void k_finish_sums(const double *__restrict__ partial, int nblocks, i
   out[k] = a;
 }
 
+// The drift check of the conserved totals (appendix: the collision and the forcing term keep
+// each component's mass; Sec. 2: the momentum of fluid and particles together).
+__global__ void k_drift_check(const double *__restrict__ sums, const double *__restrict__ psum, double *ref,
+                              double *last, unsigned *err, long long step, double tol, int set_ref) {
+  double t[5];
+  for (int k = 0; k < 5; ++k) t[k] = sums[k] + (k >= 2 && psum ? psum[k - 2] : 0.0);
+  if (set_ref) {
+    for (int k = 0; k < 5; ++k) ref[k] = t[k];
+    last[0] = -1.0;
+    last[1] = last[2] = last[3] = 0.0;
+    last[4] = 0.0;
+    return;
+  }
+  const double dA = fabs(t[0] - ref[0]) / fabs(ref[0]), dB = fabs(t[1] - ref[1]) / fabs(ref[1]);
+  const double px = t[2] - ref[2], py = t[3] - ref[3], pz = t[4] - ref[4];
+  const double dP = sqrt(px * px + py * py + pz * pz) / (fabs(ref[0]) + fabs(ref[1]));
+  last[0] = (double)step;
+  last[1] = dA;
+  last[2] = dB;
+  last[3] = dP;
+  last[4] += 1.0;
+  // NaN drifts fail the comparison below as well
+  if (!(dA <= tol) || !(dB <= tol) || !(dP <= tol)) atomicOr(err, kErrDrift);
+}
+
 inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
 }  // namespace
@@ -297,6 +322,10 @@ void launch_fluid_sums(const StepParams &P, const void *store, const float *rest
 }
 void launch_finish_sums(const double *partial, int nblocks, int nvals, double *out, cudaStream_t st) {
   k_finish_sums<<<1, 32, 0, st>>>(partial, nblocks, nvals, out);
+}
+void launch_drift_check(const double *sums, const double *psum, double *ref, double *last, unsigned *err,
+                        long long step, double tol, int set_ref, cudaStream_t st) {
+  k_drift_check<<<1, 1, 0, st>>>(sums, psum, ref, last, err, step, tol, set_ref);
 }
 
 // The step base of replayed step graphs (one thread: a write, or an increment at the end of a

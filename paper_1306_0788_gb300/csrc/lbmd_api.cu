@@ -1,5 +1,6 @@
 // lbmd_api.cu -- the C ABI (include/lbmd.h): context, device memory, argument checks and the
 // launch sequence of one coupled step.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -63,6 +64,9 @@ struct lbmd_ctx {
   unsigned *err = nullptr;
   double *diag_partial = nullptr, *diag_out = nullptr;
   int diag_blocks = 0;
+  // the FP64 drift check: reference totals [M_A, M_B, Px, Py, Pz] and the last check's
+  // {step, drift A, drift B, momentum drift, checks} (device memory, 10 doubles)
+  double *drift = nullptr;
   int64_t steps = 0, launches = 0;
   bool fluid_ready = false, types_set = false;
   unsigned sticky = 0;
@@ -134,6 +138,16 @@ int map_device_error(lbmd_ctx *c, unsigned bits) {
   if (bits & kErrTooFast)
     return fail(c, LBMD_E_PARTICLE_TOO_FAST,
                 "with md_substeps > 1 a particle moved more than one cell away within one lattice step");
+  if (bits & kErrDrift) {
+    double d[5] = {0, 0, 0, 0, 0};
+    char m[256];
+    if (cudaMemcpy(d, c->drift + 5, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess) cudaGetLastError();
+    std::snprintf(m, sizeof(m),
+                  "FP64 drift check at step %.0f: mass drift A %.3e, B %.3e, momentum drift %.3e per unit mass "
+                  "(tolerance %.3e)",
+                  d[0], d[1], d[2], d[3], c->prm.drift_tol);
+    return fail(c, LBMD_E_DRIFT, m);
+  }
   return LBMD_OK;
 }
 
@@ -204,6 +218,31 @@ int sort_particles(lbmd_ctx *c, cudaStream_t st) {
   launch_permute(P.np, c->perm, c->pa[c->pcur], c->pa[1 - c->pcur], c->slot_of_id, st);
   c->pcur = 1 - c->pcur;
   return launched(c, "particle sort", 7);  // bin, three scan passes, scatter, row order, permute
+}
+
+// FP64 totals of the current state into diag_out: [M_A, M_B, Px, Py, Pz] of the fluid and,
+// with particles, [5..7] = sum m v (K9 of the step; appendix and Sec. 2 for what they conserve).
+int enqueue_totals(lbmd_ctx *c) {
+  launch_fluid_sums(c->P, c->pop[c->cur], c->rest, c->diag_partial, c->diag_blocks, c->st);
+  launch_finish_sums(c->diag_partial, c->diag_blocks, 5, c->diag_out, c->st);
+  int r = launched(c, "fluid sums", 2);
+  if (r || c->np == 0) return r;
+  StepParams P = c->P;
+  P.np = c->np;
+  const int nb = std::min(c->diag_blocks, (c->np + 255) / 256);
+  double *part = c->diag_partial + (size_t)5 * c->diag_blocks - 3 * (size_t)nb;
+  launch_particle_momentum(P, c->pa[c->pcur], part, nb, c->st);
+  launch_finish_sums(part, nb, 3, c->diag_out + 5, c->st);
+  return launched(c, "particle momentum", 2);
+}
+
+// The drift check on the device (set_ref: take the totals as the reference instead).
+int enqueue_drift(lbmd_ctx *c, int set_ref) {
+  int r = enqueue_totals(c);
+  if (r) return r;
+  launch_drift_check(c->diag_out, c->np > 0 ? c->diag_out + 5 : nullptr, c->drift, c->drift + 5, c->err,
+                     (long long)c->steps, c->prm.drift_tol, set_ref, c->st);
+  return launched(c, "drift check");
 }
 
 }  // namespace
@@ -497,7 +536,7 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
   }
   c->diag_blocks = fluid_sum_blocks(P);
   if ((e = dalloc(&c->diag_partial, (size_t)5 * c->diag_blocks)) != cudaSuccess ||
-      (e = dalloc(&c->diag_out, 8)) != cudaSuccess ||
+      (e = dalloc(&c->diag_out, 8)) != cudaSuccess || (e = dalloc(&c->drift, 10)) != cudaSuccess ||
       (e = cudaMemset(c->err, 0, sizeof(unsigned))) != cudaSuccess) {
     cudaGetLastError();
     lbmd_destroy(c);
@@ -527,7 +566,7 @@ void lbmd_destroy(lbmd_ctx *c) {
     if (e) cudaEventDestroy(e);
   dfree(c->step_base);
   dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho); dfree(c->jp); dfree(c->err); dfree(c->rest);
-  dfree(c->diag_partial); dfree(c->diag_out);
+  dfree(c->diag_partial); dfree(c->diag_out); dfree(c->drift);
   free_particles(c);
   free_records(c);
   dfree(c->row_count); dfree(c->row_start); dfree(c->row_cursor); dfree(c->row_bsum);
@@ -578,9 +617,10 @@ int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const flo
   launch_init_equilibrium(c->P, stage, stage + N, du, c->pop[c->cur], c->rest, c->st);
   int r = launched(c, "init_equilibrium");
   if (r) return r;
+  c->steps = 0;
+  if ((r = enqueue_drift(c, 1))) return r;  // the drift check's reference
   CK(cudaStreamSynchronize(c->st), "sync");
   c->fluid_ready = true;
-  c->steps = 0;
   return LBMD_OK;
 }
 
@@ -674,6 +714,10 @@ int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, con
     int r = sort_particles(c, c->st);
     if (r) return r;
   }
+  if (c->fluid_ready) {  // the drift check's reference includes the new particles' momentum
+    const int r = enqueue_drift(c, 1);
+    if (r) return r;
+  }
   CK(cudaStreamSynchronize(c->st), "sync");
   return LBMD_OK;
 }
@@ -725,22 +769,31 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
   if (c->nbonds > 0 && c->bond_np != c->np)
     return fail(c, LBMD_E_STATE, "bonds refer to a different particle set; call lbmd_set_bonds again");
   c->P.np = c->np;
-  int s = 0, r;
-  if (c->graphs)
-    for (; s + kGraphSteps <= nsteps; s += kGraphSteps)
-      if ((r = replay_steps(c))) {
-        if (r != kGraphUnavailable) return r;
-        break;
+  const int64_t K = c->prm.diag_every;
+  int left = nsteps, r;
+  while (left > 0) {
+    // steps up to the next multiple of diag_every (the drift check runs after it), or all
+    int n = left;
+    if (K > 0) n = (int)std::min<int64_t>(left, K - c->steps % K);
+    left -= n;
+    int s = 0;
+    if (c->graphs)
+      for (; s + kGraphSteps <= n; s += kGraphSteps)
+        if ((r = replay_steps(c))) {
+          if (r != kGraphUnavailable) return r;
+          break;
+        }
+    for (; s < n; ++s) {
+      cudaEvent_t t0 = nullptr, t1 = nullptr;
+      if (c->prof) {
+        if ((r = reserve_events(c, 2))) return r;
+        t0 = c->ev[c->ev_used];
+        t1 = c->ev[c->ev_used + 1];
       }
-  for (; s < nsteps; ++s) {
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
-    if (c->prof) {
-      if ((r = reserve_events(c, 2))) return r;
-      t0 = c->ev[c->ev_used];
-      t1 = c->ev[c->ev_used + 1];
+      if ((r = one_step(c, (unsigned long long)c->steps, t0, t1, cudaEventRecordDefault))) return r;
+      if (c->prof) c->ev_used += 2;
     }
-    if ((r = one_step(c, (unsigned long long)c->steps, t0, t1, cudaEventRecordDefault))) return r;
-    if (c->prof) c->ev_used += 2;
+    if (K > 0 && c->steps % K == 0 && (r = enqueue_drift(c, 0))) return r;
   }
   return LBMD_OK;
 }
@@ -823,26 +876,32 @@ int lbmd_diagnostics(lbmd_ctx *c, double out[8]) {
   if (!c || !out) return c ? fail(c, LBMD_E_INVALID_ARG, "null output") : LBMD_E_INVALID_ARG;
   if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
   cudaSetDevice(c->dev);
-  launch_fluid_sums(c->P, c->pop[c->cur], c->rest, c->diag_partial, c->diag_blocks, c->st);
-  launch_finish_sums(c->diag_partial, c->diag_blocks, 5, c->diag_out, c->st);
-  int r = launched(c, "fluid sums", 2);
+  int r = enqueue_totals(c);
   if (r) return r;
   double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (c->np > 0) {
-    StepParams P = c->P;
-    P.np = c->np;
-    const int nb = std::min(c->diag_blocks, (c->np + 255) / 256);
-    launch_particle_momentum(P, c->pa[c->pcur], c->diag_partial + (size_t)5 * c->diag_blocks - 3 * (size_t)nb, nb,
-                             c->st);
-    launch_finish_sums(c->diag_partial + (size_t)5 * c->diag_blocks - 3 * (size_t)nb, nb, 3, c->diag_out + 5, c->st);
-    if ((r = launched(c, "particle momentum", 2))) return r;
-    CK(cudaMemcpyAsync(h, c->diag_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->st), "download");
-  } else {
-    CK(cudaMemcpyAsync(h, c->diag_out, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->st), "download");
-  }
+  CK(cudaMemcpyAsync(h, c->diag_out, sizeof(double) * (c->np > 0 ? 8 : 5), cudaMemcpyDeviceToHost, c->st),
+     "download");
   r = sync_and_check(c);
   std::memcpy(out, h, sizeof(h));
   return r;
+}
+
+int lbmd_set_drift_reference(lbmd_ctx *c) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
+  cudaSetDevice(c->dev);
+  return enqueue_drift(c, 1);
+}
+
+int lbmd_get_drift(lbmd_ctx *c, double out[5]) {
+  if (!c || !out) return c ? fail(c, LBMD_E_INVALID_ARG, "null output") : LBMD_E_INVALID_ARG;
+  if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
+  cudaSetDevice(c->dev);
+  double h[5];
+  CK(cudaMemcpyAsync(h, c->drift + 5, sizeof(h), cudaMemcpyDeviceToHost, c->st), "download");
+  CK(cudaStreamSynchronize(c->st), "sync");
+  std::memcpy(out, h, sizeof(h));
+  return LBMD_OK;
 }
 
 int64_t lbmd_step_count(const lbmd_ctx *c) { return c ? c->steps : -1; }

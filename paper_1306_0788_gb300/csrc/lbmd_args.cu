@@ -34,6 +34,9 @@ int check_params(const lbmd_params *prm, std::string &why) {
   if (!(prm->rho0_A >= 0.0) || !(prm->rho0_B >= 0.0) || !std::isfinite(prm->rho0_A) || !std::isfinite(prm->rho0_B))
     return why = "rho0_A, rho0_B must be finite and >= 0", LBMD_E_INVALID_ARG;
   if (prm->md_substeps < 1 || prm->md_substeps > 256) return why = "md_substeps must be in [1, 256]", LBMD_E_INVALID_ARG;
+  if (prm->diag_every < 0) return why = "diag_every must be >= 0", LBMD_E_INVALID_ARG;
+  if (prm->diag_every > 0 && !(prm->drift_tol > 0.0 && std::isfinite(prm->drift_tol)))
+    return why = "with diag_every > 0, drift_tol must be finite and > 0", LBMD_E_INVALID_ARG;
   if (prm->collision != LBMD_COLLISION_BGK && prm->collision != LBMD_COLLISION_MRT)
     return why = "unknown collision", LBMD_E_INVALID_ARG;
   if (prm->collision == LBMD_COLLISION_MRT)

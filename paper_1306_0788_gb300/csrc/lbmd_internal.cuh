@@ -32,6 +32,7 @@ constexpr unsigned kErrNonFinite = 1u << 1;
 constexpr unsigned kErrBond = 1u << 2;
 constexpr unsigned kErrParticle = 1u << 3;
 constexpr unsigned kErrTooFast = 1u << 4;  // a particle left its cell's neighbourhood within one sub-stepped step
+constexpr unsigned kErrDrift = 1u << 5;    // the FP64 drift check found a conserved total beyond its tolerance
 
 struct TypeParams {
   float kappa[2];   // Eq. (solvation_kappa)
@@ -230,6 +231,13 @@ cudaError_t set_update_step(cudaGraphExec_t exec, cudaGraphNode_t node, unsigned
 void launch_set_step(unsigned long long *base, unsigned long long value, cudaStream_t st);
 void launch_advance_step(unsigned long long *base, unsigned long long n, cudaStream_t st);
 int fluid_sum_blocks(const StepParams &P);
+// The FP64 drift check: compares the totals [M_A, M_B, Px, Py, Pz] of the fluid (sums[0..4])
+// plus the particle momentum (psum[0..2], NULL: no particles) with ref[5].  set_ref != 0: take
+// them as the new reference (last[4] = 0).  Otherwise last[] = {step, drift of M_A, of M_B,
+// momentum drift per unit mass, checks so far} and kErrDrift goes to err when a drift exceeds
+// tol.  One thread; reads and writes device memory only.
+void launch_drift_check(const double *sums, const double *psum, double *ref, double *last, unsigned *err,
+                        long long step, double tol, int set_ref, cudaStream_t st);
 
 // particles (lb_particles.cu)
 void launch_bin(const StepParams &P, const ParticleArrays &pa, int *row_of, int *row_count,

@@ -105,6 +105,28 @@ def disk(dims, radius: float, rho_hi: float, rho_lo: float, width: float = 2.0):
     return rho_lo + (rho_hi - rho_lo) * phiA, rho_hi - (rho_hi - rho_lo) * phiA
 
 
+def sphere(dims, radius: float, rho_hi: float, rho_lo: float, width: float = 2.0):
+    """A-rich sphere of the given radius centred in the box (at the middle of its central
+    cell), B-rich outside, tanh profile of the given width."""
+    nx, ny, nz = dims
+    z = np.arange(nz)[:, None, None] - nz / 2.0 + 0.5
+    y = np.arange(ny)[None, :, None] - ny / 2.0 + 0.5
+    x = np.arange(nx)[None, None, :] - nx / 2.0 + 0.5
+    phiA = _tanh_profile(radius - np.sqrt(x * x + y * y + z * z), width)
+    return rho_lo + (rho_hi - rho_lo) * phiA, rho_hi - (rho_hi - rho_lo) * phiA
+
+
+def slab_between(dims, z0: float, z1: float, rho_hi: float, rho_lo: float, width: float = 2.0):
+    """A-rich slab between the planes z = z0 and z = z1 (0 <= z0 < z1 <= nz, node k at z = k),
+    B-rich elsewhere, tanh profiles of the given width (periodic in z)."""
+    nx, ny, nz = dims
+    z = np.arange(nz, dtype=np.float64)
+    mid, half = 0.5 * (z0 + z1), 0.5 * (z1 - z0)
+    d = np.abs(((z - mid + nz / 2.0) % nz) - nz / 2.0)  # periodic distance from the slab's middle
+    phiA = _tanh_profile(half - d, width)[:, None, None] * np.ones((nz, ny, nx))
+    return rho_lo + (rho_hi - rho_lo) * phiA, rho_hi - (rho_hi - rho_lo) * phiA
+
+
 def random_particles(n: int, dims, min_dist: float = 1.0, seed: int = 0, max_tries: int = 200):
     """n points uniform in the periodic box with pairwise minimum-image distance > min_dist
     (sequential rejection on a cell grid)."""

@@ -27,6 +27,7 @@ LBMD_E_UNIMPLEMENTED = -7
 LBMD_E_BOND_BROKEN = -8
 LBMD_E_STATE = -9
 LBMD_E_PARTICLE_TOO_FAST = -10
+LBMD_E_DRIFT = -11
 
 LBMD_STORAGE_FP32 = 0
 LBMD_STORAGE_FP16_SHIFTED = 1
@@ -49,13 +50,13 @@ LBMD_SLOT_FAILED = 3
 EXPORTS = ("lbmd_create", "lbmd_destroy", "lbmd_set_types", "lbmd_set_debye_hueckel", "lbmd_init_fluid",
            "lbmd_set_populations", "lbmd_get_populations", "lbmd_set_particles", "lbmd_set_bonds",
            "lbmd_step", "lbmd_set_graphs", "lbmd_sync", "lbmd_clear_error", "lbmd_get_fields", "lbmd_get_particles",
-           "lbmd_diagnostics", "lbmd_step_count", "lbmd_profile_enable", "lbmd_profile_read",
+           "lbmd_diagnostics", "lbmd_set_drift_reference", "lbmd_get_drift", "lbmd_step_count", "lbmd_profile_enable", "lbmd_profile_read",
            "lbmd_launch_count", "lbmd_last_error", "lbmd_fluid_moments_static",
            "lbmd_batch_create", "lbmd_batch_destroy", "lbmd_batch_add", "lbmd_batch_remove",
            "lbmd_batch_set_types", "lbmd_batch_set_debye_hueckel", "lbmd_batch_init_fluid",
            "lbmd_batch_set_particles", "lbmd_batch_step", "lbmd_batch_poll", "lbmd_batch_slot_error",
            "lbmd_batch_step_count", "lbmd_batch_get_populations", "lbmd_batch_get_fields",
-           "lbmd_batch_get_particles", "lbmd_batch_diagnostics", "lbmd_batch_set_config",
+           "lbmd_batch_get_particles", "lbmd_batch_diagnostics", "lbmd_batch_get_drift", "lbmd_batch_set_config",
            "lbmd_batch_get_config", "lbmd_batch_tune", "lbmd_batch_info", "lbmd_batch_launch_count",
            "lbmd_batch_last_error")
 
@@ -72,7 +73,8 @@ class lbmd_params(ctypes.Structure):
                 ("kT", ctypes.c_double), ("dt", ctypes.c_double), ("storage", ctypes.c_int),
                 ("rho0_A", ctypes.c_double), ("rho0_B", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("collision", ctypes.c_int), ("lambda_bulk", ctypes.c_double), ("lambda_mom", ctypes.c_double),
-                ("lambda_ghost", ctypes.c_double), ("md_substeps", ctypes.c_int)]
+                ("lambda_ghost", ctypes.c_double), ("md_substeps", ctypes.c_int), ("diag_every", ctypes.c_int),
+                ("drift_tol", ctypes.c_double)]
 
 
 class lbmd_ptype(ctypes.Structure):
@@ -109,6 +111,8 @@ def _load():
         "lbmd_get_fields": (I, [P, P, P, P]),
         "lbmd_get_particles": (I, [P, P, P, P]),
         "lbmd_diagnostics": (I, [P, P]),
+        "lbmd_set_drift_reference": (I, [P]),
+        "lbmd_get_drift": (I, [P, P]),
         "lbmd_step_count": (ctypes.c_int64, [P]),
         "lbmd_profile_enable": (I, [P, I]),
         "lbmd_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64), I]),
@@ -132,6 +136,7 @@ def _load():
         "lbmd_batch_get_fields": (I, [P, I, P, P, P]),
         "lbmd_batch_get_particles": (I, [P, I, P, P, P]),
         "lbmd_batch_diagnostics": (I, [P, I, P]),
+        "lbmd_batch_get_drift": (I, [P, I, P]),
         "lbmd_batch_set_config": (I, [P, I, I, I, I]),
         "lbmd_batch_get_config": (I, [P, P]),
         "lbmd_batch_tune": (I, [P, P, P]),
@@ -269,6 +274,18 @@ def lbmd_diagnostics(ctx) -> np.ndarray:
     return out
 
 
+def lbmd_set_drift_reference(ctx) -> None:
+    _check(ctx, _lib.lbmd_set_drift_reference(ctx))
+
+
+def lbmd_get_drift(ctx) -> np.ndarray:
+    """[step of the last check (-1: none), mass drift A, mass drift B, momentum drift per unit
+    mass, checks since the reference]."""
+    out = np.zeros(5)
+    _check(ctx, _lib.lbmd_get_drift(ctx, _p(out)))
+    return out
+
+
 def lbmd_step_count(ctx) -> int:
     return int(_lib.lbmd_step_count(ctx))
 
@@ -395,6 +412,12 @@ def lbmd_batch_diagnostics(b, slot: int) -> np.ndarray:
     return out
 
 
+def lbmd_batch_get_drift(b, slot: int) -> np.ndarray:
+    out = np.zeros(5)
+    _bcheck(b, _lib.lbmd_batch_get_drift(b, slot, _p(out)))
+    return out
+
+
 def lbmd_batch_set_config(b, tile_sites: int, grid_moments: int, grid_collide: int, collide_blocks: int) -> None:
     _bcheck(b, _lib.lbmd_batch_set_config(b, tile_sites, grid_moments, grid_collide, collide_blocks))
 
@@ -432,12 +455,12 @@ def lbmd_batch_last_error(b) -> str:
 
 def params(dims, tau_r=1.0, g_AB=0.0, g_BA=None, kT=0.0, seed=0, storage=LBMD_STORAGE_FP32,
            rho0=(0.0, 0.0), collision=LBMD_COLLISION_BGK, lambda_bulk=None, lambda_mom=None,
-           lambda_ghost=None, md_substeps=1) -> lbmd_params:
+           lambda_ghost=None, md_substeps=1, diag_every=0, drift_tol=0.0) -> lbmd_params:
     """Convenience constructor of lbmd_params (dims = (nx, ny, nz)); MRT eigenvalues left as
-    None take the shear value -1/tau_r."""
+    None take the shear value -1/tau_r.  diag_every > 0 switches the FP64 drift check on."""
     nx, ny, nz = dims
     ls = -1.0 / tau_r
     pick = lambda v: ls if v is None else v  # noqa: E731
     return lbmd_params(nx, ny, nz, tau_r, g_AB, g_AB if g_BA is None else g_BA, kT, 1.0, storage,
                        rho0[0], rho0[1], seed, collision, pick(lambda_bulk), pick(lambda_mom), pick(lambda_ghost),
-                       md_substeps)
+                       md_substeps, diag_every, drift_tol)

@@ -91,11 +91,12 @@ def run_oracle(c: Case, nsteps: int, trace_last: bool = False):
     return f, x, v, tr
 
 
-def make_gpu(c: Case, stream=None):
+def make_gpu(c: Case, stream=None, **params):
+    """A context holding case c (params: further lbmd_params fields, e.g. the drift check)."""
     from paper_1306_0788_gb300 import lbmd as L
     ctx, _ = L.lbmd_create(L.params(c.dims, tau_r=c.tau_r, g_AB=c.g, kT=c.kT, seed=c.seed, collision=c.collision,
                                     lambda_bulk=c.lam_bulk, lambda_mom=c.lam_mom, lambda_ghost=c.lam_ghost,
-                                    md_substeps=c.md_substeps, storage=c.storage, rho0=c.rho0), stream)
+                                    md_substeps=c.md_substeps, storage=c.storage, rho0=c.rho0, **params), stream)
     types = [L.lbmd_ptype(*t) for t in c.types]
     pairs = [L.lbmd_pair(i, j, e, s) for (i, j), (e, s) in c.wca.items()]
     L.lbmd_set_types(ctx, types, pairs)

@@ -87,6 +87,16 @@ def test_create_rejects_invalid_substeps_without_device(k):
     assert e.value.code == lbmd.LBMD_E_INVALID_ARG
 
 
+@pytest.mark.parametrize("diag_every,tol", [(-1, 0.0), (5, 0.0), (5, -1e-3), (5, float("inf")), (5, float("nan"))])
+def test_create_rejects_invalid_drift_check_without_device(diag_every, tol):
+    from paper_1306_0788_gb300 import lbmd
+    p = lbmd.params((4, 4, 4), diag_every=diag_every, drift_tol=tol)
+    with pytest.raises(lbmd.LbmdError) as e:
+        lbmd.lbmd_create(p)
+    assert e.value.code == lbmd.LBMD_E_INVALID_ARG
+    assert "diag_every" in lbmd.lbmd_last_error(None)
+
+
 def test_every_entry_point_refuses_a_null_handle_without_device():
     """Each call that takes a context or a batch returns LBMD_E_INVALID_ARG (the counters -1)
     for a NULL handle, before touching the device; destroy(NULL) is a no-op."""

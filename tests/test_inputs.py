@@ -29,7 +29,8 @@ def test_phase_profiles_exchange_the_components():
     """rho_A + rho_B = rho_hi + rho_lo at every node and both stay within [rho_lo, rho_hi]."""
     dims = (48, 40, 64)
     fields = [inputs.slab_and_droplets(dims, 2.0, 0.1, n_drops=3, r_min=3.0, r_max=6.0, width=1.5, seed=1)[:2],
-              inputs.flat_slab(dims, 2.0, 0.1), inputs.disk(dims, 9.0, 2.0, 0.1)]
+              inputs.flat_slab(dims, 2.0, 0.1), inputs.disk(dims, 9.0, 2.0, 0.1),
+              inputs.sphere(dims, 9.0, 2.0, 0.1), inputs.slab_between(dims, 10.3, 50.8, 2.0, 0.1)]
     for a, b in fields:
         assert a.shape == b.shape == (64, 40, 48)
         assert np.allclose(a + b, 2.1, atol=1e-12)
@@ -106,3 +107,25 @@ def test_serving_stream_distributions():
         assert 0 <= r["np"] <= min(5000, int(0.5 * int(r["edge"] // 2.5) ** 3))
         assert 1.2 <= r["g"] <= 2.1 and 0.1 <= r["gamma"] <= 2.0 and r["steps"] == 1000
     assert reqs == inputs.serving_requests(4000, rate=50.0, seed=7)  # the same stream for the same seed
+
+
+def test_sphere_and_slab_between_put_their_interfaces_where_stated():
+    """The sphere is A-rich inside its radius and B-rich outside, with rho_A = rho_B at the stated
+    radius (along the grid line y = z = 0.5 from the centre the zero sits at x = sqrt(R^2 - 1/2));
+    slab_between has rho_A = rho_B at z0 and z1 (node k at z = k), also across the periodic wrap."""
+    dims = (40, 40, 40)
+    a, b = inputs.sphere(dims, 9.0, 2.0, 0.1, width=2.0)
+    c = np.arange(40) - 19.5
+    r = np.sqrt(c[:, None, None] ** 2 + c[None, :, None] ** 2 + c[None, None, :] ** 2)
+    assert ((a - b)[r < 6.0] > 0).all() and ((a - b)[r > 12.0] < 0).all()
+    d = (a - b)[20, 20, 20:]  # x = 0.5, 1.5, ... outwards
+    zero = np.interp(0.0, d[::-1], c[20:][::-1])
+    assert abs(zero - np.sqrt(81.0 - 0.5)) < 0.01
+    for z0, z1 in ((10.3, 30.8), (30.0, 45.0)):
+        a, b = inputs.slab_between((4, 4, 48), z0, z1, 2.0, 0.1, width=2.0)
+        d = (a - b)[:, 0, 0]
+        assert d[int(round((z0 + z1) / 2))] > 0 and d[int(round((z0 + z1) / 2 + 24)) % 48] < 0
+        for zc in (z0, z1):
+            k = int(np.floor(zc))
+            lin = d[k % 48] + (d[(k + 1) % 48] - d[k % 48]) * (zc - k)
+            assert abs(lin) < 0.01
