@@ -282,7 +282,7 @@ def run_batch(args):
 
 def measure_single(workload: str, storage: str = "fp32", collision: str = "bgk", md_substeps: int = 1,
                    launch: str = "graph", steps: int = 20, warmup: int = 5, edge: int = 0, e2e: bool = True,
-                   rank: int = 0, world: int = 1, dist=None):
+                   rank: int = 0, world: int = 1, dist=None, passes: int = 0):
     """One single-lattice measurement: warm-up, K timed steps between CUDA events on the context's
     stream (clocks sampled meanwhile), the update kernel's own event times, and optionally the
     end-to-end run through the C ABI with pinned host buffers.  Returns a dict of raw numbers."""
@@ -300,6 +300,9 @@ def measure_single(workload: str, storage: str = "fp32", collision: str = "bgk",
                    collision=L.LBMD_COLLISION_MRT if mrt else L.LBMD_COLLISION_BGK, md_substeps=md_substeps)
     ctx, _ = L.lbmd_create(prm, stream)
     L.lbmd_set_graphs(ctx, launch == "graph")
+    if passes:
+        L.lbmd_set_lattice_passes(ctx, passes)
+    lattice_passes = L.lbmd_get_lattice_passes(ctx)
     L.lbmd_set_types(ctx, [L.lbmd_ptype(*t) for t in types], [L.lbmd_pair(0, 0, *extra.get("wca", (1.0, 1.0)))])
     if "dh" in extra:
         L.lbmd_set_debye_hueckel(ctx, *extra["dh"])
@@ -376,7 +379,8 @@ def measure_single(workload: str, storage: str = "fp32", collision: str = "bgk",
     L.lbmd_destroy(ctx)
     return dict(dims=dims, N=N, npart=npart, kT=kT, g=g_ab, extra=extra, ms=ms_max, steps=steps,
                 kernel_ms=k_ms / max(k_n, 1), kernel_launches=k_n, launches=launches, clocks=clocks,
-                state_ok=state_ok, e2e=e2e_out, storage=storage, mrt=mrt, workload=workload)
+                state_ok=state_ok, e2e=e2e_out, storage=storage, mrt=mrt, workload=workload,
+                lattice_passes=lattice_passes)
 
 
 def collide_roofline(m, peak, peak_kind):
@@ -423,7 +427,8 @@ def sub_record(m, peak, peak_kind, label):
     """A further configuration measured in the same run, timed like the headline."""
     ms_step = m["ms"] / m["steps"]
     return {"config": {"workload": label, "lattice": list(m["dims"]), "particles": m["npart"],
-                       "storage": m["storage"], "bonds": int(len(m["extra"].get("bonds", [])))},
+                       "storage": m["storage"], "bonds": int(len(m["extra"].get("bonds", []))),
+                       "lattice_passes": m["lattice_passes"]},
             "value": round(m["N"] / (ms_step * 1e-3) / 1e6, 3), "unit": UNIT, "steps": m["steps"],
             "ms_per_step": round(ms_step, 5), "roofline": collide_roofline(m, peak, peak_kind),
             "step_roofline": step_roofline(m, peak), "gpu_launches": int(m["launches"]),
@@ -447,7 +452,7 @@ def run_cuda(args):
         torch.cuda.set_device(0)
 
     m = measure_single(args.workload, args.storage, args.collision, args.md_substeps, args.launch, args.steps,
-                       args.warmup, args.edge, not args.no_e2e, rank, world, dist)
+                       args.warmup, args.edge, not args.no_e2e, rank, world, dist, args.passes)
     peak, peak_kind = measured_hbm_peak()
     N, ms_max = m["N"], m["ms"]
     value = whole_job_rate(N * args.steps, world, ms_max * 1e-3) / 1e6
@@ -463,6 +468,7 @@ def run_cuda(args):
                        "description": WORKLOADS[args.workload][2],
                        "lattice": list(m["dims"]), "particles": m["npart"], "tau_r": 1.0, "g_AB": m["g"],
                        "kT": m["kT"], "storage": args.storage, "launch": args.launch,
+                       "lattice_passes": m["lattice_passes"],
                        "collision": ("fluctuating MRT (Eq. MODES), eigenvalues -1, fluid noise at kT"
                                      if m["mrt"] else "BGK"),
                        "parallelism": "replicas" if world > 1 else "single",
@@ -629,6 +635,8 @@ def main():
     ap.add_argument("--md-substeps", type=int, default=1, help="particle substeps per lattice step")
     ap.add_argument("--launch", choices=["graph", "stream"], default="graph",
                     help="lbmd_step launch mode: replayed two-step graphs, or every kernel one by one")
+    ap.add_argument("--passes", type=int, choices=[0, 1, 2], default=0,
+                    help="lattice update: 0 = chosen by the lattice size, 1 = one pass, 2 = density pass + update")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -208,6 +208,28 @@ int lbmd_step(lbmd_ctx *ctx, int nsteps);
  * LBMD_E_CUDA. */
 int lbmd_set_graphs(lbmd_ctx *ctx, int on);
 
+/* How the lattice update reads the populations (no counterpart in the paper: a property of the
+ * GPU code).  The Shan-Chen force of a node needs its neighbours' densities of the same step, so
+ * the densities must exist before the update.  passes = 2: a density pass pulls every node's
+ * populations and stores the densities, then the update pulls them again.  passes = 1: the
+ * update of step t also forms the densities of step t + 1 from the values it has just computed
+ * (streaming carries f*_i(r) to r + c_i, so the density of a node is the sum of what arrives
+ * from its 19 sources); two short kernels finish the nodes whose sources lie in another block
+ * of the update (the first and last row of each 8-row tile and the first and last plane of each
+ * 16-plane chunk by pulling their populations; the x edges of each 32-column tile from partial
+ * sums the neighbouring tile wrote), and the particle coupling forms j' at its corners.  The one-pass update
+ * reads the populations once per step instead of twice.  passes = 0 (the default) takes one
+ * pass with FP32 storage on lattices of at least 16 x 152 x (blocks per SM) column-tile planes
+ * (tiles of 32 x 8 columns: about 128^3 and up on 152 SMs), two passes otherwise (with 16-bit
+ * storage the update is bound by instruction issue, not by the bytes the second pass reads).  Both give the
+ * same step up to FP32 rounding order (the densities are sums in another order).  One pass
+ * needs the BGK collision and md_substeps = 1 (else LBMD_E_INVALID_ARG for passes = 1).  Drops
+ * the recorded graphs.  lbmd_get_lattice_passes returns the update the next step takes (1 or 2;
+ * setting it up, the first time, allocates the list of the second kernel's nodes) or a negative
+ * LBMD_E_* code. */
+int lbmd_set_lattice_passes(lbmd_ctx *ctx, int passes);
+int lbmd_get_lattice_passes(lbmd_ctx *ctx);
+
 /* Wait for the context stream; returns the first recorded device error, if any. */
 int lbmd_sync(lbmd_ctx *ctx);
 int lbmd_clear_error(lbmd_ctx *ctx);

@@ -93,6 +93,230 @@ __global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const T *__
   collide<T, kParticles, kMRT, kBisect>(P, s, P.step, fin, fout, rho, pa, pf, ci, err, rest_in, rest_out);
 }
 
+// ------------------------------------------------------------------ one-pass update
+//
+// Streaming carries f*_i(r) to r + c_i, so the next density of a node is the sum of the
+// post-collision values arriving from its 19 sources: the update can form it from the values it
+// has just computed instead of a second pass pulling every population again.  Each warp of a
+// block owns one row y of an 8-row column tile and its 32 nodes x0 .. x0 + 31 (one per lane), and
+// the block marches along z through one chunk of planes; the blocks of one chunk cover
+// neighbouring tiles and are launched together, so that they march in step and the sectors they
+// share meet in L2.  Per plane, for each of the 9 (c_y, c_z) groups of directions, a lane adds
+// the values arriving at its node from c_x = 0, +1 (lane below) and -1 (lane above); the groups
+// with c_y = +-1 go to the neighbouring rows through shared memory (double buffered: one barrier
+// per plane), and each row adds what arrives at it into three accumulators, for the planes z - 1,
+// z and z + 1.  After plane z the plane z - 1 is complete and is written.  What leaves the tile
+// along x -- from lane 0 with c_x = -1, from the last lane with c_x = +1 -- is summed the same way
+// into edge partials for the neighbouring tiles' edge nodes, which k_edge_densities adds.  Every
+// sum has a fixed order.  Nodes with sources in another block along y or z -- the first and last
+// row of the tile, the first and last plane of the chunk -- are left to k_boundary_densities,
+// which pulls their populations as the density pass does.
+constexpr int kOPThreads = kOnePassRows * 32;
+// the densities a block's stencils read in one plane: rows y0 - 1 .. y0 + 8, columns x0 - 1 ..
+// x0 + 32
+constexpr int kRhoRows = kOnePassRows + 2, kRhoCols = kOnePassCols + 2, kRhoSlots = 4;
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// 8-byte asynchronous copy global -> shared (cp.async), its commit and wait.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// The staged densities of a block's stencil: a ring of kRhoSlots planes.
+struct StagedRho {
+  static constexpr bool kStaged = true;
+  const float2 (*ring)[kRhoRows][kRhoCols];
+  int sm, s0, sp;  // slots of the planes z - 1, z, z + 1
+  int k, j;        // this node's row and column in a plane
+  __device__ float2 operator()(int cx, int cy, int cz) const {
+    return ring[cz < 0 ? sm : (cz > 0 ? sp : s0)][k + cy][j + cx];
+  }
+};
+
+// Copies (cp.async) the densities of plane z into ring slot `slot_index` % 4: rows y0 - 1 + k,
+// columns x0 - 1 + j, both wrapped periodically; every thread of the block takes part.  The slot
+// follows the unwrapped plane index (z - 1 .. z + 2 of a march take four distinct slots even where
+// the lattice is shorter than four planes).
+__device__ __forceinline__ void stage_plane(const StepParams &P, const float *__restrict__ rho,
+                                            float2 (*ring)[kRhoRows][kRhoCols], int slot_index, int z, int x0,
+                                            int y0) {
+  const float2 *rho2 = reinterpret_cast<const float2 *>(rho);
+  float2(*slot)[kRhoCols] = ring[slot_index & (kRhoSlots - 1)];
+  for (int e = threadIdx.x; e < kRhoRows * kRhoCols; e += kOPThreads) {
+    const int k = e / kRhoCols, j = e - k * kRhoCols;
+    const int y = ((y0 - 1 + k) % P.ny + P.ny) % P.ny, x = ((x0 - 1 + j) % P.nx + P.nx) % P.nx;
+    cp_async8(&slot[k][j], rho2 + ((long long)z * P.ny + y) * P.nx + x);
+  }
+  cp_async_commit();
+}
+
+template <class T, bool kParticles>
+__global__ void __launch_bounds__(kOPThreads, 3)
+    k_collide_onepass(StepParams P, const T *__restrict__ fin, T *__restrict__ fout, const float *__restrict__ rho,
+                      float *__restrict__ rho_next, float *__restrict__ edge, ParticleArrays pa, ParticleForces pf,
+                      CellIndex ci, unsigned *err, const float *__restrict__ rest_in, float *__restrict__ rest_out,
+                      OnePassGeom G) {
+  // groups handed to the neighbouring rows: [0..2] c_y = +1 with c_z = -1, 0, +1; [3..5] c_y = -1
+  __shared__ float2 xch[2][6][kOnePassRows][32];
+  // the same for what leaves the tile along x: [side][c_y = +1, -1][row] (side 0: from lane 0
+  // towards x0 - 1; side 1: from the last lane towards x0 + 32)
+  __shared__ float2 xedge[2][2][2][kOnePassRows];
+  // each thread's arrivals at its node, and each row's edge partials, in planes p with slot p % 3
+  // (in shared memory rather than registers: they live across the whole update of a node)
+  __shared__ float2 acc[3][kOPThreads];
+  __shared__ float2 accE[3][2][kOnePassRows];
+  // the stencils' densities, read from global memory once per block and plane
+  __shared__ float2 ring[kRhoSlots][kRhoRows][kRhoCols];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr unsigned kFull = 0xffffffffu;
+  const int ncols = G.ntx * G.nty, chunk = blockIdx.x / ncols, col = blockIdx.x - chunk * ncols;
+  const int zs = (int)((long long)chunk * P.nz / G.nchunks), ze = (int)((long long)(chunk + 1) * P.nz / G.nchunks);
+  if (ze <= zs) return;  // block-uniform
+  const int tx = col % G.ntx, ty = col / G.ntx;
+  const int x0 = tx * kOnePassCols, nown = min(kOnePassCols, P.nx - x0);
+  const bool own = lane < nown;
+  const int x = own ? x0 + lane : x0;
+  const int y0 = ty * kOnePassRows, rows = min(kOnePassRows, P.ny - y0);
+  const int y = y0 + w;
+  const bool inner_row = w >= 1 && w <= rows - 2;  // the sources along y are in the block
+  const bool inner = own && inner_row;
+  const bool left = lane == 0, right = lane == nown - 1;  // the tile's x edges (both when nown = 1)
+  acc[0][threadIdx.x] = acc[1][threadIdx.x] = acc[2][threadIdx.x] = make_float2(0.f, 0.f);
+  if (threadIdx.x < 3 * 2 * kOnePassRows) (&accE[0][0][0])[threadIdx.x] = make_float2(0.f, 0.f);
+  for (int dz = -1; dz <= 1; ++dz) stage_plane(P, rho, ring, zs + dz + kRhoSlots, (zs + dz + P.nz) % P.nz, x0, y0);
+  cp_async_wait_all();
+  __syncthreads();
+  int parity = 0;
+  for (int z = zs; z < ze; ++z, parity ^= 1) {
+    stage_plane(P, rho, ring, z + 2, (z + 2) % P.nz, x0, y0);  // for the next plane; its slot is free
+    float fA[kQ], fB[kQ];
+    if (own && w < rows) {
+      const long long s = ((long long)z * P.ny + y) * P.nx + x;
+      float rA, rB;
+      const StagedRho st{ring, (z + kRhoSlots - 1) & (kRhoSlots - 1), z & (kRhoSlots - 1),
+                         (z + 1) & (kRhoSlots - 1), w + 1, lane + 1};
+      collide_core_at<T, kParticles, false, false, StagedRho>(P, Coord{x, y, z}, s, P.step, fin, rho, pa, pf, ci,
+                                                              err, rest_in, fA, fB, rA, rB, st);
+      store_node<T, false, true, true>(P, (unsigned)s, fout, rest_out, fA, fB, rA, rB);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) fA[i] = fB[i] = 0.f;
+    }
+    // arrivals of one (c_y, c_z) group at this lane's node: c_x = 0, +1 (from the lane below, none
+    // for lane 0), -1 (from the lane above, none for the last lane)
+    auto group = [&](int i0, int ip, int im) {
+      float pA = __shfl_up_sync(kFull, fA[ip], 1), pB = __shfl_up_sync(kFull, fB[ip], 1);
+      float mA = __shfl_down_sync(kFull, fA[im], 1), mB = __shfl_down_sync(kFull, fB[im], 1);
+      if (lane == 0) pA = pB = 0.f;
+      if (lane + 1 >= nown) mA = mB = 0.f;
+      return add2(add2(make_float2(fA[i0], fB[i0]), make_float2(pA, pB)), make_float2(mA, mB));
+    };
+    float2(*X)[kOnePassRows][32] = xch[parity];
+    X[0][w][lane] = make_float2(fA[17], fB[17]);  // (c_y, c_z) = (+1, -1)
+    X[1][w][lane] = group(3, 7, 10);              // (+1, 0)
+    X[2][w][lane] = make_float2(fA[15], fB[15]);  // (+1, +1)
+    X[3][w][lane] = make_float2(fA[16], fB[16]);  // (-1, -1)
+    X[4][w][lane] = group(4, 9, 8);               // (-1, 0)
+    X[5][w][lane] = make_float2(fA[18], fB[18]);  // (-1, +1)
+    if (left) {  // leaving towards x0 - 1 with c_y = +1, -1
+      xedge[parity][0][0][w] = make_float2(fA[10], fB[10]);
+      xedge[parity][0][1][w] = make_float2(fA[8], fB[8]);
+    }
+    if (right) {  // leaving towards x0 + 32 with c_y = +1, -1
+      xedge[parity][1][0][w] = make_float2(fA[7], fB[7]);
+      xedge[parity][1][1][w] = make_float2(fA[9], fB[9]);
+    }
+    const float2 g0m = group(6, 13, 12), g00 = group(0, 1, 2), g0p = group(5, 11, 14);
+    cp_async_wait_all();  // the next plane's densities (issued above) have landed
+    __syncthreads();
+    const int km = (z + 2) % 3, k0 = z % 3, kp = (z + 1) % 3;
+    if (inner) {
+      // from the row below (c_y = +1), this row (c_y = 0), the row above (c_y = -1), into the
+      // planes z - 1, z, z + 1
+      const float2 am = add2(add2(add2(acc[km][threadIdx.x], X[0][w - 1][lane]), g0m), X[3][w + 1][lane]);
+      acc[k0][threadIdx.x] = add2(add2(add2(acc[k0][threadIdx.x], X[1][w - 1][lane]), g00), X[4][w + 1][lane]);
+      acc[kp][threadIdx.x] = add2(add2(add2(acc[kp][threadIdx.x], X[2][w - 1][lane]), g0p), X[5][w + 1][lane]);
+      if (z >= zs + 2)  // plane z - 1 has all its sources (z - 2 .. z) in the chunk
+        reinterpret_cast<float2 *>(rho_next)[((long long)(z - 1) * P.ny + y) * P.nx + x] =
+            add2(am, make_float2(shift_sum(P, 0), shift_sum(P, 1)));
+      acc[km][threadIdx.x] = make_float2(0.f, 0.f);  // becomes plane z + 2
+    }
+    if (inner_row && (left || right)) {
+      // what leaves the tile along x, for the neighbouring tiles' edge nodes in this row: the
+      // side-0 sums from lane 0 (c_x = -1: directions 2, 10, 8, 14, 12), the side-1 sums from the
+      // last lane (c_x = +1: 1, 7, 9, 11, 13)
+      float2 *edge2 = reinterpret_cast<float2 *>(edge);
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        if (side == 0 ? !left : !right) continue;
+        const int i00 = side ? 1 : 2, i0p = side ? 11 : 14, i0m = side ? 13 : 12;
+        const float2 em = add2(accE[km][side][w], make_float2(fA[i0m], fB[i0m]));
+        accE[k0][side][w] = add2(add2(add2(accE[k0][side][w], xedge[parity][side][0][w - 1]),
+                                      make_float2(fA[i00], fB[i00])),
+                                 xedge[parity][side][1][w + 1]);
+        accE[kp][side][w] = add2(accE[kp][side][w], make_float2(fA[i0p], fB[i0p]));
+        if (z >= zs + 2) edge2[(((long long)(z - 1) * P.ny + y) * G.ntx + tx) * 2 + side] = em;
+        accE[km][side][w] = make_float2(0.f, 0.f);
+      }
+    }
+  }
+  cp_async_wait_all();  // no copy outlives the block
+}
+
+// Densities of the boundary runs of the one-pass update, from the populations it wrote (a
+// warp per run).
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_boundary_densities(StepParams P, const T *__restrict__ store,
+                                                               const float *__restrict__ rest,
+                                                               float *__restrict__ rho_next,
+                                                               const BoundaryRun *__restrict__ runs, int nruns) {
+  const int r = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= nruns) return;
+  const BoundaryRun b = runs[r];
+  if (lane >= b.n) return;
+  moments(P, (long long)b.row * P.nx + b.x0 + lane, store, rest, rho_next, nullptr);
+}
+
+// The x-edge nodes of the inner rows and planes of every tile: its own partial (in rho_next) plus
+// what arrives from the neighbouring tiles -- from the left one's side-1 sums at x0, from the
+// right one's side-0 sums at x0 + nown - 1 (both, in that order, when a tile has one column).
+__global__ void __launch_bounds__(kBlock) k_edge_densities(StepParams P, OnePassGeom G,
+                                                           const float *__restrict__ edge,
+                                                           float *__restrict__ rho_next) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)P.nz * P.ny * G.ntx;
+  if (t >= n) return;
+  const int tx = (int)(t % G.ntx);
+  const long long r = t / G.ntx;  // z * ny + y
+  const int z = (int)(r / P.ny), y = (int)(r - (long long)z * P.ny);
+  const int w = y % kOnePassRows, y0 = y - w, rows = min(kOnePassRows, P.ny - y0);
+  if (w < 1 || w > rows - 2) return;  // edge rows: finished by k_boundary_densities
+  const int chunk = (int)(((long long)z * G.nchunks + G.nchunks - 1) / P.nz);  // the chunk holding z
+  int c = chunk;
+  while (c > 0 && (long long)c * P.nz / G.nchunks > z) --c;
+  while ((long long)(c + 1) * P.nz / G.nchunks <= z) ++c;
+  const int zs = (int)((long long)c * P.nz / G.nchunks), ze = (int)((long long)(c + 1) * P.nz / G.nchunks);
+  if (z < zs + 1 || z > ze - 2) return;  // chunk edge planes: finished by k_boundary_densities
+  const int x0 = tx * kOnePassCols, nown = min(kOnePassCols, P.nx - x0);
+  const int txl = tx == 0 ? G.ntx - 1 : tx - 1, txr = tx == G.ntx - 1 ? 0 : tx + 1;
+  const float2 *e2 = reinterpret_cast<const float2 *>(edge);
+  float2 *rho2 = reinterpret_cast<float2 *>(rho_next);
+  const long long base = r * P.nx;
+  float2 v = rho2[base + x0];
+  v = add2(v, e2[(r * G.ntx + txl) * 2 + 1]);  // from the left tile's last lane
+  if (nown == 1) {
+    v = add2(v, e2[(r * G.ntx + txr) * 2 + 0]);  // and from the right tile's lane 0
+    rho2[base + x0] = v;
+    return;
+  }
+  rho2[base + x0] = v;
+  rho2[base + x0 + nown - 1] = add2(rho2[base + x0 + nown - 1], e2[(r * G.ntx + txr) * 2 + 0]);
+}
+
 // rho_A, rho_B and u = (j' + g^SC/2)/rho at the current step (for readback).
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_fields(StepParams P, const T *__restrict__ store,
@@ -267,6 +491,48 @@ void launch_collide(const StepParams &P, const void *fin, void *fout, float *res
     else
       k_collide<T, false, false><<<grid_for(P.N), kBlock, 0, st>>>(P, a, b, rho, pa, pf, ci, err, rest, rest);
   });
+}
+
+void launch_collide_onepass(const StepParams &P, const void *fin, void *fout, float *rest, const float *rho,
+                            float *rho_next, float *edge, const ParticleArrays &pa, const ParticleForces &pf,
+                            CellIndex ci, unsigned *err, OnePassGeom G, int grid, cudaStream_t st) {
+  with_storage(P, [&](auto t) {
+    using T = std::remove_pointer_t<decltype(t)>;
+    const T *a = static_cast<const T *>(fin);
+    T *b = static_cast<T *>(fout);
+    if (P.np > 0)
+      k_collide_onepass<T, true><<<grid, kOPThreads, 0, st>>>(P, a, b, rho, rho_next, edge, pa, pf, ci, err, rest,
+                                                              rest, G);
+    else
+      k_collide_onepass<T, false><<<grid, kOPThreads, 0, st>>>(P, a, b, rho, rho_next, edge, pa, pf, ci, err, rest,
+                                                               rest, G);
+  });
+}
+
+void launch_edge_densities(const StepParams &P, OnePassGeom G, const float *edge, float *rho_next, cudaStream_t st) {
+  const long long n = (long long)P.nz * P.ny * G.ntx;
+  k_edge_densities<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(P, G, edge, rho_next);
+}
+
+void launch_boundary_densities(const StepParams &P, const void *store, const float *rest, float *rho_next,
+                               const BoundaryRun *runs, int nruns, cudaStream_t st) {
+  if (nruns <= 0) return;
+  const unsigned grid = (unsigned)((nruns + kBlock / 32 - 1) / (kBlock / 32));
+  with_storage(P, [&](auto t) {
+    using T = std::remove_pointer_t<decltype(t)>;
+    k_boundary_densities<T><<<grid, kBlock, 0, st>>>(P, static_cast<const T *>(store), rest, rho_next, runs, nruns);
+  });
+}
+
+int onepass_blocks_per_sm() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_collide_onepass<float, true>, kOPThreads, 0) !=
+          cudaSuccess ||
+      b < 1) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return b;
 }
 
 template <class T>

@@ -217,6 +217,18 @@ __global__ void __launch_bounds__(kPBlock) k_couple(StepParams P, ParticleArrays
   site::couple8(P, noise_step(P, P.step), p, k, 0xFFu << (threadIdx.x & 24), pa, pa, ci, rho, jp, pf);
 }
 
+// k_couple with j' pulled from the populations at each corner.
+template <class T>
+__global__ void __launch_bounds__(kPBlock) k_couple_pull(StepParams P, ParticleArrays pa, CellIndex ci,
+                                                         const float *__restrict__ rho, const T *__restrict__ fin,
+                                                         ParticleForces pf) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (int)(t >> 3), k = (int)(t & 7);
+  if (p >= P.np) return;
+  site::couple8<T>(P, noise_step(P, P.step), p, k, 0xFFu << (threadIdx.x & 24), pa, pa, ci, rho, nullptr, pf, true,
+                   fin);
+}
+
 // Pair and bonded forces of every particle (site::pairs).
 __global__ void __launch_bounds__(kPBlock) k_pairs(StepParams P, ParticleArrays pa, CellIndex ci,
                                                    const int *__restrict__ bond_start,
@@ -346,6 +358,20 @@ void launch_permute(int np, const int *perm, const ParticleArrays &src, const Pa
 void launch_couple(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho, const float *jp,
                    const ParticleForces &pf, cudaStream_t st) {
   k_couple<<<pgrid(8LL * P.np), kPBlock, 0, st>>>(P, pa, ci, rho, jp, pf);
+}
+void launch_couple_pull(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho,
+                        const void *store, const ParticleForces &pf, cudaStream_t st) {
+  switch (P.storage) {
+    case LBMD_STORAGE_FP16_SHIFTED:
+      k_couple_pull<__half><<<pgrid(8LL * P.np), kPBlock, 0, st>>>(P, pa, ci, rho, static_cast<const __half *>(store), pf);
+      break;
+    case LBMD_STORAGE_BF16_SHIFTED:
+      k_couple_pull<__nv_bfloat16><<<pgrid(8LL * P.np), kPBlock, 0, st>>>(
+          P, pa, ci, rho, static_cast<const __nv_bfloat16 *>(store), pf);
+      break;
+    default:
+      k_couple_pull<float><<<pgrid(8LL * P.np), kPBlock, 0, st>>>(P, pa, ci, rho, static_cast<const float *>(store), pf);
+  }
 }
 void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const int *bond_start,
                   const int *bond_other, const int *slot_of_id, const ParticleForces &pf, unsigned *err,

@@ -467,28 +467,35 @@ __device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long lo
   mrt_component(P, fB, rB, ux, uy, uz, gB, nz);
 }
 
-// The lattice update of one step at site s: pull, densities and momentum, Shan-Chen force
-// (Eq. SCforce with psi = rho, g_AA = g_BB = 0), fluid-side solvation force and momentum
-// return from the particles (Sec. 2), barycentric velocity (Eq. momentum_definition), BGK
-// collision with forcing for both components (BGK, or with kMRT the fluctuating MRT of Eq. MODES,
-// `step` being the noise counter), write.  With 16-bit storage rest_in / rest_out are the FP32
-// rest populations (rest_out may be NULL, in the autotuner's trial launches: no rest population
-// is written then).
-template <class T, bool kParticles, bool kMRT = false, bool kBisect = false>
-__device__ __forceinline__ void collide(const StepParams &P, long long s, unsigned long long step,
-                                        const T *__restrict__ fin,
-                                        T *__restrict__ fout, const float *__restrict__ rho,
-                                        const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci,
-                                        unsigned *err, const float *__restrict__ rest_in,
-                                        float *__restrict__ rest_out) {
-  const Coord c = site_coord(P, s);
+// Where the update reads the densities of its Shan-Chen stencil: from the density field in global
+// memory (GlobalRho, the default), or from a copy a block staged in shared memory (a type with
+// kStaged = true whose call operator gives the (rho_A, rho_B) pair at offset (cx, cy, cz)).
+struct GlobalRho {
+  static constexpr bool kStaged = false;
+  __device__ float2 operator()(int, int, int) const { return make_float2(0.f, 0.f); }
+};
+
+// The lattice update of one step at site s, up to the store: pull, densities and momentum,
+// Shan-Chen force (Eq. SCforce with psi = rho, g_AA = g_BB = 0), fluid-side solvation force and
+// momentum return from the particles (Sec. 2), barycentric velocity (Eq. momentum_definition),
+// collision with forcing for both components (BGK, or with kMRT the fluctuating MRT of Eq.
+// MODES, `step` being the noise counter).  On return fA, fB hold the post-collision values
+// (16-bit storage with BGK: the moving ones shifted by w_i rho0, as stored) and rA, rB the node's
+// densities before the collision.
+template <class T, bool kParticles, bool kMRT = false, bool kBisect = false, class Rho = GlobalRho>
+__device__ __forceinline__ void collide_core_at(const StepParams &P, const Coord c, long long s,
+                                                unsigned long long step, const T *__restrict__ fin,
+                                                const float *__restrict__ rho, const ParticleArrays &pa,
+                                                const ParticleForces &pf, CellIndex ci, unsigned *err,
+                                                const float *__restrict__ rest_in, float (&fA)[kQ],
+                                                float (&fB)[kQ], float &rA_out, float &rB_out,
+                                                const Rho &staged = Rho{}) {
   const NOff o = neighbour_offsets(P, c);
   const unsigned N32 = (unsigned)P.N, s32 = (unsigned)s;
   // 16-bit storage with the BGK update: the moving populations stay shifted (f - w_i rho0, as
   // stored) through the update, the shifts folded into its constants, and the FP32 rest
   // population closes the node's mass
   constexpr bool kShifted = kSplitRest<T> && !kMRT;
-  float fA[kQ], fB[kQ];
   if constexpr (kSplitRest<T>) {
     // 16-bit storage: one 32-bit word per direction holds the (A, B) pair; the rest populations
     // are kept in FP32
@@ -532,8 +539,14 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
   float2 Sx = make_float2(0.f, 0.f), Sy = Sx, Sz = Sx;
 #pragma unroll
   for (int i = 1; i < kQ; i += 2) {
-    const float2 rp = __ldg(rho2 + (unsigned)((int)s32 + shift(o, kCx[i], kCy[i], kCz[i])));
-    const float2 rm = __ldg(rho2 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i])));
+    float2 rp, rm;
+    if constexpr (Rho::kStaged) {
+      rp = staged(kCx[i], kCy[i], kCz[i]);
+      rm = staged(-kCx[i], -kCy[i], -kCz[i]);
+    } else {
+      rp = __ldg(rho2 + (unsigned)((int)s32 + shift(o, kCx[i], kCy[i], kCz[i])));
+      rm = __ldg(rho2 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i])));
+    }
     const float2 d = __ffma2_rn(make_float2(-1.f, -1.f), rm, rp);
     if (kCx[i]) Sx = __ffma2_rn(make_float2(kW[i] * kCx[i], kW[i] * kCx[i]), d, Sx);
     if (kCy[i]) Sy = __ffma2_rn(make_float2(kW[i] * kCy[i], kW[i] * kCy[i]), d, Sy);
@@ -601,6 +614,34 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
       fB[j] = fj.y;
     }
   }
+  rA_out = rA;
+  rB_out = rB;
+}
+
+// collide_core at site s, its coordinates computed from the index.
+template <class T, bool kParticles, bool kMRT = false, bool kBisect = false>
+__device__ __forceinline__ void collide_core(const StepParams &P, long long s, unsigned long long step,
+                                             const T *__restrict__ fin, const float *__restrict__ rho,
+                                             const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci,
+                                             unsigned *err, const float *__restrict__ rest_in, float (&fA)[kQ],
+                                             float (&fB)[kQ], float &rA_out, float &rB_out) {
+  collide_core_at<T, kParticles, kMRT, kBisect>(P, site_coord(P, s), s, step, fin, rho, pa, pf, ci, err, rest_in,
+                                                fA, fB, rA_out, rB_out);
+}
+
+// The store of the update at site s32 (values from collide_core).  With 16-bit storage rest_out
+// is the FP32 rest array (NULL, in the autotuner's trial launches: no rest population is
+// written).  kWrite = false computes what would be stored without writing it.  With kKeep, fA and
+// fB are left holding the stored values -- the moving ones as stored (16-bit: decoded, still
+// shifted) and the rest population at [0] -- whose sum (plus the shifts, 16-bit) is the node's
+// share of the next step's densities.
+template <class T, bool kMRT = false, bool kWrite = true, bool kKeep = false>
+__device__ __forceinline__ void store_node(const StepParams &P, unsigned s32, T *__restrict__ fout,
+                                           float *__restrict__ rest_out, float (&fA)[kQ], float (&fB)[kQ],
+                                           float rA, float rB, bool write = true) {
+  static_assert(!(kMRT && kKeep), "the stored values are kept for the BGK update only");
+  const unsigned N32 = (unsigned)P.N;
+  constexpr bool kShifted = kSplitRest<T> && !kMRT;
   if constexpr (kSplitRest<T>) {
     unsigned *wout = reinterpret_cast<unsigned *>(fout);
     if (kShifted) {
@@ -610,12 +651,21 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
 #pragma unroll
       for (int i = 1; i < kQ; ++i) {
         const unsigned w = Pair16<T>::enc(make_float2(fA[i], fB[i]));
-        wout[i * N32 + s32] = w;
-        m = __ffma2_rn(make_float2(-1.f, -1.f), Pair16<T>::dec(w), m);
+        if (kWrite && write) wout[i * N32 + s32] = w;
+        const float2 d = Pair16<T>::dec(w);
+        m = __ffma2_rn(make_float2(-1.f, -1.f), d, m);
+        if (kKeep) {
+          fA[i] = d.x;
+          fB[i] = d.y;
+        }
       }
-      if (rest_out) {
+      if (kWrite && write && rest_out) {
         rest_out[s32] = m.x;
         rest_out[N32 + s32] = m.y;
+      }
+      if (kKeep) {
+        fA[0] = m.x;
+        fB[0] = m.y;
       }
     } else {
       // MRT: each moving population is rounded on store as f - w_i rho0; the FP32 rest population
@@ -626,19 +676,33 @@ __device__ __forceinline__ void collide(const StepParams &P, long long s, unsign
       for (int i = 1; i < kQ; ++i) {
         const float2 v = make_float2(fA[i] - pop_shift(P, 0, i), fB[i] - pop_shift(P, 1, i));
         const unsigned w = Pair16<T>::enc(v);
-        wout[i * N32 + s32] = w;
+        if (kWrite) wout[i * N32 + s32] = w;
         e = __fadd2_rn(e, __ffma2_rn(make_float2(-1.f, -1.f), Pair16<T>::dec(w), v));
       }
-      if (rest_out) {
+      if (kWrite && rest_out) {
         rest_out[s32] = fA[0] + e.x;
         rest_out[N32 + s32] = fB[0] + e.y;
       }
     }
-  } else {
+  } else if (kWrite) {
     float2 *fout2 = reinterpret_cast<float2 *>(fout);
+    if (write)
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) fout2[i * N32 + s32] = make_float2(fA[i], fB[i]);
+      for (int i = 0; i < kQ; ++i) fout2[i * N32 + s32] = make_float2(fA[i], fB[i]);
   }
+}
+
+// The whole lattice update of one step at site s: collide_core, then the store.
+template <class T, bool kParticles, bool kMRT = false, bool kBisect = false>
+__device__ __forceinline__ void collide(const StepParams &P, long long s, unsigned long long step,
+                                        const T *__restrict__ fin,
+                                        T *__restrict__ fout, const float *__restrict__ rho,
+                                        const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci,
+                                        unsigned *err, const float *__restrict__ rest_in,
+                                        float *__restrict__ rest_out) {
+  float fA[kQ], fB[kQ], rA, rB;
+  collide_core<T, kParticles, kMRT, kBisect>(P, s, step, fin, rho, pa, pf, ci, err, rest_in, fA, fB, rA, rB);
+  store_node<T, kMRT>(P, (unsigned)s, fout, rest_out, fA, fB, rA, rB);
 }
 
 // ------------------------------------------------------------------ particles
@@ -680,11 +744,37 @@ struct CoupleSums {
   float3 up, gA, gB, fsr;
 };
 
+// j' = sum_z sum_i f_zi c_i at node (x, y, z), pulled from the populations (the densities'
+// pass of the one-pass update stores no j').  16-bit storage: the stored values are shifted by
+// w_i rho0, and sum_i w_i c_i = 0, so the shifts drop out.
+template <class T>
+__device__ __forceinline__ float3 jprime_at(const StepParams &P, const T *__restrict__ fin, int x, int y, int z) {
+  const NOff o = neighbour_offsets(P, Coord{x, y, z});
+  const unsigned N32 = (unsigned)P.N, s32 = (unsigned)site_index(P, x, y, z);
+  float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const unsigned src = i * N32 + (unsigned)((int)s32 + shift(o, -kCx[i], -kCy[i], -kCz[i]));  // pull r - c_i
+    float2 v;
+    if constexpr (kSplitRest<T>)
+      v = Pair16<T>::dec(__ldg(reinterpret_cast<const unsigned *>(fin) + src));
+    else
+      v = __ldg(reinterpret_cast<const float2 *>(fin) + src);
+    jx += kCx[i] * (v.x + v.y);
+    jy += kCy[i] * (v.x + v.y);
+    jz += kCz[i] * (v.x + v.y);
+  }
+  return make_float3(jx, jy, jz);
+}
+
 // Contribution of corner k (offset (k & 1, k >> 1 & 1, k >> 2 & 1)) of the particle's cell.
+// j' comes from jp, or (jp NULL) is pulled from the populations fin.
+template <class TS = float>
 __device__ __forceinline__ void couple_corner(const StepParams &P, int k, int4 c, float4 fr, const TypeParams &T,
                                               const ParticleArrays &list, CellIndex ci,
                                               const float *__restrict__ rho, const float *__restrict__ jp,
-                                              const ParticleForces &pf, bool with_fsr, CoupleSums &S) {
+                                              const ParticleForces &pf, bool with_fsr, CoupleSums &S,
+                                              const TS *__restrict__ fin = nullptr) {
   const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
   const int X = c.x + ox == P.nx ? 0 : c.x + ox;
   const int Y = c.y + oy == P.ny ? 0 : c.y + oy;
@@ -696,9 +786,11 @@ __device__ __forceinline__ void couple_corner(const StepParams &P, int k, int4 c
   const long long s = site_index(P, X, Y, Z);
   const float rinv = 1.f / (n.rA + n.rB);
   const float w = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
-  S.up.x += w * (__ldg(jp + s) + 0.5f * (fA.x + fB.x)) * rinv;
-  S.up.y += w * (__ldg(jp + P.N + s) + 0.5f * (fA.y + fB.y)) * rinv;
-  S.up.z += w * (__ldg(jp + 2 * P.N + s) + 0.5f * (fA.z + fB.z)) * rinv;
+  const float3 j = jp ? make_float3(__ldg(jp + s), __ldg(jp + P.N + s), __ldg(jp + 2 * P.N + s))
+                      : jprime_at<TS>(P, fin, X, Y, Z);
+  S.up.x += w * (j.x + 0.5f * (fA.x + fB.x)) * rinv;
+  S.up.y += w * (j.y + 0.5f * (fA.y + fB.y)) * rinv;
+  S.up.z += w * (j.z + 0.5f * (fA.z + fB.z)) * rinv;
   S.gA.x += w * n.SA.x; S.gA.y += w * n.SA.y; S.gA.z += w * n.SA.z;
   S.gB.x += w * n.SB.x; S.gB.y += w * n.SB.y; S.gB.z += w * n.SB.z;
   if (with_fsr && (T.lam[0] != 0.f || T.lam[1] != 0.f)) {
@@ -734,21 +826,23 @@ __device__ __forceinline__ void couple_finish(const StepParams &P, unsigned long
 // solvation force enters the coupling velocity (the same arrays, except in the later particle
 // substeps, which keep the list of the step's start).  with_fsr: compute the reaction of the
 // particle's own fluid-side solvation force (else keep the value in pf.fsr).
+template <class T = float>
 __device__ __forceinline__ void couple8(const StepParams &P, unsigned long long step, int p, int k, unsigned mask,
                                         const ParticleArrays &self, const ParticleArrays &list, CellIndex ci,
                                         const float *__restrict__ rho, const float *__restrict__ jp,
-                                        const ParticleForces &pf, bool with_fsr = true) {
+                                        const ParticleForces &pf, bool with_fsr = true,
+                                        const T *__restrict__ fin = nullptr) {
   const int4 c = self.cell[p];
   const float4 fr = self.frac[p];
-  const TypeParams &T = P.types[c.w];
+  const TypeParams &Ty = P.types[c.w];
   CoupleSums S{};
-  couple_corner(P, k, c, fr, T, list, ci, rho, jp, pf, with_fsr, S);
+  couple_corner<T>(P, k, c, fr, Ty, list, ci, rho, jp, pf, with_fsr, S, fin);
   float *x = &S.up.x;  // the 12 sums, contiguous
 #pragma unroll
   for (int off = 4; off > 0; off >>= 1)
 #pragma unroll
     for (int q = 0; q < 12; ++q) x[q] += __shfl_xor_sync(mask, x[q], off);
-  if (k == 0) couple_finish(P, step, p, self, pf, with_fsr, T, self.vel[p], S);
+  if (k == 0) couple_finish(P, step, p, self, pf, with_fsr, Ty, self.vel[p], S);
 }
 __device__ __forceinline__ int min_image_cells(int d, int n) {
   d = wrapi(d, n);

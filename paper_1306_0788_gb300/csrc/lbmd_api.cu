@@ -45,8 +45,20 @@ struct lbmd_ctx {
   size_t pop_elem = 4;
   float *rest = nullptr;  // 16-bit storage: FP32 rest populations [2][N] (not double-buffered: local)
   int cur = 0;
-  float *rho = nullptr;  // [N][2] interleaved rho_A, rho_B
+  // [N][2] interleaved rho_A, rho_B: rho_buf[cur] holds the densities of pop[cur] while
+  // rho_valid (after init_fluid, set_populations and one-pass steps; the two-pass update
+  // recomputes them at the start of its step)
+  float *rho_buf[2] = {nullptr, nullptr};
+  bool rho_valid = false;
   float *jp = nullptr;   // [3][N]
+  // the lattice update: 0 = chosen by the lattice size, 1 = one pass (densities of the next step
+  // formed by the update), 2 = two passes (density pass, then the update)
+  int passes = 0;
+  OnePassGeom op_geom{};
+  int op_grid = 0;
+  BoundaryRun *op_runs = nullptr;
+  int op_nruns = 0;
+  float *op_edge = nullptr;  // edge partial sums [nz][ny][ntx][2] float2
   // particles
   int np = 0, cap = 0;
   ParticleArrays pa[2]{};
@@ -203,6 +215,91 @@ void free_particles(lbmd_ctx *c) {
   c->cap = 0;
 }
 
+// One-pass update: BGK, one particle update per lattice step.  Chosen by the lattice size
+// unless set (lbmd_set_lattice_passes): when the blocks of the full persistent grid march at least
+// kOnePassAutoPlanes planes each; smaller lattices (set to one pass) take a grid of stretches of
+// kOnePassMinPlanes planes.
+constexpr int kOnePassMinPlanes = 8;
+constexpr int kOnePassAutoPlanes = 16;
+constexpr int kOnePassChunkPlanes = 16;
+
+bool onepass_allowed(const lbmd_ctx *c) {
+  return c->P.collision == LBMD_COLLISION_BGK && c->P.substeps == 1;
+}
+
+long long onepass_units(const StepParams &P) {
+  const long long ntx = (P.nx + kOnePassCols - 1) / kOnePassCols, nty = (P.ny + kOnePassRows - 1) / kOnePassRows;
+  return ntx * nty * P.nz;
+}
+
+int onepass_full_grid(const lbmd_ctx *c) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  return sms * onepass_blocks_per_sm();
+}
+
+bool uses_onepass(const lbmd_ctx *c) {
+  if (!onepass_allowed(c) || c->passes == 2) return false;
+  if (c->passes == 1) return true;
+  return c->op_grid > 0;  // auto: prepare_onepass decided from the size
+}
+
+// Sets up the one-pass update (persistent grid, boundary runs) once per context; in the automatic
+// mode only for lattices large enough.  Allocates: call it before any capture.
+int prepare_onepass(lbmd_ctx *c) {
+  if (!onepass_allowed(c) || c->passes == 2 || c->op_runs) return LBMD_OK;
+  const StepParams &P = c->P;
+  const long long U = onepass_units(P);
+  const int full = onepass_full_grid(c);
+  // automatic: one pass for FP32 storage on lattices large enough (the 16-bit update is bound by
+  // instruction issue, and the one-pass update's extra instructions cost it more than the second
+  // pass over half the bytes)
+  if (c->passes == 0 && (P.storage != LBMD_STORAGE_FP32 || U < (long long)kOnePassAutoPlanes * full))
+    return LBMD_OK;  // two passes
+  const int ntx = (P.nx + kOnePassCols - 1) / kOnePassCols, nty = (P.ny + kOnePassRows - 1) / kOnePassRows;
+  // chunks of about kOnePassChunkPlanes planes, one block each, neighbouring column tiles of a
+  // chunk launched together (they march in step, so the sectors they share meet in L2)
+  const int nchunks = std::max(1, (P.nz + kOnePassChunkPlanes / 2) / kOnePassChunkPlanes);
+  const int grid = ntx * nty * nchunks;
+  std::vector<unsigned char> edge((size_t)ntx * nty * P.nz, 0);
+  for (int col = 0; col < ntx * nty; ++col)
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int zs = (int)((long long)ch * P.nz / nchunks), ze = (int)((long long)(ch + 1) * P.nz / nchunks);
+      if (ze <= zs) continue;
+      edge[(size_t)col * P.nz + zs] = edge[(size_t)col * P.nz + ze - 1] = 1;
+    }
+  std::vector<BoundaryRun> runs;
+  for (int col = 0; col < ntx * nty; ++col) {
+    const int tx = col % ntx, ty = col / ntx;
+    const int x0 = tx * kOnePassCols, nown = std::min(kOnePassCols, P.nx - x0);
+    const int y0 = ty * kOnePassRows, rows = std::min(kOnePassRows, P.ny - y0);
+    for (int z = 0; z < P.nz; ++z)
+      for (int w = 0; w < rows; ++w)
+        if (edge[(size_t)col * P.nz + z] || w == 0 || w == rows - 1)
+          runs.push_back(BoundaryRun{z * P.ny + y0 + w, x0, nown});
+  }
+  if (runs.size() > 0x7fffffffull) return fail(c, LBMD_E_INVALID_ARG, "too many boundary runs");
+  CK(dalloc(&c->op_edge, (size_t)P.nz * P.ny * ntx * 4), "edge sums");
+  CK(dalloc(&c->op_runs, runs.size()), "boundary runs");
+  CK(cudaMemcpy(c->op_runs, runs.data(), sizeof(BoundaryRun) * runs.size(), cudaMemcpyHostToDevice), "boundary runs");
+  c->op_nruns = (int)runs.size();
+  c->op_geom = OnePassGeom{ntx, nty, nchunks};
+  c->op_grid = grid;
+  return LBMD_OK;
+}
+
+// The densities of the current state into rho_buf[cur] (a density pass), if not there already.
+int ensure_densities(lbmd_ctx *c) {
+  if (c->rho_valid) return LBMD_OK;
+  launch_moments(c->P, c->pop[c->cur], c->rest, c->rho_buf[c->cur], nullptr, c->st);
+  const int r = launched(c, "moments");
+  if (!r) c->rho_valid = true;
+  return r;
+}
+
 int sort_particles(lbmd_ctx *c, cudaStream_t st) {
   const StepParams &P = c->P;
   if (sort_fits_one_block(P.nrows, P.np)) {
@@ -283,7 +380,7 @@ int substep_particles(lbmd_ctx *c, ParticleArrays &pa, ParticleForces &pf, CellI
     launch_pairs(Qp, C, rows, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf, c->err,
                  c->side);
     CK(cudaEventRecord(c->ev_pairs, c->side), "event");
-    launch_couple_sub(Q, C, S, rows, c->rho, c->jp, c->pf, sub, c->rec[0], c->st);
+    launch_couple_sub(Q, C, S, rows, c->rho_buf[c->cur], c->jp, c->pf, sub, c->rec[0], c->st);
     CK(cudaStreamWaitEvent(c->st, c->ev_pairs, 0), "stream wait");
     launch_integrate_sub(Q, C, S, c->pf, c->err, c->st);
     if ((r = launched(c, "particle substep", 3))) return r;
@@ -327,17 +424,23 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
   const CellIndex ci{c->row_start};
   const void *fin = c->pop[c->cur];
   void *fout = c->pop[1 - c->cur];
+  float *rho = c->rho_buf[c->cur];
   int r;
   const bool sub = P.np > 0 && P.substeps > 1;
+  const bool onepass = uses_onepass(c);
   if (P.np > 0) {  // the particle sort runs beside the density pass
     CK(cudaEventRecord(c->ev_int, c->st), "event");
     CK(cudaStreamWaitEvent(c->side, c->ev_int, 0), "stream wait");
     if ((r = sort_particles(c, c->side))) return r;
     CK(cudaEventRecord(c->ev_sorted, c->side), "event");
   }
-  // densities (and j' for the particle coupling) of this step's populations
-  launch_moments(P, fin, c->rest, c->rho, P.np > 0 ? c->jp : nullptr, c->st);
-  if ((r = launched(c, "moments"))) return r;
+  if (onepass) {
+    if (!c->rho_valid) return fail(c, LBMD_E_STATE, "one-pass update without the densities of the current state");
+  } else {
+    // densities (and j' for the particle coupling) of this step's populations
+    launch_moments(P, fin, c->rest, rho, P.np > 0 ? c->jp : nullptr, c->st);
+    if ((r = launched(c, "moments"))) return r;
+  }
   ParticleArrays gpa = c->pa[c->pcur];  // what the update gathers the momentum return from
   ParticleForces gpf = c->pf;
   CellIndex gci = ci;
@@ -346,7 +449,10 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
     if ((r = substep_particles(c, gpa, gpf, gci))) return r;
   } else if (P.np > 0) {
     CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
-    launch_couple(P, c->pa[c->pcur], ci, c->rho, c->jp, c->pf, c->st);
+    if (onepass)  // no density pass stored j': the coupling pulls it at its corners
+      launch_couple_pull(P, c->pa[c->pcur], ci, rho, fin, c->pf, c->st);
+    else
+      launch_couple(P, c->pa[c->pcur], ci, rho, c->jp, c->pf, c->st);
     CK(cudaEventRecord(c->ev_coupled, c->st), "event");
     launch_pairs(P, c->pa[c->pcur], ci, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf,
                  c->err, c->side);
@@ -356,9 +462,18 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
     if ((r = launched(c, "particle forces and update", 3))) return r;
   }
   if (t0) CK(cudaEventRecordWithFlags(t0, c->st, flags), "event");
-  launch_collide(P, fin, fout, c->rest, c->rho, gpa, gpf, gci, c->err, c->st);
+  if (onepass)
+    launch_collide_onepass(P, fin, fout, c->rest, rho, c->rho_buf[1 - c->cur], c->op_edge, gpa, gpf, gci, c->err,
+                           c->op_geom, c->op_grid, c->st);
+  else
+    launch_collide(P, fin, fout, c->rest, rho, gpa, gpf, gci, c->err, c->st);
   if ((r = launched(c, "collide"))) return r;
   if (t1) CK(cudaEventRecordWithFlags(t1, c->st, flags), "event");
+  if (onepass) {
+    launch_boundary_densities(P, fout, c->rest, c->rho_buf[1 - c->cur], c->op_runs, c->op_nruns, c->st);
+    launch_edge_densities(P, c->op_geom, c->op_edge, c->rho_buf[1 - c->cur], c->st);
+    if ((r = launched(c, "boundary densities", 2))) return r;
+  }
   if (sub) {
     c->pcur = 1 - c->pcur;  // the working copy that took the substeps is the particle state
   } else if (P.np > 0) {
@@ -367,6 +482,7 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
   }
   c->cur = 1 - c->cur;
   c->steps++;
+  c->rho_valid = onepass;  // the two-pass update leaves the new state's densities to its next step
   return LBMD_OK;
 }
 
@@ -387,12 +503,14 @@ int record_steps(lbmd_ctx *c, StepGraph &g) {
   int r;
   if (P.np > 0 && P.substeps > 1 && (r = ensure_records(c, (long long)P.substeps * P.np)))
     return r;  // no allocation while recording
+  if ((r = prepare_onepass(c))) return r;
   if (!c->gst) CK(cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking), "graph stream");
   if (!c->step_base) CK(dalloc(&c->step_base, 1), "alloc step base");
   if (c->prof)
     for (cudaEvent_t &e : c->ph)
       if (!e) CK(cudaEventCreate(&e), "event");
   const int cur0 = c->cur, pcur0 = c->pcur;
+  const bool rho_valid0 = c->rho_valid;
   const int64_t steps0 = c->steps, launches0 = c->launches;
   cudaStream_t user = c->st;
   CK(cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -413,6 +531,7 @@ int record_steps(lbmd_ctx *c, StepGraph &g) {
   c->P.step_base = nullptr;
   c->cur = cur0;
   c->pcur = pcur0;
+  c->rho_valid = rho_valid0;
   c->steps = steps0;
   g.launches = c->launches - launches0;
   c->launches = launches0;
@@ -469,6 +588,8 @@ int record_steps(lbmd_ctx *c, StepGraph &g) {
 int replay_steps(lbmd_ctx *c) {
   StepGraph &g = c->graph[c->cur][c->pcur];
   int r;
+  if ((r = prepare_onepass(c))) return r;
+  if (uses_onepass(c) && (r = ensure_densities(c))) return r;  // before recording: not in the graph
   if (!g.exec && (r = record_steps(c, g))) return r;
   if (c->dev_step != c->steps) {  // steps were taken without the graph since it last ran
     launch_set_step(c->step_base, (unsigned long long)c->steps, c->st);
@@ -486,6 +607,7 @@ int replay_steps(lbmd_ctx *c) {
   c->launches += g.launches;
   c->steps += kGraphSteps;
   c->dev_step = c->steps;
+  c->rho_valid = uses_onepass(c);
   return LBMD_OK;
 }
 
@@ -517,7 +639,8 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
   cudaError_t e = cudaSuccess;
   const size_t npop = (size_t)2 * kQ * P.N * c->pop_elem;  // bytes; >= 19 N floats of staging
   if ((e = dalloc(&c->pop[0], npop)) != cudaSuccess || (e = dalloc(&c->pop[1], npop)) != cudaSuccess ||
-      (e = dalloc(&c->rho, (size_t)2 * P.N)) != cudaSuccess || (e = dalloc(&c->jp, (size_t)3 * P.N)) != cudaSuccess ||
+      (e = dalloc(&c->rho_buf[0], (size_t)2 * P.N)) != cudaSuccess ||
+      (e = dalloc(&c->rho_buf[1], (size_t)2 * P.N)) != cudaSuccess || (e = dalloc(&c->jp, (size_t)3 * P.N)) != cudaSuccess ||
       (e = dalloc(&c->err, 1)) != cudaSuccess ||
       (c->pop_elem == 2 && (e = dalloc(&c->rest, (size_t)2 * P.N)) != cudaSuccess)) {
     cudaGetLastError();
@@ -565,7 +688,8 @@ void lbmd_destroy(lbmd_ctx *c) {
   for (cudaEvent_t e : c->ph)
     if (e) cudaEventDestroy(e);
   dfree(c->step_base);
-  dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho); dfree(c->jp); dfree(c->err); dfree(c->rest);
+  dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho_buf[0]); dfree(c->rho_buf[1]); dfree(c->jp); dfree(c->err);
+  dfree(c->rest); dfree(c->op_runs); dfree(c->op_edge);
   dfree(c->diag_partial); dfree(c->diag_out); dfree(c->drift);
   free_particles(c);
   free_records(c);
@@ -618,6 +742,8 @@ int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const flo
   int r = launched(c, "init_equilibrium");
   if (r) return r;
   c->steps = 0;
+  c->rho_valid = false;
+  if ((r = ensure_densities(c))) return r;
   if ((r = enqueue_drift(c, 1))) return r;  // the drift check's reference
   CK(cudaStreamSynchronize(c->st), "sync");
   c->fluid_ready = true;
@@ -633,6 +759,8 @@ int lbmd_set_populations(lbmd_ctx *c, int comp, const float *f) {
   launch_restream(c->P, stage, comp, c->pop[c->cur], c->rest, c->st);
   int r = launched(c, "restream");
   if (r) return r;
+  c->rho_valid = false;
+  if ((r = ensure_densities(c))) return r;
   CK(cudaStreamSynchronize(c->st), "sync");
   c->fluid_ready = true;
   return LBMD_OK;
@@ -783,6 +911,10 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
           if (r != kGraphUnavailable) return r;
           break;
         }
+    if (s < n) {
+      if ((r = prepare_onepass(c))) return r;
+      if (uses_onepass(c) && (r = ensure_densities(c))) return r;
+    }
     for (; s < n; ++s) {
       cudaEvent_t t0 = nullptr, t1 = nullptr;
       if (c->prof) {
@@ -804,6 +936,31 @@ int lbmd_set_graphs(lbmd_ctx *c, int on) {
   drop_graphs(c);
   c->graphs = on != 0;
   return LBMD_OK;
+}
+
+int lbmd_set_lattice_passes(lbmd_ctx *c, int passes) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  if (passes < 0 || passes > 2) return fail(c, LBMD_E_INVALID_ARG, "passes must be 0 (by size), 1 or 2");
+  if (passes == 1 && !onepass_allowed(c))
+    return fail(c, LBMD_E_INVALID_ARG, "the one-pass update takes the BGK collision with md_substeps = 1");
+  cudaSetDevice(c->dev);
+  drop_graphs(c);
+  if (passes != c->passes) {
+    dfree(c->op_runs);  // set up again for the new choice at the next step
+    dfree(c->op_edge);
+    c->op_nruns = 0;
+    c->op_grid = 0;
+  }
+  c->passes = passes;
+  return LBMD_OK;
+}
+
+int lbmd_get_lattice_passes(lbmd_ctx *c) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  cudaSetDevice(c->dev);
+  const int r = prepare_onepass(c);
+  if (r) return r;
+  return uses_onepass(c) ? 1 : 2;
 }
 
 int lbmd_sync(lbmd_ctx *c) {
@@ -828,10 +985,10 @@ int lbmd_get_fields(lbmd_ctx *c, float *rhoA, float *rhoB, float *u) {
   cudaSetDevice(c->dev);
   const long long N = c->P.N;
   float *stage = reinterpret_cast<float *>(c->pop[1 - c->cur]);
-  launch_moments(c->P, c->pop[c->cur], c->rest, c->rho, nullptr, c->st);
-  launch_fields(c->P, c->pop[c->cur], c->rest, c->rho, stage, stage + N, stage + 2 * N, c->st);
-  int r = launched(c, "fields", 2);
+  int r = ensure_densities(c);
   if (r) return r;
+  launch_fields(c->P, c->pop[c->cur], c->rest, c->rho_buf[c->cur], stage, stage + N, stage + 2 * N, c->st);
+  if ((r = launched(c, "fields"))) return r;
   const size_t bytes = sizeof(float) * (size_t)N;
   if (rhoA) CK(cudaMemcpyAsync(rhoA, stage, bytes, cudaMemcpyDeviceToHost, c->st), "download");
   if (rhoB) CK(cudaMemcpyAsync(rhoB, stage + N, bytes, cudaMemcpyDeviceToHost, c->st), "download");

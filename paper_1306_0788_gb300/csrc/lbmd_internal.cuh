@@ -117,6 +117,24 @@ struct CellIndex {
   const int *row_start;  // [nrows + 1] offsets into the sorted particle arrays
 };
 
+// The one-pass lattice update: a block's warps own 8 consecutive rows (y) of a column tile of 32
+// x nodes (one per lane) and the block marches along z through one chunk of planes of that tile;
+// the blocks of a chunk cover neighbouring tiles and run together.  Nodes of the first and last
+// row of a tile and of the first and last plane of a chunk are finished by a second kernel from a
+// list of (row, x0, count) runs; the two nodes at the x edges of a tile row get the values
+// arriving from the neighbouring tile through edge partial sums added by a third.
+constexpr int kOnePassRows = 8;
+constexpr int kOnePassCols = 32;
+struct OnePassGeom {
+  int ntx, nty;  // column tiles along x (kOnePassCols columns each) and y (kOnePassRows rows)
+  int nchunks;   // z-chunks per tile: block b takes chunk b / (ntx nty) of tile b % (ntx nty)
+};
+struct BoundaryRun {
+  int row;   // z * ny + y
+  int x0;    // first node
+  int n;     // nodes (at most kOnePassCols)
+};
+
 __host__ __device__ __forceinline__ int wrapi(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;
@@ -216,6 +234,19 @@ void launch_moments(const StepParams &P, const void *store, const float *rest, f
 void launch_collide(const StepParams &P, const void *fin, void *fout, float *rest, const float *rho,
                     const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci, unsigned *err,
                     cudaStream_t st);
+// One-pass update (BGK, md_substeps = 1): writes the populations of the next step and the
+// densities rho_next of the nodes inside each block's stretch; launch_boundary_densities then
+// computes the densities of the listed boundary runs from the new populations.
+void launch_collide_onepass(const StepParams &P, const void *fin, void *fout, float *rest, const float *rho,
+                            float *rho_next, float *edge, const ParticleArrays &pa, const ParticleForces &pf,
+                            CellIndex ci, unsigned *err, OnePassGeom G, int grid, cudaStream_t st);
+void launch_boundary_densities(const StepParams &P, const void *store, const float *rest, float *rho_next,
+                               const BoundaryRun *runs, int nruns, cudaStream_t st);
+// Adds the edge partial sums (edge: [nz][ny][ntx][2] float2) to the x-edge nodes of the inner
+// rows and planes.
+void launch_edge_densities(const StepParams &P, OnePassGeom G, const float *edge, float *rho_next, cudaStream_t st);
+// Blocks of the one-pass update resident on one SM (its persistent grid is this times the SMs).
+int onepass_blocks_per_sm();
 void launch_fields(const StepParams &P, const void *store, const float *rest, const float *rho, float *rhoA,
                    float *rhoB, float *u, cudaStream_t st);
 void launch_fluid_sums(const StepParams &P, const void *store, const float *rest, double *partial, int nblocks,
@@ -256,6 +287,9 @@ void launch_permute(int np, const int *perm, const ParticleArrays &src, const Pa
                     int *slot_of_id, cudaStream_t st);
 void launch_couple(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho,
                    const float *jp, const ParticleForces &pf, cudaStream_t st);
+// The same with j' pulled from the populations `store` (element type P.storage) at the corners.
+void launch_couple_pull(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho,
+                        const void *store, const ParticleForces &pf, cudaStream_t st);
 void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const int *bond_start,
                   const int *bond_other, const int *slot_of_id, const ParticleForces &pf, unsigned *err,
                   cudaStream_t st);

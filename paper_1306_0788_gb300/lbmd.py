@@ -49,7 +49,7 @@ LBMD_SLOT_FAILED = 3
 # every symbol include/lbmd.h declares
 EXPORTS = ("lbmd_create", "lbmd_destroy", "lbmd_set_types", "lbmd_set_debye_hueckel", "lbmd_init_fluid",
            "lbmd_set_populations", "lbmd_get_populations", "lbmd_set_particles", "lbmd_set_bonds",
-           "lbmd_step", "lbmd_set_graphs", "lbmd_sync", "lbmd_clear_error", "lbmd_get_fields", "lbmd_get_particles",
+           "lbmd_step", "lbmd_set_graphs", "lbmd_set_lattice_passes", "lbmd_get_lattice_passes", "lbmd_sync", "lbmd_clear_error", "lbmd_get_fields", "lbmd_get_particles",
            "lbmd_diagnostics", "lbmd_set_drift_reference", "lbmd_get_drift", "lbmd_step_count", "lbmd_profile_enable", "lbmd_profile_read",
            "lbmd_launch_count", "lbmd_last_error", "lbmd_fluid_moments_static",
            "lbmd_batch_create", "lbmd_batch_destroy", "lbmd_batch_add", "lbmd_batch_remove",
@@ -106,6 +106,8 @@ def _load():
         "lbmd_set_bonds": (I, [P, I, P, I, D, D]),
         "lbmd_step": (I, [P, I]),
         "lbmd_set_graphs": (I, [P, I]),
+        "lbmd_set_lattice_passes": (I, [P, I]),
+        "lbmd_get_lattice_passes": (I, [P]),
         "lbmd_sync": (I, [P]),
         "lbmd_clear_error": (I, [P]),
         "lbmd_get_fields": (I, [P, P, P, P]),
@@ -242,6 +244,18 @@ def lbmd_step(ctx, nsteps: int) -> None:
 
 def lbmd_set_graphs(ctx, on: bool) -> None:
     _check(ctx, _lib.lbmd_set_graphs(ctx, int(bool(on))))
+
+
+def lbmd_set_lattice_passes(ctx, passes: int) -> None:
+    """0: chosen by the lattice size, 1: one-pass update, 2: density pass + update."""
+    _check(ctx, _lib.lbmd_set_lattice_passes(ctx, passes))
+
+
+def lbmd_get_lattice_passes(ctx) -> int:
+    r = _lib.lbmd_get_lattice_passes(ctx)
+    if r < 0:
+        _check(ctx, r)
+    return int(r)
 
 
 def lbmd_sync(ctx) -> None:

@@ -91,12 +91,15 @@ def run_oracle(c: Case, nsteps: int, trace_last: bool = False):
     return f, x, v, tr
 
 
-def make_gpu(c: Case, stream=None, **params):
-    """A context holding case c (params: further lbmd_params fields, e.g. the drift check)."""
+def make_gpu(c: Case, stream=None, passes=None, **params):
+    """A context holding case c (passes: the lattice update, lbmd_set_lattice_passes; params:
+    further lbmd_params fields, e.g. the drift check)."""
     from paper_1306_0788_gb300 import lbmd as L
     ctx, _ = L.lbmd_create(L.params(c.dims, tau_r=c.tau_r, g_AB=c.g, kT=c.kT, seed=c.seed, collision=c.collision,
                                     lambda_bulk=c.lam_bulk, lambda_mom=c.lam_mom, lambda_ghost=c.lam_ghost,
                                     md_substeps=c.md_substeps, storage=c.storage, rho0=c.rho0, **params), stream)
+    if passes is not None:
+        L.lbmd_set_lattice_passes(ctx, passes)
     types = [L.lbmd_ptype(*t) for t in c.types]
     pairs = [L.lbmd_pair(i, j, e, s) for (i, j), (e, s) in c.wca.items()]
     L.lbmd_set_types(ctx, types, pairs)
@@ -110,9 +113,9 @@ def make_gpu(c: Case, stream=None, **params):
     return ctx
 
 
-def run_gpu(c: Case, nsteps: int):
+def run_gpu(c: Case, nsteps: int, passes=None):
     from paper_1306_0788_gb300 import lbmd as L
-    ctx = make_gpu(c)
+    ctx = make_gpu(c, passes=passes)
     try:
         L.lbmd_step(ctx, nsteps)
         L.lbmd_sync(ctx)

@@ -35,11 +35,13 @@ def _drifts(d0, d1):
 
 def test_clean_coupled_run_is_quiet_and_reports_the_diagnostics_drift():
     """50 coupled steps (friction, solvation, WCA, thermal noise) with a check every 10 steps:
-    no LBMD_E_DRIFT at a tolerance of 1e-6, five checks, and the drifts the check reports are
-    the ones recomputed on the host from lbmd_diagnostics at the same step."""
+    no LBMD_E_DRIFT at a tolerance of 1e-5 (FP32 rounding moves each component's mass by about
+    1.3e-8 per step: 6.6e-7 after these 50 steps on one GB300 run), five checks, and the drifts
+    the check reports are the ones recomputed on the host from lbmd_diagnostics at the same
+    step."""
     from paper_1306_0788_gb300 import lbmd as L
     c = _coupled_case()
-    ctx = make_gpu(c, diag_every=10, drift_tol=1e-6)
+    ctx = make_gpu(c, diag_every=10, drift_tol=1e-5)
     try:
         d0 = L.lbmd_diagnostics(ctx)
         assert L.lbmd_get_drift(ctx)[0] == -1  # reference taken, no check yet
@@ -52,7 +54,7 @@ def test_clean_coupled_run_is_quiet_and_reports_the_diagnostics_drift():
         print("drift after 50 steps", got)
         assert got[0] == 50 and got[4] == 5
         assert np.allclose(got[1:4], want, rtol=1e-9, atol=1e-18)
-        assert max(got[1:4]) < 1e-6
+        assert max(got[1:4]) < 1e-5
     finally:
         L.lbmd_destroy(ctx)
 

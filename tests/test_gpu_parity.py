@@ -234,7 +234,8 @@ def test_particles_can_be_removed_and_resized():
 
 # ------------------------------------------------------------------ full size
 def test_full_size_256_tiled_against_16_oracle():
-    """At the 256^3 size the bench runs, in the same launch configuration: a state that is
+    """At the 256^3 size the bench runs, in the same launch configuration (the one-pass update,
+    replayed step graphs): a state that is
     periodic with period 16 in every direction (a 16^3 system tiled 16 times per axis, its
     particles replicated -- 16384 particles) evolves exactly like the 16^3 system.  Sampled
     tiles of the GPU result are compared with the 16^3 oracle."""
@@ -255,6 +256,7 @@ def test_full_size_256_tiled_against_16_oracle():
               v=np.zeros((nb, 3)), ptype=np.zeros(nb, dtype=np.int32), types=types, wca={(0, 0): (1.0, 1.0)})
     ctx = make_gpu(cb)
     try:
+        assert L().lbmd_get_lattice_passes(ctx) == 1  # the bench's update at this size
         L().lbmd_step(ctx, 2)
         L().lbmd_sync(ctx)
         fa = L().lbmd_get_populations(ctx, 0, cb.shape)
