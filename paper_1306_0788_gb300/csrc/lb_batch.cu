@@ -398,16 +398,19 @@ __global__ void __launch_bounds__(kBThreads) kb_drift_sums(const BatchDev *__res
     for (int k = threadIdx.x; k < ts; k += kBThreads) {
       const long long s = base + k;
       if (s >= P.N) break;
+      site::FloatPair m[5];  // the node's sums without rounding error; FP64 over nodes
 #pragma unroll
       for (int i = 0; i < kQ; ++i) {
-        const double a = (double)site::pop_read(P, f, R.rest, 0, i, s);
-        const double b = (double)site::pop_read(P, f, R.rest, 1, i, s);
-        acc[0] += a;
-        acc[1] += b;
-        if (kCx[i]) acc[2] += kCx[i] * (a + b);
-        if (kCy[i]) acc[3] += kCy[i] * (a + b);
-        if (kCz[i]) acc[4] += kCz[i] * (a + b);
+        const float a = site::pop_read(P, f, R.rest, 0, i, s);
+        const float b = site::pop_read(P, f, R.rest, 1, i, s);
+        m[0].add(a);
+        m[1].add(b);
+        if (kCx[i]) { m[2].add(kCx[i] > 0 ? a : -a); m[2].add(kCx[i] > 0 ? b : -b); }
+        if (kCy[i]) { m[3].add(kCy[i] > 0 ? a : -a); m[3].add(kCy[i] > 0 ? b : -b); }
+        if (kCz[i]) { m[4].add(kCz[i] > 0 ? a : -a); m[4].add(kCz[i] > 0 ? b : -b); }
       }
+#pragma unroll
+      for (int q = 0; q < 5; ++q) acc[q] += m[q].value();
     }
     __syncthreads();  // sh is free (previous tile)
 #pragma unroll

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const T *__
 // per plane), and each row adds what arrives at it into three accumulators, for the planes z - 1,
 // z and z + 1.  After plane z the plane z - 1 is complete and is written.  What leaves the tile
 // along x -- from lane 0 with c_x = -1, from the last lane with c_x = +1 -- is summed the same way
-// into edge partials for the neighbouring tiles' edge nodes, which k_edge_densities adds.  Every
+// into edge partials for the neighbouring tiles' edge nodes, which k_boundary_densities adds.  Every
 // sum has a fixed order.  Nodes with sources in another block along y or z -- the first and last
 // row of the tile, the first and last plane of the chunk -- are left to k_boundary_densities,
 // which pulls their populations as the density pass does.
@@ -267,50 +267,48 @@ __global__ void __launch_bounds__(kOPThreads, 3)
   cp_async_wait_all();  // no copy outlives the block
 }
 
-// Densities of the boundary runs of the one-pass update, from the populations it wrote (a
-// warp per run).
+// The nodes the one-pass update leaves unfinished, in one launch: blocks [0, run_blocks) take the
+// boundary runs, a warp per run, and compute their densities from the new populations as the
+// density pass does; the blocks after them add the edge partial sums to the x-edge nodes of the
+// inner rows and planes of every tile -- its own partial (in rho_next) plus what arrives from the
+// neighbouring tiles: from the left one's side-1 sums at x0, from the right one's side-0 sums at
+// x0 + nown - 1 (both, in that order, when a tile has one column).  The two sets of nodes are
+// disjoint.
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_boundary_densities(StepParams P, const T *__restrict__ store,
+__global__ void __launch_bounds__(kBlock) k_boundary_densities(StepParams P, OnePassGeom G, const T *__restrict__ store,
                                                                const float *__restrict__ rest,
                                                                float *__restrict__ rho_next,
-                                                               const BoundaryRun *__restrict__ runs, int nruns) {
-  const int r = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (r >= nruns) return;
-  const BoundaryRun b = runs[r];
-  if (lane >= b.n) return;
-  moments(P, (long long)b.row * P.nx + b.x0 + lane, store, rest, rho_next, nullptr);
-}
-
-// The x-edge nodes of the inner rows and planes of every tile: its own partial (in rho_next) plus
-// what arrives from the neighbouring tiles -- from the left one's side-1 sums at x0, from the
-// right one's side-0 sums at x0 + nown - 1 (both, in that order, when a tile has one column).
-__global__ void __launch_bounds__(kBlock) k_edge_densities(StepParams P, OnePassGeom G,
-                                                           const float *__restrict__ edge,
-                                                           float *__restrict__ rho_next) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                                                               const BoundaryRun *__restrict__ runs, int nruns,
+                                                               int run_blocks, const float *__restrict__ edge) {
+  if ((int)blockIdx.x < run_blocks) {
+    const int r = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= nruns) return;
+    const BoundaryRun b = runs[r];
+    if (lane >= b.n) return;
+    moments(P, (long long)b.row * P.nx + b.x0 + lane, store, rest, rho_next, nullptr);
+    return;
+  }
+  const long long t = (long long)(blockIdx.x - run_blocks) * blockDim.x + threadIdx.x;
   const long long n = (long long)P.nz * P.ny * G.ntx;
   if (t >= n) return;
   const int tx = (int)(t % G.ntx);
   const long long r = t / G.ntx;  // z * ny + y
   const int z = (int)(r / P.ny), y = (int)(r - (long long)z * P.ny);
   const int w = y % kOnePassRows, y0 = y - w, rows = min(kOnePassRows, P.ny - y0);
-  if (w < 1 || w > rows - 2) return;  // edge rows: finished by k_boundary_densities
-  const int chunk = (int)(((long long)z * G.nchunks + G.nchunks - 1) / P.nz);  // the chunk holding z
-  int c = chunk;
+  if (w < 1 || w > rows - 2) return;  // tile edge rows: boundary runs
+  int c = (int)((long long)z * G.nchunks / P.nz);  // the chunk holding z: start(c) <= z < start(c + 1)
   while (c > 0 && (long long)c * P.nz / G.nchunks > z) --c;
   while ((long long)(c + 1) * P.nz / G.nchunks <= z) ++c;
   const int zs = (int)((long long)c * P.nz / G.nchunks), ze = (int)((long long)(c + 1) * P.nz / G.nchunks);
-  if (z < zs + 1 || z > ze - 2) return;  // chunk edge planes: finished by k_boundary_densities
+  if (z < zs + 1 || z > ze - 2) return;  // chunk edge planes: boundary runs
   const int x0 = tx * kOnePassCols, nown = min(kOnePassCols, P.nx - x0);
   const int txl = tx == 0 ? G.ntx - 1 : tx - 1, txr = tx == G.ntx - 1 ? 0 : tx + 1;
   const float2 *e2 = reinterpret_cast<const float2 *>(edge);
   float2 *rho2 = reinterpret_cast<float2 *>(rho_next);
   const long long base = r * P.nx;
-  float2 v = rho2[base + x0];
-  v = add2(v, e2[(r * G.ntx + txl) * 2 + 1]);  // from the left tile's last lane
+  float2 v = add2(rho2[base + x0], e2[(r * G.ntx + txl) * 2 + 1]);  // from the left tile's last lane
   if (nown == 1) {
-    v = add2(v, e2[(r * G.ntx + txr) * 2 + 0]);  // and from the right tile's lane 0
-    rho2[base + x0] = v;
+    rho2[base + x0] = add2(v, e2[(r * G.ntx + txr) * 2 + 0]);  // and from the right tile's lane 0
     return;
   }
   rho2[base + x0] = v;
@@ -359,7 +357,8 @@ __global__ void __launch_bounds__(kBlock) k_fields(StepParams P, const T *__rest
 }
 
 // FP64 block partial sums of [M_A, M_B, Px, Py, Pz] over the stored buffer (streaming
-// permutes populations, so sums over stored and post-streaming values agree).
+// permutes populations, so sums over stored and post-streaming values agree), each node's sums
+// formed as FloatPair (lb_site.cuh): five FP64 additions per node instead of about ninety.
 constexpr int kSumBlock = 256;
 template <class T>
 __global__ void __launch_bounds__(kSumBlock) k_fluid_sums(StepParams P, const T *__restrict__ store,
@@ -368,16 +367,19 @@ __global__ void __launch_bounds__(kSumBlock) k_fluid_sums(StepParams P, const T 
   double acc[5] = {0, 0, 0, 0, 0};
   for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < P.N;
        s += (long long)gridDim.x * blockDim.x) {
+    FloatPair m[5];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      const double a = (double)pop_read(P, store, rest, 0, i, s);
-      const double b = (double)pop_read(P, store, rest, 1, i, s);
-      acc[0] += a;
-      acc[1] += b;
-      if (kCx[i]) acc[2] += kCx[i] * (a + b);
-      if (kCy[i]) acc[3] += kCy[i] * (a + b);
-      if (kCz[i]) acc[4] += kCz[i] * (a + b);
+      const float a = pop_read(P, store, rest, 0, i, s);
+      const float b = pop_read(P, store, rest, 1, i, s);
+      m[0].add(a);
+      m[1].add(b);
+      if (kCx[i]) { m[2].add(kCx[i] > 0 ? a : -a); m[2].add(kCx[i] > 0 ? b : -b); }
+      if (kCy[i]) { m[3].add(kCy[i] > 0 ? a : -a); m[3].add(kCy[i] > 0 ? b : -b); }
+      if (kCz[i]) { m[4].add(kCz[i] > 0 ? a : -a); m[4].add(kCz[i] > 0 ? b : -b); }
     }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[k] += m[k].value();
   }
   __shared__ double sh[5][kSumBlock];
 #pragma unroll
@@ -509,18 +511,16 @@ void launch_collide_onepass(const StepParams &P, const void *fin, void *fout, fl
   });
 }
 
-void launch_edge_densities(const StepParams &P, OnePassGeom G, const float *edge, float *rho_next, cudaStream_t st) {
-  const long long n = (long long)P.nz * P.ny * G.ntx;
-  k_edge_densities<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(P, G, edge, rho_next);
-}
-
-void launch_boundary_densities(const StepParams &P, const void *store, const float *rest, float *rho_next,
-                               const BoundaryRun *runs, int nruns, cudaStream_t st) {
-  if (nruns <= 0) return;
-  const unsigned grid = (unsigned)((nruns + kBlock / 32 - 1) / (kBlock / 32));
+void launch_boundary_densities(const StepParams &P, OnePassGeom G, const void *store, const float *rest,
+                               float *rho_next, const BoundaryRun *runs, int nruns, const float *edge,
+                               cudaStream_t st) {
+  const long long run_blocks = (nruns + kBlock / 32 - 1) / (kBlock / 32);
+  const long long edge_blocks = ((long long)P.nz * P.ny * G.ntx + kBlock - 1) / kBlock;
+  if (run_blocks + edge_blocks <= 0) return;
   with_storage(P, [&](auto t) {
     using T = std::remove_pointer_t<decltype(t)>;
-    k_boundary_densities<T><<<grid, kBlock, 0, st>>>(P, static_cast<const T *>(store), rest, rho_next, runs, nruns);
+    k_boundary_densities<T><<<(unsigned)(run_blocks + edge_blocks), kBlock, 0, st>>>(
+        P, G, static_cast<const T *>(store), rest, rho_next, runs, nruns, (int)run_blocks, edge);
   });
 }
 

@@ -80,6 +80,24 @@ struct Pair16<__nv_bfloat16> {
 
 __device__ __forceinline__ float pop_shift(const StepParams &P, int comp, int i) { return kW[i] * P.rho0[comp]; }
 
+// A sum of FP32 values without rounding error: kept as an unevaluated pair (hi, lo) of FP32
+// numbers, each addition split by Knuth's error-free two-sum (s + e == hi + x exactly; plain FP32
+// additions, nothing the compiler may contract).  FP64 arithmetic is slow on this GPU, so the FP64
+// reductions form each node's sums this way and add only the node totals, hi + lo, in FP64.  The
+// pair holds about 48 significant bits: a node total of a few dozen values carries a relative error
+// of ~2^-47 at most.
+struct FloatPair {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Element index of direction i of component c at site s: [19][N][2], the (A, B) pair of a
 // direction at a node side by side (one 8-byte word in FP32, one 4-byte word in 16 bits).
 template <class T>
@@ -779,15 +797,16 @@ __device__ __forceinline__ void couple_corner(const StepParams &P, int k, int4 c
   const int X = c.x + ox == P.nx ? 0 : c.x + ox;
   const int Y = c.y + oy == P.ny ? 0 : c.y + oy;
   const int Z = c.z + oz == P.nz ? 0 : c.z + oz;
+  const long long s = site_index(P, X, Y, Z);
+  // j' first: pulled from the populations, its 18 loads are in flight with those of the stencil
+  const float3 j = jp ? make_float3(__ldg(jp + s), __ldg(jp + P.N + s), __ldg(jp + 2 * P.N + s))
+                      : jprime_at<TS>(P, fin, X, Y, Z);
   const NodeState n = node_state(P, rho, X, Y, Z);
   float3 fA = make_float3(-P.gAB * n.rA * n.SB.x, -P.gAB * n.rA * n.SB.y, -P.gAB * n.rA * n.SB.z);
   float3 fB = make_float3(-P.gBA * n.rB * n.SA.x, -P.gBA * n.rB * n.SA.y, -P.gBA * n.rB * n.SA.z);
   gather_coupling(P, X, Y, Z, n.rA, n.rB, list, pf, ci, false, fA, fB);
-  const long long s = site_index(P, X, Y, Z);
   const float rinv = 1.f / (n.rA + n.rB);
   const float w = (ox ? fr.x : 1.f - fr.x) * (oy ? fr.y : 1.f - fr.y) * (oz ? fr.z : 1.f - fr.z);
-  const float3 j = jp ? make_float3(__ldg(jp + s), __ldg(jp + P.N + s), __ldg(jp + 2 * P.N + s))
-                      : jprime_at<TS>(P, fin, X, Y, Z);
   S.up.x += w * (j.x + 0.5f * (fA.x + fB.x)) * rinv;
   S.up.y += w * (j.y + 0.5f * (fA.y + fB.y)) * rinv;
   S.up.z += w * (j.z + 0.5f * (fA.z + fB.z)) * rinv;

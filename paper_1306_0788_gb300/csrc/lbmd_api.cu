@@ -33,12 +33,17 @@ struct lbmd_ctx {
   lbmd_params prm{};
   cudaStream_t st = nullptr;
   // the particle sort and the pair forces depend on the particles only, so they run on a side
-  // stream beside the density pass: side waits for the previous step's update (ev_int), st waits
-  // for the sort before the coupling (ev_sorted).  The particle update waits on side for the
-  // coupling (ev_coupled) and writes the other particle buffer, beside the lattice update that
-  // gathers from this one; st waits for it (ev_pairs), so every step ends on st
+  // stream: the pair forces beside the coupling, the particle update (waiting for the coupling,
+  // ev_coupled) beside the lattice update that gathers from the sorted copy, and the sort of the
+  // updated particles once the lattice update has read that copy (ev_collided), beside the kernels
+  // that follow it on st; st waits for the sort (ev_sorted) at the end of a launch sequence or
+  // before the next coupling.  ev_int and ev_pairs order the substeps of MD sub-stepping.
   cudaStream_t side = nullptr;
   cudaEvent_t ev_int = nullptr, ev_sorted = nullptr, ev_pairs = nullptr, ev_coupled = nullptr;
+  // the particle sort of the next step runs on side right after the lattice update (ev_collided),
+  // beside what follows it on st; sort_pending: st has not waited for it yet
+  cudaEvent_t ev_collided = nullptr;
+  bool sort_pending = false;
   int dev = 0;
   StepParams P{};
   unsigned char *pop[2] = {nullptr, nullptr};  // population buffers, element type P.storage
@@ -418,7 +423,12 @@ int reserve_events(lbmd_ctx *c, size_t n) {
 // One coupled step on st and side.  `step` is the noise counter the kernels get: the lattice
 // step, or, while a graph is recorded, the step's offset in it (the kernels add the base).
 // t0, t1 (or null): events recorded around the lattice update, with `flags`.
-int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t1, unsigned flags) {
+// The particles are kept sorted between steps: every step ends by sorting the updated particles
+// for the next one, on the side stream once the lattice update has read the sorted arrays, so that
+// the sort runs beside the kernels that follow the update on st (the boundary densities, or the
+// next step's density pass).  join: st waits for that sort before returning (else the next step
+// does, before its particle coupling).
+int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t1, unsigned flags, bool join) {
   StepParams &P = c->P;
   P.step = step;
   const CellIndex ci{c->row_start};
@@ -428,11 +438,11 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
   int r;
   const bool sub = P.np > 0 && P.substeps > 1;
   const bool onepass = uses_onepass(c);
-  if (P.np > 0) {  // the particle sort runs beside the density pass
+  if (P.np > 0 && !sub) {
+    // fork the side stream from the step's start (while st records a graph, this is also what
+    // makes the side stream's work part of the graph)
     CK(cudaEventRecord(c->ev_int, c->st), "event");
     CK(cudaStreamWaitEvent(c->side, c->ev_int, 0), "stream wait");
-    if ((r = sort_particles(c, c->side))) return r;
-    CK(cudaEventRecord(c->ev_sorted, c->side), "event");
   }
   if (onepass) {
     if (!c->rho_valid) return fail(c, LBMD_E_STATE, "one-pass update without the densities of the current state");
@@ -441,14 +451,16 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
     launch_moments(P, fin, c->rest, rho, P.np > 0 ? c->jp : nullptr, c->st);
     if ((r = launched(c, "moments"))) return r;
   }
+  if (P.np > 0 && c->sort_pending) {  // the previous step's sort of these particles
+    CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
+    c->sort_pending = false;
+  }
   ParticleArrays gpa = c->pa[c->pcur];  // what the update gathers the momentum return from
   ParticleForces gpf = c->pf;
   CellIndex gci = ci;
   if (sub) {
-    CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
     if ((r = substep_particles(c, gpa, gpf, gci))) return r;
   } else if (P.np > 0) {
-    CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
     if (onepass)  // no density pass stored j': the coupling pulls it at its corners
       launch_couple_pull(P, c->pa[c->pcur], ci, rho, fin, c->pf, c->st);
     else
@@ -458,7 +470,6 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
                  c->err, c->side);
     CK(cudaStreamWaitEvent(c->side, c->ev_coupled, 0), "stream wait");
     launch_integrate(P, c->pa[c->pcur], c->pa[1 - c->pcur], c->pf, c->err, c->side);
-    CK(cudaEventRecord(c->ev_pairs, c->side), "event");
     if ((r = launched(c, "particle forces and update", 3))) return r;
   }
   if (t0) CK(cudaEventRecordWithFlags(t0, c->st, flags), "event");
@@ -469,16 +480,24 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
     launch_collide(P, fin, fout, c->rest, rho, gpa, gpf, gci, c->err, c->st);
   if ((r = launched(c, "collide"))) return r;
   if (t1) CK(cudaEventRecordWithFlags(t1, c->st, flags), "event");
+  if (P.np > 0) CK(cudaEventRecord(c->ev_collided, c->st), "event");
   if (onepass) {
-    launch_boundary_densities(P, fout, c->rest, c->rho_buf[1 - c->cur], c->op_runs, c->op_nruns, c->st);
-    launch_edge_densities(P, c->op_geom, c->op_edge, c->rho_buf[1 - c->cur], c->st);
-    if ((r = launched(c, "boundary densities", 2))) return r;
+    launch_boundary_densities(P, c->op_geom, fout, c->rest, c->rho_buf[1 - c->cur], c->op_runs, c->op_nruns,
+                              c->op_edge, c->st);
+    if ((r = launched(c, "boundary densities"))) return r;
   }
-  if (sub) {
-    c->pcur = 1 - c->pcur;  // the working copy that took the substeps is the particle state
-  } else if (P.np > 0) {
-    CK(cudaStreamWaitEvent(c->st, c->ev_pairs, 0), "stream wait");
-    c->pcur = 1 - c->pcur;  // the updated copy is the particle state
+  if (P.np > 0) {
+    // the updated particles (the working copy that took the substeps, or the update's output) are
+    // the state; sort them for the next step into the arrays the lattice update has just read
+    c->pcur = 1 - c->pcur;
+    CK(cudaStreamWaitEvent(c->side, c->ev_collided, 0), "stream wait");
+    if ((r = sort_particles(c, c->side))) return r;
+    CK(cudaEventRecord(c->ev_sorted, c->side), "event");
+    c->sort_pending = true;
+    if (join) {
+      CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
+      c->sort_pending = false;
+    }
   }
   c->cur = 1 - c->cur;
   c->steps++;
@@ -510,7 +529,7 @@ int record_steps(lbmd_ctx *c, StepGraph &g) {
     for (cudaEvent_t &e : c->ph)
       if (!e) CK(cudaEventCreate(&e), "event");
   const int cur0 = c->cur, pcur0 = c->pcur;
-  const bool rho_valid0 = c->rho_valid;
+  const bool rho_valid0 = c->rho_valid, sort_pending0 = c->sort_pending;
   const int64_t steps0 = c->steps, launches0 = c->launches;
   cudaStream_t user = c->st;
   CK(cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -519,7 +538,7 @@ int record_steps(lbmd_ctx *c, StepGraph &g) {
   r = LBMD_OK;
   for (int j = 0; j < kGraphSteps && !r; ++j)
     r = one_step(c, (unsigned long long)j, c->prof ? c->ph[2 * j] : nullptr, c->prof ? c->ph[2 * j + 1] : nullptr,
-                 cudaEventRecordExternal);
+                 cudaEventRecordExternal, j == kGraphSteps - 1);
   if (!r) {
     launch_advance_step(c->step_base, kGraphSteps, c->gst);
     r = launched(c, "step counter");
@@ -532,6 +551,7 @@ int record_steps(lbmd_ctx *c, StepGraph &g) {
   c->cur = cur0;
   c->pcur = pcur0;
   c->rho_valid = rho_valid0;
+  c->sort_pending = sort_pending0;
   c->steps = steps0;
   g.launches = c->launches - launches0;
   c->launches = launches0;
@@ -652,7 +672,8 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
       (e = cudaEventCreateWithFlags(&c->ev_int, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_sorted, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_pairs, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&c->ev_coupled, cudaEventDisableTiming)) != cudaSuccess) {
+      (e = cudaEventCreateWithFlags(&c->ev_coupled, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_collided, cudaEventDisableTiming)) != cudaSuccess) {
     cudaGetLastError();
     lbmd_destroy(c);
     return fail(nullptr, LBMD_E_CUDA, std::string("stream / event creation: ") + cudaGetErrorString(e));
@@ -683,6 +704,7 @@ void lbmd_destroy(lbmd_ctx *c) {
   if (c->ev_sorted) cudaEventDestroy(c->ev_sorted);
   if (c->ev_pairs) cudaEventDestroy(c->ev_pairs);
   if (c->ev_coupled) cudaEventDestroy(c->ev_coupled);
+  if (c->ev_collided) cudaEventDestroy(c->ev_collided);
   drop_graphs(c);
   if (c->gst) cudaStreamDestroy(c->gst);
   for (cudaEvent_t e : c->ph)
@@ -842,6 +864,7 @@ int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, con
     int r = sort_particles(c, c->st);
     if (r) return r;
   }
+  c->sort_pending = false;
   if (c->fluid_ready) {  // the drift check's reference includes the new particles' momentum
     const int r = enqueue_drift(c, 1);
     if (r) return r;
@@ -922,7 +945,7 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
         t0 = c->ev[c->ev_used];
         t1 = c->ev[c->ev_used + 1];
       }
-      if ((r = one_step(c, (unsigned long long)c->steps, t0, t1, cudaEventRecordDefault))) return r;
+      if ((r = one_step(c, (unsigned long long)c->steps, t0, t1, cudaEventRecordDefault, true))) return r;
       if (c->prof) c->ev_used += 2;
     }
     if (K > 0 && c->steps % K == 0 && (r = enqueue_drift(c, 0))) return r;
@@ -1003,17 +1026,21 @@ int lbmd_get_particles(lbmd_ctx *c, double *x, double *v, double *f) {
   if (n == 0) return sync_and_check(c);
   std::vector<int4> hc(n);
   std::vector<float4> hf(n), hv(n), ht(n);
-  std::vector<int> hid(n);
+  std::vector<int> hid(n), htid(n);
   const ParticleArrays &pa = c->pa[c->pcur];
+  // the total forces are in the order of the copy the particle update wrote, which the sort for
+  // the next step leaves in the other buffer
+  const ParticleArrays &pt = c->pa[1 - c->pcur];
   CK(cudaMemcpyAsync(hc.data(), pa.cell, sizeof(int4) * n, cudaMemcpyDeviceToHost, c->st), "download");
   CK(cudaMemcpyAsync(hf.data(), pa.frac, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->st), "download");
   CK(cudaMemcpyAsync(hv.data(), pa.vel, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->st), "download");
   CK(cudaMemcpyAsync(ht.data(), c->pf.total, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->st), "download");
   CK(cudaMemcpyAsync(hid.data(), pa.pid, sizeof(int) * n, cudaMemcpyDeviceToHost, c->st), "download");
+  CK(cudaMemcpyAsync(htid.data(), pt.pid, sizeof(int) * n, cudaMemcpyDeviceToHost, c->st), "download");
   int r = sync_and_check(c);
   for (int j = 0; j < n; ++j) {
-    const int id = hid[j];
-    if (id < 0 || id >= n) return fail(c, LBMD_E_CUDA, "corrupt particle ids");
+    const int id = hid[j], tid = htid[j];
+    if (id < 0 || id >= n || tid < 0 || tid >= n) return fail(c, LBMD_E_CUDA, "corrupt particle ids");
     if (x) {
       x[3 * id] = hc[j].x + (double)hf[j].x;
       x[3 * id + 1] = hc[j].y + (double)hf[j].y;
@@ -1023,7 +1050,7 @@ int lbmd_get_particles(lbmd_ctx *c, double *x, double *v, double *f) {
       v[3 * id] = hv[j].x; v[3 * id + 1] = hv[j].y; v[3 * id + 2] = hv[j].z;
     }
     if (f) {
-      f[3 * id] = ht[j].x; f[3 * id + 1] = ht[j].y; f[3 * id + 2] = ht[j].z;
+      f[3 * tid] = ht[j].x; f[3 * tid + 1] = ht[j].y; f[3 * tid + 2] = ht[j].z;
     }
   }
   return r;

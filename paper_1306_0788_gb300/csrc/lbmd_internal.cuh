@@ -240,11 +240,11 @@ void launch_collide(const StepParams &P, const void *fin, void *fout, float *res
 void launch_collide_onepass(const StepParams &P, const void *fin, void *fout, float *rest, const float *rho,
                             float *rho_next, float *edge, const ParticleArrays &pa, const ParticleForces &pf,
                             CellIndex ci, unsigned *err, OnePassGeom G, int grid, cudaStream_t st);
-void launch_boundary_densities(const StepParams &P, const void *store, const float *rest, float *rho_next,
-                               const BoundaryRun *runs, int nruns, cudaStream_t st);
-// Adds the edge partial sums (edge: [nz][ny][ntx][2] float2) to the x-edge nodes of the inner
-// rows and planes.
-void launch_edge_densities(const StepParams &P, OnePassGeom G, const float *edge, float *rho_next, cudaStream_t st);
+// Also adds the edge partial sums (edge: [nz][ny][ntx][2] float2) to the x-edge nodes of the inner
+// rows and planes, in the same launch.
+void launch_boundary_densities(const StepParams &P, OnePassGeom G, const void *store, const float *rest,
+                               float *rho_next, const BoundaryRun *runs, int nruns, const float *edge,
+                               cudaStream_t st);
 // Blocks of the one-pass update resident on one SM (its persistent grid is this times the SMs).
 int onepass_blocks_per_sm();
 void launch_fields(const StepParams &P, const void *store, const float *rest, const float *rho, float *rhoA,
