@@ -157,7 +157,7 @@ __device__ __forceinline__ void stage_plane(const StepParams &P, const float *__
 template <class T, bool kParticles>
 __global__ void __launch_bounds__(kOPThreads, 3)
     k_collide_onepass(StepParams P, const T *__restrict__ fin, T *__restrict__ fout, const float *__restrict__ rho,
-                      float *__restrict__ rho_next, float *__restrict__ edge, ParticleArrays pa, ParticleForces pf,
+                      float *__restrict__ rho_next, OnePassOut out, ParticleArrays pa, ParticleForces pf,
                       CellIndex ci, unsigned *err, const float *__restrict__ rest_in, float *__restrict__ rest_out,
                       OnePassGeom G) {
   // groups handed to the neighbouring rows: [0..2] c_y = +1 with c_z = -1, 0, +1; [3..5] c_y = -1
@@ -169,6 +169,8 @@ __global__ void __launch_bounds__(kOPThreads, 3)
   // (in shared memory rather than registers: they live across the whole update of a node)
   __shared__ float2 acc[3][kOPThreads];
   __shared__ float2 accE[3][2][kOnePassRows];
+  // what leaves the tile across its bottom (0) and top (1) row, per lane
+  __shared__ float2 accY[3][2][32];
   // the stencils' densities, read from global memory once per block and plane
   __shared__ float2 ring[kRhoSlots][kRhoRows][kRhoCols];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -183,10 +185,14 @@ __global__ void __launch_bounds__(kOPThreads, 3)
   const int y0 = ty * kOnePassRows, rows = min(kOnePassRows, P.ny - y0);
   const int y = y0 + w;
   const bool inner_row = w >= 1 && w <= rows - 2;  // the sources along y are in the block
-  const bool inner = own && inner_row;
   const bool left = lane == 0, right = lane == nown - 1;  // the tile's x edges (both when nown = 1)
   acc[0][threadIdx.x] = acc[1][threadIdx.x] = acc[2][threadIdx.x] = make_float2(0.f, 0.f);
   if (threadIdx.x < 3 * 2 * kOnePassRows) (&accE[0][0][0])[threadIdx.x] = make_float2(0.f, 0.f);
+  if (threadIdx.x < 3 * 2 * 32) (&accY[0][0][0])[threadIdx.x] = make_float2(0.f, 0.f);
+  // rows whose partial sums the block forms: the inner ones, and with y partials the edge rows too
+  // (lacking what arrives from the neighbouring tile's row, which that tile sends)
+  const bool summed_row = w < rows && (G.ypart || inner_row);
+  const bool lo = w > 0, hi = w < rows - 1;  // the rows below / above are in the block
   for (int dz = -1; dz <= 1; ++dz) stage_plane(P, rho, ring, zs + dz + kRhoSlots, (zs + dz + P.nz) % P.nz, x0, y0);
   cp_async_wait_all();
   __syncthreads();
@@ -234,52 +240,82 @@ __global__ void __launch_bounds__(kOPThreads, 3)
     cp_async_wait_all();  // the next plane's densities (issued above) have landed
     __syncthreads();
     const int km = (z + 2) % 3, k0 = z % 3, kp = (z + 1) % 3;
-    if (inner) {
+    const bool write = z >= zs + 2;  // plane z - 1 has all its sources (z - 2 .. z) in the chunk
+    const float2 zero = make_float2(0.f, 0.f);
+    if (own && summed_row) {
       // from the row below (c_y = +1), this row (c_y = 0), the row above (c_y = -1), into the
       // planes z - 1, z, z + 1
-      const float2 am = add2(add2(add2(acc[km][threadIdx.x], X[0][w - 1][lane]), g0m), X[3][w + 1][lane]);
-      acc[k0][threadIdx.x] = add2(add2(add2(acc[k0][threadIdx.x], X[1][w - 1][lane]), g00), X[4][w + 1][lane]);
-      acc[kp][threadIdx.x] = add2(add2(add2(acc[kp][threadIdx.x], X[2][w - 1][lane]), g0p), X[5][w + 1][lane]);
-      if (z >= zs + 2)  // plane z - 1 has all its sources (z - 2 .. z) in the chunk
+      const float2 am = add2(add2(add2(acc[km][threadIdx.x], lo ? X[0][w - 1][lane] : zero), g0m),
+                             hi ? X[3][w + 1][lane] : zero);
+      acc[k0][threadIdx.x] = add2(add2(add2(acc[k0][threadIdx.x], lo ? X[1][w - 1][lane] : zero), g00),
+                                  hi ? X[4][w + 1][lane] : zero);
+      acc[kp][threadIdx.x] = add2(add2(add2(acc[kp][threadIdx.x], lo ? X[2][w - 1][lane] : zero), g0p),
+                                  hi ? X[5][w + 1][lane] : zero);
+      if (write)
         reinterpret_cast<float2 *>(rho_next)[((long long)(z - 1) * P.ny + y) * P.nx + x] =
             add2(am, make_float2(shift_sum(P, 0), shift_sum(P, 1)));
-      acc[km][threadIdx.x] = make_float2(0.f, 0.f);  // becomes plane z + 2
+      acc[km][threadIdx.x] = zero;  // becomes plane z + 2
     }
-    if (inner_row && (left || right)) {
+    if (summed_row && (left || right)) {
       // what leaves the tile along x, for the neighbouring tiles' edge nodes in this row: the
       // side-0 sums from lane 0 (c_x = -1: directions 2, 10, 8, 14, 12), the side-1 sums from the
       // last lane (c_x = +1: 1, 7, 9, 11, 13)
-      float2 *edge2 = reinterpret_cast<float2 *>(edge);
+      float2 *edge2 = reinterpret_cast<float2 *>(out.edge);
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         if (side == 0 ? !left : !right) continue;
         const int i00 = side ? 1 : 2, i0p = side ? 11 : 14, i0m = side ? 13 : 12;
         const float2 em = add2(accE[km][side][w], make_float2(fA[i0m], fB[i0m]));
-        accE[k0][side][w] = add2(add2(add2(accE[k0][side][w], xedge[parity][side][0][w - 1]),
+        accE[k0][side][w] = add2(add2(add2(accE[k0][side][w], lo ? xedge[parity][side][0][w - 1] : zero),
                                       make_float2(fA[i00], fB[i00])),
-                                 xedge[parity][side][1][w + 1]);
+                                 hi ? xedge[parity][side][1][w + 1] : zero);
         accE[kp][side][w] = add2(accE[kp][side][w], make_float2(fA[i0p], fB[i0p]));
-        if (z >= zs + 2) edge2[(((long long)(z - 1) * P.ny + y) * G.ntx + tx) * 2 + side] = em;
-        accE[km][side][w] = make_float2(0.f, 0.f);
+        if (write) edge2[(((long long)(z - 1) * P.ny + y) * G.ntx + tx) * 2 + side] = em;
+        accE[km][side][w] = zero;
+      }
+    }
+    if (G.ypart && own && (w == 0 || w == rows - 1)) {
+      // what leaves the tile across its bottom row (the c_y = -1 groups of row 0) or its top row
+      // (the c_y = +1 groups of the last row), for the neighbouring tile's edge row
+      const int sy = w == 0 ? 0 : 1, g = sy ? 0 : 3;
+      const float2 ym = add2(accY[km][sy][lane], X[g][w][lane]);
+      accY[k0][sy][lane] = add2(accY[k0][sy][lane], X[g + 1][w][lane]);
+      accY[kp][sy][lane] = add2(accY[kp][sy][lane], X[g + 2][w][lane]);
+      if (write)
+        reinterpret_cast<float2 *>(out.yedge)[(((long long)sy * P.nz + (z - 1)) * G.nty + ty) * (G.ntx * kOnePassCols) +
+                                              x0 + lane] = ym;
+      accY[km][sy][lane] = zero;
+      // the value leaving each corner diagonally (c_z = 0: it arrives in this plane)
+      if ((left || right) && z >= zs + 1 && z <= ze - 2) {
+        const int k = (sy << 1) | (right ? 1 : 0);  // 0: bottom-left ... 3: top-right
+        // directions 8, 9, 10, 7 (constant indices: the arrays stay in registers)
+        const float2 d = sy ? (right ? make_float2(fA[7], fB[7]) : make_float2(fA[10], fB[10]))
+                            : (right ? make_float2(fA[9], fB[9]) : make_float2(fA[8], fB[8]));
+        reinterpret_cast<float2 *>(out.diag)[(((long long)z * G.nty + ty) * G.ntx + tx) * 4 + k] = d;
       }
     }
   }
   cp_async_wait_all();  // no copy outlives the block
 }
 
-// The nodes the one-pass update leaves unfinished, in one launch: blocks [0, run_blocks) take the
-// boundary runs, a warp per run, and compute their densities from the new populations as the
-// density pass does; the blocks after them add the edge partial sums to the x-edge nodes of the
-// inner rows and planes of every tile -- its own partial (in rho_next) plus what arrives from the
-// neighbouring tiles: from the left one's side-1 sums at x0, from the right one's side-0 sums at
-// x0 + nown - 1 (both, in that order, when a tile has one column).  The two sets of nodes are
-// disjoint.
+// The nodes the one-pass update leaves unfinished, in one launch of three block ranges:
+//  1. the boundary runs, a warp per run: their densities from the new populations, as the density
+//     pass computes them (the first and last plane of each chunk; without y partials also the
+//     first and last row of each tile);
+//  2. the x-edge nodes of the inner rows: own partial (in rho_next) plus what arrives from the
+//     neighbouring tile -- from the left one's side-1 sums at x0, from the right one's side-0 sums
+//     at x0 + nown - 1 (both, in that order, when a tile has one column);
+//  3. with y partials, the edge rows: own partial plus what the tile below (for the bottom row) or
+//     above (for the top row) sends across, and at the two corners also the x-neighbour's edge-row
+//     sums and the value the diagonal neighbour sends, in that order.
+// All inner planes only (chunk edge planes are runs); the sets of nodes are disjoint.
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_boundary_densities(StepParams P, OnePassGeom G, const T *__restrict__ store,
                                                                const float *__restrict__ rest,
                                                                float *__restrict__ rho_next,
                                                                const BoundaryRun *__restrict__ runs, int nruns,
-                                                               int run_blocks, const float *__restrict__ edge) {
+                                                               int run_blocks, int edge_blocks, OnePassOut out,
+                                                               const unsigned char *__restrict__ inner_plane) {
   if ((int)blockIdx.x < run_blocks) {
     const int r = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (r >= nruns) return;
@@ -288,31 +324,61 @@ __global__ void __launch_bounds__(kBlock) k_boundary_densities(StepParams P, One
     moments(P, (long long)b.row * P.nx + b.x0 + lane, store, rest, rho_next, nullptr);
     return;
   }
-  const long long t = (long long)(blockIdx.x - run_blocks) * blockDim.x + threadIdx.x;
-  const long long n = (long long)P.nz * P.ny * G.ntx;
-  if (t >= n) return;
-  const int tx = (int)(t % G.ntx);
-  const long long r = t / G.ntx;  // z * ny + y
-  const int z = (int)(r / P.ny), y = (int)(r - (long long)z * P.ny);
-  const int w = y % kOnePassRows, y0 = y - w, rows = min(kOnePassRows, P.ny - y0);
-  if (w < 1 || w > rows - 2) return;  // tile edge rows: boundary runs
-  int c = (int)((long long)z * G.nchunks / P.nz);  // the chunk holding z: start(c) <= z < start(c + 1)
-  while (c > 0 && (long long)c * P.nz / G.nchunks > z) --c;
-  while ((long long)(c + 1) * P.nz / G.nchunks <= z) ++c;
-  const int zs = (int)((long long)c * P.nz / G.nchunks), ze = (int)((long long)(c + 1) * P.nz / G.nchunks);
-  if (z < zs + 1 || z > ze - 2) return;  // chunk edge planes: boundary runs
-  const int x0 = tx * kOnePassCols, nown = min(kOnePassCols, P.nx - x0);
-  const int txl = tx == 0 ? G.ntx - 1 : tx - 1, txr = tx == G.ntx - 1 ? 0 : tx + 1;
-  const float2 *e2 = reinterpret_cast<const float2 *>(edge);
+  const float2 *e2 = reinterpret_cast<const float2 *>(out.edge);
   float2 *rho2 = reinterpret_cast<float2 *>(rho_next);
-  const long long base = r * P.nx;
-  float2 v = add2(rho2[base + x0], e2[(r * G.ntx + txl) * 2 + 1]);  // from the left tile's last lane
-  if (nown == 1) {
-    rho2[base + x0] = add2(v, e2[(r * G.ntx + txr) * 2 + 0]);  // and from the right tile's lane 0
+  if ((int)blockIdx.x < run_blocks + edge_blocks) {
+    // 32-bit index arithmetic: nz ny ntx < N < 2^32 / 19
+    const unsigned t = (unsigned)(blockIdx.x - run_blocks) * blockDim.x + threadIdx.x;
+    const unsigned n = (unsigned)P.nz * P.ny * G.ntx;
+    if (t >= n) return;
+    const unsigned r = t / G.ntx;  // z * ny + y
+    const int tx = (int)(t - r * G.ntx);
+    const int z = (int)(r / P.ny), y = (int)(r - (unsigned)z * P.ny);
+    const int w = y % kOnePassRows, y0 = y - w, rows = min(kOnePassRows, P.ny - y0);
+    if (w < 1 || w > rows - 2) return;  // tile edge rows: runs, or range 3
+    if (!inner_plane[z]) return;        // chunk edge planes: runs
+    const int x0 = tx * kOnePassCols, nown = min(kOnePassCols, P.nx - x0);
+    const int txl = tx == 0 ? G.ntx - 1 : tx - 1, txr = tx == G.ntx - 1 ? 0 : tx + 1;
+    const long long base = (long long)r * P.nx;
+    const float2 v = add2(rho2[base + x0], e2[((long long)r * G.ntx + txl) * 2 + 1]);  // from the left tile's last lane
+    if (nown == 1) {
+      rho2[base + x0] = add2(v, e2[((long long)r * G.ntx + txr) * 2 + 0]);  // and from the right tile's lane 0
+      return;
+    }
+    rho2[base + x0] = v;
+    rho2[base + x0 + nown - 1] = add2(rho2[base + x0 + nown - 1], e2[((long long)r * G.ntx + txr) * 2 + 0]);
     return;
   }
-  rho2[base + x0] = v;
-  rho2[base + x0 + nown - 1] = add2(rho2[base + x0 + nown - 1], e2[(r * G.ntx + txr) * 2 + 0]);
+  // 3: edge rows (y partials): thread per (z, tile row, bottom / top, x)
+  const unsigned t = (unsigned)(blockIdx.x - run_blocks - edge_blocks) * blockDim.x + threadIdx.x;
+  const unsigned n = (unsigned)P.nz * G.nty * 2 * P.nx;
+  if (t >= n) return;
+  const unsigned q = t / P.nx;
+  const int x = (int)(t - q * P.nx);
+  const int sy = (int)(q & 1u);
+  const unsigned zt = q >> 1;
+  const int z = (int)(zt / G.nty), ty = (int)(zt - (unsigned)z * G.nty);
+  if (!inner_plane[z]) return;
+  const int y0 = ty * kOnePassRows, rows = min(kOnePassRows, P.ny - y0), y = sy ? y0 + rows - 1 : y0;
+  const int tx = x / kOnePassCols, x0 = tx * kOnePassCols, nown = min(kOnePassCols, P.nx - x0);
+  const int txl = tx == 0 ? G.ntx - 1 : tx - 1, txr = tx == G.ntx - 1 ? 0 : tx + 1;
+  const int tyn = sy ? (ty == G.nty - 1 ? 0 : ty + 1) : (ty == 0 ? G.nty - 1 : ty - 1);  // the tile sending across
+  const float2 *y2 = reinterpret_cast<const float2 *>(out.yedge);
+  const float2 *d2 = reinterpret_cast<const float2 *>(out.diag);
+  const long long node = ((long long)z * P.ny + y) * P.nx + x;
+  // the bottom row gets what the tile below sends up (its side 1), the top row what the tile
+  // above sends down (its side 0)
+  float2 v = add2(rho2[node], y2[(((long long)(1 - sy) * P.nz + z) * G.nty + tyn) * (G.ntx * kOnePassCols) + x]);
+  const long long er = (long long)z * P.ny + y;
+  if (x == x0) {  // corner: the left tile's side-1 sums of this row, the diagonal value
+    v = add2(v, e2[(er * G.ntx + txl) * 2 + 1]);
+    v = add2(v, d2[(((long long)z * G.nty + tyn) * G.ntx + txl) * 4 + (sy ? 1 : 3)]);
+  }
+  if (x == x0 + nown - 1) {  // corner: the right tile's side-0 sums of this row, the diagonal value
+    v = add2(v, e2[(er * G.ntx + txr) * 2 + 0]);
+    v = add2(v, d2[(((long long)z * G.nty + tyn) * G.ntx + txr) * 4 + (sy ? 0 : 2)]);
+  }
+  rho2[node] = v;
 }
 
 // rho_A, rho_B and u = (j' + g^SC/2)/rho at the current step (for readback).
@@ -496,31 +562,33 @@ void launch_collide(const StepParams &P, const void *fin, void *fout, float *res
 }
 
 void launch_collide_onepass(const StepParams &P, const void *fin, void *fout, float *rest, const float *rho,
-                            float *rho_next, float *edge, const ParticleArrays &pa, const ParticleForces &pf,
+                            float *rho_next, OnePassOut out, const ParticleArrays &pa, const ParticleForces &pf,
                             CellIndex ci, unsigned *err, OnePassGeom G, int grid, cudaStream_t st) {
   with_storage(P, [&](auto t) {
     using T = std::remove_pointer_t<decltype(t)>;
     const T *a = static_cast<const T *>(fin);
     T *b = static_cast<T *>(fout);
     if (P.np > 0)
-      k_collide_onepass<T, true><<<grid, kOPThreads, 0, st>>>(P, a, b, rho, rho_next, edge, pa, pf, ci, err, rest,
+      k_collide_onepass<T, true><<<grid, kOPThreads, 0, st>>>(P, a, b, rho, rho_next, out, pa, pf, ci, err, rest,
                                                               rest, G);
     else
-      k_collide_onepass<T, false><<<grid, kOPThreads, 0, st>>>(P, a, b, rho, rho_next, edge, pa, pf, ci, err, rest,
+      k_collide_onepass<T, false><<<grid, kOPThreads, 0, st>>>(P, a, b, rho, rho_next, out, pa, pf, ci, err, rest,
                                                                rest, G);
   });
 }
 
 void launch_boundary_densities(const StepParams &P, OnePassGeom G, const void *store, const float *rest,
-                               float *rho_next, const BoundaryRun *runs, int nruns, const float *edge,
-                               cudaStream_t st) {
+                               float *rho_next, const BoundaryRun *runs, int nruns, OnePassOut out,
+                               const unsigned char *inner_plane, cudaStream_t st) {
   const long long run_blocks = (nruns + kBlock / 32 - 1) / (kBlock / 32);
   const long long edge_blocks = ((long long)P.nz * P.ny * G.ntx + kBlock - 1) / kBlock;
-  if (run_blocks + edge_blocks <= 0) return;
+  const long long row_blocks = G.ypart ? ((long long)P.nz * G.nty * 2 * P.nx + kBlock - 1) / kBlock : 0;
+  if (run_blocks + edge_blocks + row_blocks <= 0) return;
   with_storage(P, [&](auto t) {
     using T = std::remove_pointer_t<decltype(t)>;
-    k_boundary_densities<T><<<(unsigned)(run_blocks + edge_blocks), kBlock, 0, st>>>(
-        P, G, static_cast<const T *>(store), rest, rho_next, runs, nruns, (int)run_blocks, edge);
+    k_boundary_densities<T><<<(unsigned)(run_blocks + edge_blocks + row_blocks), kBlock, 0, st>>>(
+        P, G, static_cast<const T *>(store), rest, rho_next, runs, nruns, (int)run_blocks, (int)edge_blocks, out,
+        inner_plane);
   });
 }
 

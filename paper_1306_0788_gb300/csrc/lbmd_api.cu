@@ -63,7 +63,8 @@ struct lbmd_ctx {
   int op_grid = 0;
   BoundaryRun *op_runs = nullptr;
   int op_nruns = 0;
-  float *op_edge = nullptr;  // edge partial sums [nz][ny][ntx][2] float2
+  float *op_edge = nullptr, *op_yedge = nullptr, *op_diag = nullptr;  // partial sums (OnePassOut)
+  unsigned char *op_inner = nullptr;  // [nz]: plane neither first nor last of its chunk
   // particles
   int np = 0, cap = 0;
   ParticleArrays pa[2]{};
@@ -276,6 +277,9 @@ int prepare_onepass(lbmd_ctx *c) {
       if (ze <= zs) continue;
       edge[(size_t)col * P.nz + zs] = edge[(size_t)col * P.nz + ze - 1] = 1;
     }
+  // edge rows from partial sums when every tile has at least 3 rows and 2 columns
+  const int ry = P.ny % kOnePassRows, rx = P.nx % kOnePassCols;
+  const int ypart = (P.ny >= 3 && (ry == 0 || ry >= 3) && P.nx >= 2 && (rx == 0 || rx >= 2)) ? 1 : 0;
   std::vector<BoundaryRun> runs;
   for (int col = 0; col < ntx * nty; ++col) {
     const int tx = col % ntx, ty = col / ntx;
@@ -283,15 +287,28 @@ int prepare_onepass(lbmd_ctx *c) {
     const int y0 = ty * kOnePassRows, rows = std::min(kOnePassRows, P.ny - y0);
     for (int z = 0; z < P.nz; ++z)
       for (int w = 0; w < rows; ++w)
-        if (edge[(size_t)col * P.nz + z] || w == 0 || w == rows - 1)
+        if (edge[(size_t)col * P.nz + z] || (!ypart && (w == 0 || w == rows - 1)))
           runs.push_back(BoundaryRun{z * P.ny + y0 + w, x0, nown});
   }
   if (runs.size() > 0x7fffffffull) return fail(c, LBMD_E_INVALID_ARG, "too many boundary runs");
   CK(dalloc(&c->op_edge, (size_t)P.nz * P.ny * ntx * 4), "edge sums");
+  {
+    std::vector<unsigned char> inner((size_t)P.nz, 0);
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int zs = (int)((long long)ch * P.nz / nchunks), ze = (int)((long long)(ch + 1) * P.nz / nchunks);
+      for (int z = zs + 1; z <= ze - 2; ++z) inner[z] = 1;
+    }
+    CK(dalloc(&c->op_inner, inner.size()), "plane table");
+    CK(cudaMemcpy(c->op_inner, inner.data(), inner.size(), cudaMemcpyHostToDevice), "plane table");
+  }
+  if (ypart) {
+    CK(dalloc(&c->op_yedge, (size_t)2 * P.nz * nty * ntx * kOnePassCols * 2), "edge sums");
+    CK(dalloc(&c->op_diag, (size_t)P.nz * nty * ntx * 4 * 2), "edge sums");
+  }
   CK(dalloc(&c->op_runs, runs.size()), "boundary runs");
   CK(cudaMemcpy(c->op_runs, runs.data(), sizeof(BoundaryRun) * runs.size(), cudaMemcpyHostToDevice), "boundary runs");
   c->op_nruns = (int)runs.size();
-  c->op_geom = OnePassGeom{ntx, nty, nchunks};
+  c->op_geom = OnePassGeom{ntx, nty, nchunks, ypart};
   c->op_grid = grid;
   return LBMD_OK;
 }
@@ -474,8 +491,9 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
   }
   if (t0) CK(cudaEventRecordWithFlags(t0, c->st, flags), "event");
   if (onepass)
-    launch_collide_onepass(P, fin, fout, c->rest, rho, c->rho_buf[1 - c->cur], c->op_edge, gpa, gpf, gci, c->err,
-                           c->op_geom, c->op_grid, c->st);
+    launch_collide_onepass(P, fin, fout, c->rest, rho, c->rho_buf[1 - c->cur],
+                           OnePassOut{c->op_edge, c->op_yedge, c->op_diag}, gpa, gpf, gci, c->err, c->op_geom,
+                           c->op_grid, c->st);
   else
     launch_collide(P, fin, fout, c->rest, rho, gpa, gpf, gci, c->err, c->st);
   if ((r = launched(c, "collide"))) return r;
@@ -483,7 +501,7 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
   if (P.np > 0) CK(cudaEventRecord(c->ev_collided, c->st), "event");
   if (onepass) {
     launch_boundary_densities(P, c->op_geom, fout, c->rest, c->rho_buf[1 - c->cur], c->op_runs, c->op_nruns,
-                              c->op_edge, c->st);
+                              OnePassOut{c->op_edge, c->op_yedge, c->op_diag}, c->op_inner, c->st);
     if ((r = launched(c, "boundary densities"))) return r;
   }
   if (P.np > 0) {
@@ -711,7 +729,7 @@ void lbmd_destroy(lbmd_ctx *c) {
     if (e) cudaEventDestroy(e);
   dfree(c->step_base);
   dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho_buf[0]); dfree(c->rho_buf[1]); dfree(c->jp); dfree(c->err);
-  dfree(c->rest); dfree(c->op_runs); dfree(c->op_edge);
+  dfree(c->rest); dfree(c->op_runs); dfree(c->op_edge); dfree(c->op_yedge); dfree(c->op_diag); dfree(c->op_inner);
   dfree(c->diag_partial); dfree(c->diag_out); dfree(c->drift);
   free_particles(c);
   free_records(c);
@@ -971,6 +989,9 @@ int lbmd_set_lattice_passes(lbmd_ctx *c, int passes) {
   if (passes != c->passes) {
     dfree(c->op_runs);  // set up again for the new choice at the next step
     dfree(c->op_edge);
+    dfree(c->op_yedge);
+    dfree(c->op_diag);
+    dfree(c->op_inner);
     c->op_nruns = 0;
     c->op_grid = 0;
   }

@@ -128,6 +128,14 @@ constexpr int kOnePassCols = 32;
 struct OnePassGeom {
   int ntx, nty;  // column tiles along x (kOnePassCols columns each) and y (kOnePassRows rows)
   int nchunks;   // z-chunks per tile: block b takes chunk b / (ntx nty) of tile b % (ntx nty)
+  int ypart;     // every tile has >= 3 rows and >= 2 columns: the edge rows are finished from
+                 // partial sums (else their densities are pulled like the chunk edge planes)
+};
+// Partial sums the update writes for nodes whose sources lie in other blocks.
+struct OnePassOut {
+  float *edge;   // [nz][ny][ntx][2] float2: what leaves a tile row along x (side 0: -x, 1: +x)
+  float *yedge;  // [2][nz][nty][ntx * 32] float2: what leaves a tile across its bottom (0) / top (1) row
+  float *diag;   // [nz][nty][ntx][4] float2: the one value leaving each corner diagonally
 };
 struct BoundaryRun {
   int row;   // z * ny + y
@@ -238,13 +246,13 @@ void launch_collide(const StepParams &P, const void *fin, void *fout, float *res
 // densities rho_next of the nodes inside each block's stretch; launch_boundary_densities then
 // computes the densities of the listed boundary runs from the new populations.
 void launch_collide_onepass(const StepParams &P, const void *fin, void *fout, float *rest, const float *rho,
-                            float *rho_next, float *edge, const ParticleArrays &pa, const ParticleForces &pf,
+                            float *rho_next, OnePassOut out, const ParticleArrays &pa, const ParticleForces &pf,
                             CellIndex ci, unsigned *err, OnePassGeom G, int grid, cudaStream_t st);
-// Also adds the edge partial sums (edge: [nz][ny][ntx][2] float2) to the x-edge nodes of the inner
-// rows and planes, in the same launch.
+// Also adds the partial sums of `out` to the tile-edge nodes of the inner planes, in the same launch.
+// inner_plane[z] != 0: z is neither the first nor the last plane of its chunk.
 void launch_boundary_densities(const StepParams &P, OnePassGeom G, const void *store, const float *rest,
-                               float *rho_next, const BoundaryRun *runs, int nruns, const float *edge,
-                               cudaStream_t st);
+                               float *rho_next, const BoundaryRun *runs, int nruns, OnePassOut out,
+                               const unsigned char *inner_plane, cudaStream_t st);
 // Blocks of the one-pass update resident on one SM (its persistent grid is this times the SMs).
 int onepass_blocks_per_sm();
 void launch_fields(const StepParams &P, const void *store, const float *rest, const float *rho, float *rhoA,

@@ -3,9 +3,10 @@
 The update of step t also forms the densities of step t + 1 from the post-collision values it
 has just computed (streaming carries f*_i(r) to r + c_i), instead of a density pass pulling every
 population again; a second kernel finishes the nodes whose sources lie in another block.  These
-tests force the one-pass update at sizes the oracle runs in seconds -- ragged tiles along x (30
-columns per warp) and y (8 rows per block), lattices narrower than a tile, blocks whose stretch
-of planes spans two column tiles -- and hold it to the same tolerances as the two-pass update:
+tests force the one-pass update at sizes the oracle runs in seconds -- ragged tiles along x (32
+columns per warp) and y (8 rows per block), lattices narrower than a tile, one-column tiles, tiles
+whose edge rows are pulled and tiles whose edge rows come from partial sums -- and hold it to the
+same tolerances as the two-pass update:
 populations within 1e-5 after 10 steps, positions within 1e-4 after 100 steps; the densities it
 forms are checked node by node against the sum of the populations; the two updates agree to
 rounding order; graphs replay it bit for bit.  At 256^3 the bench's launch (one pass, chosen by
@@ -23,7 +24,11 @@ pytestmark = pytest.mark.gpu
 POP_TOL = 1e-5
 POS_TOL = 1e-4
 
-SIZES = [(20, 18, 16), (31, 9, 13), (33, 17, 12), (1, 16, 12), (2, 3, 5), (64, 20, 24), (7, 25, 30)]
+# tiles of 32 x 8 columns: ragged along x and y, narrower than a tile, one-column tiles (33), tiles
+# of 1 or 2 rows (edge rows pulled) and of >= 3 rows and >= 2 columns (edge rows from partial sums:
+# (2, 3, 5), (64, 20, 24), (40, 11, 18), (34, 24, 20), (64, 16, 40))
+SIZES = [(20, 18, 16), (31, 9, 13), (33, 17, 12), (1, 16, 12), (2, 3, 5), (64, 20, 24), (7, 25, 30), (40, 11, 18),
+         (34, 24, 20), (64, 16, 40)]
 
 
 def L():
