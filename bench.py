@@ -29,9 +29,11 @@ METRIC = "coupled 2-comp D3Q19 MLUPS & HBM-roofline %; replica p50/p99 latency"
 UNIT = "MLUPS"
 HBM_FALLBACK_GBS = 6800.0
 HBM_NOMINAL_GBS = 7900.0
-# DRAM bytes per node moved by k_collide (dram__bytes_read + dram__bytes_write of one ncu capture
-# of the 128^3 case of this workload, scaled per node), per storage with a capture of its own.
-COLLIDE_TRAFFIC_BYTES_PER_NODE = {"fp32": 290.0, "bf16": 147.2}
+# DRAM bytes per node moved by the lattice update (dram__bytes_read + dram__bytes_write of one ncu
+# capture of this workload at a smaller edge, scaled per node), per (storage, lattice passes) with a
+# capture of its own: the one-pass update at 192^3 (1144.6 + 1096.3 MB over 7,077,888 nodes), the
+# two-pass update at 128^3.
+COLLIDE_TRAFFIC_BYTES_PER_NODE = {("fp32", 1): 316.6, ("fp32", 2): 290.0, ("bf16", 2): 147.2}
 # The fluctuating MRT update is bound by instruction issue, not by HBM: warp instructions per
 # node of k_collide<float, true, true> (smsp__inst_executed.sum / nodes of one ncu capture of the
 # 128^3 case), and the issue peak of the GPU: one warp instruction per cycle per scheduler, 4
@@ -72,17 +74,19 @@ WORKLOADS = {
 
 STORAGES = {"fp32": (0, 4), "fp16": (1, 2), "bf16": (2, 2)}  # name: (LBMD_STORAGE_*, bytes per value)
 
-# Errors of the 16-bit storages against the FP64 oracle, as measured and bounded by the GPU tests
-# of tests/test_gpu_precision.py (one GB300 run): the 10-step population error, the Laplace
-# pressure jump of 3-D droplets (64^3, R = 8, 12, 16, 1000 steps; relative) with the fitted
-# 2 gamma, the flat-interface position (lattice units) and the particle MSD over 1000 steps.
+# Errors of the 16-bit storages against the FP64 oracle, as measured (one GB300 run) by the GPU
+# tests of tests/test_gpu_precision.py, which assert bounds above these values: the 10-step
+# population error, the Laplace pressure jump of 3-D droplets (64^3, R = 8, 12, 16, 1000 steps;
+# largest relative error) and the fitted 2 gamma, the position of flat interfaces relaxing from
+# off-coexistence densities (lattice units, after 500 / 2000 steps) and the particle MSD over
+# 1000 steps (relative).
 PRECISION_ERRORS = {
-    "fp16": {"population_10_steps": 2.8e-6, "laplace_dp_3d": None, "laplace_2gamma_3d": None,
-             "interface_position": None, "msd_1000_steps": 7.1e-8,
-             "measured_by": "tests/test_gpu_precision.py"},
-    "bf16": {"population_10_steps": 1.0e-5, "laplace_dp_3d": None, "laplace_2gamma_3d": None,
-             "interface_position": None, "msd_1000_steps": 9.2e-7,
-             "measured_by": "tests/test_gpu_precision.py"},
+    "fp16": {"population_10_steps": 2.8e-6, "laplace_dp_3d": 0.0255, "laplace_2gamma_3d": 0.0506,
+             "interface_position_500_steps": 0.0218, "interface_position_2000_steps": 0.2515,
+             "msd_1000_steps": 1.08e-7, "measured_by": "tests/test_gpu_precision.py"},
+    "bf16": {"population_10_steps": 1.0e-5, "laplace_dp_3d": 0.2027, "laplace_2gamma_3d": 0.4521,
+             "interface_position_500_steps": 0.2023, "interface_position_2000_steps": 1.7084,
+             "msd_1000_steps": 8.73e-7, "measured_by": "tests/test_gpu_precision.py"},
 }
 
 
@@ -92,15 +96,17 @@ def survey_bytes_per_site(storage: str = "fp32") -> int:
     return 2 * 19 * STORAGES[storage][1] * 2
 
 
-def algorithmic_bytes_per_site(storage: str = "fp32") -> int:
-    """Algorithmic bytes per node of the collide kernel: both components' populations read
+def algorithmic_bytes_per_site(storage: str = "fp32", passes: int = 2) -> int:
+    """Algorithmic bytes per node of the lattice update kernel: both components' populations read
     (pull) and written once, plus the node's two FP32 densities of the Shan-Chen stencil (8; the
-    neighbours' come from cache).  FP32: 2*19*4*2 + 8 = 312.  16-bit storage: the 18 moving
-    populations in 2 bytes and the rest population in FP32, 2*(18*2 + 4)*2 + 8 = 168."""
+    neighbours' come from cache), and for the one-pass update the next step's densities it writes
+    (8).  FP32: 2*19*4*2 + 8 = 312 (+ 8 = 320 in one pass).  16-bit storage: the 18 moving
+    populations in 2 bytes and the rest population in FP32, 2*(18*2 + 4)*2 + 8 = 168 (+ 8)."""
     b = STORAGES[storage][1]
+    extra = 8 if passes == 1 else 0
     if b == 4:
-        return 2 * 19 * 4 * 2 + 8
-    return 2 * (18 * b + 4) * 2 + 8
+        return 2 * 19 * 4 * 2 + 8 + extra
+    return 2 * (18 * b + 4) * 2 + 8 + extra
 
 
 def measured_hbm_peak():
@@ -386,7 +392,7 @@ def measure_single(workload: str, storage: str = "fp32", collision: str = "bgk",
 def collide_roofline(m, peak, peak_kind):
     """Roofline of the lattice update kernel alone (HBM; the issue rate for the MRT update)."""
     N = m["N"]
-    bps = algorithmic_bytes_per_site(m["storage"])
+    bps = algorithmic_bytes_per_site(m["storage"], m["lattice_passes"])
     achieved = bps * N / (m["kernel_ms"] * 1e-3) / 1e9
     if m["mrt"]:
         clk = m["clocks"].get("sm_mhz") or 2070.0
@@ -402,14 +408,17 @@ def collide_roofline(m, peak, peak_kind):
                 "kernel_ms": round(m["kernel_ms"], 5), "kernel_launches": m["kernel_launches"],
                 "hbm_frac": round(achieved / peak, 4),
                 "traffic": int(MRT_TRAFFIC_BYTES_PER_NODE * N) if m["storage"] == "fp32" else None}
+    onep = m["lattice_passes"] == 1
     return {"bound": "hbm", "scope": "kernel only (the lattice update)",
-            "kernel": "k_collide (pull streaming + Shan-Chen + coupling gather + BGK/forcing, both components)",
+            "kernel": ("k_collide_onepass (pull streaming + Shan-Chen + coupling gather + BGK/forcing, both components, "
+                       "and the next step's densities)" if onep else
+                       "k_collide (pull streaming + Shan-Chen + coupling gather + BGK/forcing, both components)"),
             "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "bytes_per_site": bps,
             "frac_on_survey_bytes": round(survey_bytes_per_site(m["storage"]) * N / (m["kernel_ms"] * 1e-3) / 1e9 / peak, 4),
             "kernel_ms": round(m["kernel_ms"], 5), "kernel_launches": m["kernel_launches"],
-            "traffic": (None if m["storage"] not in COLLIDE_TRAFFIC_BYTES_PER_NODE
-                        else int(COLLIDE_TRAFFIC_BYTES_PER_NODE[m["storage"]] * N))}
+            "traffic": (None if (m["storage"], m["lattice_passes"]) not in COLLIDE_TRAFFIC_BYTES_PER_NODE
+                        else int(COLLIDE_TRAFFIC_BYTES_PER_NODE[(m["storage"], m["lattice_passes"])] * N))}
 
 
 def step_roofline(m, peak):

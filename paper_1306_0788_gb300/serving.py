@@ -39,6 +39,11 @@ KT = 1e-4
 MASS = 200.0
 WIDTH = 2.0
 SPACING = 2.5
+# Every replica checks its mass per component and total momentum against its state at admission
+# every DIAG_EVERY steps and fails alone (LBMD_E_DRIFT) past DRIFT_TOL: FP32 rounding moves them by
+# about 1e-8 per step, so 1e-4 over a request's steps flags only a broken state.
+DIAG_EVERY = 250
+DRIFT_TOL = 1e-4
 
 
 def coexistence(g_rho: float):
@@ -66,7 +71,8 @@ def replica_fluid(req):
 
 def replica_params(req) -> L.lbmd_params:
     e = req["edge"]
-    return L.params((e, e, e), tau_r=TAU_R, g_AB=req["g"], kT=KT, seed=req["seed"])
+    return L.params((e, e, e), tau_r=TAU_R, g_AB=req["g"], kT=KT, seed=req["seed"],
+                    diag_every=DIAG_EVERY, drift_tol=DRIFT_TOL)
 
 
 def admit(batch, req) -> int:

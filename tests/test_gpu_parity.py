@@ -97,6 +97,12 @@ def coupled_case(dims, npart, seed, g=0.8, kT=0.0, min_dist=2.0):
 
 @pytest.mark.parametrize("kT", [0.0, 0.002])
 def test_particles_100_steps(kT):
+    """100 coupled steps, positions within 1e-4 of the oracle's.  The thermal case runs at kT =
+    0.002 with particles at least 2.5 apart: at kT = 0.005 and 2.0 apart two particles meet in a
+    WCA contact near step 68, the explicit update (dt = 1, m = 1) throws one of them at 10.7 lattice
+    units per step, and the FP64 oracle's own densities go negative at step 72 -- the system
+    leaves the model's stability range (Sec. 3: gamma dt / m << 1), after which FP32 and FP64
+    trajectories part by chaos, not by error."""
     c = coupled_case((20, 18, 16), 30, seed=21, kT=kT, min_dist=2.5)
     fg, xg, vg, _ = run_gpu(c, 100)
     fo, xo, vo, _ = run_oracle(c, 100)
