@@ -109,12 +109,18 @@ __global__ void __launch_bounds__(kBlock, 3) k_collide(StepParams P, const T *__
 // along x -- from lane 0 with c_x = -1, from the last lane with c_x = +1 -- is summed the same way
 // into edge partials for the neighbouring tiles' edge nodes, which k_boundary_densities adds.  Every
 // sum has a fixed order.  Nodes with sources in another block along y or z -- the first and last
-// row of the tile, the first and last plane of the chunk -- are left to k_boundary_densities,
-// which pulls their populations as the density pass does.
+// row of the tile, the first and last plane of the chunk -- get the same treatment: the block
+// writes its part (across the tile's bottom and top rows per lane; for the planes below and at
+// the chunk's start, and at and above its end, what its accumulators hold), and
+// k_boundary_densities adds the parts of the two blocks.  Where a lattice is too thin for the
+// partial sums (tiles of fewer than 3 rows or 2 columns; one plane), k_boundary_densities pulls
+// those nodes' populations as the density pass does.
 constexpr int kOPThreads = kOnePassRows * 32;
 // the densities a block's stencils read in one plane: rows y0 - 1 .. y0 + 8, columns x0 - 1 ..
 // x0 + 32
 constexpr int kRhoRows = kOnePassRows + 2, kRhoCols = kOnePassCols + 2, kRhoSlots = 4;
+static_assert(kOnePassCols == 32 && kRhoCols - 32 <= 32, "a warp stages a ring row with one or two copies per lane");
+static_assert(kOnePassRows - 1 <= 15, "pair barriers 1 .. kOnePassRows - 1");
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
@@ -125,6 +131,10 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Named barrier `id` (1 .. 15; 0 is __syncthreads) for `n` threads of the block, all of whose
+// warps take it convergently.
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
 
 // The staged densities of a block's stencil: a ring of kRhoSlots planes.
 struct StagedRho {
@@ -137,20 +147,47 @@ struct StagedRho {
   }
 };
 
-// Copies (cp.async) the densities of plane z into ring slot `slot_index` % 4: rows y0 - 1 + k,
-// columns x0 - 1 + j, both wrapped periodically; every thread of the block takes part.  The slot
-// follows the unwrapped plane index (z - 1 .. z + 2 of a march take four distinct slots even where
-// the lattice is shorter than four planes).
-__device__ __forceinline__ void stage_plane(const StepParams &P, const float *__restrict__ rho,
-                                            float2 (*ring)[kRhoRows][kRhoCols], int slot_index, int z, int x0,
-                                            int y0) {
-  const float2 *rho2 = reinterpret_cast<const float2 *>(rho);
-  float2(*slot)[kRhoCols] = ring[slot_index & (kRhoSlots - 1)];
+// The elements of a staged plane: element e of the kRhoRows x kRhoCols rows y0 - 1 + e / kRhoCols,
+// columns x0 - 1 + e % kRhoCols (both wrapped periodically) has the offset src[e] = y nx + x within
+// a plane.  The same for every plane of a march: computed once per block, kept in shared memory
+// (not in registers, which the update needs).
+__device__ __forceinline__ void stage_sources(const StepParams &P, int x0, int y0, int *src) {
   for (int e = threadIdx.x; e < kRhoRows * kRhoCols; e += kOPThreads) {
-    const int k = e / kRhoCols, j = e - k * kRhoCols;
-    const int y = ((y0 - 1 + k) % P.ny + P.ny) % P.ny, x = ((x0 - 1 + j) % P.nx + P.nx) % P.nx;
-    cp_async8(&slot[k][j], rho2 + ((long long)z * P.ny + y) * P.nx + x);
+    const int r = e / kRhoCols, j = e - r * kRhoCols;
+    const int y = ((y0 - 1 + r) % P.ny + P.ny) % P.ny, x = ((x0 - 1 + j) % P.nx + P.nx) % P.nx;
+    src[e] = y * P.nx + x;
   }
+}
+
+// The part of plane z's staged densities warp w copies (cp.async) into ring slot `slot_index` % 4:
+// ring row w + 1, and the halo rows 0 (warp 0) and kRhoRows - 1 (the last warp).  The stencils
+// of warp w read ring rows w .. w + 2, which warps w - 1 .. w + 1 copy.
+__device__ __forceinline__ void stage_rows(const StepParams &P, const float *__restrict__ rho,
+                                           float2 (*ring)[kRhoRows][kRhoCols], int slot_index, int z,
+                                           const int *src, int w, int lane) {
+  const float2 *plane = reinterpret_cast<const float2 *>(rho) + (long long)z * P.ny * P.nx;
+  float2 *slot = &ring[slot_index & (kRhoSlots - 1)][0][0];
+  auto row = [&](int r) {
+    const int e = r * kRhoCols + lane;
+    cp_async8(slot + e, plane + src[e]);
+    if (lane < kRhoCols - 32) cp_async8(slot + e + 32, plane + src[e + 32]);
+  };
+  row(w + 1);
+  if (w == 0) row(0);
+  if (w == kOnePassRows - 1) row(kRhoRows - 1);
+  cp_async_commit();
+}
+
+// Copies (cp.async) the densities of plane z into ring slot `slot_index` % 4 (the elements of
+// stage_sources); every thread of the block takes part.  The slot follows the unwrapped plane
+// index (z - 1 .. z + 2 of a march take four distinct slots even where the lattice is shorter than
+// four planes).
+__device__ __forceinline__ void stage_plane(const StepParams &P, const float *__restrict__ rho,
+                                            float2 (*ring)[kRhoRows][kRhoCols], int slot_index, int z,
+                                            const int *src) {
+  const float2 *plane = reinterpret_cast<const float2 *>(rho) + (long long)z * P.ny * P.nx;
+  float2 *slot = &ring[slot_index & (kRhoSlots - 1)][0][0];
+  for (int e = threadIdx.x; e < kRhoRows * kRhoCols; e += kOPThreads) cp_async8(slot + e, plane + src[e]);
   cp_async_commit();
 }
 
@@ -173,6 +210,7 @@ __global__ void __launch_bounds__(kOPThreads, 3)
   __shared__ float2 accY[3][2][32];
   // the stencils' densities, read from global memory once per block and plane
   __shared__ float2 ring[kRhoSlots][kRhoRows][kRhoCols];
+  __shared__ int stage_src[kRhoRows * kRhoCols];  // where each staged element comes from (stage_sources)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr unsigned kFull = 0xffffffffu;
   const int ncols = G.ntx * G.nty, chunk = blockIdx.x / ncols, col = blockIdx.x - chunk * ncols;
@@ -193,12 +231,16 @@ __global__ void __launch_bounds__(kOPThreads, 3)
   // (lacking what arrives from the neighbouring tile's row, which that tile sends)
   const bool summed_row = w < rows && (G.ypart || inner_row);
   const bool lo = w > 0, hi = w < rows - 1;  // the rows below / above are in the block
-  for (int dz = -1; dz <= 1; ++dz) stage_plane(P, rho, ring, zs + dz + kRhoSlots, (zs + dz + P.nz) % P.nz, x0, y0);
+  stage_sources(P, x0, y0, stage_src);
+  __syncthreads();
+  for (int dz = -1; dz <= 1; ++dz)
+    stage_plane(P, rho, ring, zs + dz + kRhoSlots, (zs + dz + P.nz) % P.nz, stage_src);
   cp_async_wait_all();
   __syncthreads();
   int parity = 0;
   for (int z = zs; z < ze; ++z, parity ^= 1) {
-    stage_plane(P, rho, ring, z + 2, (z + 2) % P.nz, x0, y0);  // for the next plane; its slot is free
+    const int z2 = z + 2 < P.nz ? z + 2 : (z + 2) % P.nz;
+    stage_rows(P, rho, ring, z + 2, z2, stage_src, w, lane);  // for the next plane; its slot is free
     float fA[kQ], fB[kQ];
     if (own && w < rows) {
       const long long s = ((long long)z * P.ny + y) * P.nx + x;
@@ -237,10 +279,19 @@ __global__ void __launch_bounds__(kOPThreads, 3)
       xedge[parity][1][1][w] = make_float2(fA[9], fB[9]);
     }
     const float2 g0m = group(6, 13, 12), g00 = group(0, 1, 2), g0p = group(5, 11, 14);
-    cp_async_wait_all();  // the next plane's densities (issued above) have landed
-    __syncthreads();
+    cp_async_wait_all();  // this warp's rows of the next plane's densities (issued above) have landed
+    // The exchange with the rows below and above, and the staged rows they read: a barrier with
+    // each neighbouring warp only (pair (w - 1, w) is barrier w), taken in that order.  A warp
+    // passes plane z's barriers after its neighbours have written plane z's exchange and staged
+    // rows, and writes the same buffers again (plane z + 2) only after they have passed plane
+    // z + 1's, i.e. after they have read plane z's.
+    if (w > 0) bar_sync(w, 64);
+    if (w < kOnePassRows - 1) bar_sync(w + 1, 64);
     const int km = (z + 2) % 3, k0 = z % 3, kp = (z + 1) % 3;
-    const bool write = z >= zs + 2;  // plane z - 1 has all its sources (z - 2 .. z) in the chunk
+    // plane z - 1 has all its sources (z - 2 .. z) in the chunk, or (with z partial sums) it is the
+    // first plane of the chunk or the one below it, and this is the upper chunk's part
+    const bool write = G.zpart || z >= zs + 2;
+    const int zm = z == 0 ? P.nz - 1 : z - 1;
     const float2 zero = make_float2(0.f, 0.f);
     if (own && summed_row) {
       // from the row below (c_y = +1), this row (c_y = 0), the row above (c_y = -1), into the
@@ -252,7 +303,7 @@ __global__ void __launch_bounds__(kOPThreads, 3)
       acc[kp][threadIdx.x] = add2(add2(add2(acc[kp][threadIdx.x], lo ? X[2][w - 1][lane] : zero), g0p),
                                   hi ? X[5][w + 1][lane] : zero);
       if (write)
-        reinterpret_cast<float2 *>(rho_next)[((long long)(z - 1) * P.ny + y) * P.nx + x] =
+        reinterpret_cast<float2 *>(rho_next)[((long long)zm * P.ny + y) * P.nx + x] =
             add2(am, make_float2(shift_sum(P, 0), shift_sum(P, 1)));
       acc[km][threadIdx.x] = zero;  // becomes plane z + 2
     }
@@ -270,7 +321,7 @@ __global__ void __launch_bounds__(kOPThreads, 3)
                                       make_float2(fA[i00], fB[i00])),
                                  hi ? xedge[parity][side][1][w + 1] : zero);
         accE[kp][side][w] = add2(accE[kp][side][w], make_float2(fA[i0p], fB[i0p]));
-        if (write) edge2[(((long long)(z - 1) * P.ny + y) * G.ntx + tx) * 2 + side] = em;
+        if (write) edge2[(((long long)zm * P.ny + y) * G.ntx + tx) * 2 + side] = em;
         accE[km][side][w] = zero;
       }
     }
@@ -282,11 +333,11 @@ __global__ void __launch_bounds__(kOPThreads, 3)
       accY[k0][sy][lane] = add2(accY[k0][sy][lane], X[g + 1][w][lane]);
       accY[kp][sy][lane] = add2(accY[kp][sy][lane], X[g + 2][w][lane]);
       if (write)
-        reinterpret_cast<float2 *>(out.yedge)[(((long long)sy * P.nz + (z - 1)) * G.nty + ty) * (G.ntx * kOnePassCols) +
+        reinterpret_cast<float2 *>(out.yedge)[(((long long)sy * P.nz + zm) * G.nty + ty) * (G.ntx * kOnePassCols) +
                                               x0 + lane] = ym;
       accY[km][sy][lane] = zero;
       // the value leaving each corner diagonally (c_z = 0: it arrives in this plane)
-      if ((left || right) && z >= zs + 1 && z <= ze - 2) {
+      if ((left || right) && (G.zpart || (z >= zs + 1 && z <= ze - 2))) {
         const int k = (sy << 1) | (right ? 1 : 0);  // 0: bottom-left ... 3: top-right
         // directions 8, 9, 10, 7 (constant indices: the arrays stay in registers)
         const float2 d = sy ? (right ? make_float2(fA[7], fB[7]) : make_float2(fA[10], fB[10]))
@@ -295,29 +346,78 @@ __global__ void __launch_bounds__(kOPThreads, 3)
       }
     }
   }
+  if (G.zpart) {
+    // this chunk's part of the planes ze - 1 and ze, the first two planes of the boundary with the
+    // next chunk (slots 2 b, 2 b + 1): what the last iteration left in the accumulators
+    const int b = chunk + 1 == G.nchunks ? 0 : chunk + 1;
+    const int k0 = (ze - 1) % 3, kp = ze % 3;
+    if (own && summed_row) {
+      float2 *zo = reinterpret_cast<float2 *>(out.zown);
+      zo[((long long)(2 * b) * P.ny + y) * P.nx + x] = acc[k0][threadIdx.x];
+      zo[((long long)(2 * b + 1) * P.ny + y) * P.nx + x] = acc[kp][threadIdx.x];
+    }
+    if (summed_row && (left || right)) {
+      float2 *ze2 = reinterpret_cast<float2 *>(out.zedge);
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        if (side == 0 ? !left : !right) continue;
+        ze2[(((long long)(2 * b) * P.ny + y) * G.ntx + tx) * 2 + side] = accE[k0][side][w];
+        ze2[(((long long)(2 * b + 1) * P.ny + y) * G.ntx + tx) * 2 + side] = accE[kp][side][w];
+      }
+    }
+    if (G.ypart && own && (w == 0 || w == rows - 1)) {
+      const int sy = w == 0 ? 0 : 1;
+      float2 *zy = reinterpret_cast<float2 *>(out.zyedge);
+      const long long stride = (long long)G.nty * G.ntx * kOnePassCols;
+      zy[((long long)sy * 2 * G.nchunks + 2 * b) * stride + (long long)ty * G.ntx * kOnePassCols + x0 + lane] =
+          accY[k0][sy][lane];
+      zy[((long long)sy * 2 * G.nchunks + 2 * b + 1) * stride + (long long)ty * G.ntx * kOnePassCols + x0 + lane] =
+          accY[kp][sy][lane];
+    }
+  }
   cp_async_wait_all();  // no copy outlives the block
 }
 
-// The nodes the one-pass update leaves unfinished, in one launch of three block ranges:
+// The nodes the one-pass update leaves unfinished, in one launch of five block ranges (range 5
+// first):
 //  1. the boundary runs, a warp per run: their densities from the new populations, as the density
-//     pass computes them (the first and last plane of each chunk; without y partials also the
-//     first and last row of each tile);
+//     pass computes them (without y partials the first and last row of each tile; without z
+//     partials the first and last plane of each chunk);
 //  2. the x-edge nodes of the inner rows: own partial (in rho_next) plus what arrives from the
 //     neighbouring tile -- from the left one's side-1 sums at x0, from the right one's side-0 sums
 //     at x0 + nown - 1 (both, in that order, when a tile has one column);
 //  3. with y partials, the edge rows: own partial plus what the tile below (for the bottom row) or
 //     above (for the top row) sends across, and at the two corners also the x-neighbour's edge-row
-//     sums and the value the diagonal neighbour sends, in that order.
-// All inner planes only (chunk edge planes are runs); the sets of nodes are disjoint.
+//     sums and the value the diagonal neighbour sends, in that order;
+//  4. with z partials, the other nodes of the chunk-edge planes: own partial plus the lower
+//     chunk's;
+//  5. with particles, j' of the new populations at the 8 corners of each particle's cell, for the
+//     next step's coupling (jc, by particle id; pn: the particles as the next step starts).
+// In ranges 2 and 3 a chunk-edge plane's node adds the lower chunk's part after each term.  The
+// sets of nodes are disjoint, and every node's sum has a fixed order.
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_boundary_densities(StepParams P, OnePassGeom G, const T *__restrict__ store,
                                                                const float *__restrict__ rest,
                                                                float *__restrict__ rho_next,
                                                                const BoundaryRun *__restrict__ runs, int nruns,
-                                                               int run_blocks, int edge_blocks, OnePassOut out,
-                                                               const unsigned char *__restrict__ inner_plane) {
-  if ((int)blockIdx.x < run_blocks) {
-    const int r = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+                                                               int corner_blocks, int run_blocks, int edge_blocks,
+                                                               int row_blocks, OnePassOut out,
+                                                               const int *__restrict__ zslot, ParticleArrays pn,
+                                                               int np, float4 *__restrict__ jc) {
+  // the latency-bound corner j' blocks first, so that they run beside the others
+  if ((int)blockIdx.x < corner_blocks) {
+    // 5: corner j' (a thread per particle and corner)
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8LL * np) return;
+    const int p = (int)(t >> 3), k = (int)(t & 7);
+    const Coord cc = cell_corner(P, __ldg(pn.cell + p), k);
+    const float3 j = jprime_at<T>(P, store, cc.x, cc.y, cc.z);
+    jc[(long long)__ldg(pn.pid + p) * 8 + k] = make_float4(j.x, j.y, j.z, 0.f);
+    return;
+  }
+  const int bid = (int)blockIdx.x - corner_blocks;
+  if (bid < run_blocks) {
+    const int r = bid * (kBlock / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (r >= nruns) return;
     const BoundaryRun b = runs[r];
     if (lane >= b.n) return;
@@ -325,10 +425,13 @@ __global__ void __launch_bounds__(kBlock) k_boundary_densities(StepParams P, One
     return;
   }
   const float2 *e2 = reinterpret_cast<const float2 *>(out.edge);
+  const float2 *zo = reinterpret_cast<const float2 *>(out.zown);
+  const float2 *ze2 = reinterpret_cast<const float2 *>(out.zedge);
   float2 *rho2 = reinterpret_cast<float2 *>(rho_next);
-  if ((int)blockIdx.x < run_blocks + edge_blocks) {
+  const long long plane = (long long)P.ny * P.nx;
+  if (bid < run_blocks + edge_blocks) {
     // 32-bit index arithmetic: nz ny ntx < N < 2^32 / 19
-    const unsigned t = (unsigned)(blockIdx.x - run_blocks) * blockDim.x + threadIdx.x;
+    const unsigned t = (unsigned)(bid - run_blocks) * blockDim.x + threadIdx.x;
     const unsigned n = (unsigned)P.nz * P.ny * G.ntx;
     if (t >= n) return;
     const unsigned r = t / G.ntx;  // z * ny + y
@@ -336,49 +439,89 @@ __global__ void __launch_bounds__(kBlock) k_boundary_densities(StepParams P, One
     const int z = (int)(r / P.ny), y = (int)(r - (unsigned)z * P.ny);
     const int w = y % kOnePassRows, y0 = y - w, rows = min(kOnePassRows, P.ny - y0);
     if (w < 1 || w > rows - 2) return;  // tile edge rows: runs, or range 3
-    if (!inner_plane[z]) return;        // chunk edge planes: runs
+    const int q = zslot[z];             // chunk-edge plane: its slot in the z arrays
+    if (q >= 0 && !G.zpart) return;     // runs
     const int x0 = tx * kOnePassCols, nown = min(kOnePassCols, P.nx - x0);
     const int txl = tx == 0 ? G.ntx - 1 : tx - 1, txr = tx == G.ntx - 1 ? 0 : tx + 1;
     const long long base = (long long)r * P.nx;
-    const float2 v = add2(rho2[base + x0], e2[((long long)r * G.ntx + txl) * 2 + 1]);  // from the left tile's last lane
-    if (nown == 1) {
-      rho2[base + x0] = add2(v, e2[((long long)r * G.ntx + txr) * 2 + 0]);  // and from the right tile's lane 0
+    const long long zb = ((long long)q * P.ny + y) * P.nx;  // this row in the z arrays (q >= 0)
+    const long long zr = (long long)q * P.ny + y;
+    float2 v = rho2[base + x0];
+    if (q >= 0) v = add2(v, zo[zb + x0]);
+    v = add2(v, e2[((long long)r * G.ntx + txl) * 2 + 1]);  // from the left tile's last lane
+    if (q >= 0) v = add2(v, ze2[(zr * G.ntx + txl) * 2 + 1]);
+    if (nown == 1) {  // and from the right tile's lane 0
+      v = add2(v, e2[((long long)r * G.ntx + txr) * 2 + 0]);
+      if (q >= 0) v = add2(v, ze2[(zr * G.ntx + txr) * 2 + 0]);
+      rho2[base + x0] = v;
       return;
     }
     rho2[base + x0] = v;
-    rho2[base + x0 + nown - 1] = add2(rho2[base + x0 + nown - 1], e2[((long long)r * G.ntx + txr) * 2 + 0]);
+    const int xr = x0 + nown - 1;
+    v = rho2[base + xr];
+    if (q >= 0) v = add2(v, zo[zb + xr]);
+    v = add2(v, e2[((long long)r * G.ntx + txr) * 2 + 0]);
+    if (q >= 0) v = add2(v, ze2[(zr * G.ntx + txr) * 2 + 0]);
+    rho2[base + xr] = v;
     return;
   }
-  // 3: edge rows (y partials): thread per (z, tile row, bottom / top, x)
-  const unsigned t = (unsigned)(blockIdx.x - run_blocks - edge_blocks) * blockDim.x + threadIdx.x;
-  const unsigned n = (unsigned)P.nz * G.nty * 2 * P.nx;
+  if (bid < run_blocks + edge_blocks + row_blocks) {
+    // 3: edge rows (y partials): thread per (z, tile row, bottom / top, x)
+    const unsigned t = (unsigned)(bid - run_blocks - edge_blocks) * blockDim.x + threadIdx.x;
+    const unsigned n = (unsigned)P.nz * G.nty * 2 * P.nx;
+    if (t >= n) return;
+    const unsigned qq = t / P.nx;
+    const int x = (int)(t - qq * P.nx);
+    const int sy = (int)(qq & 1u);
+    const unsigned zt = qq >> 1;
+    const int z = (int)(zt / G.nty), ty = (int)(zt - (unsigned)z * G.nty);
+    const int q = zslot[z];
+    if (q >= 0 && !G.zpart) return;  // runs
+    const int y0 = ty * kOnePassRows, rows = min(kOnePassRows, P.ny - y0), y = sy ? y0 + rows - 1 : y0;
+    const int tx = x / kOnePassCols, x0 = tx * kOnePassCols, nown = min(kOnePassCols, P.nx - x0);
+    const int txl = tx == 0 ? G.ntx - 1 : tx - 1, txr = tx == G.ntx - 1 ? 0 : tx + 1;
+    const int tyn = sy ? (ty == G.nty - 1 ? 0 : ty + 1) : (ty == 0 ? G.nty - 1 : ty - 1);  // the tile sending across
+    const float2 *y2 = reinterpret_cast<const float2 *>(out.yedge);
+    const float2 *zy = reinterpret_cast<const float2 *>(out.zyedge);
+    const float2 *d2 = reinterpret_cast<const float2 *>(out.diag);
+    const long long node = ((long long)z * P.ny + y) * P.nx + x;
+    const long long ystride = (long long)G.ntx * kOnePassCols;
+    float2 v = rho2[node];
+    if (q >= 0) v = add2(v, zo[(long long)q * plane + (long long)y * P.nx + x]);
+    // the bottom row gets what the tile below sends up (its side 1), the top row what the tile
+    // above sends down (its side 0)
+    v = add2(v, y2[(((long long)(1 - sy) * P.nz + z) * G.nty + tyn) * ystride + x]);
+    if (q >= 0) v = add2(v, zy[(((long long)(1 - sy) * 2 * G.nchunks + q) * G.nty + tyn) * ystride + x]);
+    const long long er = (long long)z * P.ny + y, zr = (long long)q * P.ny + y;
+    if (x == x0) {  // corner: the left tile's side-1 sums of this row, the diagonal value
+      v = add2(v, e2[(er * G.ntx + txl) * 2 + 1]);
+      if (q >= 0) v = add2(v, ze2[(zr * G.ntx + txl) * 2 + 1]);
+      v = add2(v, d2[(((long long)z * G.nty + tyn) * G.ntx + txl) * 4 + (sy ? 1 : 3)]);
+    }
+    if (x == x0 + nown - 1) {  // corner: the right tile's side-0 sums of this row, the diagonal value
+      v = add2(v, e2[(er * G.ntx + txr) * 2 + 0]);
+      if (q >= 0) v = add2(v, ze2[(zr * G.ntx + txr) * 2 + 0]);
+      v = add2(v, d2[(((long long)z * G.nty + tyn) * G.ntx + txr) * 4 + (sy ? 0 : 2)]);
+    }
+    rho2[node] = v;
+    return;
+  }
+  // 4: the other nodes of the chunk-edge planes (z partials): thread per (slot, y, x)
+  const unsigned t = (unsigned)(bid - run_blocks - edge_blocks - row_blocks) * blockDim.x + threadIdx.x;
+  const unsigned n = (unsigned)(2 * G.nchunks) * P.ny * P.nx;
   if (t >= n) return;
-  const unsigned q = t / P.nx;
-  const int x = (int)(t - q * P.nx);
-  const int sy = (int)(q & 1u);
-  const unsigned zt = q >> 1;
-  const int z = (int)(zt / G.nty), ty = (int)(zt - (unsigned)z * G.nty);
-  if (!inner_plane[z]) return;
-  const int y0 = ty * kOnePassRows, rows = min(kOnePassRows, P.ny - y0), y = sy ? y0 + rows - 1 : y0;
-  const int tx = x / kOnePassCols, x0 = tx * kOnePassCols, nown = min(kOnePassCols, P.nx - x0);
-  const int txl = tx == 0 ? G.ntx - 1 : tx - 1, txr = tx == G.ntx - 1 ? 0 : tx + 1;
-  const int tyn = sy ? (ty == G.nty - 1 ? 0 : ty + 1) : (ty == 0 ? G.nty - 1 : ty - 1);  // the tile sending across
-  const float2 *y2 = reinterpret_cast<const float2 *>(out.yedge);
-  const float2 *d2 = reinterpret_cast<const float2 *>(out.diag);
-  const long long node = ((long long)z * P.ny + y) * P.nx + x;
-  // the bottom row gets what the tile below sends up (its side 1), the top row what the tile
-  // above sends down (its side 0)
-  float2 v = add2(rho2[node], y2[(((long long)(1 - sy) * P.nz + z) * G.nty + tyn) * (G.ntx * kOnePassCols) + x]);
-  const long long er = (long long)z * P.ny + y;
-  if (x == x0) {  // corner: the left tile's side-1 sums of this row, the diagonal value
-    v = add2(v, e2[(er * G.ntx + txl) * 2 + 1]);
-    v = add2(v, d2[(((long long)z * G.nty + tyn) * G.ntx + txl) * 4 + (sy ? 1 : 3)]);
-  }
-  if (x == x0 + nown - 1) {  // corner: the right tile's side-0 sums of this row, the diagonal value
-    v = add2(v, e2[(er * G.ntx + txr) * 2 + 0]);
-    v = add2(v, d2[(((long long)z * G.nty + tyn) * G.ntx + txr) * 4 + (sy ? 0 : 2)]);
-  }
-  rho2[node] = v;
+  const unsigned qy = t / P.nx;
+  const int x = (int)(t - qy * P.nx);
+  const int q = (int)(qy / P.ny), y = (int)(qy - (unsigned)q * P.ny);
+  const int w = y % kOnePassRows, rows = min(kOnePassRows, P.ny - (y - w));
+  if (w < 1 || w > rows - 2) return;  // tile edge rows: runs, or range 3
+  const int xt = x % kOnePassCols, nown = min(kOnePassCols, P.nx - (x - xt));
+  if (xt == 0 || xt == nown - 1) return;  // x edges: range 2
+  // the plane of slot q: zs - 1 (q even) or zs (q odd) of chunk q / 2
+  const int zs = (int)((long long)(q >> 1) * P.nz / G.nchunks);
+  const int z = (q & 1) ? zs : (zs == 0 ? P.nz - 1 : zs - 1);
+  const long long node = (long long)z * plane + (long long)y * P.nx + x;
+  rho2[node] = add2(rho2[node], zo[(long long)q * plane + (long long)y * P.nx + x]);
 }
 
 // rho_A, rho_B and u = (j' + g^SC/2)/rho at the current step (for readback).
@@ -463,12 +606,15 @@ __global__ void __launch_bounds__(kSumBlock) k_fluid_sums(StepParams P, const T 
 }
 
 __global__ void k_finish_sums(const double *__restrict__ partial, int nblocks, int nvals, double *__restrict__ out) {
-  // one thread per value, sequential over blocks: deterministic order
-  const int k = threadIdx.x;
-  if (k >= nvals) return;
+  // one warp per value: lane l adds the blocks l, l + 32, ... in order, then a fixed shuffle tree
+  // (deterministic; 32 chains instead of one long chain of dependent FP64 additions)
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (k >= nvals) return;  // warp-uniform
   double a = 0.0;
-  for (int b = 0; b < nblocks; ++b) a += partial[(long long)b * nvals + k];
-  out[k] = a;
+  for (int b = lane; b < nblocks; b += 32) a += partial[(long long)b * nvals + k];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+  if (lane == 0) out[k] = a;
 }
 
 // The drift check of the conserved totals (appendix: the collision and the forcing term keep
@@ -579,16 +725,20 @@ void launch_collide_onepass(const StepParams &P, const void *fin, void *fout, fl
 
 void launch_boundary_densities(const StepParams &P, OnePassGeom G, const void *store, const float *rest,
                                float *rho_next, const BoundaryRun *runs, int nruns, OnePassOut out,
-                               const unsigned char *inner_plane, cudaStream_t st) {
+                               const int *zslot, const ParticleArrays &pn, int np, float4 *jc, cudaStream_t st) {
   const long long run_blocks = (nruns + kBlock / 32 - 1) / (kBlock / 32);
   const long long edge_blocks = ((long long)P.nz * P.ny * G.ntx + kBlock - 1) / kBlock;
   const long long row_blocks = G.ypart ? ((long long)P.nz * G.nty * 2 * P.nx + kBlock - 1) / kBlock : 0;
-  if (run_blocks + edge_blocks + row_blocks <= 0) return;
+  const long long zplane_blocks = G.zpart ? ((long long)2 * G.nchunks * P.ny * P.nx + kBlock - 1) / kBlock : 0;
+  if (!jc) np = 0;
+  const long long corner_blocks = (8LL * np + kBlock - 1) / kBlock;
+  const long long blocks = run_blocks + edge_blocks + row_blocks + zplane_blocks + corner_blocks;
+  if (blocks <= 0) return;
   with_storage(P, [&](auto t) {
     using T = std::remove_pointer_t<decltype(t)>;
-    k_boundary_densities<T><<<(unsigned)(run_blocks + edge_blocks + row_blocks), kBlock, 0, st>>>(
-        P, G, static_cast<const T *>(store), rest, rho_next, runs, nruns, (int)run_blocks, (int)edge_blocks, out,
-        inner_plane);
+    k_boundary_densities<T><<<(unsigned)blocks, kBlock, 0, st>>>(
+        P, G, static_cast<const T *>(store), rest, rho_next, runs, nruns, (int)corner_blocks, (int)run_blocks,
+        (int)edge_blocks, (int)row_blocks, out, zslot, pn, np, jc);
   });
 }
 
@@ -655,7 +805,7 @@ void launch_fluid_sums(const StepParams &P, const void *store, const float *rest
   });
 }
 void launch_finish_sums(const double *partial, int nblocks, int nvals, double *out, cudaStream_t st) {
-  k_finish_sums<<<1, 32, 0, st>>>(partial, nblocks, nvals, out);
+  k_finish_sums<<<1, 32 * nvals, 0, st>>>(partial, nblocks, nvals, out);
 }
 void launch_drift_check(const double *sums, const double *psum, double *ref, double *last, unsigned *err,
                         long long step, double tol, int set_ref, cudaStream_t st) {

@@ -217,16 +217,28 @@ __global__ void __launch_bounds__(kPBlock) k_couple(StepParams P, ParticleArrays
   site::couple8(P, noise_step(P, P.step), p, k, 0xFFu << (threadIdx.x & 24), pa, pa, ci, rho, jp, pf);
 }
 
-// k_couple with j' pulled from the populations at each corner.
-template <class T>
-__global__ void __launch_bounds__(kPBlock) k_couple_pull(StepParams P, ParticleArrays pa, CellIndex ci,
-                                                         const float *__restrict__ rho, const T *__restrict__ fin,
-                                                         ParticleForces pf) {
+// k_couple with j' at each corner already formed (jc, 8 float4 per particle id).
+__global__ void __launch_bounds__(kPBlock) k_couple_jc(StepParams P, ParticleArrays pa, CellIndex ci,
+                                                       const float *__restrict__ rho, const float4 *__restrict__ jc,
+                                                       ParticleForces pf) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = (int)(t >> 3), k = (int)(t & 7);
   if (p >= P.np) return;
-  site::couple8<T>(P, noise_step(P, P.step), p, k, 0xFFu << (threadIdx.x & 24), pa, pa, ci, rho, nullptr, pf, true,
-                   fin);
+  site::couple8(P, noise_step(P, P.step), p, k, 0xFFu << (threadIdx.x & 24), pa, pa, ci, rho, nullptr, pf, true,
+                jc);
+}
+
+// j' = sum_z sum_i f_zi c_i of the populations `store` at the 8 corners of every particle's cell,
+// into jc[pid * 8 + corner] (the values k_couple_jc reads).
+template <class T>
+__global__ void __launch_bounds__(kPBlock) k_corner_jprime(StepParams P, ParticleArrays pa, int np,
+                                                           const T *__restrict__ store, float4 *__restrict__ jc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 8LL * np) return;
+  const int p = (int)(t >> 3), k = (int)(t & 7);
+  const site::Coord cc = site::cell_corner(P, __ldg(pa.cell + p), k);
+  const float3 j = site::jprime_at<T>(P, store, cc.x, cc.y, cc.z);
+  jc[(long long)__ldg(pa.pid + p) * 8 + k] = make_float4(j.x, j.y, j.z, 0.f);
 }
 
 // Pair and bonded forces of every particle (site::pairs).
@@ -359,18 +371,23 @@ void launch_couple(const StepParams &P, const ParticleArrays &pa, CellIndex ci, 
                    const ParticleForces &pf, cudaStream_t st) {
   k_couple<<<pgrid(8LL * P.np), kPBlock, 0, st>>>(P, pa, ci, rho, jp, pf);
 }
-void launch_couple_pull(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho,
-                        const void *store, const ParticleForces &pf, cudaStream_t st) {
+void launch_couple_jc(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho,
+                      const float4 *jc, const ParticleForces &pf, cudaStream_t st) {
+  k_couple_jc<<<pgrid(8LL * P.np), kPBlock, 0, st>>>(P, pa, ci, rho, jc, pf);
+}
+void launch_corner_jprime(const StepParams &P, const ParticleArrays &pa, int np, const void *store, float4 *jc,
+                          cudaStream_t st) {
+  if (np <= 0) return;
   switch (P.storage) {
     case LBMD_STORAGE_FP16_SHIFTED:
-      k_couple_pull<__half><<<pgrid(8LL * P.np), kPBlock, 0, st>>>(P, pa, ci, rho, static_cast<const __half *>(store), pf);
+      k_corner_jprime<__half><<<pgrid(8LL * np), kPBlock, 0, st>>>(P, pa, np, static_cast<const __half *>(store), jc);
       break;
     case LBMD_STORAGE_BF16_SHIFTED:
-      k_couple_pull<__nv_bfloat16><<<pgrid(8LL * P.np), kPBlock, 0, st>>>(
-          P, pa, ci, rho, static_cast<const __nv_bfloat16 *>(store), pf);
+      k_corner_jprime<__nv_bfloat16><<<pgrid(8LL * np), kPBlock, 0, st>>>(
+          P, pa, np, static_cast<const __nv_bfloat16 *>(store), jc);
       break;
     default:
-      k_couple_pull<float><<<pgrid(8LL * P.np), kPBlock, 0, st>>>(P, pa, ci, rho, static_cast<const float *>(store), pf);
+      k_corner_jprime<float><<<pgrid(8LL * np), kPBlock, 0, st>>>(P, pa, np, static_cast<const float *>(store), jc);
   }
 }
 void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const int *bond_start,

@@ -785,22 +785,30 @@ __device__ __forceinline__ float3 jprime_at(const StepParams &P, const T *__rest
   return make_float3(jx, jy, jz);
 }
 
-// Contribution of corner k (offset (k & 1, k >> 1 & 1, k >> 2 & 1)) of the particle's cell.
-// j' comes from jp, or (jp NULL) is pulled from the populations fin.
-template <class TS = float>
+// Node of corner k (offset (k & 1, k >> 1 & 1, k >> 2 & 1)) of the cell c, wrapped.
+__device__ __forceinline__ Coord cell_corner(const StepParams &P, int4 c, int k) {
+  const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
+  return Coord{c.x + ox == P.nx ? 0 : c.x + ox, c.y + oy == P.ny ? 0 : c.y + oy, c.z + oz == P.nz ? 0 : c.z + oz};
+}
+
+// Contribution of corner k of the particle's cell.  j' comes from jc (this particle's 8 corner
+// values, formed beforehand) when not NULL, else from the field jp.
 __device__ __forceinline__ void couple_corner(const StepParams &P, int k, int4 c, float4 fr, const TypeParams &T,
                                               const ParticleArrays &list, CellIndex ci,
                                               const float *__restrict__ rho, const float *__restrict__ jp,
                                               const ParticleForces &pf, bool with_fsr, CoupleSums &S,
-                                              const TS *__restrict__ fin = nullptr) {
+                                              const float4 *__restrict__ jc = nullptr) {
   const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
-  const int X = c.x + ox == P.nx ? 0 : c.x + ox;
-  const int Y = c.y + oy == P.ny ? 0 : c.y + oy;
-  const int Z = c.z + oz == P.nz ? 0 : c.z + oz;
+  const Coord cc = cell_corner(P, c, k);
+  const int X = cc.x, Y = cc.y, Z = cc.z;
   const long long s = site_index(P, X, Y, Z);
-  // j' first: pulled from the populations, its 18 loads are in flight with those of the stencil
-  const float3 j = jp ? make_float3(__ldg(jp + s), __ldg(jp + P.N + s), __ldg(jp + 2 * P.N + s))
-                      : jprime_at<TS>(P, fin, X, Y, Z);
+  float3 j;
+  if (jc) {
+    const float4 v = __ldg(jc + k);
+    j = make_float3(v.x, v.y, v.z);
+  } else {
+    j = make_float3(__ldg(jp + s), __ldg(jp + P.N + s), __ldg(jp + 2 * P.N + s));
+  }
   const NodeState n = node_state(P, rho, X, Y, Z);
   float3 fA = make_float3(-P.gAB * n.rA * n.SB.x, -P.gAB * n.rA * n.SB.y, -P.gAB * n.rA * n.SB.z);
   float3 fB = make_float3(-P.gBA * n.rB * n.SA.x, -P.gBA * n.rB * n.SA.y, -P.gBA * n.rB * n.SA.z);
@@ -845,17 +853,16 @@ __device__ __forceinline__ void couple_finish(const StepParams &P, unsigned long
 // solvation force enters the coupling velocity (the same arrays, except in the later particle
 // substeps, which keep the list of the step's start).  with_fsr: compute the reaction of the
 // particle's own fluid-side solvation force (else keep the value in pf.fsr).
-template <class T = float>
 __device__ __forceinline__ void couple8(const StepParams &P, unsigned long long step, int p, int k, unsigned mask,
                                         const ParticleArrays &self, const ParticleArrays &list, CellIndex ci,
                                         const float *__restrict__ rho, const float *__restrict__ jp,
                                         const ParticleForces &pf, bool with_fsr = true,
-                                        const T *__restrict__ fin = nullptr) {
+                                        const float4 *__restrict__ jc = nullptr) {
   const int4 c = self.cell[p];
   const float4 fr = self.frac[p];
   const TypeParams &Ty = P.types[c.w];
   CoupleSums S{};
-  couple_corner<T>(P, k, c, fr, Ty, list, ci, rho, jp, pf, with_fsr, S, fin);
+  couple_corner(P, k, c, fr, Ty, list, ci, rho, jp, pf, with_fsr, S, jc ? jc + (long long)self.pid[p] * 8 : nullptr);
   float *x = &S.up.x;  // the 12 sums, contiguous
 #pragma unroll
   for (int off = 4; off > 0; off >>= 1)

@@ -44,6 +44,9 @@ struct lbmd_ctx {
   // beside what follows it on st; sort_pending: st has not waited for it yet
   cudaEvent_t ev_collided = nullptr;
   bool sort_pending = false;
+  // one pass with particles: ev_integrated (the particle update done, on side) orders the boundary
+  // kernel, which forms the next step's corner j' (jc) at the updated positions, after it
+  cudaEvent_t ev_integrated = nullptr;
   int dev = 0;
   StepParams P{};
   unsigned char *pop[2] = {nullptr, nullptr};  // population buffers, element type P.storage
@@ -56,6 +59,10 @@ struct lbmd_ctx {
   float *rho_buf[2] = {nullptr, nullptr};
   bool rho_valid = false;
   float *jp = nullptr;   // [3][N]
+  // [cap][8] j' at the corners of each particle's cell (by particle id), for the coupling of the
+  // one-pass update; jc_valid: formed from the current populations and positions
+  float4 *jc = nullptr;
+  bool jc_valid = false;
   // the lattice update: 0 = chosen by the lattice size, 1 = one pass (densities of the next step
   // formed by the update), 2 = two passes (density pass, then the update)
   int passes = 0;
@@ -63,8 +70,8 @@ struct lbmd_ctx {
   int op_grid = 0;
   BoundaryRun *op_runs = nullptr;
   int op_nruns = 0;
-  float *op_edge = nullptr, *op_yedge = nullptr, *op_diag = nullptr;  // partial sums (OnePassOut)
-  unsigned char *op_inner = nullptr;  // [nz]: plane neither first nor last of its chunk
+  OnePassOut op_out{};     // partial sums (all buffers owned by the context)
+  int *op_zslot = nullptr;  // [nz]: -1, or the chunk-edge plane's slot in op_out's z arrays
   // particles
   int np = 0, cap = 0;
   ParticleArrays pa[2]{};
@@ -217,7 +224,8 @@ void free_particles(lbmd_ctx *c) {
     dfree(c->pa[b].pid);
   }
   dfree(c->pf.fric); dfree(c->pf.psA); dfree(c->pf.psB); dfree(c->pf.fsr); dfree(c->pf.pair); dfree(c->pf.total);
-  dfree(c->slot_of_id); dfree(c->row_of); dfree(c->perm);
+  dfree(c->slot_of_id); dfree(c->row_of); dfree(c->perm); dfree(c->jc);
+  c->jc_valid = false;
   c->cap = 0;
 }
 
@@ -253,6 +261,20 @@ bool uses_onepass(const lbmd_ctx *c) {
   return c->op_grid > 0;  // auto: prepare_onepass decided from the size
 }
 
+// Frees what prepare_onepass set up.
+void free_onepass(lbmd_ctx *c) {
+  dfree(c->op_runs);
+  dfree(c->op_out.edge);
+  dfree(c->op_out.yedge);
+  dfree(c->op_out.diag);
+  dfree(c->op_out.zown);
+  dfree(c->op_out.zedge);
+  dfree(c->op_out.zyedge);
+  dfree(c->op_zslot);
+  c->op_nruns = 0;
+  c->op_grid = 0;
+}
+
 // Sets up the one-pass update (persistent grid, boundary runs) once per context; in the automatic
 // mode only for lattices large enough.  Allocates: call it before any capture.
 int prepare_onepass(lbmd_ctx *c) {
@@ -277,9 +299,11 @@ int prepare_onepass(lbmd_ctx *c) {
       if (ze <= zs) continue;
       edge[(size_t)col * P.nz + zs] = edge[(size_t)col * P.nz + ze - 1] = 1;
     }
-  // edge rows from partial sums when every tile has at least 3 rows and 2 columns
+  // edge rows from partial sums when every tile has at least 3 rows and 2 columns; chunk-edge
+  // planes when the lattice is at least 2 planes deep
   const int ry = P.ny % kOnePassRows, rx = P.nx % kOnePassCols;
   const int ypart = (P.ny >= 3 && (ry == 0 || ry >= 3) && P.nx >= 2 && (rx == 0 || rx >= 2)) ? 1 : 0;
+  const int zpart = P.nz >= 2 ? 1 : 0;
   std::vector<BoundaryRun> runs;
   for (int col = 0; col < ntx * nty; ++col) {
     const int tx = col % ntx, ty = col / ntx;
@@ -287,28 +311,35 @@ int prepare_onepass(lbmd_ctx *c) {
     const int y0 = ty * kOnePassRows, rows = std::min(kOnePassRows, P.ny - y0);
     for (int z = 0; z < P.nz; ++z)
       for (int w = 0; w < rows; ++w)
-        if (edge[(size_t)col * P.nz + z] || (!ypart && (w == 0 || w == rows - 1)))
+        if ((!zpart && edge[(size_t)col * P.nz + z]) || (!ypart && (w == 0 || w == rows - 1)))
           runs.push_back(BoundaryRun{z * P.ny + y0 + w, x0, nown});
   }
   if (runs.size() > 0x7fffffffull) return fail(c, LBMD_E_INVALID_ARG, "too many boundary runs");
-  CK(dalloc(&c->op_edge, (size_t)P.nz * P.ny * ntx * 4), "edge sums");
+  CK(dalloc(&c->op_out.edge, (size_t)P.nz * P.ny * ntx * 4), "edge sums");
   {
-    std::vector<unsigned char> inner((size_t)P.nz, 0);
+    // slot 2 b (plane zs - 1) and 2 b + 1 (plane zs) of the boundary below chunk b
+    std::vector<int> zslot((size_t)P.nz, -1);
     for (int ch = 0; ch < nchunks; ++ch) {
-      const int zs = (int)((long long)ch * P.nz / nchunks), ze = (int)((long long)(ch + 1) * P.nz / nchunks);
-      for (int z = zs + 1; z <= ze - 2; ++z) inner[z] = 1;
+      const int zs = (int)((long long)ch * P.nz / nchunks);
+      zslot[(size_t)(zs == 0 ? P.nz - 1 : zs - 1)] = 2 * ch;
+      zslot[(size_t)zs] = 2 * ch + 1;
     }
-    CK(dalloc(&c->op_inner, inner.size()), "plane table");
-    CK(cudaMemcpy(c->op_inner, inner.data(), inner.size(), cudaMemcpyHostToDevice), "plane table");
+    CK(dalloc(&c->op_zslot, zslot.size()), "plane table");
+    CK(cudaMemcpy(c->op_zslot, zslot.data(), sizeof(int) * zslot.size(), cudaMemcpyHostToDevice), "plane table");
   }
   if (ypart) {
-    CK(dalloc(&c->op_yedge, (size_t)2 * P.nz * nty * ntx * kOnePassCols * 2), "edge sums");
-    CK(dalloc(&c->op_diag, (size_t)P.nz * nty * ntx * 4 * 2), "edge sums");
+    CK(dalloc(&c->op_out.yedge, (size_t)2 * P.nz * nty * ntx * kOnePassCols * 2), "edge sums");
+    CK(dalloc(&c->op_out.diag, (size_t)P.nz * nty * ntx * 4 * 2), "edge sums");
+  }
+  if (zpart) {
+    CK(dalloc(&c->op_out.zown, (size_t)2 * nchunks * P.ny * P.nx * 2), "chunk-edge sums");
+    CK(dalloc(&c->op_out.zedge, (size_t)2 * nchunks * P.ny * ntx * 4), "chunk-edge sums");
+    if (ypart) CK(dalloc(&c->op_out.zyedge, (size_t)2 * 2 * nchunks * nty * ntx * kOnePassCols * 2), "chunk-edge sums");
   }
   CK(dalloc(&c->op_runs, runs.size()), "boundary runs");
   CK(cudaMemcpy(c->op_runs, runs.data(), sizeof(BoundaryRun) * runs.size(), cudaMemcpyHostToDevice), "boundary runs");
   c->op_nruns = (int)runs.size();
-  c->op_geom = OnePassGeom{ntx, nty, nchunks, ypart};
+  c->op_geom = OnePassGeom{ntx, nty, nchunks, ypart, zpart};
   c->op_grid = grid;
   return LBMD_OK;
 }
@@ -319,6 +350,20 @@ int ensure_densities(lbmd_ctx *c) {
   launch_moments(c->P, c->pop[c->cur], c->rest, c->rho_buf[c->cur], nullptr, c->st);
   const int r = launched(c, "moments");
   if (!r) c->rho_valid = true;
+  return r;
+}
+
+// One pass with particles (one particle update per step): the corner j' of the current state
+// into jc, if not there already.
+int ensure_corner_j(lbmd_ctx *c) {
+  if (c->jc_valid || c->np == 0 || c->P.substeps > 1 || !uses_onepass(c)) return LBMD_OK;
+  if (c->sort_pending) {  // the arrays read here are the ones the pending sort writes
+    CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
+    c->sort_pending = false;
+  }
+  launch_corner_jprime(c->P, c->pa[c->pcur], c->np, c->pop[c->cur], c->jc, c->st);
+  const int r = launched(c, "corner j'");
+  if (!r) c->jc_valid = true;
   return r;
 }
 
@@ -478,9 +523,10 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
   if (sub) {
     if ((r = substep_particles(c, gpa, gpf, gci))) return r;
   } else if (P.np > 0) {
-    if (onepass)  // no density pass stored j': the coupling pulls it at its corners
-      launch_couple_pull(P, c->pa[c->pcur], ci, rho, fin, c->pf, c->st);
-    else
+    if (onepass) {  // no density pass stored j': the previous step's boundary kernel formed it at the corners
+      if (!c->jc_valid) return fail(c, LBMD_E_STATE, "one-pass coupling without the corner j' of the current state");
+      launch_couple_jc(P, c->pa[c->pcur], ci, rho, c->jc, c->pf, c->st);
+    } else
       launch_couple(P, c->pa[c->pcur], ci, rho, c->jp, c->pf, c->st);
     CK(cudaEventRecord(c->ev_coupled, c->st), "event");
     launch_pairs(P, c->pa[c->pcur], ci, c->nbonds ? c->bond_start : nullptr, c->bond_other, c->slot_of_id, c->pf,
@@ -488,20 +534,24 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
     CK(cudaStreamWaitEvent(c->side, c->ev_coupled, 0), "stream wait");
     launch_integrate(P, c->pa[c->pcur], c->pa[1 - c->pcur], c->pf, c->err, c->side);
     if ((r = launched(c, "particle forces and update", 3))) return r;
+    if (onepass) CK(cudaEventRecord(c->ev_integrated, c->side), "event");
   }
   if (t0) CK(cudaEventRecordWithFlags(t0, c->st, flags), "event");
   if (onepass)
     launch_collide_onepass(P, fin, fout, c->rest, rho, c->rho_buf[1 - c->cur],
-                           OnePassOut{c->op_edge, c->op_yedge, c->op_diag}, gpa, gpf, gci, c->err, c->op_geom,
+                           c->op_out, gpa, gpf, gci, c->err, c->op_geom,
                            c->op_grid, c->st);
   else
     launch_collide(P, fin, fout, c->rest, rho, gpa, gpf, gci, c->err, c->st);
   if ((r = launched(c, "collide"))) return r;
   if (t1) CK(cudaEventRecordWithFlags(t1, c->st, flags), "event");
   if (P.np > 0) CK(cudaEventRecord(c->ev_collided, c->st), "event");
+  const bool corner_j = onepass && P.np > 0 && !sub;  // the boundary kernel forms the next step's jc
   if (onepass) {
+    if (corner_j) CK(cudaStreamWaitEvent(c->st, c->ev_integrated, 0), "stream wait");
     launch_boundary_densities(P, c->op_geom, fout, c->rest, c->rho_buf[1 - c->cur], c->op_runs, c->op_nruns,
-                              OnePassOut{c->op_edge, c->op_yedge, c->op_diag}, c->op_inner, c->st);
+                              c->op_out, c->op_zslot, c->pa[1 - c->pcur], corner_j ? P.np : 0,
+                              corner_j ? c->jc : nullptr, c->st);
     if ((r = launched(c, "boundary densities"))) return r;
   }
   if (P.np > 0) {
@@ -520,6 +570,7 @@ int one_step(lbmd_ctx *c, unsigned long long step, cudaEvent_t t0, cudaEvent_t t
   c->cur = 1 - c->cur;
   c->steps++;
   c->rho_valid = onepass;  // the two-pass update leaves the new state's densities to its next step
+  c->jc_valid = corner_j;
   return LBMD_OK;
 }
 
@@ -547,7 +598,7 @@ int record_steps(lbmd_ctx *c, StepGraph &g) {
     for (cudaEvent_t &e : c->ph)
       if (!e) CK(cudaEventCreate(&e), "event");
   const int cur0 = c->cur, pcur0 = c->pcur;
-  const bool rho_valid0 = c->rho_valid, sort_pending0 = c->sort_pending;
+  const bool rho_valid0 = c->rho_valid, sort_pending0 = c->sort_pending, jc_valid0 = c->jc_valid;
   const int64_t steps0 = c->steps, launches0 = c->launches;
   cudaStream_t user = c->st;
   CK(cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -570,6 +621,7 @@ int record_steps(lbmd_ctx *c, StepGraph &g) {
   c->pcur = pcur0;
   c->rho_valid = rho_valid0;
   c->sort_pending = sort_pending0;
+  c->jc_valid = jc_valid0;
   c->steps = steps0;
   g.launches = c->launches - launches0;
   c->launches = launches0;
@@ -627,7 +679,8 @@ int replay_steps(lbmd_ctx *c) {
   StepGraph &g = c->graph[c->cur][c->pcur];
   int r;
   if ((r = prepare_onepass(c))) return r;
-  if (uses_onepass(c) && (r = ensure_densities(c))) return r;  // before recording: not in the graph
+  if (uses_onepass(c) && ((r = ensure_densities(c)) || (r = ensure_corner_j(c))))
+    return r;  // before recording: not in the graph
   if (!g.exec && (r = record_steps(c, g))) return r;
   if (c->dev_step != c->steps) {  // steps were taken without the graph since it last ran
     launch_set_step(c->step_base, (unsigned long long)c->steps, c->st);
@@ -646,6 +699,7 @@ int replay_steps(lbmd_ctx *c) {
   c->steps += kGraphSteps;
   c->dev_step = c->steps;
   c->rho_valid = uses_onepass(c);
+  c->jc_valid = c->rho_valid && c->np > 0 && c->P.substeps == 1;
   return LBMD_OK;
 }
 
@@ -691,7 +745,8 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
       (e = cudaEventCreateWithFlags(&c->ev_sorted, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_pairs, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_coupled, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&c->ev_collided, cudaEventDisableTiming)) != cudaSuccess) {
+      (e = cudaEventCreateWithFlags(&c->ev_collided, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_integrated, cudaEventDisableTiming)) != cudaSuccess) {
     cudaGetLastError();
     lbmd_destroy(c);
     return fail(nullptr, LBMD_E_CUDA, std::string("stream / event creation: ") + cudaGetErrorString(e));
@@ -723,13 +778,15 @@ void lbmd_destroy(lbmd_ctx *c) {
   if (c->ev_pairs) cudaEventDestroy(c->ev_pairs);
   if (c->ev_coupled) cudaEventDestroy(c->ev_coupled);
   if (c->ev_collided) cudaEventDestroy(c->ev_collided);
+  if (c->ev_integrated) cudaEventDestroy(c->ev_integrated);
   drop_graphs(c);
   if (c->gst) cudaStreamDestroy(c->gst);
   for (cudaEvent_t e : c->ph)
     if (e) cudaEventDestroy(e);
   dfree(c->step_base);
   dfree(c->pop[0]); dfree(c->pop[1]); dfree(c->rho_buf[0]); dfree(c->rho_buf[1]); dfree(c->jp); dfree(c->err);
-  dfree(c->rest); dfree(c->op_runs); dfree(c->op_edge); dfree(c->op_yedge); dfree(c->op_diag); dfree(c->op_inner);
+  dfree(c->rest);
+  free_onepass(c);
   dfree(c->diag_partial); dfree(c->diag_out); dfree(c->drift);
   free_particles(c);
   free_records(c);
@@ -783,6 +840,7 @@ int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const flo
   if (r) return r;
   c->steps = 0;
   c->rho_valid = false;
+  c->jc_valid = false;
   if ((r = ensure_densities(c))) return r;
   if ((r = enqueue_drift(c, 1))) return r;  // the drift check's reference
   CK(cudaStreamSynchronize(c->st), "sync");
@@ -800,6 +858,7 @@ int lbmd_set_populations(lbmd_ctx *c, int comp, const float *f) {
   int r = launched(c, "restream");
   if (r) return r;
   c->rho_valid = false;
+  c->jc_valid = false;
   if ((r = ensure_densities(c))) return r;
   CK(cudaStreamSynchronize(c->st), "sync");
   c->fluid_ready = true;
@@ -851,6 +910,7 @@ int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, con
     if (e == cudaSuccess) e = dalloc(&c->slot_of_id, n);
     if (e == cudaSuccess) e = dalloc(&c->row_of, n);
     if (e == cudaSuccess) e = dalloc(&c->perm, n);
+    if (e == cudaSuccess) e = dalloc(&c->jc, (size_t)n * 8);
     if (e == cudaSuccess && !c->row_count) e = dalloc(&c->row_count, (size_t)P.nrows + 1);
     if (e == cudaSuccess && !c->row_start) e = dalloc(&c->row_start, (size_t)P.nrows + 1);
     if (e == cudaSuccess && !c->row_cursor) e = dalloc(&c->row_cursor, (size_t)P.nrows + 1);
@@ -873,6 +933,7 @@ int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, con
   c->np = n;
   P.np = n;
   c->pcur = 0;
+  c->jc_valid = false;
   if (n > 0) {
     CK(cudaMemcpyAsync(c->pa[0].cell, hc.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, c->st), "upload");
     CK(cudaMemcpyAsync(c->pa[0].frac, hf.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, c->st), "upload");
@@ -954,7 +1015,7 @@ int lbmd_step(lbmd_ctx *c, int nsteps) {
         }
     if (s < n) {
       if ((r = prepare_onepass(c))) return r;
-      if (uses_onepass(c) && (r = ensure_densities(c))) return r;
+      if (uses_onepass(c) && ((r = ensure_densities(c)) || (r = ensure_corner_j(c)))) return r;
     }
     for (; s < n; ++s) {
       cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -987,13 +1048,8 @@ int lbmd_set_lattice_passes(lbmd_ctx *c, int passes) {
   cudaSetDevice(c->dev);
   drop_graphs(c);
   if (passes != c->passes) {
-    dfree(c->op_runs);  // set up again for the new choice at the next step
-    dfree(c->op_edge);
-    dfree(c->op_yedge);
-    dfree(c->op_diag);
-    dfree(c->op_inner);
-    c->op_nruns = 0;
-    c->op_grid = 0;
+    free_onepass(c);  // set up again for the new choice at the next step
+    c->jc_valid = false;
   }
   c->passes = passes;
   return LBMD_OK;

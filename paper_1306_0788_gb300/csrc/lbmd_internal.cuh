@@ -119,23 +119,33 @@ struct CellIndex {
 
 // The one-pass lattice update: a block's warps own 8 consecutive rows (y) of a column tile of 32
 // x nodes (one per lane) and the block marches along z through one chunk of planes of that tile;
-// the blocks of a chunk cover neighbouring tiles and run together.  Nodes of the first and last
-// row of a tile and of the first and last plane of a chunk are finished by a second kernel from a
-// list of (row, x0, count) runs; the two nodes at the x edges of a tile row get the values
-// arriving from the neighbouring tile through edge partial sums added by a third.
+// the blocks of a chunk cover neighbouring tiles and run together.  A node whose sources lie in
+// other blocks gets its density from partial sums: each block writes what it holds for the node,
+// and a second kernel adds the parts.  Where a lattice is too thin for that (edge rows of tiles
+// with fewer than 3 rows or 2 columns; the planes of a lattice one plane deep) the second kernel
+// pulls the node's populations instead, from a list of (row, x0, count) runs.
 constexpr int kOnePassRows = 8;
 constexpr int kOnePassCols = 32;
 struct OnePassGeom {
   int ntx, nty;  // column tiles along x (kOnePassCols columns each) and y (kOnePassRows rows)
   int nchunks;   // z-chunks per tile: block b takes chunk b / (ntx nty) of tile b % (ntx nty)
   int ypart;     // every tile has >= 3 rows and >= 2 columns: the edge rows are finished from
-                 // partial sums (else their densities are pulled like the chunk edge planes)
+                 // partial sums (else their densities are pulled)
+  int zpart;     // nz >= 2: the first and last plane of each chunk are finished from partial sums
+                 // (else pulled)
 };
-// Partial sums the update writes for nodes whose sources lie in other blocks.
+// Partial sums the update writes for nodes whose sources lie in other blocks.  A chunk-edge plane
+// (the plane zs - 1 or zs at the boundary between the chunk below and the chunk starting at zs)
+// gets its sources from two chunks: the upper chunk's part goes where an inner plane's does
+// (rho_next, edge, yedge at the plane's index), the lower chunk's into the z arrays, at the slot
+// 2 b + (0 for zs - 1, 1 for zs) of the boundary b = the upper chunk's index.
 struct OnePassOut {
   float *edge;   // [nz][ny][ntx][2] float2: what leaves a tile row along x (side 0: -x, 1: +x)
   float *yedge;  // [2][nz][nty][ntx * 32] float2: what leaves a tile across its bottom (0) / top (1) row
   float *diag;   // [nz][nty][ntx][4] float2: the one value leaving each corner diagonally
+  float *zown;   // [2 nchunks][ny][nx] float2: the lower chunk's sums at its own nodes
+  float *zedge;  // [2 nchunks][ny][ntx][2] float2: its edge sums
+  float *zyedge; // [2][2 nchunks][nty][ntx * 32] float2: its y-edge sums
 };
 struct BoundaryRun {
   int row;   // z * ny + y
@@ -242,17 +252,20 @@ void launch_moments(const StepParams &P, const void *store, const float *rest, f
 void launch_collide(const StepParams &P, const void *fin, void *fout, float *rest, const float *rho,
                     const ParticleArrays &pa, const ParticleForces &pf, CellIndex ci, unsigned *err,
                     cudaStream_t st);
-// One-pass update (BGK, md_substeps = 1): writes the populations of the next step and the
-// densities rho_next of the nodes inside each block's stretch; launch_boundary_densities then
-// computes the densities of the listed boundary runs from the new populations.
+// One-pass update (BGK, md_substeps = 1): writes the populations of the next step, the densities
+// rho_next of the nodes whose sources are all in one block, and the partial sums of `out` for the
+// others; launch_boundary_densities then finishes those.
 void launch_collide_onepass(const StepParams &P, const void *fin, void *fout, float *rest, const float *rho,
                             float *rho_next, OnePassOut out, const ParticleArrays &pa, const ParticleForces &pf,
                             CellIndex ci, unsigned *err, OnePassGeom G, int grid, cudaStream_t st);
-// Also adds the partial sums of `out` to the tile-edge nodes of the inner planes, in the same launch.
-// inner_plane[z] != 0: z is neither the first nor the last plane of its chunk.
+// Adds the partial sums of `out` where they belong and pulls the densities of the listed boundary
+// runs from the new populations, in one launch.  zslot[z]: -1 where z is neither the first nor the
+// last plane of its chunk, else its slot in the z arrays of `out`.  With jc (not NULL), the same
+// launch also forms j' of the new populations at the 8 corners of the cells of the np particles
+// pn, into jc[pid * 8 + corner] (what launch_couple_jc reads).
 void launch_boundary_densities(const StepParams &P, OnePassGeom G, const void *store, const float *rest,
                                float *rho_next, const BoundaryRun *runs, int nruns, OnePassOut out,
-                               const unsigned char *inner_plane, cudaStream_t st);
+                               const int *zslot, const ParticleArrays &pn, int np, float4 *jc, cudaStream_t st);
 // Blocks of the one-pass update resident on one SM (its persistent grid is this times the SMs).
 int onepass_blocks_per_sm();
 void launch_fields(const StepParams &P, const void *store, const float *rest, const float *rho, float *rhoA,
@@ -295,9 +308,14 @@ void launch_permute(int np, const int *perm, const ParticleArrays &src, const Pa
                     int *slot_of_id, cudaStream_t st);
 void launch_couple(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho,
                    const float *jp, const ParticleForces &pf, cudaStream_t st);
-// The same with j' pulled from the populations `store` (element type P.storage) at the corners.
-void launch_couple_pull(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho,
-                        const void *store, const ParticleForces &pf, cudaStream_t st);
+// The same with j' at the corners from jc (8 float4 per particle id, launch_corner_jprime or the
+// one-pass update's boundary kernel).
+void launch_couple_jc(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const float *rho,
+                      const float4 *jc, const ParticleForces &pf, cudaStream_t st);
+// j' of the populations `store` (element type P.storage) at the 8 corners of the cells of the np
+// particles pa, into jc[pid * 8 + corner].
+void launch_corner_jprime(const StepParams &P, const ParticleArrays &pa, int np, const void *store, float4 *jc,
+                          cudaStream_t st);
 void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, const int *bond_start,
                   const int *bond_other, const int *slot_of_id, const ParticleForces &pf, unsigned *err,
                   cudaStream_t st);

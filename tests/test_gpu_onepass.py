@@ -26,9 +26,11 @@ POS_TOL = 1e-4
 
 # tiles of 32 x 8 columns: ragged along x and y, narrower than a tile, one-column tiles (33), tiles
 # of 1 or 2 rows (edge rows pulled) and of >= 3 rows and >= 2 columns (edge rows from partial sums:
-# (2, 3, 5), (64, 20, 24), (40, 11, 18), (34, 24, 20), (64, 16, 40))
+# (2, 3, 5), (64, 20, 24), (40, 11, 18), (34, 24, 20), (64, 16, 40), (40, 16, 3)); one z-chunk, two
+# (24, 30) and three (40); chunk-edge planes from partial sums (nz >= 2: the two planes of nz = 2
+# are both chunk-edge planes, each with parts from both ends of the one chunk) or pulled (nz = 1)
 SIZES = [(20, 18, 16), (31, 9, 13), (33, 17, 12), (1, 16, 12), (2, 3, 5), (64, 20, 24), (7, 25, 30), (40, 11, 18),
-         (34, 24, 20), (64, 16, 40)]
+         (34, 24, 20), (64, 16, 40), (20, 9, 2), (33, 11, 1), (40, 16, 3)]
 
 
 def L():
