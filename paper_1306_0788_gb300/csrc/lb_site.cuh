@@ -538,16 +538,23 @@ __device__ __forceinline__ void collide_core_at(const StepParams &P, const Coord
     }
   }
   // The two components go through the same arithmetic: it runs on (A, B) pairs with the
-  // packed two-lane FP32 instructions.
-  float2 r2s = make_float2(0.f, 0.f);
-  float jx = 0.f, jy = 0.f, jz = 0.f;
+  // packed two-lane FP32 instructions.  Directions come in opposite pairs (2p + 1, 2p + 2): the
+  // densities sum the pair sums, the momenta the pair differences (c_{2p+2} = -c_{2p+1}).
+  float2 r2s = make_float2(fA[0], fB[0]);
+  float2 jx2 = make_float2(0.f, 0.f), jy2 = jx2, jz2 = jx2;
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    r2s = __fadd2_rn(r2s, make_float2(fA[i], fB[i]));
-    jx += kCx[i] * (fA[i] + fB[i]);
-    jy += kCy[i] * (fA[i] + fB[i]);
-    jz += kCz[i] * (fA[i] + fB[i]);
+  for (int i = 1; i < kQ; i += 2) {
+    const float2 a = make_float2(fA[i], fB[i]), b = make_float2(fA[i + 1], fB[i + 1]);
+    r2s = __fadd2_rn(r2s, __fadd2_rn(a, b));
+    const float2 d = __fadd2_rn(a, make_float2(-b.x, -b.y));
+    if (kCx[i] > 0) jx2 = __fadd2_rn(jx2, d);
+    if (kCx[i] < 0) jx2 = __fadd2_rn(jx2, make_float2(-d.x, -d.y));
+    if (kCy[i] > 0) jy2 = __fadd2_rn(jy2, d);
+    if (kCy[i] < 0) jy2 = __fadd2_rn(jy2, make_float2(-d.x, -d.y));
+    if (kCz[i] > 0) jz2 = __fadd2_rn(jz2, d);
+    if (kCz[i] < 0) jz2 = __fadd2_rn(jz2, make_float2(-d.x, -d.y));
   }
+  const float jx = jx2.x + jx2.y, jy = jy2.x + jy2.y, jz = jz2.x + jz2.y;
   if (kShifted) r2s = __fadd2_rn(r2s, make_float2(shift_sum(P, 0), shift_sum(P, 1)));
   const float rA = r2s.x, rB = r2s.y;
   // S_z = sum_i w_i rho_z(r + c_i) c_i from the density field of this step, as (S_A, S_B) pairs,
@@ -661,7 +668,7 @@ __device__ __forceinline__ void store_node(const StepParams &P, unsigned s32, T 
   const unsigned N32 = (unsigned)P.N;
   constexpr bool kShifted = kSplitRest<T> && !kMRT;
   if constexpr (kSplitRest<T>) {
-    unsigned *wout = reinterpret_cast<unsigned *>(fout);
+    unsigned *wout = reinterpret_cast<unsigned *>(fout) + s32;  // direction i at wout[i N]
     if (kShifted) {
       // store the 18 shifted (A, B) pairs; the rest population takes what keeps the node's mass
       // at its value before the update (the BGK update and the forcing term conserve it exactly)
@@ -669,7 +676,7 @@ __device__ __forceinline__ void store_node(const StepParams &P, unsigned s32, T 
 #pragma unroll
       for (int i = 1; i < kQ; ++i) {
         const unsigned w = Pair16<T>::enc(make_float2(fA[i], fB[i]));
-        if (kWrite && write) wout[i * N32 + s32] = w;
+        if (kWrite && write) wout[(size_t)i * N32] = w;
         const float2 d = Pair16<T>::dec(w);
         m = __ffma2_rn(make_float2(-1.f, -1.f), d, m);
         if (kKeep) {
@@ -694,7 +701,7 @@ __device__ __forceinline__ void store_node(const StepParams &P, unsigned s32, T 
       for (int i = 1; i < kQ; ++i) {
         const float2 v = make_float2(fA[i] - pop_shift(P, 0, i), fB[i] - pop_shift(P, 1, i));
         const unsigned w = Pair16<T>::enc(v);
-        if (kWrite) wout[i * N32 + s32] = w;
+        if (kWrite) wout[(size_t)i * N32] = w;
         e = __fadd2_rn(e, __ffma2_rn(make_float2(-1.f, -1.f), Pair16<T>::dec(w), v));
       }
       if (kWrite && rest_out) {
@@ -703,10 +710,10 @@ __device__ __forceinline__ void store_node(const StepParams &P, unsigned s32, T 
       }
     }
   } else if (kWrite) {
-    float2 *fout2 = reinterpret_cast<float2 *>(fout);
+    float2 *fout2 = reinterpret_cast<float2 *>(fout) + s32;  // direction i at fout2[i N]
     if (write)
 #pragma unroll
-      for (int i = 0; i < kQ; ++i) fout2[i * N32 + s32] = make_float2(fA[i], fB[i]);
+      for (int i = 0; i < kQ; ++i) fout2[(size_t)i * N32] = make_float2(fA[i], fB[i]);
   }
 }
 
