@@ -278,7 +278,8 @@ void free_onepass(lbmd_ctx *c) {
 // Sets up the one-pass update (persistent grid, boundary runs) once per context; in the automatic
 // mode only for lattices large enough.  Allocates: call it before any capture.
 int prepare_onepass(lbmd_ctx *c) {
-  if (!onepass_allowed(c) || c->passes == 2 || c->op_runs) return LBMD_OK;
+  // set up already (op_grid; the run list may be empty: every node finished from partial sums)
+  if (!onepass_allowed(c) || c->passes == 2 || c->op_grid > 0) return LBMD_OK;
   const StepParams &P = c->P;
   const long long U = onepass_units(P);
   const int full = onepass_full_grid(c);
@@ -287,6 +288,7 @@ int prepare_onepass(lbmd_ctx *c) {
   // pass over half the bytes)
   if (c->passes == 0 && (P.storage != LBMD_STORAGE_FP32 || U < (long long)kOnePassAutoPlanes * full))
     return LBMD_OK;  // two passes
+  free_onepass(c);  // what an earlier attempt that failed part-way left
   const int ntx = (P.nx + kOnePassCols - 1) / kOnePassCols, nty = (P.ny + kOnePassRows - 1) / kOnePassRows;
   // chunks of about kOnePassChunkPlanes planes, one block each, neighbouring column tiles of a
   // chunk launched together (they march in step, so the sectors they share meet in L2)

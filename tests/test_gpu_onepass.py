@@ -129,6 +129,27 @@ def test_one_and_two_passes_agree_and_graphs_replay_bit_for_bit():
     assert np.abs(out["one"][1] - out["two"][1]).max() <= 1e-5
 
 
+def test_setup_allocates_once():
+    """The one-pass update's buffers (partial sums, plane table, run list -- empty on this lattice,
+    whose every node is finished from partial sums) are set up once per context: many steps, as
+    graph replays and as single launches, leave the device's free memory where the first step
+    left it."""
+    import torch
+    c = _coupled((128, 64, 48), 40, 7, 0.0)
+    ctx = make_gpu(c, passes=1)
+    try:
+        L().lbmd_step(ctx, 3)  # set-up, graphs recorded, one single launch
+        L().lbmd_sync(ctx)
+        free0, _ = torch.cuda.mem_get_info()
+        for _ in range(40):
+            L().lbmd_step(ctx, 3)
+        L().lbmd_sync(ctx)
+        free1, _ = torch.cuda.mem_get_info()
+        assert free0 - free1 < 4 << 20, (free0, free1)
+    finally:
+        L().lbmd_destroy(ctx)
+
+
 def test_mode_choice_and_limits():
     """Small lattices take two passes by default; the one-pass update refuses the fluctuating
     MRT collision and MD sub-stepping."""
