@@ -83,6 +83,37 @@ def test_coupled_10_steps_populations_forces():
     assert np.abs(Fg - Fo).max() <= 1e-4 * max(np.abs(Fo).max(), 1e-3)
 
 
+def test_coupled_across_chunks_and_tile_edges():
+    """Three z-chunks (nz = 40), edge rows and chunk-edge planes from partial sums, and 80
+    particles: the corner j' of the coupling and the momentum return land on tile edges, chunk-edge
+    planes and their corners; 20 coupled steps against the oracle."""
+    c = _coupled((40, 16, 40), 80, 31, 0.002)
+    fg, xg, _, _ = run_gpu(c, 20, passes=1)
+    fo, xo, _, _ = run_oracle(c, 20)
+    assert pop_error(fg, fo) <= POP_TOL
+    assert position_error(xg, xo, c.x, c.dims) <= POS_TOL
+
+
+def test_switching_the_lattice_form_mid_run():
+    """One pass, then two, then one again on the same context (each switch drops the graphs and the
+    one-pass buffers; the densities and corner j' are formed again where needed): the run equals
+    the oracle's within the 10-step tolerance after 12 steps."""
+    c = _coupled((34, 24, 20), 40, 33, 0.002)
+    ctx = make_gpu(c, passes=1)
+    try:
+        for passes, n in ((1, 4), (2, 4), (1, 4)):
+            L().lbmd_set_lattice_passes(ctx, passes)
+            L().lbmd_step(ctx, n)
+        L().lbmd_sync(ctx)
+        fg = np.stack([L().lbmd_get_populations(ctx, 0, c.shape), L().lbmd_get_populations(ctx, 1, c.shape)])
+        xg, _, _ = L().lbmd_get_particles(ctx, c.n)
+    finally:
+        L().lbmd_destroy(ctx)
+    fo, xo, _, _ = run_oracle(c, 12)
+    assert pop_error(fg, fo) <= POP_TOL
+    assert position_error(xg, xo, c.x, c.dims) <= POS_TOL
+
+
 @pytest.mark.parametrize("kT", [0.0, 0.002])
 def test_particles_100_steps(kT):
     c = _coupled((20, 18, 16), 30, 21, kT)
