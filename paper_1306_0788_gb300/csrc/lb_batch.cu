@@ -385,6 +385,14 @@ __device__ __forceinline__ bool drift_due(const RepDev &R, const RepState &S) {
 template <class T>
 __global__ void __launch_bounds__(kBThreads) kb_drift_sums(const BatchDev *__restrict__ B) {
   __shared__ double sh[5][kBThreads];
+  // most steps have no replica due: one look at all replicas in parallel, instead of a chain of
+  // dependent loads per tile
+  bool any = false;
+  for (int r = threadIdx.x; r < B->nrep; r += blockDim.x) {
+    const int slot = B->rep_slot[r];
+    any = any || drift_due(B->rep[slot], B->state[slot]);
+  }
+  if (!__syncthreads_or(any)) return;
   const int ts = B->tile_sites;
   for (int t = blockIdx.x; t < B->ntiles; t += gridDim.x) {
     const int slot = B->tile_slot[t];
