@@ -214,10 +214,12 @@ int lbmd_set_graphs(lbmd_ctx *ctx, int on);
  * populations and stores the densities, then the update pulls them again.  passes = 1: the
  * update of step t also forms the densities of step t + 1 from the values it has just computed
  * (streaming carries f*_i(r) to r + c_i, so the density of a node is the sum of what arrives
- * from its 19 sources); two short kernels finish the nodes whose sources lie in another block
- * of the update (the first and last row of each 8-row tile and the first and last plane of each
- * 16-plane chunk by pulling their populations; the x edges of each 32-column tile from partial
- * sums the neighbouring tile wrote), and the particle coupling forms j' at its corners.  The one-pass update
+ * from its 19 sources); one short kernel finishes the nodes whose sources lie in another block
+ * of the update (the x edges of each 32-column tile, the first and last row of each 8-row tile
+ * and the first and last plane of each 16-plane chunk) by adding the partial sums the blocks
+ * wrote -- or, on lattices too thin for them (tiles of 1-2 rows, one plane), by pulling their
+ * populations -- and forms j' at the corners of the particles' cells for the next step's
+ * coupling.  The one-pass update
  * reads the populations once per step instead of twice.  passes = 0 (the default) takes one
  * pass with FP32 storage on lattices of at least 16 x 152 x (blocks per SM) column-tile planes
  * (tiles of 32 x 8 columns: about 128^3 and up on 152 SMs), two passes otherwise (with 16-bit
@@ -225,7 +227,7 @@ int lbmd_set_graphs(lbmd_ctx *ctx, int on);
  * same step up to FP32 rounding order (the densities are sums in another order).  One pass
  * needs the BGK collision and md_substeps = 1 (else LBMD_E_INVALID_ARG for passes = 1).  Drops
  * the recorded graphs.  lbmd_get_lattice_passes returns the update the next step takes (1 or 2;
- * setting it up, the first time, allocates the list of the second kernel's nodes) or a negative
+ * setting it up, the first time, allocates the partial-sum buffers) or a negative
  * LBMD_E_* code. */
 int lbmd_set_lattice_passes(lbmd_ctx *ctx, int passes);
 int lbmd_get_lattice_passes(lbmd_ctx *ctx);
