@@ -149,16 +149,65 @@ __global__ void __launch_bounds__(kBThreads, 4) kb_moments(const BatchDev *__res
 // up to 128 registers, none spilled) -- the autotuner picks.
 // kMRT: this launch updates the replicas with the fluctuating MRT collision (and skips the BGK
 // ones); the step runs both, each with its own register budget.
+// The first tile at or after t, in steps of the grid, that this launch updates (ntiles if none):
+// uniform across the block.
+__device__ __forceinline__ int next_update_tile(const BatchDev *__restrict__ B, int t, bool mrt) {
+  for (; t < B->ntiles; t += gridDim.x) {
+    const int slot = B->tile_slot[t];
+    if (B->left[slot] > 0 && (B->rep[slot].P.collision == LBMD_COLLISION_MRT) == mrt) break;
+  }
+  return t;
+}
+
+// Fill c for tile t of `slot` (all threads call it; the parameters are copied when the slot
+// differs from `have`, the one c held).  No barrier: the caller orders it.
+template <class T>
+__device__ __forceinline__ void fill_tile(TileCtx<T> &c, const BatchDev *__restrict__ B, int t, int slot, int &have,
+                                          int tuning) {
+  if (slot != have) {
+    const int *src = reinterpret_cast<const int *>(&B->rep[slot].P);
+    int *dst = reinterpret_cast<int *>(&c.P);
+    for (int k = threadIdx.x; k < (int)(sizeof(StepParams) / sizeof(int)); k += kBThreads) dst[k] = src[k];
+  }
+  if (threadIdx.x == 0) {
+    const RepDev &R = B->rep[slot];
+    const RepLayout &L = B->lay[slot];
+    const int cur = B->state[slot].cur;
+    c.fin = static_cast<const T *>(R.pop[cur]);
+    c.fout = static_cast<T *>(R.pop[cur ^ 1]);
+    c.rest_in = R.rest;
+    c.rest_out = tuning ? nullptr : R.rest;
+    c.rho = R.rho;
+    c.jp = R.P.np > 0 ? R.jp : nullptr;
+    c.err = &B->state[slot].err;
+    c.row_start = (!tuning && R.P.np > 0) ? B->row_start + L.row0 : nullptr;
+    c.base = (long long)(t - L.tile0) * B->tile_sites;
+    c.step = B->state[slot].step;
+    c.pa = B->S;
+    c.pf = B->pf;
+  }
+  have = slot;
+}
+
+// kMinBlocks: blocks per SM the register budget is sized for (3: 80 registers, some spilled; 2:
+// up to 128 registers, none spilled) -- the autotuner picks.
+// kMRT: this launch updates the replicas with the fluctuating MRT collision (and skips the BGK
+// ones); the step runs both, each with its own register budget.
+// The tile contexts are double-buffered: the next tile's is filled before this tile's sites are
+// updated, and one barrier per tile publishes it (and frees this one).
 template <class T, int kMinBlocks, bool kMRT>
 __global__ void __launch_bounds__(kBThreads, kMinBlocks) kb_collide(const BatchDev *__restrict__ B, int tuning) {
-  __shared__ TileCtx<T> c;
+  __shared__ TileCtx<T> cb[2];
   const int ts = B->tile_sites;
-  int have = -1;
-  for (int t = blockIdx.x; t < B->ntiles; t += gridDim.x) {
-    const int slot = B->tile_slot[t];
-    // uniform across the block
-    if (B->left[slot] <= 0 || (B->rep[slot].P.collision == LBMD_COLLISION_MRT) != kMRT) continue;
-    load_tile(c, B, t, slot, have, tuning);
+  int have[2] = {-1, -1};
+  int t = next_update_tile(B, blockIdx.x, kMRT);
+  if (t >= B->ntiles) return;  // uniform across the block
+  fill_tile(cb[0], B, t, B->tile_slot[t], have[0], tuning);
+  __syncthreads();
+  for (int b = 0; t < B->ntiles; b ^= 1) {
+    const int tn = next_update_tile(B, t + gridDim.x, kMRT);
+    if (tn < B->ntiles) fill_tile(cb[b ^ 1], B, tn, B->tile_slot[tn], have[b ^ 1], tuning);
+    const TileCtx<T> &c = cb[b];
     for (int k = threadIdx.x; k < ts; k += kBThreads) {
       const long long s = c.base + k;
       if (s >= c.P.N) break;
@@ -169,6 +218,8 @@ __global__ void __launch_bounds__(kBThreads, kMinBlocks) kb_collide(const BatchD
         site::collide<T, false, kMRT>(c.P, s, c.step, c.fin, c.fout, c.rho, c.pa, c.pf, CellIndex{nullptr},
                                       c.err, c.rest_in, c.rest_out);
     }
+    __syncthreads();  // the next context is complete; this one is free for the tile after it
+    t = tn;
   }
 }
 
