@@ -96,59 +96,6 @@ struct TileCtx {
   ParticleForces pf;
 };
 
-// Fill c for tile t of `slot` (all threads call it; the parameters are copied when the slot
-// changes).  Ends with a barrier: c is ready for every thread.
-template <class T>
-__device__ __forceinline__ void load_tile(TileCtx<T> &c, const BatchDev *__restrict__ B, int t, int slot, int &have,
-                                          int tuning) {
-  __syncthreads();  // every thread is done with the previous tile
-  if (slot != have) {
-    const int *src = reinterpret_cast<const int *>(&B->rep[slot].P);
-    int *dst = reinterpret_cast<int *>(&c.P);
-    for (int k = threadIdx.x; k < (int)(sizeof(StepParams) / sizeof(int)); k += kBThreads) dst[k] = src[k];
-  }
-  if (threadIdx.x == 0) {
-    const RepDev &R = B->rep[slot];
-    const RepLayout &L = B->lay[slot];
-    const int cur = B->state[slot].cur;
-    c.fin = static_cast<const T *>(R.pop[cur]);
-    c.fout = static_cast<T *>(R.pop[cur ^ 1]);
-    c.rest_in = R.rest;
-    c.rest_out = tuning ? nullptr : R.rest;
-    c.rho = R.rho;
-    c.jp = R.P.np > 0 ? R.jp : nullptr;
-    c.err = &B->state[slot].err;
-    c.row_start = (!tuning && R.P.np > 0) ? B->row_start + L.row0 : nullptr;
-    c.base = (long long)(t - L.tile0) * B->tile_sites;
-    c.step = B->state[slot].step;
-    c.pa = B->S;
-    c.pf = B->pf;
-  }
-  __syncthreads();
-  have = slot;
-}
-
-template <class T>
-__global__ void __launch_bounds__(kBThreads, 4) kb_moments(const BatchDev *__restrict__ B) {
-  __shared__ TileCtx<T> c;
-  const int ts = B->tile_sites;
-  int have = -1;
-  for (int t = blockIdx.x; t < B->ntiles; t += gridDim.x) {
-    const int slot = B->tile_slot[t];
-    if (B->left[slot] <= 0) continue;  // uniform across the block
-    load_tile(c, B, t, slot, have, 0);
-    for (int k = threadIdx.x; k < ts; k += kBThreads) {
-      const long long s = c.base + k;
-      if (s >= c.P.N) break;
-      site::moments<T>(c.P, s, c.fin, c.rest_in, c.rho, c.jp);
-    }
-  }
-}
-
-// kMinBlocks: blocks per SM the register budget is sized for (3: 80 registers, some spilled; 2:
-// up to 128 registers, none spilled) -- the autotuner picks.
-// kMRT: this launch updates the replicas with the fluctuating MRT collision (and skips the BGK
-// ones); the step runs both, each with its own register budget.
 // The first tile at or after t, in steps of the grid, that this launch updates (ntiles if none):
 // uniform across the block.
 __device__ __forceinline__ int next_update_tile(const BatchDev *__restrict__ B, int t, bool mrt) {
@@ -189,6 +136,37 @@ __device__ __forceinline__ void fill_tile(TileCtx<T> &c, const BatchDev *__restr
   have = slot;
 }
 
+// The density pass over the tiles of the replicas still taking steps, with the tile contexts
+// double-buffered like the update's.
+__device__ __forceinline__ int next_live_tile(const BatchDev *__restrict__ B, int t) {
+  for (; t < B->ntiles; t += gridDim.x)
+    if (B->left[B->tile_slot[t]] > 0) break;
+  return t;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBThreads, 4) kb_moments(const BatchDev *__restrict__ B) {
+  __shared__ TileCtx<T> cb[2];
+  const int ts = B->tile_sites;
+  int have0 = -1, have1 = -1;  // the slots whose parameters cb[0], cb[1] hold
+  int t = next_live_tile(B, blockIdx.x);
+  if (t >= B->ntiles) return;  // uniform across the block
+  fill_tile(cb[0], B, t, B->tile_slot[t], have0, 0);
+  __syncthreads();
+  for (int b = 0; t < B->ntiles; b ^= 1) {
+    const int tn = next_live_tile(B, t + gridDim.x);
+    if (tn < B->ntiles) fill_tile(cb[b ^ 1], B, tn, B->tile_slot[tn], b ? have0 : have1, 0);
+    const TileCtx<T> &c = cb[b];
+    for (int k = threadIdx.x; k < ts; k += kBThreads) {
+      const long long s = c.base + k;
+      if (s >= c.P.N) break;
+      site::moments<T>(c.P, s, c.fin, c.rest_in, c.rho, c.jp);
+    }
+    __syncthreads();  // the next context is complete; this one is free for the tile after it
+    t = tn;
+  }
+}
+
 // kMinBlocks: blocks per SM the register budget is sized for (3: 80 registers, some spilled; 2:
 // up to 128 registers, none spilled) -- the autotuner picks.
 // kMRT: this launch updates the replicas with the fluctuating MRT collision (and skips the BGK
@@ -199,14 +177,14 @@ template <class T, int kMinBlocks, bool kMRT>
 __global__ void __launch_bounds__(kBThreads, kMinBlocks) kb_collide(const BatchDev *__restrict__ B, int tuning) {
   __shared__ TileCtx<T> cb[2];
   const int ts = B->tile_sites;
-  int have[2] = {-1, -1};
+  int have0 = -1, have1 = -1;  // the slots whose parameters cb[0], cb[1] hold
   int t = next_update_tile(B, blockIdx.x, kMRT);
   if (t >= B->ntiles) return;  // uniform across the block
-  fill_tile(cb[0], B, t, B->tile_slot[t], have[0], tuning);
+  fill_tile(cb[0], B, t, B->tile_slot[t], have0, tuning);
   __syncthreads();
   for (int b = 0; t < B->ntiles; b ^= 1) {
     const int tn = next_update_tile(B, t + gridDim.x, kMRT);
-    if (tn < B->ntiles) fill_tile(cb[b ^ 1], B, tn, B->tile_slot[tn], have[b ^ 1], tuning);
+    if (tn < B->ntiles) fill_tile(cb[b ^ 1], B, tn, B->tile_slot[tn], b ? have0 : have1, tuning);
     const TileCtx<T> &c = cb[b];
     for (int k = threadIdx.x; k < ts; k += kBThreads) {
       const long long s = c.base + k;
