@@ -251,8 +251,9 @@ int lbmd_diagnostics(lbmd_ctx *ctx, double out[8]);
 
 /* The FP64 drift check (lbmd_params.diag_every; appendix: mass; Sec. 2: momentum).
  * lbmd_set_drift_reference takes the current totals as the reference (enqueued on the context
- * stream; lbmd_init_fluid and lbmd_set_particles do the same, lbmd_set_populations does not, so
- * that a state changed by hand between steps is measured against the run's start).
+ * stream; lbmd_init_fluid and lbmd_set_particles do the same when diag_every > 0,
+ * lbmd_set_populations does not, so that a state changed by hand between steps is measured
+ * against the run's start).
  * lbmd_get_drift synchronises and returns, for the last check, out[0] = its step count (-1: no
  * check yet), out[1], out[2] = the relative mass drift of A and B, out[3] = the momentum drift
  * per unit mass, out[4] = the number of checks since the reference was taken.  It does not

@@ -1217,6 +1217,10 @@ int lbmd_batch_init_fluid(lbmd_batch *b, int slot, const float *rhoA, const floa
   const RepState st0{cur, 0u, 0ull, 0ull, sl.prm.diag_every > 0 ? 1u : 0u, 0u};
   sl.ref_pending = sl.prm.diag_every > 0;
   BK(cudaMemcpyAsync(b->d_state + slot, &st0, sizeof(RepState), cudaMemcpyHostToDevice, b->st), "reset state");
+  // no check yet (lbmd_batch_get_drift before the first step: step -1, no checks)
+  static const double kNoCheck[5] = {-1, 0, 0, 0, 0};
+  BK(cudaMemcpyAsync(b->d_drift + (size_t)slot * 10 + 5, kNoCheck, sizeof(kNoCheck), cudaMemcpyHostToDevice, b->st),
+     "reset drift");
   sl.mirror = st0;
   sl.queued = 0;
   if (!sl.fluid_ready) b->dirty = true;

@@ -403,6 +403,9 @@ int enqueue_totals(lbmd_ctx *c) {
 }
 
 // The drift check on the device (set_ref: take the totals as the reference instead).
+// The drift table before any reference: no reference, no check yet (step -1, no checks).
+const double kDriftNone[10] = {0, 0, 0, 0, 0, -1, 0, 0, 0, 0};
+
 int enqueue_drift(lbmd_ctx *c, int set_ref) {
   int r = enqueue_totals(c);
   if (r) return r;
@@ -756,6 +759,7 @@ int lbmd_create(const lbmd_params *prm, void *stream, lbmd_ctx **out, unsigned *
   c->diag_blocks = fluid_sum_blocks(P);
   if ((e = dalloc(&c->diag_partial, (size_t)5 * c->diag_blocks)) != cudaSuccess ||
       (e = dalloc(&c->diag_out, 8)) != cudaSuccess || (e = dalloc(&c->drift, 10)) != cudaSuccess ||
+      (e = cudaMemcpy(c->drift, kDriftNone, sizeof(kDriftNone), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemset(c->err, 0, sizeof(unsigned))) != cudaSuccess) {
     cudaGetLastError();
     lbmd_destroy(c);
@@ -844,7 +848,8 @@ int lbmd_init_fluid(lbmd_ctx *c, const float *rhoA, const float *rhoB, const flo
   c->rho_valid = false;
   c->jc_valid = false;
   if ((r = ensure_densities(c))) return r;
-  if ((r = enqueue_drift(c, 1))) return r;  // the drift check's reference
+  // the drift check's reference (a context that never checks takes it only when asked)
+  if (c->prm.diag_every > 0 && (r = enqueue_drift(c, 1))) return r;
   CK(cudaStreamSynchronize(c->st), "sync");
   c->fluid_ready = true;
   return LBMD_OK;
@@ -946,7 +951,7 @@ int lbmd_set_particles(lbmd_ctx *c, int n, const double *x, const double *v, con
     if (r) return r;
   }
   c->sort_pending = false;
-  if (c->fluid_ready) {  // the drift check's reference includes the new particles' momentum
+  if (c->fluid_ready && c->prm.diag_every > 0) {  // the drift check's reference includes the new particles' momentum
     const int r = enqueue_drift(c, 1);
     if (r) return r;
   }

@@ -205,3 +205,21 @@ def test_batch_replica_with_broken_momentum_stops_alone():
         assert bad[0] == 5 and abs(bad[3] / want - 1) < 0.01
     finally:
         L.lbmd_batch_destroy(b)
+
+
+def test_no_check_without_diag_every():
+    """diag_every = 0 (the default): no check runs and none is reported (step -1, no checks), with
+    no reference taken by lbmd_init_fluid or lbmd_set_particles; lbmd_set_drift_reference still
+    takes one on request."""
+    from paper_1306_0788_gb300 import lbmd as L
+    c = _coupled_case()
+    ctx = make_gpu(c)
+    try:
+        L.lbmd_step(ctx, 12)
+        L.lbmd_sync(ctx)
+        d = L.lbmd_get_drift(ctx)
+        assert d[0] == -1 and d[4] == 0 and max(d[1:4]) == 0
+        L.lbmd_set_drift_reference(ctx)
+        assert L.lbmd_get_drift(ctx)[0] == -1
+    finally:
+        L.lbmd_destroy(ctx)
