@@ -58,7 +58,9 @@ def test_ten_step_populations(storage):
     c = Case(dims=dims, g=1.68 / SCALE, rhoA=rA, rhoB=rB)
     fo, *_ = run_oracle(c, 10)
     fg, _ = _gpu(c, 10, storage, (SCALE, SCALE))
-    assert pop_error(fg, fo) <= BOUNDS[storage]["pop10"]
+    err = pop_error(fg, fo)
+    print("populations 10 steps", storage, err)
+    assert err <= BOUNDS[storage]["pop10"]
 
 
 @functools.lru_cache(maxsize=None)
@@ -88,6 +90,7 @@ def test_laplace_pressure_and_mass_drift(storage, radius):
         return p[16, 16] - p[0, 0]
 
     fg, drift = _gpu(c, 3000, storage, (float(rA.mean()), float(rB.mean())))
+    print("laplace quasi-2d", storage, radius, "dp error", abs(dp(fg) - dp(fo)) / abs(dp(fo)), "mass drift", drift)
     assert abs(dp(fg) - dp(fo)) <= BOUNDS[storage]["dp"] * abs(dp(fo))
     assert drift <= BOUNDS[storage]["drift"]
 
