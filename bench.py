@@ -30,10 +30,10 @@ UNIT = "MLUPS"
 HBM_FALLBACK_GBS = 6800.0
 HBM_NOMINAL_GBS = 7900.0
 # DRAM bytes per node moved by the lattice update (dram__bytes_read + dram__bytes_write of one ncu
-# capture of this workload at a smaller edge, scaled per node), per (storage, lattice passes) with a
-# capture of its own: the one-pass update at 192^3 (1144.0 + 1118.1 MB over 7,077,888 nodes), the
-# two-pass updates at 128^3.
-COLLIDE_TRAFFIC_BYTES_PER_NODE = {("fp32", 1): 319.6, ("fp32", 2): 289.6, ("bf16", 2): 146.9, ("fp16", 2): 146.8}
+# capture, per node), per (storage, lattice passes): the bench's own 256^3 launch for the one-pass
+# FP32 update (2707.8 + 2717.9 MB) and the FP16 / BF16 updates (a one-pass metric set, captured at
+# full size); the two-pass FP32 update from a 128^3 capture of the same workload, scaled per node.
+COLLIDE_TRAFFIC_BYTES_PER_NODE = {("fp32", 1): 323.4, ("fp32", 2): 289.6, ("bf16", 2): 165.7, ("fp16", 2): 165.6}
 # The fluctuating MRT update is bound by instruction issue, not by HBM: warp instructions per
 # node of k_collide<float, true, true> (smsp__inst_executed.sum / nodes of one ncu capture of the
 # 128^3 case), and the issue peak of the GPU: one warp instruction per cycle per scheduler, 4
