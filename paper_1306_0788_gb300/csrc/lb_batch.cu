@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kBThreads = 256;   // lattice kernels
 constexpr int kBPThreads = 128;  // particle and row kernels
+constexpr int kPairGrid = 4;     // the coupling's and the pair forces' grid, in particle grids
 
 // ------------------------------------------------------------------ device tables
 
@@ -956,8 +957,11 @@ int enqueue_step(lbmd_batch *b) {
   cudaEventRecord(b->ev_sorted, sd);
   launch_batched_moments(b, b->grid_moments);
   cudaStreamWaitEvent(b->st, b->ev_sorted, 0);
-  kb_couple<<<gp, kBPThreads, 0, b->st>>>(B);
-  kb_pairs<<<gp, kBPThreads, 0, sd>>>(B);
+  // the coupling and the pair forces walk chains of dependent loads per particle: a grid of
+  // kPairGrid times the particle grid (blocks beyond the resident ones queue) leaves each of their
+  // threads about one particle instead of a few in a row
+  kb_couple<<<kPairGrid * gp, kBPThreads, 0, b->st>>>(B);
+  kb_pairs<<<kPairGrid * gp, kBPThreads, 0, sd>>>(B);
   cudaEventRecord(b->ev_pairs, sd);
   const int nc = launch_batched_collide(b, b->grid_collide, b->collide_blocks, 0);
   cudaStreamWaitEvent(b->st, b->ev_pairs, 0);
