@@ -323,15 +323,19 @@ __device__ __forceinline__ void gather_coupling(const StepParams &P, int x, int 
 // al., SC'11) with counter (site, step low, step high, 0x464c0000 + k) and key = seed, uniforms
 // from the top 24 bits, Box-Muller on both uniform pairs.  The logarithm and the sine / cosine
 // are the hardware approximations (absolute error ~1e-6 on a normal, far below what the
-// populations can resolve); the generator's integer stream is exact.
+// populations can resolve), and so is the radius: x rsqrt(x), a few ulp from sqrt(x); the
+// generator's integer stream is exact.  A uniform (v + 1/2) 2^-24 is one FFMA: the scaling by a
+// power of two is exact, so one rounding of v 2^-24 + 2^-25 gives the same float.
 __device__ __forceinline__ float4 fluid_normals4(unsigned long long seed, unsigned long long step, unsigned site,
                                                  unsigned k) {
   const uint4 r = philox4x32_10(make_uint4(site, (unsigned)step, (unsigned)(step >> 32), 0x464c0000u + k),
                                 make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
-  const float sc = 1.f / 16777216.f;
-  const float u0 = ((float)(r.x >> 8) + 0.5f) * sc, u1 = ((float)(r.y >> 8) + 0.5f) * sc;
-  const float u2 = ((float)(r.z >> 8) + 0.5f) * sc, u3 = ((float)(r.w >> 8) + 0.5f) * sc;
-  const float a = sqrtf(-2.f * __logf(u0)), b = sqrtf(-2.f * __logf(u2));
+  const float sc = 1.f / 16777216.f, h = 0.5f / 16777216.f;
+  const float u0 = fmaf((float)(r.x >> 8), sc, h), u1 = fmaf((float)(r.y >> 8), sc, h);
+  const float u2 = fmaf((float)(r.z >> 8), sc, h), u3 = fmaf((float)(r.w >> 8), sc, h);
+  // u0 = 1 (v = 2^24 - 1 rounds up) gives x = 0: the floor keeps 0 * rsqrt from being NaN
+  const float xa = -2.f * __logf(u0), xb = -2.f * __logf(u2);
+  const float a = xa * rsqrtf(fmaxf(xa, 1e-30f)), b = xb * rsqrtf(fmaxf(xb, 1e-30f));
   const float two_pi = 6.28318530717958647692f;
   float s1, c1, s3, c3;
   __sincosf(two_pi * u1, &s1, &c1);
@@ -339,150 +343,156 @@ __device__ __forceinline__ float4 fluid_normals4(unsigned long long seed, unsign
   return make_float4(a * c1, a * s1, b * c3, b * s3);
 }
 
-// Eq. MODES for one component: modes m_k = sum_i e_k(c_i) f_i (lb_modes.h), each relaxed toward
-// its equilibrium value with factor 1 + lambda_k, plus the moment of the forcing term and the
-// noise nz[k]; back to populations f_i = w_i sum_k e_k(c_i) m_k / b_k.  The equilibrium moments
-// of f^eq(rho_z, u) are rho_z u (momentum), rho_z u u (stress), 0 (kinetic); those of the
-// forcing term are (2 + lambda_M)/2 g, and G for the stress (appendix), 0 for the kinetic modes.
+// Eq. MODES, per component: modes m_k = sum_i e_k(c_i) f_i (lb_modes.h), each relaxed toward its
+// equilibrium value with factor 1 + lambda_k, plus the moment of the forcing term and the noise;
+// back to populations f_i = w_i sum_k e_k(c_i) m_k / b_k.  The equilibrium moments of
+// f^eq(rho_z, u) are rho_z u (momentum), rho_z u u (stress), 0 (kinetic); those of the forcing
+// term are (2 + lambda_M)/2 g, and G for the stress (appendix), 0 for the kinetic modes.
 // Directions come in opposite pairs (2p + 1, 2p + 2) and every e_k is even or odd in c, so both
 // transforms work on the pair sums and differences: half the arithmetic of the plain sums.
 __device__ __host__ constexpr bool mode_even(int k) { return k == 0 || (k >= 4 && k <= 9) || k >= 16; }
 
-__device__ __forceinline__ void mrt_component(const StepParams &P, float f[kQ], float rz, float ux, float uy,
-                                              float uz, float3 g, const float nz[kQ]) {
+// The collision of both components with the fluctuating MRT operator (Eq. MODES), the two
+// components' transforms run together on (A, B) pairs with the packed two-lane FP32 instructions.  With noise: the three momentum normals are
+// shared by A (+) and B (-), amplitude over sqrt(rho_A rho_B / rho); the stress and kinetic modes
+// take normals 3-17 (A) and 18-32 (B) of the site's 36.  Each normal is added to its relaxed mode
+// as it is drawn, so that no component's noise is held whole.
+__device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long long step, unsigned site,
+                                           float fA[kQ], float fB[kQ], float rA, float rB, float ux, float uy,
+                                           float uz, float3 gA, float3 gB) {
   constexpr int kPairs = (kQ - 1) / 2;
-  float sp[kPairs], dp[kPairs];
-#pragma unroll
-  for (int p = 0; p < kPairs; ++p) {
-    sp[p] = f[2 * p + 1] + f[2 * p + 2];
-    dp[p] = f[2 * p + 1] - f[2 * p + 2];
-  }
-  float m[kQ];
-#pragma unroll
-  for (int k = 0; k < kQ; ++k) {
-    float a = mode_even(k) ? (float)mode_poly(k, 0, 0, 0) * f[0] : 0.f;
+  // modes m_k = sum_i e_k(c_i) f_i of both components, from the pair sums and differences
+  float2 m[kQ];
+  {
+    float2 sp[kPairs], dp[kPairs];
 #pragma unroll
     for (int p = 0; p < kPairs; ++p) {
-      const int i = 2 * p + 1;
-      const int e = mode_poly(k, kCx[i], kCy[i], kCz[i]);
-      const float v = mode_even(k) ? sp[p] : dp[p];
-      if (e == 1)
-        a += v;
-      else if (e == -1)
-        a -= v;
-      else if (e != 0)
-        a += (float)e * v;
+      const float2 u = make_float2(fA[2 * p + 1], fB[2 * p + 1]), v = make_float2(fA[2 * p + 2], fB[2 * p + 2]);
+      sp[p] = __fadd2_rn(u, v);
+      dp[p] = __fadd2_rn(u, make_float2(-v.x, -v.y));
     }
-    m[k] = a;
-  }
-  const float uu = ux * ux + uy * uy + uz * uz, ug = ux * g.x + uy * g.y + uz * g.z;
-  const float meq[10] = {rz,
-                         rz * ux,
-                         rz * uy,
-                         rz * uz,
-                         rz * uu,
-                         rz * (3.f * ux * ux - uu),
-                         rz * (uy * uy - uz * uz),
-                         rz * ux * uy,
-                         rz * uy * uz,
-                         rz * uz * ux};
-  const float mg[10] = {0.f,
-                        P.force[1] * g.x,
-                        P.force[2] * g.y,
-                        P.force[3] * g.z,
-                        P.force[4] * ug,
-                        P.force[5] * (3.f * ux * g.x - ug),
-                        P.force[6] * (uy * g.y - uz * g.z),
-                        P.force[7] * (ux * g.y + uy * g.x),
-                        P.force[8] * (uy * g.z + uz * g.y),
-                        P.force[9] * (uz * g.x + ux * g.z)};
-  // relaxed modes, scaled by 1 / b_k for the way back
+    const float2 f0 = make_float2(fA[0], fB[0]);
 #pragma unroll
-  for (int k = 0; k < kQ; ++k) {
-    float v;
-    if (k == 0)
-      v = m[0];
-    else if (k < 10)
-      v = meq[k] + P.relax[k] * (m[k] - meq[k]) + mg[k] + nz[k];
-    else
-      v = P.relax[k] * m[k] + nz[k];
-    m[k] = v * (9.f / (float)mode_norm9(k));
+    for (int k = 0; k < kQ; ++k) {
+      const float e0 = (float)mode_poly(k, 0, 0, 0);
+      float2 a = mode_even(k) ? make_float2(e0 * f0.x, e0 * f0.y) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) {
+        const int i = 2 * p + 1;
+        const int e = mode_poly(k, kCx[i], kCy[i], kCz[i]);
+        const float2 v = mode_even(k) ? sp[p] : dp[p];
+        if (e == 1)
+          a = __fadd2_rn(a, v);
+        else if (e == -1)
+          a = __fadd2_rn(a, make_float2(-v.x, -v.y));
+        else if (e != 0)
+          a = __ffma2_rn(make_float2((float)e, (float)e), v, a);
+      }
+      m[k] = a;
+    }
   }
+  // equilibrium moments rho_z (u, u u) and the forcing term's moments of each component; relaxed
+  const float uu = ux * ux + uy * uy + uz * uz;
+  const float2 rz = make_float2(rA, rB);
+  const float2 gx = make_float2(gA.x, gB.x), gy = make_float2(gA.y, gB.y), gz = make_float2(gA.z, gB.z);
+  const float2 ug = make_float2(ux * gA.x + uy * gA.y + uz * gA.z, ux * gB.x + uy * gB.y + uz * gB.z);
+  auto sc = [](float a, float2 v) { return make_float2(a * v.x, a * v.y); };
+  auto ad = [](float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); };
+  auto sb = [](float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); };
+  const float2 meq[10] = {rz,
+                          sc(ux, rz),
+                          sc(uy, rz),
+                          sc(uz, rz),
+                          sc(uu, rz),
+                          sc(3.f * ux * ux - uu, rz),
+                          sc(uy * uy - uz * uz, rz),
+                          sc(ux * uy, rz),
+                          sc(uy * uz, rz),
+                          sc(uz * ux, rz)};
+  const float2 mg[10] = {make_float2(0.f, 0.f),
+                         sc(P.force[1], gx),
+                         sc(P.force[2], gy),
+                         sc(P.force[3], gz),
+                         sc(P.force[4], ug),
+                         sc(P.force[5], sb(sc(3.f * ux, gx), ug)),
+                         sc(P.force[6], sb(sc(uy, gy), sc(uz, gz))),
+                         sc(P.force[7], ad(sc(ux, gy), sc(uy, gx))),
+                         sc(P.force[8], ad(sc(uy, gz), sc(uz, gy))),
+                         sc(P.force[9], ad(sc(uz, gx), sc(ux, gz)))};
+#pragma unroll
+  for (int k = 1; k < kQ; ++k) {
+    if (k < 10)
+      m[k] = ad(__ffma2_rn(make_float2(P.relax[k], P.relax[k]), sb(m[k], meq[k]), meq[k]), mg[k]);
+    else
+      m[k] = sc(P.relax[k], m[k]);
+  }
+  if (P.fluct) {
+    // sqrt(rho_A), sqrt(rho_B) and sqrt(rho_A rho_B / rho) from reciprocal square roots, as the
+    // Box-Muller radius (a density of 0 gives 0)
+    const float sA = rA * rsqrtf(fmaxf(rA, 1e-30f)), sB = rB * rsqrtf(fmaxf(rB, 1e-30f));
+    const float am = P.noise[1] * sA * sB * rsqrtf(rA + rB);
+    // A: normals 0-3 (momentum, shared; then mode 4), 4-15 (modes 5-16), 16, 17 (modes 17, 18)
+    float4 q = fluid_normals4(P.seed, step, site, 0);
+    m[1] = ad(m[1], make_float2(am * q.x, -am * q.x));
+    m[2] = ad(m[2], make_float2(am * q.y, -am * q.y));
+    m[3] = ad(m[3], make_float2(am * q.z, -am * q.z));
+    m[4].x += P.noise[4] * sA * q.w;
+#pragma unroll
+    for (int c = 1; c <= 3; ++c) {
+      q = fluid_normals4(P.seed, step, site, c);
+      const int k = 4 * c + 1;
+      m[k].x += P.noise[k] * sA * q.x;
+      m[k + 1].x += P.noise[k + 1] * sA * q.y;
+      m[k + 2].x += P.noise[k + 2] * sA * q.z;
+      m[k + 3].x += P.noise[k + 3] * sA * q.w;
+    }
+    q = fluid_normals4(P.seed, step, site, 4);
+    m[17].x += P.noise[17] * sA * q.x;
+    m[18].x += P.noise[18] * sA * q.y;
+    // B: modes 4, 5 from the last two of that draw, then 6-18
+    m[4].y += P.noise[4] * sB * q.z;
+    m[5].y += P.noise[5] * sB * q.w;
+#pragma unroll
+    for (int c = 5; c <= 7; ++c) {
+      q = fluid_normals4(P.seed, step, site, c);
+      const int k = 4 * c - 14;
+      m[k].y += P.noise[k] * sB * q.x;
+      m[k + 1].y += P.noise[k + 1] * sB * q.y;
+      m[k + 2].y += P.noise[k + 2] * sB * q.z;
+      m[k + 3].y += P.noise[k + 3] * sB * q.w;
+    }
+    q = fluid_normals4(P.seed, step, site, 8);
+    m[18].y += P.noise[18] * sB * q.x;
+  }
+  // scaled by 1 / b_k for the way back
+#pragma unroll
+  for (int k = 0; k < kQ; ++k) m[k] = sc(9.f / (float)mode_norm9(k), m[k]);
   // moving populations from the modes; the rest population takes what the node's density
   // (unchanged by the collision) leaves, so that the FP32 weights, whose sum is not exactly 1,
   // do not bias the mass every step
-  float moving = 0.f;
+  float2 moving = make_float2(0.f, 0.f);
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
     const int i = 2 * p + 1;
-    float even = 0.f, odd = 0.f;
+    float2 even = make_float2(0.f, 0.f), odd = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < kQ; ++k) {
       const int e = mode_poly(k, kCx[i], kCy[i], kCz[i]);
       if (e == 0) continue;
       if (mode_even(k))
-        even += (float)e * m[k];
+        even = __ffma2_rn(make_float2((float)e, (float)e), m[k], even);
       else
-        odd += (float)e * m[k];
+        odd = __ffma2_rn(make_float2((float)e, (float)e), m[k], odd);
     }
-    f[i] = kW[i] * (even + odd);
-    f[i + 1] = kW[i] * (even - odd);
-    moving += f[i] + f[i + 1];
+    const float2 fi = sc(kW[i], ad(even, odd)), fj = sc(kW[i], sb(even, odd));
+    fA[i] = fi.x;
+    fB[i] = fi.y;
+    fA[i + 1] = fj.x;
+    fB[i + 1] = fj.y;
+    moving = ad(moving, ad(fi, fj));
   }
-  f[0] = rz - moving;
-}
-
-// The collision of both components with the fluctuating MRT operator.  With noise: the three
-// momentum normals are shared by A (+) and B (-), amplitude over sqrt(rho_A rho_B / rho); the
-// stress and kinetic modes take normals 3-17 (A) and 18-32 (B) of the site's 36.
-__device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long long step, unsigned site,
-                                           float fA[kQ], float fB[kQ], float rA, float rB, float ux, float uy,
-                                           float uz, float3 gA, float3 gB) {
-  float nz[kQ];
-#pragma unroll
-  for (int k = 0; k < kQ; ++k) nz[k] = 0.f;
-  float rmx = 0.f, rmy = 0.f, rmz = 0.f, b0 = 0.f, b1 = 0.f, am = 0.f;
-  if (P.fluct) {
-    am = P.noise[1] * sqrtf(rA * rB / (rA + rB));
-    const float sA = sqrtf(rA);
-    float4 q = fluid_normals4(P.seed, step, site, 0);
-    rmx = q.x; rmy = q.y; rmz = q.z;
-    nz[1] = am * rmx; nz[2] = am * rmy; nz[3] = am * rmz;
-    nz[4] = P.noise[4] * sA * q.w;
-#pragma unroll
-    for (int c = 1; c <= 3; ++c) {
-      q = fluid_normals4(P.seed, step, site, c);
-      const int k = 4 * c + 1;
-      nz[k] = P.noise[k] * sA * q.x;
-      nz[k + 1] = P.noise[k + 1] * sA * q.y;
-      nz[k + 2] = P.noise[k + 2] * sA * q.z;
-      nz[k + 3] = P.noise[k + 3] * sA * q.w;
-    }
-    q = fluid_normals4(P.seed, step, site, 4);
-    nz[17] = P.noise[17] * sA * q.x;
-    nz[18] = P.noise[18] * sA * q.y;
-    b0 = q.z;
-    b1 = q.w;
-  }
-  mrt_component(P, fA, rA, ux, uy, uz, gA, nz);
-  if (P.fluct) {
-    const float sB = sqrtf(rB);
-    nz[1] = -am * rmx; nz[2] = -am * rmy; nz[3] = -am * rmz;
-    nz[4] = P.noise[4] * sB * b0;
-    nz[5] = P.noise[5] * sB * b1;
-#pragma unroll
-    for (int c = 5; c <= 7; ++c) {
-      const float4 q = fluid_normals4(P.seed, step, site, c);
-      const int k = 4 * c - 14;
-      nz[k] = P.noise[k] * sB * q.x;
-      nz[k + 1] = P.noise[k + 1] * sB * q.y;
-      nz[k + 2] = P.noise[k + 2] * sB * q.z;
-      nz[k + 3] = P.noise[k + 3] * sB * q.w;
-    }
-    const float4 q = fluid_normals4(P.seed, step, site, 8);
-    nz[18] = P.noise[18] * sB * q.x;
-  }
-  mrt_component(P, fB, rB, ux, uy, uz, gB, nz);
+  fA[0] = rA - moving.x;
+  fB[0] = rB - moving.y;
 }
 
 // Where the update reads the densities of its Shan-Chen stencil: from the density field in global
