@@ -330,17 +330,21 @@ __device__ __forceinline__ float4 fluid_normals4(unsigned long long seed, unsign
                                                  unsigned k) {
   const uint4 r = philox4x32_10(make_uint4(site, (unsigned)step, (unsigned)(step >> 32), 0x464c0000u + k),
                                 make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
-  const float sc = 1.f / 16777216.f, h = 0.5f / 16777216.f;
-  const float u0 = fmaf((float)(r.x >> 8), sc, h), u1 = fmaf((float)(r.y >> 8), sc, h);
-  const float u2 = fmaf((float)(r.z >> 8), sc, h), u3 = fmaf((float)(r.w >> 8), sc, h);
+  // the two Box-Muller pairs side by side: (u0, u2) give the radii, (u1, u3) the angles
+  const float2 sc = make_float2(1.f / 16777216.f, 1.f / 16777216.f), h = make_float2(0.5f / 16777216.f, 0.5f / 16777216.f);
+  const float2 ur = __ffma2_rn(make_float2((float)(r.x >> 8), (float)(r.z >> 8)), sc, h);
+  const float2 ua = __ffma2_rn(make_float2((float)(r.y >> 8), (float)(r.w >> 8)), sc, h);
   // u0 = 1 (v = 2^24 - 1 rounds up) gives x = 0: the floor keeps 0 * rsqrt from being NaN
-  const float xa = -2.f * __logf(u0), xb = -2.f * __logf(u2);
-  const float a = xa * rsqrtf(fmaxf(xa, 1e-30f)), b = xb * rsqrtf(fmaxf(xb, 1e-30f));
+  const float2 x = __fmul2_rn(make_float2(-2.f, -2.f), make_float2(__logf(ur.x), __logf(ur.y)));
+  const float2 rad = __fmul2_rn(x, make_float2(rsqrtf(fmaxf(x.x, 1e-30f)), rsqrtf(fmaxf(x.y, 1e-30f))));
   const float two_pi = 6.28318530717958647692f;
+  const float2 ang = __fmul2_rn(make_float2(two_pi, two_pi), ua);
   float s1, c1, s3, c3;
-  __sincosf(two_pi * u1, &s1, &c1);
-  __sincosf(two_pi * u3, &s3, &c3);
-  return make_float4(a * c1, a * s1, b * c3, b * s3);
+  __sincosf(ang.x, &s1, &c1);
+  __sincosf(ang.y, &s3, &c3);
+  const float2 n01 = __fmul2_rn(make_float2(rad.x, rad.x), make_float2(c1, s1));
+  const float2 n23 = __fmul2_rn(make_float2(rad.y, rad.y), make_float2(c3, s3));
+  return make_float4(n01.x, n01.y, n23.x, n23.y);
 }
 
 // Eq. MODES, per component: modes m_k = sum_i e_k(c_i) f_i (lb_modes.h), each relaxed toward its
@@ -396,9 +400,10 @@ __device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long lo
   const float2 rz = make_float2(rA, rB);
   const float2 gx = make_float2(gA.x, gB.x), gy = make_float2(gA.y, gB.y), gz = make_float2(gA.z, gB.z);
   const float2 ug = make_float2(ux * gA.x + uy * gA.y + uz * gA.z, ux * gB.x + uy * gB.y + uz * gB.z);
-  auto sc = [](float a, float2 v) { return make_float2(a * v.x, a * v.y); };
-  auto ad = [](float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); };
-  auto sb = [](float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); };
+  // scaling, sum and difference of (A, B) pairs (packed: the compiler does not pair scalar ones)
+  auto sc = [](float a, float2 v) { return __fmul2_rn(make_float2(a, a), v); };
+  auto ad = [](float2 a, float2 b) { return __fadd2_rn(a, b); };
+  auto sb = [](float2 a, float2 b) { return __ffma2_rn(make_float2(-1.f, -1.f), b, a); };
   const float2 meq[10] = {rz,
                           sc(ux, rz),
                           sc(uy, rz),
@@ -433,9 +438,10 @@ __device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long lo
     const float am = P.noise[1] * sA * sB * rsqrtf(rA + rB);
     // A: normals 0-3 (momentum, shared; then mode 4), 4-15 (modes 5-16), 16, 17 (modes 17, 18)
     float4 q = fluid_normals4(P.seed, step, site, 0);
-    m[1] = ad(m[1], make_float2(am * q.x, -am * q.x));
-    m[2] = ad(m[2], make_float2(am * q.y, -am * q.y));
-    m[3] = ad(m[3], make_float2(am * q.z, -am * q.z));
+    const float2 amAB = make_float2(am, -am);
+    m[1] = __ffma2_rn(amAB, make_float2(q.x, q.x), m[1]);
+    m[2] = __ffma2_rn(amAB, make_float2(q.y, q.y), m[2]);
+    m[3] = __ffma2_rn(amAB, make_float2(q.z, q.z), m[3]);
     m[4].x += P.noise[4] * sA * q.w;
 #pragma unroll
     for (int c = 1; c <= 3; ++c) {
