@@ -331,7 +331,8 @@ __device__ __forceinline__ float4 fluid_normals4(unsigned long long seed, unsign
   const uint4 r = philox4x32_10(make_uint4(site, (unsigned)step, (unsigned)(step >> 32), 0x464c0000u + k),
                                 make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
   // the two Box-Muller pairs side by side: (u0, u2) give the radii, (u1, u3) the angles
-  const float2 sc = make_float2(1.f / 16777216.f, 1.f / 16777216.f), h = make_float2(0.5f / 16777216.f, 0.5f / 16777216.f);
+  const float2 sc = make_float2(1.f / 16777216.f, 1.f / 16777216.f);
+  const float2 h = make_float2(0.5f / 16777216.f, 0.5f / 16777216.f);
   const float2 ur = __ffma2_rn(make_float2((float)(r.x >> 8), (float)(r.z >> 8)), sc, h);
   const float2 ua = __ffma2_rn(make_float2((float)(r.y >> 8), (float)(r.w >> 8)), sc, h);
   // u0 = 1 (v = 2^24 - 1 rounds up) gives x = 0: the floor keeps 0 * rsqrt from being NaN
@@ -357,10 +358,11 @@ __device__ __forceinline__ float4 fluid_normals4(unsigned long long seed, unsign
 __device__ __host__ constexpr bool mode_even(int k) { return k == 0 || (k >= 4 && k <= 9) || k >= 16; }
 
 // The collision of both components with the fluctuating MRT operator (Eq. MODES), the two
-// components' transforms run together on (A, B) pairs with the packed two-lane FP32 instructions.  With noise: the three momentum normals are
-// shared by A (+) and B (-), amplitude over sqrt(rho_A rho_B / rho); the stress and kinetic modes
-// take normals 3-17 (A) and 18-32 (B) of the site's 36.  Each normal is added to its relaxed mode
-// as it is drawn, so that no component's noise is held whole.
+// components' arithmetic run together on (A, B) pairs with the packed two-lane FP32
+// instructions.  With noise: the three momentum normals are shared by A (+) and B (-), amplitude
+// over sqrt(rho_A rho_B / rho); the stress and kinetic modes take normals 3-17 (A) and 18-32 (B)
+// of the site's 36.  Each normal is added to its relaxed mode as it is drawn, so that no
+// component's noise is held whole.
 __device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long long step, unsigned site,
                                            float fA[kQ], float fB[kQ], float rA, float rB, float ux, float uy,
                                            float uz, float3 gA, float3 gB) {
