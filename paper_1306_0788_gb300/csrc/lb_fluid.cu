@@ -197,8 +197,10 @@ __global__ void __launch_bounds__(kOPThreads, 3)
                       float *__restrict__ rho_next, OnePassOut out, ParticleArrays pa, ParticleForces pf,
                       CellIndex ci, unsigned *err, const float *__restrict__ rest_in, float *__restrict__ rest_out,
                       OnePassGeom G) {
-  // groups handed to the neighbouring rows: [0..2] c_y = +1 with c_z = -1, 0, +1; [3..5] c_y = -1
-  __shared__ float2 xch[2][6][kOnePassRows][32];
+  // groups handed to the neighbouring rows: [0..2] c_y = +1 with c_z = -1, 0, +1; [3..5] c_y = -1;
+  // row w at index w + 1, indices 0 and kOnePassRows + 1 always 0 (the rows beyond the tile, whose
+  // parts arrive as partial sums), so that a row adds its neighbours' without a select
+  __shared__ float2 xch[2][6][kOnePassRows + 2][32];
   // the same for what leaves the tile along x: [side][c_y = +1, -1][row] (side 0: from lane 0
   // towards x0 - 1; side 1: from the last lane towards x0 + 32)
   __shared__ float2 xedge[2][2][2][kOnePassRows];
@@ -225,6 +227,10 @@ __global__ void __launch_bounds__(kOPThreads, 3)
   const bool inner_row = w >= 1 && w <= rows - 2;  // the sources along y are in the block
   const bool left = lane == 0, right = lane == nown - 1;  // the tile's x edges (both when nown = 1)
   acc[0][threadIdx.x] = acc[1][threadIdx.x] = acc[2][threadIdx.x] = make_float2(0.f, 0.f);
+  for (int e = threadIdx.x; e < 2 * 6 * 2 * 32; e += kOPThreads) {
+    const int r = (e >> 5) & 1, pg = e >> 6;
+    xch[pg / 6][pg % 6][r ? kOnePassRows + 1 : 0][e & 31] = make_float2(0.f, 0.f);
+  }
   if (threadIdx.x < 3 * 2 * kOnePassRows) (&accE[0][0][0])[threadIdx.x] = make_float2(0.f, 0.f);
   if (threadIdx.x < 3 * 2 * 32) (&accY[0][0][0])[threadIdx.x] = make_float2(0.f, 0.f);
   // rows whose partial sums the block forms: the inner ones, and with y partials the edge rows too
@@ -263,13 +269,13 @@ __global__ void __launch_bounds__(kOPThreads, 3)
       if (lane + 1 >= nown) mA = mB = 0.f;
       return add2(add2(make_float2(fA[i0], fB[i0]), make_float2(pA, pB)), make_float2(mA, mB));
     };
-    float2(*X)[kOnePassRows][32] = xch[parity];
-    X[0][w][lane] = make_float2(fA[17], fB[17]);  // (c_y, c_z) = (+1, -1)
-    X[1][w][lane] = group(3, 7, 10);              // (+1, 0)
-    X[2][w][lane] = make_float2(fA[15], fB[15]);  // (+1, +1)
-    X[3][w][lane] = make_float2(fA[16], fB[16]);  // (-1, -1)
-    X[4][w][lane] = group(4, 9, 8);               // (-1, 0)
-    X[5][w][lane] = make_float2(fA[18], fB[18]);  // (-1, +1)
+    float2(*X)[kOnePassRows + 2][32] = xch[parity];
+    X[0][w + 1][lane] = make_float2(fA[17], fB[17]);  // (c_y, c_z) = (+1, -1)
+    X[1][w + 1][lane] = group(3, 7, 10);              // (+1, 0)
+    X[2][w + 1][lane] = make_float2(fA[15], fB[15]);  // (+1, +1)
+    X[3][w + 1][lane] = make_float2(fA[16], fB[16]);  // (-1, -1)
+    X[4][w + 1][lane] = group(4, 9, 8);               // (-1, 0)
+    X[5][w + 1][lane] = make_float2(fA[18], fB[18]);  // (-1, +1)
     if (left) {  // leaving towards x0 - 1 with c_y = +1, -1
       xedge[parity][0][0][w] = make_float2(fA[10], fB[10]);
       xedge[parity][0][1][w] = make_float2(fA[8], fB[8]);
@@ -295,13 +301,11 @@ __global__ void __launch_bounds__(kOPThreads, 3)
     const float2 zero = make_float2(0.f, 0.f);
     if (own && summed_row) {
       // from the row below (c_y = +1), this row (c_y = 0), the row above (c_y = -1), into the
-      // planes z - 1, z, z + 1
-      const float2 am = add2(add2(add2(acc[km][threadIdx.x], lo ? X[0][w - 1][lane] : zero), g0m),
-                             hi ? X[3][w + 1][lane] : zero);
-      acc[k0][threadIdx.x] = add2(add2(add2(acc[k0][threadIdx.x], lo ? X[1][w - 1][lane] : zero), g00),
-                                  hi ? X[4][w + 1][lane] : zero);
-      acc[kp][threadIdx.x] = add2(add2(add2(acc[kp][threadIdx.x], lo ? X[2][w - 1][lane] : zero), g0p),
-                                  hi ? X[5][w + 1][lane] : zero);
+      // planes z - 1, z, z + 1 (rows beyond the block and the rows of a ragged tile's absent
+      // warps hold 0)
+      const float2 am = add2(add2(add2(acc[km][threadIdx.x], X[0][w][lane]), g0m), X[3][w + 2][lane]);
+      acc[k0][threadIdx.x] = add2(add2(add2(acc[k0][threadIdx.x], X[1][w][lane]), g00), X[4][w + 2][lane]);
+      acc[kp][threadIdx.x] = add2(add2(add2(acc[kp][threadIdx.x], X[2][w][lane]), g0p), X[5][w + 2][lane]);
       if (write)
         reinterpret_cast<float2 *>(rho_next)[((long long)zm * P.ny + y) * P.nx + x] =
             add2(am, make_float2(shift_sum(P, 0), shift_sum(P, 1)));
@@ -329,9 +333,9 @@ __global__ void __launch_bounds__(kOPThreads, 3)
       // what leaves the tile across its bottom row (the c_y = -1 groups of row 0) or its top row
       // (the c_y = +1 groups of the last row), for the neighbouring tile's edge row
       const int sy = w == 0 ? 0 : 1, g = sy ? 0 : 3;
-      const float2 ym = add2(accY[km][sy][lane], X[g][w][lane]);
-      accY[k0][sy][lane] = add2(accY[k0][sy][lane], X[g + 1][w][lane]);
-      accY[kp][sy][lane] = add2(accY[kp][sy][lane], X[g + 2][w][lane]);
+      const float2 ym = add2(accY[km][sy][lane], X[g][w + 1][lane]);
+      accY[k0][sy][lane] = add2(accY[k0][sy][lane], X[g + 1][w + 1][lane]);
+      accY[kp][sy][lane] = add2(accY[kp][sy][lane], X[g + 2][w + 1][lane]);
       if (write)
         reinterpret_cast<float2 *>(out.yedge)[(((long long)sy * P.nz + zm) * G.nty + ty) * (G.ntx * kOnePassCols) +
                                               x0 + lane] = ym;
