@@ -239,22 +239,55 @@ def _block(x, rho, dims, block=8):
     return c.var() / c.mean(), np.corrcoef(c.ravel(), r.ravel())[0, 1]
 
 
+DEMIX_SEEDS = tuple(range(3, 19))
+
+
+def _demix_oracle_stats(seed, dims=(32, 32, 2), steps=1500, n=100):
+    """The oracle's run of one seed of the ensemble below, and the initial placement's dispersion
+    (a pool worker: imports nothing that touches the GPU)."""
+    x = inputs.random_particles(n, dims, DEMIX["sigma"], seed=seed)
+    xo, rho = _demix_oracle(dims, 0.01, steps, x, seed=seed)
+    return _block(xo, rho.sum(0), dims), _block(x, rho.sum(0), dims)[0]
+
+
 def test_particle_fluid_demixing_statistics_match_oracle():
-    """32 x 32 x 2, 100 particles, 1500 steps from the same input on both sides (single
-    trajectories part after a few dozen steps, see above): the block anti-correlation of
-    particles and fluid agrees within 0.15 and both spread beyond independent placement (the
-    dispersion of 16 blocks of ~6 particles is a noisy statistic; the 20000-step run below
-    tests its growth)."""
+    """32 x 32 x 2, 100 particles, 1500 steps, sixteen seeds, each from the same input on both
+    sides.  Single trajectories part after a few dozen steps (see above), so what is compared is
+    the ensemble: Sec. 3's demixing is a statistical property.  One realisation's block
+    dispersion (16 blocks of ~6 particles) is a noisy number -- the oracle alone gives 0.39 to
+    2.99 after 1500 steps over these seeds -- while the block anti-correlation of particles and
+    fluid is steadier (-0.68 to -0.96).  Both sides: the mean anti-correlation is strong and
+    agrees within 0.1, and the mean dispersion has grown over the initial placement's (the
+    20000-step run below tests how far it grows).  Measured: the GPU ensemble is a little less
+    demixed at 1500 steps than the oracle's (mean correlation -0.86 against -0.91, dispersion
+    1.20 against 1.43 from 0.87), with the update's arithmetic in either of the orders it has had;
+    the FP32 and FP64 trajectories part where a particle chatters across a link-selection plane
+    (Eq. solvation_lambda), so FP32 rounding can shift these statistics."""
+    import concurrent.futures
+    import multiprocessing
     dims = (32, 32, 2)
-    x, xg, a, b = _demix_gpu(dims, 0.01, 1500, 100)
+    stats = {"gpu": [], "oracle": [], "initial": []}
     t = time.perf_counter()
-    xo, rho = _demix_oracle(dims, 0.01, 1500, x)
-    TIMES["demixing_32x32x2_1500_steps_oracle_s"] = time.perf_counter() - t
-    dg, cg = _block(xg, a.astype(np.float64) + b, dims)
-    do, co = _block(xo, rho.sum(0), dims)
-    TIMES["demixing_32x32x2_stats"] = {"gpu": [dg, cg], "oracle": [do, co]}
-    assert cg < -0.7 and co < -0.7 and abs(cg - co) < 0.15
-    assert dg > 1.2 and do > 1.2
+    # the oracle's runs go to a pool of fresh (spawned) processes while the GPU runs its own
+    workers = max(1, min(len(DEMIX_SEEDS), os.cpu_count() or 1))
+    with concurrent.futures.ProcessPoolExecutor(max_workers=workers,
+                                                mp_context=multiprocessing.get_context("spawn")) as pool:
+        futures = [pool.submit(_demix_oracle_stats, seed) for seed in DEMIX_SEEDS]
+        for seed in DEMIX_SEEDS:
+            _, xg, a, b = _demix_gpu(dims, 0.01, 1500, 100, seed=seed)
+            stats["gpu"].append(_block(xg, a.astype(np.float64) + b, dims))
+        for f in futures:
+            o, d0 = f.result()
+            stats["oracle"].append(o)
+            stats["initial"].append(d0)
+    TIMES["demixing_32x32x2_1500_steps_16_seeds_s"] = time.perf_counter() - t
+    TIMES["demixing_32x32x2_stats"] = stats
+    d0 = np.mean(stats["initial"])
+    dg, cg = np.mean(stats["gpu"], axis=0)
+    do, co = np.mean(stats["oracle"], axis=0)
+    print("demixing ensemble means: initial dispersion %.3f; GPU %.3f, %.3f; oracle %.3f, %.3f" % (d0, dg, cg, do, co))
+    assert cg < -0.8 and co < -0.8 and abs(cg - co) < 0.1
+    assert dg > d0 and do > d0
 
 
 def test_particle_fluid_demixing_20000_steps():
