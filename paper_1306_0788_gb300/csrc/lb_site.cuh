@@ -613,7 +613,14 @@ __device__ __forceinline__ void collide_core_at(const StepParams &P, const Coord
     mrt_update(P, step, s32, fA, fB, rA, rB, ux, uy, uz, gA, gB);
   } else {
     // BGK + forcing, f* = (1 - 1/tau) f + (1/tau) f^eq + Delta^g, per pair of opposite directions
-    // (c_j = -c_i): f^eq and Delta^g split into parts even and odd in c.
+    // (c_j = -c_i), with f^eq and Delta^g split into parts even and odd in c.  Per component, with
+    // cu = c_i.u and cg = c_i.g_z:
+    //   f*_i = om1 f_i + even + odd,   f*_j = om1 f_j + even - odd,
+    //   even = w_i E + 4.5 w_i om rho cu^2 + 9 w_i fp cu cg,   odd = 3 w_i om rho cu + 3 w_i fp cg,
+    //   E = om rho (1 - 1.5 u^2) - 3 fp u.g_z   (less om rho0 with shifted storage),
+    // and the rest population f*_0 = om1 f_0 + w_0 E.  The node-wide factors w E, 4.5 w om rho and
+    // 3 w om rho are formed once for each weight of the moving directions (1/18 axis, 1/36
+    // diagonal).
     const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
     const float om = P.inv_tau, om1 = 1.f - om, fp = P.force_pref;
     const float2 gx = make_float2(gA.x, gB.x), gy = make_float2(gA.y, gB.y), gz = make_float2(gA.z, gB.z);
@@ -623,34 +630,37 @@ __device__ __forceinline__ void collide_core_at(const StepParams &P, const Coord
                                              __ffma2_rn(make_float2(uy, uy), gy, __fmul2_rn(make_float2(ux, ux), gx))));
     const float2 a2 = __fmul2_rn(make_float2(om, om), make_float2(rA, rB));
     const float2 om1_2 = make_float2(om1, om1);
+    float2 E = __ffma2_rn(a2, make_float2(1.f - usq15, 1.f - usq15), __fmul2_rn(make_float2(-fp, -fp), ug3));
     if (!kShifted) {  // (with 16-bit storage the rest population is set by the mass closure)
-      const float e0 = kW[0] * (1.f - usq15), q0 = -kW[0] * fp;
-      const float2 f0 = __ffma2_rn(om1_2, make_float2(fA[0], fB[0]),
-                                   __ffma2_rn(a2, make_float2(e0, e0), __fmul2_rn(make_float2(q0, q0), ug3)));
+      const float2 f0 = __ffma2_rn(om1_2, make_float2(fA[0], fB[0]), __fmul2_rn(make_float2(kW[0], kW[0]), E));
       fA[0] = f0.x;
       fB[0] = f0.y;
+    } else {
+      // shifted storage: f~* = (1 - om) f~ + om (f^eq - w_i rho0) + Delta^g
+      E = __ffma2_rn(make_float2(-om, -om), make_float2(P.rho0[0], P.rho0[1]), E);
     }
+    constexpr float wa = kW[1], wd = kW[7];  // axis, diagonal
+    const float2 Ea = __fmul2_rn(make_float2(wa, wa), E), Ed = __fmul2_rn(make_float2(wd, wd), E);
+    const float2 Qa = __fmul2_rn(make_float2(4.5f * wa, 4.5f * wa), a2), Qd = __fmul2_rn(make_float2(4.5f * wd, 4.5f * wd), a2);
+    const float2 Ra = __fmul2_rn(make_float2(3.f * wa, 3.f * wa), a2), Rd = __fmul2_rn(make_float2(3.f * wd, 3.f * wd), a2);
+    const float fp9a = (9.f * wa) * fp, fp9d = (9.f * wd) * fp, fp3a = (3.f * wa) * fp, fp3d = (3.f * wd) * fp;
 #pragma unroll
     for (int i = 1; i < kQ; i += 2) {
       const int j = i + 1;
+      const bool axis = i < 7;  // directions 1-6 move along an axis
+      const float2 Ew = axis ? Ea : Ed, Qw = axis ? Qa : Qd, Rw = axis ? Ra : Rd;
+      const float fp9 = axis ? fp9a : fp9d, fp3 = axis ? fp3a : fp3d;
       const float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
       // c_i . g_z for both components (each c component is -1, 0 or 1)
       float2 cg = make_float2(0.f, 0.f);
       if (kCx[i]) cg = __ffma2_rn(make_float2((float)kCx[i], (float)kCx[i]), gx, cg);
       if (kCy[i]) cg = __ffma2_rn(make_float2((float)kCy[i], (float)kCy[i]), gy, cg);
       if (kCz[i]) cg = __ffma2_rn(make_float2((float)kCz[i], (float)kCz[i]), gz, cg);
-      const float sym = kW[i] * (1.f + 4.5f * cu * cu - usq15), anti = 3.f * kW[i] * cu;
-      const float wf = kW[i] * fp, wf9cu = 9.f * wf * cu, wf3 = 3.f * wf;
-      // even and odd forcing parts: wf (9 cu c.g - 3 u.g), 3 wf c.g
-      float2 fs = __ffma2_rn(make_float2(wf9cu, wf9cu), cg, __fmul2_rn(make_float2(-wf, -wf), ug3));
-      // shifted storage: f~* = (1 - om) f~ + om (f^eq - w_i rho0) + Delta^g
-      if (kShifted) fs = __ffma2_rn(make_float2(-om * kW[i], -om * kW[i]), make_float2(P.rho0[0], P.rho0[1]), fs);
-      const float2 fa = __fmul2_rn(make_float2(wf3, wf3), cg);
-      const float2 fi = __ffma2_rn(om1_2, make_float2(fA[i], fB[i]),
-                                   __ffma2_rn(a2, make_float2(sym + anti, sym + anti), __fadd2_rn(fs, fa)));
-      const float2 fj = __ffma2_rn(om1_2, make_float2(fA[j], fB[j]),
-                                   __ffma2_rn(a2, make_float2(sym - anti, sym - anti),
-                                              __ffma2_rn(make_float2(-1.f, -1.f), fa, fs)));
+      const float c9 = fp9 * cu;
+      const float2 even = __ffma2_rn(make_float2(c9, c9), cg, __ffma2_rn(make_float2(cu * cu, cu * cu), Qw, Ew));
+      const float2 odd = __ffma2_rn(Rw, make_float2(cu, cu), __fmul2_rn(make_float2(fp3, fp3), cg));
+      const float2 fi = __ffma2_rn(om1_2, make_float2(fA[i], fB[i]), __fadd2_rn(even, odd));
+      const float2 fj = __ffma2_rn(om1_2, make_float2(fA[j], fB[j]), __ffma2_rn(make_float2(-1.f, -1.f), odd, even));
       fA[i] = fi.x;
       fB[i] = fi.y;
       fA[j] = fj.x;

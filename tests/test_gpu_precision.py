@@ -190,10 +190,10 @@ IFACE_TIMES = (500, 1000, 2000)
 # stated interface-position errors (lattice units) against the FP64 oracle.  BF16's 8
 # significant bits round the shifted populations at this density scale (values up to ~60 w_i)
 # by ~0.4 %, systematically near a steady state: while the bulk densities relax the error of its
-# interfaces grows to 0.2 (500 steps), 0.3 (1000) and 1.7 lattice units (2000 steps, one GB300
-# run) -- BF16 storage does not resolve this slow relaxation.  FP16's grows the same way, to 0.02,
-# 0.07 and 0.25 lattice units: the rounding of a 16-bit population is the same from step to step
-# near a steady state, so it biases the slow diffusive relaxation of the bulk densities.
+# interfaces grows to 0.27 (500 steps), 0.50 (1000) and 1.6 lattice units (2000 steps, one GB300
+# run) -- BF16 storage does not resolve this slow relaxation.  FP16's grows the same way, to
+# 0.001, 0.03 and 0.18 lattice units: the rounding of a 16-bit population is the same from step
+# to step near a steady state, so it biases the slow diffusive relaxation of the bulk densities.
 IFACE_BOUNDS = {"fp32": 1e-3, "fp16": 0.5, "bf16": 2.5}
 
 
