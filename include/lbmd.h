@@ -245,6 +245,28 @@ int lbmd_get_fields(lbmd_ctx *ctx, float *rhoA, float *rhoB, float *u);
  * [n][3] doubles in the caller's order; any pointer may be NULL. */
 int lbmd_get_particles(lbmd_ctx *ctx, double *x, double *v, double *f);
 
+/* Device-memory variants of the three getters above, for callers that keep the state on the
+ * GPU (torch tensors, their own kernels): the same values in the same layouts -- rhoA, rhoB
+ * [nz][ny][nx] and u [nz][ny][nx][3] FP32; f [19][nz][ny][nx] FP32 (the unshifted post-streaming
+ * values of component comp); x, v, f [n][3] FP64 in the caller's particle order, n the count of
+ * the last lbmd_set_particles -- written into caller-owned DEVICE buffers of the context's device,
+ * with no copy through the host and no host synchronisation.  stream: a cudaStream_t of the caller
+ * (NULL = the legacy default stream); the outputs are written after the context's queued steps and
+ * after the work already queued on stream, and before any work queued on stream after the call
+ * returns, so the caller may use them on stream at once.  Any output pointer may be NULL, except
+ * f_dev of lbmd_get_populations_dev.  Each non-NULL pointer is checked before any launch: it must
+ * be device (or managed) memory and, where the driver reports the allocation's extent, the stated
+ * length from it must lie inside that allocation; otherwise LBMD_E_INVALID_ARG (nothing written).
+ * A buffer carved from a larger allocation (a caching allocator's pool) is checked against that
+ * whole allocation only: the caller must still pass buffers of the stated lengths.  These
+ * calls do not synchronise, so device-side failures of earlier steps are reported by the next
+ * call that does (lbmd_sync, the host getters, lbmd_diagnostics).  Errors: LBMD_E_INVALID_ARG,
+ * LBMD_E_STATE (fluid not initialised), LBMD_E_CUDA.  The paper defines the fields (Sec. 2: the
+ * densities, Eq. momentum_definition for u) but no interface to them. */
+int lbmd_get_fields_dev(lbmd_ctx *ctx, float *rhoA_dev, float *rhoB_dev, float *u_dev, void *stream);
+int lbmd_get_populations_dev(lbmd_ctx *ctx, int comp, float *f_dev, void *stream);
+int lbmd_get_particles_dev(lbmd_ctx *ctx, double *x_dev, double *v_dev, double *f_dev, void *stream);
+
 /* FP64 reductions on the device: out[0..1] = total mass of A and B, out[2..4] = fluid
  * momentum sum_r j'(r), out[5..7] = particle momentum sum m v. */
 int lbmd_diagnostics(lbmd_ctx *ctx, double out[8]);

@@ -336,6 +336,41 @@ __global__ void __launch_bounds__(kMomBlock) k_particle_momentum(StepParams P, P
     for (int k = 0; k < 3; ++k) partial[(long long)blockIdx.x * 3 + k] = sh[k][0];
 }
 
+// Particle state in the caller's order: entry j of the sorted arrays is particle pa.pid[j], and
+// total force j is that of particle tid_of[j].  The ids are a permutation of 0..n-1; an id out of
+// range (which no step writes) is skipped rather than written out of bounds.
+__global__ void __launch_bounds__(kPBlock) k_particles_out(int n, ParticleArrays pa, const int *__restrict__ tid_of,
+                                                           const float4 *__restrict__ total, double *__restrict__ x,
+                                                           double *__restrict__ v, double *__restrict__ f) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int id = pa.pid[j];
+  if (id >= 0 && id < n) {
+    if (x) {
+      const int4 c = pa.cell[j];
+      const float4 q = pa.frac[j];
+      x[3LL * id] = c.x + (double)q.x;  // exact: an integer plus an FP32 fraction fits FP64
+      x[3LL * id + 1] = c.y + (double)q.y;
+      x[3LL * id + 2] = c.z + (double)q.z;
+    }
+    if (v) {
+      const float4 w = pa.vel[j];
+      v[3LL * id] = w.x;
+      v[3LL * id + 1] = w.y;
+      v[3LL * id + 2] = w.z;
+    }
+  }
+  if (f) {
+    const int t = tid_of[j];
+    if (t >= 0 && t < n) {
+      const float4 g = total[j];
+      f[3LL * t] = g.x;
+      f[3LL * t + 1] = g.y;
+      f[3LL * t + 2] = g.z;
+    }
+  }
+}
+
 }  // namespace
 
 void launch_bin(const StepParams &P, const ParticleArrays &pa, int *row_of, int *row_count, unsigned *err,
@@ -415,6 +450,10 @@ void launch_rec_permute(int n, const int *perm, const ReactionRecords &src, cons
 void launch_particle_momentum(const StepParams &P, const ParticleArrays &pa, double *partial, int nblocks,
                               cudaStream_t st) {
   k_particle_momentum<<<nblocks, kMomBlock, 0, st>>>(P, pa, partial);
+}
+void launch_particles_out(int n, const ParticleArrays &pa, const int *tid_of, const float4 *total, double *x,
+                          double *v, double *f, cudaStream_t st) {
+  k_particles_out<<<pgrid(n), kPBlock, 0, st>>>(n, pa, tid_of, total, x, v, f);
 }
 
 }  // namespace lbmd

@@ -151,6 +151,9 @@ int static_fail(int code, const std::string &m) {
 }
 
 }  // namespace
+
+bool device_buffer_ok(const void *p, size_t bytes) { return device_range_ok(p, bytes); }
+
 }  // namespace lbmd
 
 using namespace lbmd;

@@ -47,6 +47,9 @@ struct lbmd_ctx {
   // one pass with particles: ev_integrated (the particle update done, on side) orders the boundary
   // kernel, which forms the next step's corner j' (jc) at the updated positions, after it
   cudaEvent_t ev_integrated = nullptr;
+  // the device-memory getters: the caller's stream's queued work before their writes (dev_in),
+  // and their writes before what the caller queues next (dev_out); created on first use
+  cudaEvent_t ev_dev_in = nullptr, ev_dev_out = nullptr;
   int dev = 0;
   StepParams P{};
   unsigned char *pop[2] = {nullptr, nullptr};  // population buffers, element type P.storage
@@ -785,6 +788,8 @@ void lbmd_destroy(lbmd_ctx *c) {
   if (c->ev_coupled) cudaEventDestroy(c->ev_coupled);
   if (c->ev_collided) cudaEventDestroy(c->ev_collided);
   if (c->ev_integrated) cudaEventDestroy(c->ev_integrated);
+  if (c->ev_dev_in) cudaEventDestroy(c->ev_dev_in);
+  if (c->ev_dev_out) cudaEventDestroy(c->ev_dev_out);
   drop_graphs(c);
   if (c->gst) cudaStreamDestroy(c->gst);
   for (cudaEvent_t e : c->ph)
@@ -1138,6 +1143,91 @@ int lbmd_get_particles(lbmd_ctx *c, double *x, double *v, double *f) {
     }
   }
   return r;
+}
+
+// The device-memory getters write into caller buffers on the context's stream, ordered after the
+// work already queued on the caller's stream and before the work the caller queues there next.
+static int dev_getter_begin(lbmd_ctx *c, cudaStream_t caller) {
+  if (!c->ev_dev_in) CK(cudaEventCreateWithFlags(&c->ev_dev_in, cudaEventDisableTiming), "event");
+  if (!c->ev_dev_out) CK(cudaEventCreateWithFlags(&c->ev_dev_out, cudaEventDisableTiming), "event");
+  if (caller != c->st) {
+    CK(cudaEventRecord(c->ev_dev_in, caller), "event");
+    CK(cudaStreamWaitEvent(c->st, c->ev_dev_in, 0), "stream wait");
+  }
+  return LBMD_OK;
+}
+
+static int dev_getter_end(lbmd_ctx *c, cudaStream_t caller) {
+  if (caller != c->st) {
+    CK(cudaEventRecord(c->ev_dev_out, c->st), "event");
+    CK(cudaStreamWaitEvent(caller, c->ev_dev_out, 0), "stream wait");
+  }
+  return LBMD_OK;
+}
+
+static int dev_buffers_ok(lbmd_ctx *c, const char *name, const void *p, size_t bytes) {
+  if (p && !device_buffer_ok(p, bytes))
+    return fail(c, LBMD_E_INVALID_ARG,
+                std::string(name) + " is not device memory of this context's device holding " +
+                    std::to_string(bytes) + " bytes");
+  return LBMD_OK;
+}
+
+int lbmd_get_fields_dev(lbmd_ctx *c, float *rhoA, float *rhoB, float *u, void *stream) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
+  cudaSetDevice(c->dev);
+  const long long N = c->P.N;
+  const size_t bytes = sizeof(float) * (size_t)N;
+  int r;
+  if ((r = dev_buffers_ok(c, "rhoA_dev", rhoA, bytes)) || (r = dev_buffers_ok(c, "rhoB_dev", rhoB, bytes)) ||
+      (r = dev_buffers_ok(c, "u_dev", u, 3 * bytes)))
+    return r;
+  if (!rhoA && !rhoB && !u) return LBMD_OK;
+  const cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  if ((r = dev_getter_begin(c, caller))) return r;
+  // outputs the caller does not want go to the spare population buffer, as in lbmd_get_fields
+  float *stage = reinterpret_cast<float *>(c->pop[1 - c->cur]);
+  if ((r = ensure_densities(c))) return r;
+  launch_fields(c->P, c->pop[c->cur], c->rest, c->rho_buf[c->cur], rhoA ? rhoA : stage, rhoB ? rhoB : stage + N,
+                u ? u : stage + 2 * N, c->st);
+  if ((r = launched(c, "fields"))) return r;
+  return dev_getter_end(c, caller);
+}
+
+int lbmd_get_populations_dev(lbmd_ctx *c, int comp, float *f, void *stream) {
+  if (!c || !f || comp < 0 || comp > 1) return c ? fail(c, LBMD_E_INVALID_ARG, "bad arguments") : LBMD_E_INVALID_ARG;
+  if (!c->fluid_ready) return fail(c, LBMD_E_STATE, "fluid not initialised");
+  cudaSetDevice(c->dev);
+  int r;
+  if ((r = dev_buffers_ok(c, "f_dev", f, sizeof(float) * kQ * (size_t)c->P.N))) return r;
+  const cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  if ((r = dev_getter_begin(c, caller))) return r;
+  launch_unstream(c->P, c->pop[c->cur], c->rest, comp, f, c->st);
+  if ((r = launched(c, "unstream"))) return r;
+  return dev_getter_end(c, caller);
+}
+
+int lbmd_get_particles_dev(lbmd_ctx *c, double *x, double *v, double *f, void *stream) {
+  if (!c) return LBMD_E_INVALID_ARG;
+  cudaSetDevice(c->dev);
+  const int n = c->np;
+  const size_t bytes = sizeof(double) * 3 * (size_t)n;
+  int r;
+  if ((r = dev_buffers_ok(c, "x_dev", x, bytes)) || (r = dev_buffers_ok(c, "v_dev", v, bytes)) ||
+      (r = dev_buffers_ok(c, "f_dev", f, bytes)))
+    return r;
+  if (n == 0 || (!x && !v && !f)) return LBMD_OK;
+  const cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  if ((r = dev_getter_begin(c, caller))) return r;
+  if (c->sort_pending) {  // the arrays read here are the ones the pending sort writes
+    CK(cudaStreamWaitEvent(c->st, c->ev_sorted, 0), "stream wait");
+    c->sort_pending = false;
+  }
+  // the total forces are in the order of the copy the particle update wrote (as in lbmd_get_particles)
+  launch_particles_out(n, c->pa[c->pcur], c->pa[1 - c->pcur].pid, c->pf.total, x, v, f, c->st);
+  if ((r = launched(c, "particles out"))) return r;
+  return dev_getter_end(c, caller);
 }
 
 int lbmd_diagnostics(lbmd_ctx *c, double out[8]) {

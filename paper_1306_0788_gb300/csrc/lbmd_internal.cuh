@@ -321,6 +321,14 @@ void launch_pairs(const StepParams &P, const ParticleArrays &pa, CellIndex ci, c
                   cudaStream_t st);
 void launch_integrate(const StepParams &P, const ParticleArrays &src, const ParticleArrays &dst,
                       const ParticleForces &pf, unsigned *err, cudaStream_t st);
+// Positions (cell + fraction, in FP64), velocities and the total forces of the last step of n
+// particles into device arrays [n][3] in the caller's particle order; any output may be null.
+// tid_of: the caller's index of each entry of total (the order the particle update wrote them).
+void launch_particles_out(int n, const ParticleArrays &pa, const int *tid_of, const float4 *total, double *x,
+                          double *v, double *f, cudaStream_t st);
+// True if [p, p + bytes) is device (or managed) memory inside one allocation of the current
+// context (checked with the runtime's pointer attributes and the driver's allocation extent).
+bool device_buffer_ok(const void *p, size_t bytes);
 void launch_particle_momentum(const StepParams &P, const ParticleArrays &pa, double *partial, int nblocks,
                               cudaStream_t st);
 // MD sub-stepping (lb_particles.cu)

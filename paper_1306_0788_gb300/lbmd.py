@@ -50,6 +50,7 @@ LBMD_SLOT_FAILED = 3
 EXPORTS = ("lbmd_create", "lbmd_destroy", "lbmd_set_types", "lbmd_set_debye_hueckel", "lbmd_init_fluid",
            "lbmd_set_populations", "lbmd_get_populations", "lbmd_set_particles", "lbmd_set_bonds",
            "lbmd_step", "lbmd_set_graphs", "lbmd_set_lattice_passes", "lbmd_get_lattice_passes", "lbmd_sync", "lbmd_clear_error", "lbmd_get_fields", "lbmd_get_particles",
+           "lbmd_get_fields_dev", "lbmd_get_populations_dev", "lbmd_get_particles_dev",
            "lbmd_diagnostics", "lbmd_set_drift_reference", "lbmd_get_drift", "lbmd_step_count", "lbmd_profile_enable", "lbmd_profile_read",
            "lbmd_launch_count", "lbmd_last_error", "lbmd_fluid_moments_static",
            "lbmd_batch_create", "lbmd_batch_destroy", "lbmd_batch_add", "lbmd_batch_remove",
@@ -112,6 +113,9 @@ def _load():
         "lbmd_clear_error": (I, [P]),
         "lbmd_get_fields": (I, [P, P, P, P]),
         "lbmd_get_particles": (I, [P, P, P, P]),
+        "lbmd_get_fields_dev": (I, [P, P, P, P, P]),
+        "lbmd_get_populations_dev": (I, [P, I, P, P]),
+        "lbmd_get_particles_dev": (I, [P, P, P, P, P]),
         "lbmd_diagnostics": (I, [P, P]),
         "lbmd_set_drift_reference": (I, [P]),
         "lbmd_get_drift": (I, [P, P]),
@@ -280,6 +284,24 @@ def lbmd_get_particles(ctx, n: int):
     x, v, f = np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3))
     _check(ctx, _lib.lbmd_get_particles(ctx, _p(x), _p(v), _p(f)))
     return x, v, f
+
+
+def lbmd_get_fields_dev(ctx, rhoA_dev_ptr, rhoB_dev_ptr, u_dev_ptr, stream=None) -> None:
+    """Device pointers (ints, e.g. tensor.data_ptr(); 0 or None to skip one) of rhoA, rhoB
+    [nz, ny, nx] and u [nz, ny, nx, 3] FP32, written in the order of stream."""
+    _check(ctx, _lib.lbmd_get_fields_dev(ctx, rhoA_dev_ptr or None, rhoB_dev_ptr or None, u_dev_ptr or None,
+                                         stream_handle(stream)))
+
+
+def lbmd_get_populations_dev(ctx, comp: int, f_dev_ptr: int, stream=None) -> None:
+    """Device pointer of f [19, nz, ny, nx] FP32 of component comp, written in the order of stream."""
+    _check(ctx, _lib.lbmd_get_populations_dev(ctx, comp, f_dev_ptr, stream_handle(stream)))
+
+
+def lbmd_get_particles_dev(ctx, x_dev_ptr, v_dev_ptr, f_dev_ptr, stream=None) -> None:
+    """Device pointers (or 0 / None) of x, v, f [n, 3] FP64 in the caller's particle order."""
+    _check(ctx, _lib.lbmd_get_particles_dev(ctx, x_dev_ptr or None, v_dev_ptr or None, f_dev_ptr or None,
+                                            stream_handle(stream)))
 
 
 def lbmd_diagnostics(ctx) -> np.ndarray:
