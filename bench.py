@@ -31,8 +31,8 @@ HBM_FALLBACK_GBS = 6800.0
 HBM_NOMINAL_GBS = 7900.0
 # DRAM bytes per node moved by the lattice update (dram__bytes_read + dram__bytes_write of one ncu
 # capture of the bench's own 256^3 launch, per node), per (storage, lattice passes): one-pass FP32
-# 2706.7 + 2717.8 MB, two-pass FP32 2690.3 + 2515.6 MB, FP16 1479.4 + 1299.2 MB, BF16 1479.4 +
-# 1299.3 MB (a metric set that takes one ncu pass, so the full-size launch is captured).
+# 2706.7 + 2717.8 MB, two-pass FP32 2690.3 + 2515.6 MB, FP16 1479.4 + 1299.3 MB, BF16 1479.5 +
+# 1299.2 MB (a metric set that takes one ncu pass, so the full-size launch is captured).
 COLLIDE_TRAFFIC_BYTES_PER_NODE = {("fp32", 1): 323.3, ("fp32", 2): 310.3, ("bf16", 2): 165.6, ("fp16", 2): 165.6}
 # The fluctuating MRT update is bound by instruction issue, not by HBM: warp instructions per
 # node of k_collide<float, true, true> (smsp__inst_executed.sum / nodes of one ncu capture of the

@@ -64,6 +64,12 @@ struct Pair16<__half> {
     memcpy(&w, &h, 4);
     return w;
   }
+  // acc += dec(w), each lane one mixed-precision addition (the 16-bit operand converts exactly)
+  static __device__ __forceinline__ void add_to(unsigned w, float2 &acc) {
+    const unsigned short lo = (unsigned short)(w & 0xffffu), hi = (unsigned short)(w >> 16);
+    asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(acc.x) : "h"(lo));
+    asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(acc.y) : "h"(hi));
+  }
 };
 template <>
 struct Pair16<__nv_bfloat16> {
@@ -75,6 +81,11 @@ struct Pair16<__nv_bfloat16> {
     unsigned w;
     memcpy(&w, &h, 4);
     return w;
+  }
+  static __device__ __forceinline__ void add_to(unsigned w, float2 &acc) {
+    const unsigned short lo = (unsigned short)(w & 0xffffu), hi = (unsigned short)(w >> 16);
+    asm("add.rn.f32.bf16 %0, %1, %0;" : "+f"(acc.x) : "h"(lo));
+    asm("add.rn.f32.bf16 %0, %1, %0;" : "+f"(acc.y) : "h"(hi));
   }
 };
 
@@ -701,16 +712,27 @@ __device__ __forceinline__ void store_node(const StepParams &P, unsigned s32, T 
       // store the 18 shifted (A, B) pairs; the rest population takes what keeps the node's mass
       // at its value before the update (the BGK update and the forcing term conserve it exactly)
       float2 m = make_float2(rA - shift_sum(P, 0), rB - shift_sum(P, 1));
+      if constexpr (kKeep) {
 #pragma unroll
-      for (int i = 1; i < kQ; ++i) {
-        const unsigned w = Pair16<T>::enc(make_float2(fA[i], fB[i]));
-        if (kWrite && write) wout[(size_t)i * N32] = w;
-        const float2 d = Pair16<T>::dec(w);
-        m = __ffma2_rn(make_float2(-1.f, -1.f), d, m);
-        if (kKeep) {
+        for (int i = 1; i < kQ; ++i) {
+          const unsigned w = Pair16<T>::enc(make_float2(fA[i], fB[i]));
+          if (kWrite && write) wout[(size_t)i * N32] = w;
+          const float2 d = Pair16<T>::dec(w);
+          m = __ffma2_rn(make_float2(-1.f, -1.f), d, m);
           fA[i] = d.x;
           fB[i] = d.y;
         }
+      } else {
+        // the closure negated, -m + d per stored value with mixed-precision additions: round to
+        // nearest is symmetric, so each partial is exactly minus the m - d of the form above
+        float2 nm = make_float2(-m.x, -m.y);
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) {
+          const unsigned w = Pair16<T>::enc(make_float2(fA[i], fB[i]));
+          if (kWrite && write) wout[(size_t)i * N32] = w;
+          Pair16<T>::add_to(w, nm);
+        }
+        m = make_float2(-nm.x, -nm.y);
       }
       if (kWrite && write && rest_out) {
         rest_out[s32] = m.x;
