@@ -90,7 +90,7 @@ PRECISION_ERRORS = {
 }
 
 
-def survey_bytes_per_site(storage: str = "fp32") -> int:
+def onepass_min_bytes_per_site(storage: str = "fp32") -> int:
     """The one-pass minimum of a site update: both components' populations read and written
     once, 2 * 19 * 4 * 2 = 304 B in FP32 and 2 * 19 * 2 * 2 = 152 B with 16-bit storage."""
     return 2 * 19 * STORAGES[storage][1] * 2
@@ -421,7 +421,7 @@ def collide_roofline(m, peak, peak_kind):
                        "k_collide (pull streaming + Shan-Chen + coupling gather + BGK/forcing, both components)"),
             "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "bytes_per_site": bps,
-            "frac_on_survey_bytes": round(survey_bytes_per_site(m["storage"]) * N / (m["kernel_ms"] * 1e-3) / 1e9 / peak, 4),
+            "frac_on_onepass_min_bytes": round(onepass_min_bytes_per_site(m["storage"]) * N / (m["kernel_ms"] * 1e-3) / 1e9 / peak, 4),
             "kernel_ms": round(m["kernel_ms"], 5), "kernel_launches": m["kernel_launches"],
             "traffic": (None if (m["storage"], m["lattice_passes"]) not in COLLIDE_TRAFFIC_BYTES_PER_NODE
                         else int(COLLIDE_TRAFFIC_BYTES_PER_NODE[(m["storage"], m["lattice_passes"])] * N))}
@@ -431,7 +431,7 @@ def step_roofline(m, peak):
     """The whole coupled step against the one-pass minimum of the lattice update (populations read
     and written once: 304 B per site in FP32, 152 B with 16-bit storage), against the measured
     copy bandwidth and the nominal 7.9 TB/s."""
-    bps = survey_bytes_per_site(m["storage"])
+    bps = onepass_min_bytes_per_site(m["storage"])
     achieved = bps * m["N"] / (m["ms"] / m["steps"] * 1e-3) / 1e9
     return {"bound": "hbm", "scope": "whole coupled step (every kernel, particles included)",
             "bytes_per_site": bps, "achieved": round(achieved, 1), "unit": "GB/s",
