@@ -38,8 +38,8 @@ COLLIDE_TRAFFIC_BYTES_PER_NODE = {("fp32", 1): 323.3, ("fp32", 2): 310.3, ("bf16
 # node of k_collide<float, true, true> (smsp__inst_executed.sum / nodes of one ncu capture of the
 # 128^3 case), and the issue peak of the GPU: one warp instruction per cycle per scheduler, 4
 # schedulers per SM, 152 SMs, at the SM clock.
-MRT_WARP_INSTR_PER_NODE = 55.05
-MRT_TRAFFIC_BYTES_PER_NODE = 289.8  # DRAM bytes per node of the same capture (160.3 read + 129.5 written)
+MRT_WARP_INSTR_PER_NODE = 49.55
+MRT_TRAFFIC_BYTES_PER_NODE = 289.7  # DRAM bytes per node of the same capture (160.3 read + 129.4 written)
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 # The slab/droplet workload uses the density scale of the paper's ferrofluid example (Sec. 4.5):

@@ -331,16 +331,17 @@ __device__ __forceinline__ void gather_coupling(const StepParams &P, int x, int 
 // ------------------------------------------------------------------ fluctuating MRT
 
 // Unit normals 4k .. 4k+3 of the fluid noise at one site and step: Philox4x32-10 (Salmon et
-// al., SC'11) with counter (site, step low, step high, 0x464c0000 + k) and key = seed, uniforms
-// from the top 24 bits, Box-Muller on both uniform pairs.  The logarithm and the sine / cosine
+// al., SC'11) with counter (site, step low, step high, 0x464c0000 + k) and key = seed (its round
+// keys formed once, StepParams::noise_keys), uniforms from the top 24 bits, Box-Muller on both
+// uniform pairs.  The logarithm and the sine / cosine
 // are the hardware approximations (absolute error ~1e-6 on a normal, far below what the
 // populations can resolve), and so is the radius: x rsqrt(x), a few ulp from sqrt(x); the
 // generator's integer stream is exact.  A uniform (v + 1/2) 2^-24 is one FFMA: the scaling by a
 // power of two is exact, so one rounding of v 2^-24 + 2^-25 gives the same float.
-__device__ __forceinline__ float4 fluid_normals4(unsigned long long seed, unsigned long long step, unsigned site,
-                                                 unsigned k) {
-  const uint4 r = philox4x32_10(make_uint4(site, (unsigned)step, (unsigned)(step >> 32), 0x464c0000u + k),
-                                make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+__device__ __forceinline__ float4 fluid_normals4(const uint2 *__restrict__ keys, unsigned long long step,
+                                                 unsigned site, unsigned k) {
+  const uint4 r = philox4x32_10_keyed(make_uint4(site, (unsigned)step, (unsigned)(step >> 32), 0x464c0000u + k),
+                                      keys);
   // the two Box-Muller pairs side by side: (u0, u2) give the radii, (u1, u3) the angles
   const float2 sc = make_float2(1.f / 16777216.f, 1.f / 16777216.f);
   const float2 h = make_float2(0.5f / 16777216.f, 0.5f / 16777216.f);
@@ -450,7 +451,7 @@ __device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long lo
     const float sA = rA * rsqrtf(fmaxf(rA, 1e-30f)), sB = rB * rsqrtf(fmaxf(rB, 1e-30f));
     const float am = P.noise[1] * sA * sB * rsqrtf(rA + rB);
     // A: normals 0-3 (momentum, shared; then mode 4), 4-15 (modes 5-16), 16, 17 (modes 17, 18)
-    float4 q = fluid_normals4(P.seed, step, site, 0);
+    float4 q = fluid_normals4(P.noise_keys, step, site, 0);
     const float2 amAB = make_float2(am, -am);
     m[1] = __ffma2_rn(amAB, make_float2(q.x, q.x), m[1]);
     m[2] = __ffma2_rn(amAB, make_float2(q.y, q.y), m[2]);
@@ -458,14 +459,14 @@ __device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long lo
     m[4].x += P.noise[4] * sA * q.w;
 #pragma unroll
     for (int c = 1; c <= 3; ++c) {
-      q = fluid_normals4(P.seed, step, site, c);
+      q = fluid_normals4(P.noise_keys, step, site, c);
       const int k = 4 * c + 1;
       m[k].x += P.noise[k] * sA * q.x;
       m[k + 1].x += P.noise[k + 1] * sA * q.y;
       m[k + 2].x += P.noise[k + 2] * sA * q.z;
       m[k + 3].x += P.noise[k + 3] * sA * q.w;
     }
-    q = fluid_normals4(P.seed, step, site, 4);
+    q = fluid_normals4(P.noise_keys, step, site, 4);
     m[17].x += P.noise[17] * sA * q.x;
     m[18].x += P.noise[18] * sA * q.y;
     // B: modes 4, 5 from the last two of that draw, then 6-18
@@ -473,14 +474,14 @@ __device__ __forceinline__ void mrt_update(const StepParams &P, unsigned long lo
     m[5].y += P.noise[5] * sB * q.w;
 #pragma unroll
     for (int c = 5; c <= 7; ++c) {
-      q = fluid_normals4(P.seed, step, site, c);
+      q = fluid_normals4(P.noise_keys, step, site, c);
       const int k = 4 * c - 14;
       m[k].y += P.noise[k] * sB * q.x;
       m[k + 1].y += P.noise[k + 1] * sB * q.y;
       m[k + 2].y += P.noise[k + 2] * sB * q.z;
       m[k + 3].y += P.noise[k + 3] * sB * q.w;
     }
-    q = fluid_normals4(P.seed, step, site, 8);
+    q = fluid_normals4(P.noise_keys, step, site, 8);
     m[18].y += P.noise[18] * sB * q.x;
   }
   // scaled by 1 / b_k for the way back

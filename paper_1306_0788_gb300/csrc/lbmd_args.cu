@@ -63,6 +63,14 @@ void fill_step_params(const lbmd_params *prm, StepParams &P) {
   P.rho0[0] = prm->storage == LBMD_STORAGE_FP32 ? 0.f : (float)prm->rho0_A;
   P.rho0[1] = prm->storage == LBMD_STORAGE_FP32 ? 0.f : (float)prm->rho0_B;
   P.seed = prm->seed;
+  {
+    uint2 k = make_uint2((unsigned)prm->seed, (unsigned)(prm->seed >> 32));
+    for (int r = 0; r < 10; ++r) {
+      P.noise_keys[r] = k;
+      k.x += 0x9E3779B9u;  // the Weyl increments of philox4x32_10's key schedule
+      k.y += 0xBB67AE85u;
+    }
+  }
   P.ntypes = 0;
   P.bond_kind = LBMD_BOND_FENE;
   // fluctuating MRT factors (Eq. MODES): eigenvalue per mode, forcing moments of the paper's

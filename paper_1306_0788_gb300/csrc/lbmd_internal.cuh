@@ -76,6 +76,10 @@ struct StepParams {
   float noise_scale;
   float relax[kQ], force[kQ], noise[kQ];
   unsigned long long seed, step;
+  // the round keys of the fluid noise's generator (Philox4x32-10 under the key (seed lo, seed hi)):
+  // round r uses the key plus r times the Weyl increments.  The same for every draw of a run, so
+  // they are formed once on the host instead of per draw.
+  uint2 noise_keys[10];
   // replayed step graphs: the particle kernels' noise counter is step + *step_base * step_mul,
   // the device-resident base being the lattice step at the replay's start (null: step alone);
   // the lattice update keeps its counter in `step` (patched into its graph node per replay)
@@ -202,6 +206,20 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
     k.x += 0x9E3779B9u;
     k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// The same generator with its ten round keys given (k_r of philox4x32_10's key schedule, r = 0 .. 9):
+// for many draws under one key, with no key schedule per draw.
+__device__ __forceinline__ uint4 philox4x32_10_keyed(uint4 c, const uint2 *__restrict__ rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = 0xD2511F53ull * c.x;
+    const unsigned long long p1 = 0xCD9E8D57ull * c.z;
+    const unsigned hi0 = (unsigned)(p0 >> 32), lo0 = (unsigned)p0;
+    const unsigned hi1 = (unsigned)(p1 >> 32), lo1 = (unsigned)p1;
+    c = make_uint4(hi1 ^ c.y ^ rk[r].x, lo1, hi0 ^ c.w ^ rk[r].y, lo0);
   }
   return c;
 }
