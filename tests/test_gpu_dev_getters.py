@@ -107,3 +107,34 @@ def test_device_getters_refuse_host_memory():
         L.lbmd_sync(ctx)
     finally:
         L.lbmd_destroy(ctx)
+
+
+def test_device_getters_edge_cases():
+    """Before the fluid is set the field and population getters return LBMD_E_STATE; with no
+    particles the particle getter writes nothing and succeeds; with every output NULL nothing is
+    launched."""
+    torch = pytest.importorskip("torch")
+    from paper_1306_0788_gb300 import lbmd as L
+
+    dims = (8, 6, 4)
+    ctx, _ = L.lbmd_create(L.params(dims))
+    try:
+        buf = torch.full((19,) + dims[::-1], 7.0, dtype=torch.float32, device="cuda")
+        for call in (lambda: L.lbmd_get_fields_dev(ctx, buf.data_ptr(), None, None),
+                     lambda: L.lbmd_get_populations_dev(ctx, 0, buf.data_ptr())):
+            with pytest.raises(L.LbmdError) as e:
+                call()
+            assert e.value.code == L.LBMD_E_STATE
+        ones = np.ones(dims[::-1], dtype=np.float32)
+        L.lbmd_init_fluid(ctx, ones, ones)
+        x = torch.full((4, 3), 7.0, dtype=torch.float64, device="cuda")
+        L.lbmd_get_particles_dev(ctx, x.data_ptr(), x.data_ptr(), x.data_ptr())  # no particles
+        launches = L.lbmd_launch_count(ctx)
+        L.lbmd_get_fields_dev(ctx, None, None, None)
+        assert L.lbmd_launch_count(ctx) == launches
+        L.lbmd_get_fields_dev(ctx, buf.data_ptr(), None, None)
+        torch.cuda.synchronize()
+        assert (x.cpu() == 7.0).all()
+        assert np.allclose(buf.cpu().numpy()[0], 1.0)  # rho_A of the uniform fluid in the first N floats
+    finally:
+        L.lbmd_destroy(ctx)
